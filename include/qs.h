@@ -1,0 +1,187 @@
+/*
+ * qs.h — C interface of the GB300 (sm_103a) state-vector quantum-circuit simulator.
+ *
+ * The operation implemented is the one of QueenV2 (arXiv 2409.14697):
+ *   - Sec. II-A, Eq. 1: an N-qubit state is the vector of 2^N complex amplitudes a_i,
+ *     i in [0, 2^N).  Qubit q is bit q of i (qubit 0 least significant, so low qubits
+ *     are contiguous in memory; Sec. II-B speaks of moving qubits to the "least
+ *     significant bits" for locality).
+ *   - Sec. II-A, Eq. 2: a one-qubit gate G replaces every pair (a_{..0_q..}, a_{..1_q..})
+ *     by G times the pair.
+ *   - Sec. II-A, Eq. 3 and the sentence before it: a k-qubit gate is a 2^k x 2^k matrix
+ *     applied to every group of 2^k amplitudes that differ only in its operand bits.
+ *     For operands (q_0, ..., q_{k-1}) the row index inside the group is
+ *     s = sum_j bit(q_j) * 2^(k-1-j): the first operand is the most significant, the
+ *     row order of Eq. 3, whose printed CNOT matrix makes the first operand the control.
+ *   - Sec. II-B / III: gate fusion, qubit reordering and in-cache (block-by-block)
+ *     execution are how the library schedules that work; they never change the result
+ *     beyond floating-point rounding.
+ *
+ * Conventions for every function:
+ *   - Return value: QS_OK (0) on success, a negative QS_ERR_* code on failure
+ *     (QS_NOT_READY = 1 only from qs_poll).  On failure a message is available from
+ *     qs_last_error() (thread-local, valid until the next call on the same thread).
+ *   - Ownership: the caller owns every host array it passes; the library copies what it
+ *     needs before returning.  The library owns all device memory it allocates.  Output
+ *     arrays are allocated by the caller.
+ *   - Amplitude layout (host and device): interleaved (re, im), index i at element i;
+ *     complex128 = two doubles (16 bytes), complex64 = two floats (8 bytes).
+ *   - Thread safety: a qs_state must be used by one thread at a time; a qs_server is
+ *     thread-safe.  Calls are synchronous unless stated otherwise.
+ *   - Failure detection: no device code traps or asserts.  Device-side bounded waits
+ *     return QS_ERR_TIMEOUT; CUDA errors return QS_ERR_CUDA with the CUDA message.
+ */
+#ifndef QSIM_QS_H_
+#define QSIM_QS_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define QS_ABI_VERSION 1
+#define QS_MAX_QUBITS 36      /* index arithmetic limit; memory is the real limit */
+#define QS_MAX_GATE_QUBITS 8  /* operands per gate record */
+
+typedef struct qs_state qs_state;   /* opaque: one state vector resident in HBM */
+typedef struct qs_server qs_server; /* opaque: serving runtime (continuous batching) */
+
+typedef enum { QS_C64 = 1, QS_C128 = 2 } qs_dtype;
+
+enum {
+    QS_OK = 0,
+    QS_NOT_READY = 1,
+    QS_ERR_INVALID = -1,     /* bad argument: qubit out of range, repeated operand, ... */
+    QS_ERR_NOMEM = -2,       /* device memory or admission budget exhausted */
+    QS_ERR_CUDA = -3,        /* a CUDA runtime/driver call failed */
+    QS_ERR_TIMEOUT = -4,     /* a bounded device-side wait gave up */
+    QS_ERR_BUSY = -5,        /* object still has work in flight */
+    QS_ERR_UNSUPPORTED = -6  /* valid request this build does not implement */
+};
+
+/* Gate types.  Matrices (first operand most significant in the group index):
+ *   H = [[1,1],[1,-1]]/sqrt2      X, Y, Z = Pauli       S = diag(1,i)   T = diag(1,e^{i pi/4})
+ *   RX(t) = exp(-i t X/2)  RY(t) = exp(-i t Y/2)  RZ(t) = exp(-i t Z/2) (global phase kept)
+ *   P(l) = diag(1, e^{i l})
+ *   U3(t,p,l) = [[cos(t/2), -e^{il} sin(t/2)], [e^{ip} sin(t/2), e^{i(p+l)} cos(t/2)]]
+ *   CNOT(c,t) = Eq. 3           CZ = diag(1,1,1,-1)       SWAP exchanges |01>,|10>
+ *   CU3(c,t; t,p,l) = |0><0| (x) I + |1><1| (x) U3        CP(l) = diag(1,1,1,e^{il})
+ *   RZZ(t) = exp(-i t Z(x)Z/2)
+ *   DENSE: the caller's 2^nq x 2^nq matrix, row-major, interleaved (re, im) doubles. */
+typedef enum {
+    QS_H = 0, QS_X = 1, QS_Y = 2, QS_Z = 3, QS_S = 4, QS_T = 5,
+    QS_RX = 6, QS_RY = 7, QS_RZ = 8, QS_P = 9, QS_U3 = 10,
+    QS_CNOT = 11, QS_CZ = 12, QS_SWAP = 13, QS_CU3 = 14, QS_CP = 15, QS_RZZ = 16,
+    QS_DENSE = 17
+} qs_gate_type;
+
+/* One gate record (72 bytes).  q[0..nq-1] are distinct qubits < n; p[] holds the angles
+ * (theta, phi, lambda) of the parametrised types; m is read only for QS_DENSE (nq <= 6)
+ * and must stay valid for the duration of the call that receives the record. */
+typedef struct {
+    int32_t type;
+    int32_t nq;
+    int32_t q[QS_MAX_GATE_QUBITS];
+    double p[3];
+    const double *m;
+} qs_gate;
+
+/* Execution modes for qs_apply_circuit. */
+enum {
+    QS_MODE_AUTO = 0,     /* fuse + plan in-cache chunk passes (default) */
+    QS_MODE_GATE = 1,     /* plain gate by gate: one streaming launch per gate */
+    QS_MODE_CHUNK = 2,    /* every gate through in-shared-memory chunk passes */
+    QS_MODE_FUSED = 3     /* fuse to dense k-qubit blocks, one full pass per block */
+};
+/* Arithmetic used for complex128 gate updates. */
+enum {
+    QS_PREC_DEFAULT = 0,  /* native FP64 */
+    QS_PREC_FP64 = 1      /* native FP64 */
+};
+
+/* Options for qs_apply_circuit; pass NULL for defaults.  Zero fields mean "choose". */
+typedef struct {
+    int32_t mode;         /* QS_MODE_* */
+    int32_t fuse_k;       /* max qubits of a fused block (0: choose; 1 disables fusion) */
+    int32_t chunk_m;      /* local qubits of a chunk pass (0: choose) */
+    int32_t precision;    /* QS_PREC_* */
+    int32_t reserved[4];
+} qs_options;
+
+/* Statistics of the last qs_apply_circuit on a state. */
+typedef struct {
+    int64_t gates_in;      /* gate records received */
+    int64_t ops_after_fuse;/* operations after fusion */
+    int64_t passes;        /* full state-vector passes launched (each = 1 read + 1 write) */
+    int64_t launches;      /* kernel launches */
+    double bytes;          /* algorithmic HBM bytes of those launches */
+} qs_stats;
+
+/* ---- library ------------------------------------------------------------------ */
+
+/* Thread-local message of the last failure on this thread ("" if none). */
+const char *qs_last_error(void);
+/* Number of kernel launches this library has issued in the process so far. */
+uint64_t qs_launch_count(void);
+/* ABI version (QS_ABI_VERSION) and the CUDA device count; no allocation. */
+int qs_version(int32_t *abi, int32_t *device_count);
+
+/* ---- state lifetime (Eq. 1) --------------------------------------------------- */
+
+/* Allocates a 2^n_qubits-amplitude state of dtype dt on the current CUDA device and
+ * sets it to |0...0> (a_0 = 1).  1 <= n_qubits <= QS_MAX_QUBITS.  The state gets its own
+ * non-blocking CUDA stream.  QS_ERR_NOMEM if 2^n * bytes-per-amplitude does not fit. */
+int qs_create(int n_qubits, qs_dtype dt, qs_state **out);
+/* As qs_create, but over caller-owned device memory dev_ptr of `bytes` bytes (at least
+ * 2^n * bytes-per-amplitude, 256-byte aligned), e.g. a PyTorch tensor, on the caller's
+ * CUDA stream `stream` (cudaStream_t, may be NULL for the legacy stream).  The memory is
+ * NOT initialised and NOT freed by qs_destroy. */
+int qs_create_on(int n_qubits, qs_dtype dt, void *dev_ptr, uint64_t bytes, void *stream,
+                 qs_state **out);
+/* Waits for the state's stream and frees what the library allocated. */
+int qs_destroy(qs_state *s);
+/* Makes later launches of this state run on `stream` (cudaStream_t). */
+int qs_set_stream(qs_state *s, void *stream);
+/* Blocks until all work queued on the state's stream is done. */
+int qs_synchronize(qs_state *s);
+/* Sets the state to |0...0> (asynchronous on the state's stream). */
+int qs_reset(qs_state *s);
+/* Number of qubits, dtype and the device pointer of the amplitudes (for inspection). */
+int qs_info(const qs_state *s, int32_t *n_qubits, int32_t *dtype, void **dev_ptr);
+
+/* ---- gates (Eq. 2, Eq. 3, Sec. II-B, Sec. III) --------------------------------- */
+
+/* Applies gates[0..n_gates-1] in order to the state.  The records are validated first
+ * (QS_ERR_INVALID: unknown type, wrong nq, operand out of range or repeated, dense
+ * matrix missing); nothing is applied if any record is invalid.  The call queues the
+ * work on the state's stream and returns once it is queued (use qs_synchronize, or any
+ * reading call, to wait).  Options: see qs_options. */
+int qs_apply_circuit(qs_state *s, const qs_gate *gates, size_t n_gates, const qs_options *opt);
+/* Statistics of the last qs_apply_circuit on s. */
+int qs_last_stats(const qs_state *s, qs_stats *out);
+
+/* ---- amplitudes and reductions -------------------------------------------------- */
+
+/* Copies cnt amplitudes [off, off+cnt) from host memory (the state's dtype, interleaved)
+ * into the state; synchronous.  QS_ERR_INVALID if the range exceeds 2^n. */
+int qs_set_amplitudes(qs_state *s, uint64_t off, uint64_t cnt, const void *host_src);
+/* Copies cnt amplitudes [off, off+cnt) of the state to host memory (state's dtype);
+ * synchronous (waits for queued gates). */
+int qs_amplitudes(qs_state *s, uint64_t off, uint64_t cnt, void *host_dst);
+/* Squared norm sum_i |a_i|^2, accumulated in FP64 in a fixed order (deterministic). */
+int qs_norm(qs_state *s, double *out);
+/* <Z_q> = sum_i |a_i|^2 (1 - 2 bit_q(i)) for q = 0..n-1 into out[0..n-1] (FP64, fixed
+ * order, not divided by the norm); also the squared norm into *norm_out if non-NULL. */
+int qs_expectation_z(qs_state *s, double *out, double *norm_out);
+/* The k amplitudes with the largest |a_i|^2 (ties: lower index first), sorted; idx[k]
+ * receives indices, amp[2k] the interleaved amplitudes as doubles.  k <= min(2^n, 4096). */
+int qs_top_amplitudes(qs_state *s, uint32_t k, uint64_t *idx, double *amp);
+/* Scales the state by 1/sqrt(norm) (norm computed in FP64); returns the old norm. */
+int qs_renormalize(qs_state *s, double *old_norm);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* QSIM_QS_H_ */

@@ -1,0 +1,363 @@
+// C interface (include/qs.h): state handles, the circuit executor, amplitude I/O and
+// reductions.  Every C entry point catches qs::Error and returns its code.
+#include <atomic>
+#include <cstring>
+#include <mutex>
+
+#include "plan.h"
+#include "qs_internal.h"
+
+struct qs_state {
+    qs::DeviceState d;
+    bool owns_memory = true;
+    bool owns_stream = true;
+    qs_stats stats{};
+};
+
+namespace qs {
+
+namespace {
+thread_local std::string g_last_error;
+std::atomic<uint64_t> g_launches{0};
+}  // namespace
+
+void fail(int code, const std::string &msg) { throw Error{code, msg}; }
+
+void cuda_check(cudaError_t e, const char *what) {
+    if (e != cudaSuccess) {
+        const int code = (e == cudaErrorMemoryAllocation) ? QS_ERR_NOMEM : QS_ERR_CUDA;
+        fail(code, std::string(what) + ": " + cudaGetErrorString(e));
+    }
+}
+
+void count_launch(uint64_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
+int device_sm_count() {
+    int dev = 0;
+    QS_CUDA(cudaGetDevice(&dev));
+    static std::mutex mu;
+    static int cache[64] = {0};
+    std::lock_guard<std::mutex> lk(mu);
+    if (dev < 64 && cache[dev]) return cache[dev];
+    int sms = 0;
+    QS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    if (dev < 64) cache[dev] = sms;
+    return sms;
+}
+
+void ensure_scratch(DeviceState &st, size_t bytes) {
+    if (st.scratch_bytes >= bytes) return;
+    if (st.scratch) {
+        QS_CUDA(cudaStreamSynchronize(st.stream));
+        QS_CUDA(cudaFree(st.scratch));
+        st.scratch = nullptr;
+        st.scratch_bytes = 0;
+    }
+    const size_t cap = std::max<size_t>(bytes, 1 << 20);
+    QS_CUDA(cudaMalloc(&st.scratch, cap));
+    st.scratch_bytes = cap;
+}
+
+// Parameter arena: two halves used alternately by successive qs_apply_circuit calls.
+// Before a half is reused, the event recorded after its last copy is waited on, so the
+// pinned staging memory is never rewritten while a copy from it may still be pending.
+static void arena_begin(DeviceState &st) {
+    st.arena_cur ^= 1;
+    st.arena_used = 0;
+    if (st.arena_ev[st.arena_cur]) QS_CUDA(cudaEventSynchronize(st.arena_ev[st.arena_cur]));
+}
+
+static void arena_end(DeviceState &st) {
+    if (!st.arena_ev[st.arena_cur])
+        QS_CUDA(cudaEventCreateWithFlags(&st.arena_ev[st.arena_cur], cudaEventDisableTiming));
+    QS_CUDA(cudaEventRecord(st.arena_ev[st.arena_cur], st.stream));
+}
+
+void *upload_params(DeviceState &st, const void *host, size_t bytes) {
+    const int c = st.arena_cur;
+    const size_t need = ((st.arena_used + 255) & ~size_t(255)) + bytes;
+    if (need > st.arena_cap[c]) {
+        // grow: nothing queued may still read the old half
+        QS_CUDA(cudaStreamSynchronize(st.stream));
+        if (st.arena_dev[c]) QS_CUDA(cudaFree(st.arena_dev[c]));
+        if (st.arena_host[c]) QS_CUDA(cudaFreeHost(st.arena_host[c]));
+        st.arena_dev[c] = st.arena_host[c] = nullptr;
+        const size_t cap = std::max<size_t>(need * 2, 1 << 16);
+        QS_CUDA(cudaMalloc(&st.arena_dev[c], cap));
+        QS_CUDA(cudaMallocHost(&st.arena_host[c], cap));
+        st.arena_cap[c] = cap;
+        st.arena_used = 0;
+    }
+    const size_t off = (st.arena_used + 255) & ~size_t(255);
+    std::memcpy((char *)st.arena_host[c] + off, host, bytes);
+    void *dst = (char *)st.arena_dev[c] + off;
+    QS_CUDA(cudaMemcpyAsync(dst, (char *)st.arena_host[c] + off, bytes, cudaMemcpyHostToDevice, st.stream));
+    st.arena_used = off + bytes;
+    return dst;
+}
+
+static size_t amp_bytes(int dtype) { return dtype == QS_C128 ? 16 : 8; }
+
+static void destroy_state(qs_state *s) {
+    DeviceState &d = s->d;
+    if (d.stream) cudaStreamSynchronize(d.stream);
+    for (int c = 0; c < 2; c++) {
+        if (d.arena_dev[c]) cudaFree(d.arena_dev[c]);
+        if (d.arena_host[c]) cudaFreeHost(d.arena_host[c]);
+        if (d.arena_ev[c]) cudaEventDestroy(d.arena_ev[c]);
+    }
+    if (d.scratch) cudaFree(d.scratch);
+    if (s->owns_memory && d.psi) cudaFree(d.psi);
+    if (s->owns_stream && d.stream) cudaStreamDestroy(d.stream);
+    delete s;
+}
+
+// Runs the executor for one circuit (validated, lowered).
+static void execute(qs_state *s, const std::vector<Op> &ops, const qs_options &o) {
+    DeviceState &d = s->d;
+    qs_stats st{};
+    st.gates_in = (int64_t)ops.size();
+    const uint64_t l0 = g_launches.load();
+    arena_begin(d);
+    int mode = o.mode;
+    if (mode == QS_MODE_GATE) {
+        for (const Op &op : ops) {
+            launch_stream_op(d, op);
+            st.passes++;
+            st.bytes += stream_bytes(op, d.n, d.dtype);
+        }
+        st.ops_after_fuse = (int64_t)ops.size();
+    } else if (mode == QS_MODE_FUSED) {
+        const int k = o.fuse_k > 0 ? o.fuse_k : 3;
+        const std::vector<Op> fused = fuse_ops(ops, std::min(k, 6));
+        for (const Op &op : fused) {
+            launch_stream_op(d, op);
+            st.passes++;
+            st.bytes += stream_bytes(op, d.n, d.dtype);
+        }
+        st.ops_after_fuse = (int64_t)fused.size();
+    } else if (mode == QS_MODE_AUTO || mode == QS_MODE_CHUNK) {
+        run_planned(d, ops, o, st);
+    } else {
+        arena_end(d);
+        fail(QS_ERR_INVALID, "unknown mode");
+    }
+    arena_end(d);
+    st.launches = (int64_t)(g_launches.load() - l0);
+    s->stats = st;
+}
+
+}  // namespace qs
+
+using namespace qs;
+
+#define QS_API_BEGIN try {
+#define QS_API_END                                  \
+    }                                               \
+    catch (const qs::Error &e) {                    \
+        qs::g_last_error = e.msg;                   \
+        return e.code;                              \
+    }                                               \
+    catch (const std::bad_alloc &) {                \
+        qs::g_last_error = "host allocation failed"; \
+        return QS_ERR_NOMEM;                        \
+    }                                               \
+    catch (const std::exception &e) {               \
+        qs::g_last_error = e.what();                \
+        return QS_ERR_CUDA;                         \
+    }                                               \
+    qs::g_last_error.clear();                       \
+    return QS_OK;
+
+extern "C" {
+
+const char *qs_last_error(void) { return qs::g_last_error.c_str(); }
+
+uint64_t qs_launch_count(void) { return qs::g_launches.load(); }
+
+int qs_version(int32_t *abi, int32_t *device_count) {
+    QS_API_BEGIN
+    if (abi) *abi = QS_ABI_VERSION;
+    if (device_count) {
+        int c = 0;
+        if (cudaGetDeviceCount(&c) != cudaSuccess) c = 0;
+        *device_count = c;
+    }
+    QS_API_END
+}
+
+static void check_new(int n, qs_dtype dt, qs_state **out) {
+    if (!out) fail(QS_ERR_INVALID, "out is NULL");
+    if (n < 1 || n > QS_MAX_QUBITS) fail(QS_ERR_INVALID, "n_qubits out of range");
+    if (dt != QS_C64 && dt != QS_C128) fail(QS_ERR_INVALID, "unknown dtype");
+}
+
+int qs_create(int n_qubits, qs_dtype dt, qs_state **out) {
+    QS_API_BEGIN
+    check_new(n_qubits, dt, out);
+    *out = nullptr;
+    qs_state *s = new qs_state();
+    s->d.n = n_qubits;
+    s->d.dtype = dt;
+    try {
+        QS_CUDA(cudaStreamCreateWithFlags(&s->d.stream, cudaStreamNonBlocking));
+        const size_t bytes = amp_bytes(dt) << n_qubits;
+        cudaError_t e = cudaMalloc(&s->d.psi, bytes);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            s->d.psi = nullptr;
+            fail(QS_ERR_NOMEM, "cannot allocate " + std::to_string(bytes) + " bytes of device memory");
+        }
+        launch_set_zero_state(s->d);
+        QS_CUDA(cudaStreamSynchronize(s->d.stream));
+    } catch (...) {
+        destroy_state(s);
+        throw;
+    }
+    *out = s;
+    QS_API_END
+}
+
+int qs_create_on(int n_qubits, qs_dtype dt, void *dev_ptr, uint64_t bytes, void *stream,
+                 qs_state **out) {
+    QS_API_BEGIN
+    check_new(n_qubits, dt, out);
+    if (!dev_ptr) fail(QS_ERR_INVALID, "dev_ptr is NULL");
+    if (((uintptr_t)dev_ptr & 255) != 0) fail(QS_ERR_INVALID, "dev_ptr must be 256-byte aligned");
+    if (bytes < (amp_bytes(dt) << n_qubits)) fail(QS_ERR_INVALID, "buffer too small for the state");
+    qs_state *s = new qs_state();
+    s->d.n = n_qubits;
+    s->d.dtype = dt;
+    s->d.psi = dev_ptr;
+    s->d.stream = (cudaStream_t)stream;
+    s->owns_memory = false;
+    s->owns_stream = false;
+    *out = s;
+    QS_API_END
+}
+
+int qs_destroy(qs_state *s) {
+    QS_API_BEGIN
+    if (!s) fail(QS_ERR_INVALID, "state is NULL");
+    destroy_state(s);
+    QS_API_END
+}
+
+int qs_set_stream(qs_state *s, void *stream) {
+    QS_API_BEGIN
+    if (!s) fail(QS_ERR_INVALID, "state is NULL");
+    QS_CUDA(cudaStreamSynchronize(s->d.stream));
+    if (s->owns_stream && s->d.stream) QS_CUDA(cudaStreamDestroy(s->d.stream));
+    s->d.stream = (cudaStream_t)stream;
+    s->owns_stream = false;
+    QS_API_END
+}
+
+int qs_synchronize(qs_state *s) {
+    QS_API_BEGIN
+    if (!s) fail(QS_ERR_INVALID, "state is NULL");
+    QS_CUDA(cudaStreamSynchronize(s->d.stream));
+    QS_API_END
+}
+
+int qs_reset(qs_state *s) {
+    QS_API_BEGIN
+    if (!s) fail(QS_ERR_INVALID, "state is NULL");
+    launch_set_zero_state(s->d);
+    QS_API_END
+}
+
+int qs_info(const qs_state *s, int32_t *n_qubits, int32_t *dtype, void **dev_ptr) {
+    QS_API_BEGIN
+    if (!s) fail(QS_ERR_INVALID, "state is NULL");
+    if (n_qubits) *n_qubits = s->d.n;
+    if (dtype) *dtype = s->d.dtype;
+    if (dev_ptr) *dev_ptr = s->d.psi;
+    QS_API_END
+}
+
+int qs_apply_circuit(qs_state *s, const qs_gate *gates, size_t n_gates, const qs_options *opt) {
+    QS_API_BEGIN
+    if (!s) fail(QS_ERR_INVALID, "state is NULL");
+    if (n_gates && !gates) fail(QS_ERR_INVALID, "gates is NULL");
+    qs_options o{};
+    if (opt) o = *opt;
+    std::vector<Op> ops;
+    ops.reserve(n_gates);
+    for (size_t i = 0; i < n_gates; i++) {
+        try {
+            validate_gate(gates[i], s->d.n);
+        } catch (const Error &e) {
+            fail(e.code, "gate " + std::to_string(i) + ": " + e.msg);
+        }
+    }
+    for (size_t i = 0; i < n_gates; i++) ops.push_back(lower_gate(gates[i]));
+    execute(s, ops, o);
+    QS_API_END
+}
+
+int qs_last_stats(const qs_state *s, qs_stats *out) {
+    QS_API_BEGIN
+    if (!s || !out) fail(QS_ERR_INVALID, "NULL argument");
+    *out = s->stats;
+    QS_API_END
+}
+
+int qs_set_amplitudes(qs_state *s, uint64_t off, uint64_t cnt, const void *host_src) {
+    QS_API_BEGIN
+    if (!s || (cnt && !host_src)) fail(QS_ERR_INVALID, "NULL argument");
+    const uint64_t N = 1ull << s->d.n;
+    if (off > N || cnt > N - off) fail(QS_ERR_INVALID, "amplitude range out of bounds");
+    const size_t B = amp_bytes(s->d.dtype);
+    QS_CUDA(cudaMemcpyAsync((char *)s->d.psi + off * B, host_src, cnt * B, cudaMemcpyHostToDevice, s->d.stream));
+    QS_CUDA(cudaStreamSynchronize(s->d.stream));
+    QS_API_END
+}
+
+int qs_amplitudes(qs_state *s, uint64_t off, uint64_t cnt, void *host_dst) {
+    QS_API_BEGIN
+    if (!s || (cnt && !host_dst)) fail(QS_ERR_INVALID, "NULL argument");
+    const uint64_t N = 1ull << s->d.n;
+    if (off > N || cnt > N - off) fail(QS_ERR_INVALID, "amplitude range out of bounds");
+    const size_t B = amp_bytes(s->d.dtype);
+    QS_CUDA(cudaMemcpyAsync(host_dst, (const char *)s->d.psi + off * B, cnt * B, cudaMemcpyDeviceToHost, s->d.stream));
+    QS_CUDA(cudaStreamSynchronize(s->d.stream));
+    QS_API_END
+}
+
+int qs_norm(qs_state *s, double *out) {
+    QS_API_BEGIN
+    if (!s || !out) fail(QS_ERR_INVALID, "NULL argument");
+    reduce_expz(s->d, out, nullptr);
+    QS_API_END
+}
+
+int qs_expectation_z(qs_state *s, double *out, double *norm_out) {
+    QS_API_BEGIN
+    if (!s || !out) fail(QS_ERR_INVALID, "NULL argument");
+    double nrm = 0.0;
+    reduce_expz(s->d, &nrm, out);
+    if (norm_out) *norm_out = nrm;
+    QS_API_END
+}
+
+int qs_top_amplitudes(qs_state *s, uint32_t k, uint64_t *idx, double *amp) {
+    QS_API_BEGIN
+    if (!s || (k && (!idx || !amp))) fail(QS_ERR_INVALID, "NULL argument");
+    top_k(s->d, k, idx, amp);
+    QS_API_END
+}
+
+int qs_renormalize(qs_state *s, double *old_norm) {
+    QS_API_BEGIN
+    if (!s) fail(QS_ERR_INVALID, "state is NULL");
+    double nrm = 0.0;
+    reduce_expz(s->d, &nrm, nullptr);
+    if (!(nrm > 0.0)) fail(QS_ERR_INVALID, "state has zero norm");
+    launch_scale(s->d, 1.0 / std::sqrt(nrm));
+    QS_CUDA(cudaStreamSynchronize(s->d.stream));
+    if (old_norm) *old_norm = nrm;
+    QS_API_END
+}
+
+}  // extern "C"

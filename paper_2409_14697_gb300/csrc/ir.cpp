@@ -1,0 +1,263 @@
+// Host gate IR: validation, lowering of gate records to Ops, fusion.
+//
+// Gate semantics follow QueenV2 (arXiv 2409.14697) Sec. II-A: Eq. 2 (one-qubit pair
+// update), Eq. 3 (CNOT on a group of four, first operand = control) and the k-qubit
+// generalisation stated before Eq. 3.  The paper prints no other gate matrix; the ones
+// below are the standard definitions listed in include/qs.h.  Sec. III-B notes that
+// further gates are built from supported unitaries: QS_DENSE carries any such block.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <stdexcept>
+
+#include "qs_internal.h"
+
+namespace qs {
+
+namespace {
+
+const cd kI(0.0, 1.0);
+
+int expected_arity(int type) {
+    switch (type) {
+    case QS_H: case QS_X: case QS_Y: case QS_Z: case QS_S: case QS_T:
+    case QS_RX: case QS_RY: case QS_RZ: case QS_P: case QS_U3:
+        return 1;
+    case QS_CNOT: case QS_CZ: case QS_SWAP: case QS_CU3: case QS_CP: case QS_RZZ:
+        return 2;
+    case QS_DENSE:
+        return 0;
+    default:
+        return -1;
+    }
+}
+
+// U3(theta, phi, lambda), OpenQASM 2 convention, row-major.
+std::vector<cd> u3(double t, double p, double l) {
+    const double c = std::cos(0.5 * t), s = std::sin(0.5 * t);
+    return {cd(c, 0.0), -std::polar(1.0, l) * s, std::polar(1.0, p) * s,
+            std::polar(1.0, p + l) * c};
+}
+
+}  // namespace
+
+void validate_gate(const qs_gate &g, int n) {
+    const int want = expected_arity(g.type);
+    if (want < 0) fail(QS_ERR_INVALID, "unknown gate type " + std::to_string(g.type));
+    if (want == 0) {
+        if (g.nq < 1 || g.nq > 6) fail(QS_ERR_INVALID, "dense gate needs 1 <= nq <= 6");
+        if (!g.m) fail(QS_ERR_INVALID, "dense gate without matrix");
+    } else if (g.nq != want) {
+        fail(QS_ERR_INVALID, "gate type " + std::to_string(g.type) + " takes " +
+                                 std::to_string(want) + " qubits, got " + std::to_string(g.nq));
+    }
+    uint64_t seen = 0;
+    for (int j = 0; j < g.nq; j++) {
+        if (g.q[j] < 0 || g.q[j] >= n)
+            fail(QS_ERR_INVALID, "qubit " + std::to_string(g.q[j]) + " out of range for " +
+                                     std::to_string(n) + " qubits");
+        if ((seen >> g.q[j]) & 1) fail(QS_ERR_INVALID, "repeated operand qubit");
+        seen |= 1ull << g.q[j];
+    }
+    for (int j = 0; j < 3; j++)
+        if (!std::isfinite(g.p[j])) fail(QS_ERR_INVALID, "non-finite gate parameter");
+    if (g.type == QS_DENSE) {
+        const size_t cnt = 2ull << (2 * g.nq);
+        for (size_t i = 0; i < cnt; i++)
+            if (!std::isfinite(g.m[i])) fail(QS_ERR_INVALID, "non-finite dense matrix entry");
+    }
+}
+
+Op lower_gate(const qs_gate &g) {
+    Op op;
+    op.k = g.nq;
+    for (int j = 0; j < g.nq; j++) op.q[j] = g.q[j];
+    const double *p = g.p;
+    switch (g.type) {
+    case QS_H: op.kind = K_H; break;
+    case QS_X: op.kind = K_PERM1; break;
+    case QS_Y: op.kind = K_DENSE1; op.m = {0.0, -kI, kI, 0.0}; break;
+    case QS_Z: op.kind = K_DIAG1; op.m = {1.0, -1.0}; break;
+    case QS_S: op.kind = K_DIAG1; op.m = {1.0, kI}; break;
+    case QS_T: op.kind = K_DIAG1; op.m = {1.0, std::polar(1.0, M_PI / 4)}; break;
+    case QS_RX: {
+        const double c = std::cos(0.5 * p[0]), s = std::sin(0.5 * p[0]);
+        op.kind = K_DENSE1;
+        op.m = {c, -kI * s, -kI * s, c};
+        break;
+    }
+    case QS_RY: {
+        const double c = std::cos(0.5 * p[0]), s = std::sin(0.5 * p[0]);
+        op.kind = K_DENSE1;
+        op.m = {c, -s, s, c};
+        break;
+    }
+    case QS_RZ:
+        op.kind = K_DIAG1;
+        op.m = {std::polar(1.0, -0.5 * p[0]), std::polar(1.0, 0.5 * p[0])};
+        break;
+    case QS_P: op.kind = K_DIAG1; op.m = {1.0, std::polar(1.0, p[0])}; break;
+    case QS_U3: op.kind = K_DENSE1; op.m = u3(p[0], p[1], p[2]); break;
+    case QS_CNOT: op.kind = K_CTRL1; op.m = {0.0, 1.0, 1.0, 0.0}; break;
+    case QS_CU3: op.kind = K_CTRL1; op.m = u3(p[0], p[1], p[2]); break;
+    case QS_SWAP: op.kind = K_SWAP; break;
+    case QS_CZ: op.kind = K_DIAG; op.m = {1.0, 1.0, 1.0, -1.0}; break;
+    case QS_CP: op.kind = K_DIAG; op.m = {1.0, 1.0, 1.0, std::polar(1.0, p[0])}; break;
+    case QS_RZZ: {
+        const cd e = std::polar(1.0, -0.5 * p[0]), f = std::polar(1.0, 0.5 * p[0]);
+        op.kind = K_DIAG;
+        op.m = {e, f, f, e};
+        break;
+    }
+    case QS_DENSE: {
+        const size_t d = 1ull << g.nq;
+        op.m.resize(d * d);
+        for (size_t i = 0; i < d * d; i++) op.m[i] = cd(g.m[2 * i], g.m[2 * i + 1]);
+        op.kind = g.nq == 1 ? K_DENSE1 : K_DENSE;
+        break;
+    }
+    default:
+        fail(QS_ERR_INVALID, "unknown gate type");
+    }
+    return op;
+}
+
+std::vector<cd> Op::full() const {
+    const size_t d = 1ull << k;
+    std::vector<cd> f(d * d, 0.0);
+    switch (kind) {
+    case K_H: {
+        const double r = 1.0 / std::sqrt(2.0);
+        f = {r, r, r, -r};
+        break;
+    }
+    case K_PERM1: f = {0.0, 1.0, 1.0, 0.0}; break;
+    case K_DIAG1: f = {m[0], 0.0, 0.0, m[1]}; break;
+    case K_DENSE1: f = m; break;
+    case K_CTRL1:   // rows/cols: (c,t) = 00, 01, 10, 11
+        f[0] = 1.0;
+        f[5] = 1.0;
+        f[10] = m[0]; f[11] = m[1];
+        f[14] = m[2]; f[15] = m[3];
+        break;
+    case K_SWAP: f[0] = 1.0; f[6] = 1.0; f[9] = 1.0; f[15] = 1.0; break;
+    case K_DIAG:
+        for (size_t i = 0; i < d; i++) f[i * d + i] = m[i];
+        break;
+    case K_DENSE: f = m; break;
+    }
+    return f;
+}
+
+namespace {
+
+// Embeds op (on its own operand order) into the qubit list Q (Q[0] most significant):
+// returns the 2^|Q| x 2^|Q| matrix acting as op on its qubits and as identity elsewhere.
+std::vector<cd> embed(const Op &op, const std::vector<int> &Q) {
+    const int K = (int)Q.size();
+    const size_t D = 1ull << K;
+    const std::vector<cd> f = op.full();
+    const size_t d = 1ull << op.k;
+    int pos[8];  // position (bit index within the Q sub-index) of each operand
+    uint64_t opbits = 0;
+    for (int j = 0; j < op.k; j++) {
+        int found = -1;
+        for (int t = 0; t < K; t++)
+            if (Q[t] == op.q[j]) found = t;
+        pos[j] = K - 1 - found;
+        opbits |= 1ull << pos[j];
+    }
+    auto sub = [&](uint64_t r) {
+        uint64_t s = 0;
+        for (int j = 0; j < op.k; j++) s |= ((r >> pos[j]) & 1ull) << (op.k - 1 - j);
+        return s;
+    };
+    std::vector<cd> out(D * D, 0.0);
+    for (uint64_t r = 0; r < D; r++)
+        for (uint64_t c = 0; c < D; c++) {
+            if ((r & ~opbits) != (c & ~opbits)) continue;
+            out[r * D + c] = f[sub(r) * d + sub(c)];
+        }
+    return out;
+}
+
+bool is_diagonal(const Op &op) { return op.kind == K_DIAG1 || op.kind == K_DIAG; }
+
+}  // namespace
+
+std::vector<Op> fuse_ops(const std::vector<Op> &ops, int fuse_k) {
+    if (fuse_k <= 1) return ops;
+    std::vector<Op> out;
+    std::vector<int> Q;                  // qubits of the current block, Q[0] most significant
+    std::vector<cd> U;                   // its matrix
+    std::vector<const Op *> members;     // ops absorbed into the current block
+    bool diag = true;
+
+    auto flush = [&]() {
+        if (members.empty()) return;
+        if (members.size() == 1) {
+            out.push_back(*members[0]);
+        } else {
+            Op b;
+            b.k = (int)Q.size();
+            for (int j = 0; j < b.k; j++) b.q[j] = Q[j];
+            const size_t D = 1ull << b.k;
+            if (diag) {
+                b.kind = b.k == 1 ? K_DIAG1 : K_DIAG;
+                b.m.resize(D);
+                for (size_t i = 0; i < D; i++) b.m[i] = U[i * D + i];
+            } else {
+                b.kind = b.k == 1 ? K_DENSE1 : K_DENSE;
+                b.m = U;
+            }
+            out.push_back(std::move(b));
+        }
+        members.clear();
+        Q.clear();
+        U.clear();
+        diag = true;
+    };
+
+    for (const Op &op : ops) {
+        std::vector<int> nQ = Q;
+        for (int j = 0; j < op.k; j++) {
+            bool have = false;
+            for (int x : nQ) have |= x == op.q[j];
+            if (!have) nQ.push_back(op.q[j]);
+        }
+        if ((int)nQ.size() > fuse_k) {
+            flush();
+            nQ.assign(op.q, op.q + op.k);
+        }
+        // keep the block's qubits sorted high-to-low so that equal sets give equal orders
+        std::sort(nQ.begin(), nQ.end(), [](int a, int b) { return a > b; });
+        const size_t D = 1ull << nQ.size();
+        std::vector<cd> newU;
+        if (members.empty()) {
+            Op tmp = op;
+            newU = embed(tmp, nQ);
+        } else {
+            Op cur;
+            cur.kind = K_DENSE;
+            cur.k = (int)Q.size();
+            for (int j = 0; j < cur.k; j++) cur.q[j] = Q[j];
+            cur.m = U;
+            const std::vector<cd> A = embed(cur, nQ), B = embed(op, nQ);
+            newU.assign(D * D, 0.0);
+            for (size_t r = 0; r < D; r++)
+                for (size_t t = 0; t < D; t++) {
+                    const cd b = B[r * D + t];
+                    if (b == cd(0.0)) continue;
+                    for (size_t c = 0; c < D; c++) newU[r * D + c] += b * A[t * D + c];
+                }
+        }
+        Q = nQ;
+        U = std::move(newU);
+        members.push_back(&op);
+        diag = diag && is_diagonal(op);
+    }
+    flush();
+    return out;
+}
+
+}  // namespace qs

@@ -1,0 +1,120 @@
+// Internal declarations of the state-vector library (host side + kernel launchers).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <complex>
+#include <cstdint>
+#include <string>
+#include <type_traits>
+#include <vector>
+
+#include "qs.h"
+
+namespace qs {
+
+using cd = std::complex<double>;
+
+// ---------------------------------------------------------------------------------
+// Errors: every internal failure throws qs::Error; the C entry points translate it to
+// a return code and the thread-local message.
+struct Error {
+    int code;
+    std::string msg;
+};
+[[noreturn]] void fail(int code, const std::string &msg);
+void cuda_check(cudaError_t e, const char *what);
+#define QS_CUDA(x) ::qs::cuda_check((x), #x)
+
+// Counts kernel launches of this library (process-wide).
+void count_launch(uint64_t n = 1);
+
+// ---------------------------------------------------------------------------------
+// Lowered operations (host IR).  Every gate record becomes one Op: its operand qubits
+// (first = most significant of the group index, Eq. 3's row order) and a structural
+// kind that tells the kernels which amplitudes of each group it touches.
+enum OpKind : int32_t {
+    K_H = 0,       // Hadamard on q[0]
+    K_PERM1,       // X on q[0]: exchange the pair
+    K_DIAG1,       // diag(d0, d1) on q[0]
+    K_DENSE1,      // 2x2 on q[0]
+    K_CTRL1,       // control q[0] = 1, 2x2 matrix u on target q[1]
+    K_SWAP,        // exchange |01>,|10> of (q[0], q[1])
+    K_DIAG,        // diagonal on k qubits: m holds the 2^k diagonal entries
+    K_DENSE,       // dense 2^k x 2^k on k qubits (k >= 2), m row-major
+};
+
+struct Op {
+    OpKind kind;
+    int k = 0;          // operand count
+    int q[8] = {0};     // operands
+    std::vector<cd> m;  // K_DIAG1: 2 entries; K_DENSE1/K_CTRL1: 4; K_DIAG: 2^k; K_DENSE: 4^k
+    // The full 2^k x 2^k matrix of the op on q[0..k-1] (row-major).
+    std::vector<cd> full() const;
+    uint64_t qmask() const {
+        uint64_t r = 0;
+        for (int j = 0; j < k; j++) r |= 1ull << q[j];
+        return r;
+    }
+};
+
+// Validates one gate record against an n-qubit state (throws QS_ERR_INVALID).
+void validate_gate(const qs_gate &g, int n);
+// Lowers a validated record to an Op (own gate definitions, FP64).
+Op lower_gate(const qs_gate &g);
+
+// Gate fusion (Sec. II-B "Gate Fusion", Sec. III-A tier 5): greedily merges runs of
+// consecutive ops into dense blocks on at most fuse_k qubits.  FP64 host products.
+std::vector<Op> fuse_ops(const std::vector<Op> &ops, int fuse_k);
+
+// ---------------------------------------------------------------------------------
+// Device-side geometry of a streaming application: each group is one base index with
+// the fixed bits (sorted ascending, in element units) cleared; set_mask bits forced
+// to one; the op touches nt elements at base | set_mask | off[t].
+struct StreamGeom {
+    int nf;             // number of fixed bits (1..3)
+    int fb[3];          // fixed bits, ascending (element index space)
+    uint64_t set_mask;  // forced-one bits (element index space)
+    int nt;             // touched elements per group (1, 2 or 4)
+    uint64_t off[4];    // offsets of the touched elements
+    uint64_t n_groups;  // 2^(n_elem_bits - nf)
+};
+
+struct DeviceState {
+    void *psi = nullptr;  // amplitudes
+    int n = 0;            // qubits
+    int dtype = QS_C128;
+    cudaStream_t stream = nullptr;
+    // scratch for reductions (owned by the state)
+    void *scratch = nullptr;
+    size_t scratch_bytes = 0;
+    int num_sms = 0;
+    // parameter arenas (double-buffered per qs_apply_circuit call)
+    void *arena_dev[2] = {nullptr, nullptr};
+    void *arena_host[2] = {nullptr, nullptr};
+    size_t arena_cap[2] = {0, 0};
+    size_t arena_used = 0;
+    int arena_cur = 0;
+    cudaEvent_t arena_ev[2] = {nullptr, nullptr};
+};
+
+// Launchers (kernels live in the .cu files).  All are asynchronous on st.stream.
+void launch_stream_op(DeviceState &st, const Op &op);           // K1, one op, one pass
+void launch_set_zero_state(DeviceState &st);                    // |0..0>
+void launch_scale(DeviceState &st, double f);                   // psi *= f
+// Reductions (K4).  expz may be null (norm only).  Results are copied to host.
+void reduce_expz(DeviceState &st, double *norm, double *expz);
+void top_k(DeviceState &st, uint32_t k, uint64_t *idx, double *amp);
+
+// Algorithmic bytes of one streaming application of op on an n-qubit state.
+double stream_bytes(const Op &op, int n, int dtype);
+
+// Copies `bytes` of host data into the state's device parameter arena (asynchronously,
+// ordered on st.stream before any later launch) and returns the device address.
+void *upload_params(DeviceState &st, const void *host, size_t bytes);
+
+// Scratch helper: makes sure st.scratch holds at least `bytes`.
+void ensure_scratch(DeviceState &st, size_t bytes);
+int device_sm_count();
+
+}  // namespace qs

@@ -1,0 +1,283 @@
+"""Thin ctypes binding of the C interface in include/qs.h (argument marshalling only).
+
+Every function keeps the C name (``qs_create``, ``qs_apply_circuit``, ...).  Gates
+are passed either as ``qs_gate`` records or as ``(name, qubits, params)`` tuples
+(``("dense", qubits, matrix)`` for a dense block), which :func:`gate_records`
+converts.  Nothing here computes amplitudes: every step runs in ``libqsim.so``.
+Importing this module fails loudly if the library has not been built.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libqsim.so")
+
+QS_C64, QS_C128 = 1, 2
+QS_OK, QS_NOT_READY = 0, 1
+QS_ERR_INVALID, QS_ERR_NOMEM, QS_ERR_CUDA, QS_ERR_TIMEOUT, QS_ERR_BUSY, QS_ERR_UNSUPPORTED = -1, -2, -3, -4, -5, -6
+QS_MODE_AUTO, QS_MODE_GATE, QS_MODE_CHUNK, QS_MODE_FUSED = 0, 1, 2, 3
+QS_PREC_DEFAULT, QS_PREC_FP64 = 0, 1
+
+GATE_TYPES = {
+    "h": 0, "x": 1, "y": 2, "z": 3, "s": 4, "t": 5,
+    "rx": 6, "ry": 7, "rz": 8, "p": 9, "u3": 10,
+    "cnot": 11, "cz": 12, "swap": 13, "cu3": 14, "cp": 15, "rzz": 16,
+    "dense": 17,
+}
+
+
+class QsError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"qs error {code}: {msg}")
+        self.code = code
+
+
+class qs_gate(ctypes.Structure):
+    _fields_ = [("type", ctypes.c_int32), ("nq", ctypes.c_int32), ("q", ctypes.c_int32 * 8),
+                ("p", ctypes.c_double * 3), ("m", ctypes.POINTER(ctypes.c_double))]
+
+
+class qs_options(ctypes.Structure):
+    _fields_ = [("mode", ctypes.c_int32), ("fuse_k", ctypes.c_int32), ("chunk_m", ctypes.c_int32),
+                ("precision", ctypes.c_int32), ("reserved", ctypes.c_int32 * 4)]
+
+
+class qs_stats(ctypes.Structure):
+    _fields_ = [("gates_in", ctypes.c_int64), ("ops_after_fuse", ctypes.c_int64),
+                ("passes", ctypes.c_int64), ("launches", ctypes.c_int64), ("bytes", ctypes.c_double)]
+
+
+_lib = None
+_VP = ctypes.c_void_p
+_DP = ctypes.POINTER(ctypes.c_double)
+_U64P = ctypes.POINTER(ctypes.c_uint64)
+
+# name -> (restype, argtypes)
+_SIGS = {
+    "qs_last_error": (ctypes.c_char_p, []),
+    "qs_launch_count": (ctypes.c_uint64, []),
+    "qs_version": (ctypes.c_int, [ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]),
+    "qs_create": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.POINTER(_VP)]),
+    "qs_create_on": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, _VP, ctypes.c_uint64, _VP, ctypes.POINTER(_VP)]),
+    "qs_destroy": (ctypes.c_int, [_VP]),
+    "qs_set_stream": (ctypes.c_int, [_VP, _VP]),
+    "qs_synchronize": (ctypes.c_int, [_VP]),
+    "qs_reset": (ctypes.c_int, [_VP]),
+    "qs_info": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(_VP)]),
+    "qs_apply_circuit": (ctypes.c_int, [_VP, ctypes.POINTER(qs_gate), ctypes.c_size_t, ctypes.POINTER(qs_options)]),
+    "qs_last_stats": (ctypes.c_int, [_VP, ctypes.POINTER(qs_stats)]),
+    "qs_set_amplitudes": (ctypes.c_int, [_VP, ctypes.c_uint64, ctypes.c_uint64, _VP]),
+    "qs_amplitudes": (ctypes.c_int, [_VP, ctypes.c_uint64, ctypes.c_uint64, _VP]),
+    "qs_norm": (ctypes.c_int, [_VP, _DP]),
+    "qs_expectation_z": (ctypes.c_int, [_VP, _DP, _DP]),
+    "qs_top_amplitudes": (ctypes.c_int, [_VP, ctypes.c_uint32, _U64P, _DP]),
+    "qs_renormalize": (ctypes.c_int, [_VP, _DP]),
+}
+
+
+def load():
+    """Loads libqsim.so (raises if it is missing: there is no fallback path)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"{LIB_PATH} is not built; run __graft_entry__.build()")
+        lib = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+    return _lib
+
+
+def exported_symbols():
+    return list(_SIGS)
+
+
+def _check(rc):
+    if rc < 0:
+        raise QsError(rc, load().qs_last_error().decode())
+    return rc
+
+
+def gate_records(gates):
+    """(name, qubits, params) tuples -> ctypes array of qs_gate (dense matrices kept alive
+    in the array's ``_keep`` attribute)."""
+    arr = (qs_gate * max(len(gates), 1))()
+    keep = []
+    for i, (name, qubits, params) in enumerate(gates):
+        g = arr[i]
+        g.type = GATE_TYPES[name]
+        g.nq = len(qubits)
+        for j, q in enumerate(qubits):
+            g.q[j] = int(q)
+        if name == "dense":
+            m = np.ascontiguousarray(params, dtype=np.complex128).reshape(-1).view(np.float64)
+            keep.append(m)
+            g.m = m.ctypes.data_as(_DP)
+        else:
+            for j, v in enumerate(params):
+                g.p[j] = float(v)
+    arr._keep = keep
+    return arr
+
+
+def options(mode=QS_MODE_AUTO, fuse_k=0, chunk_m=0, precision=QS_PREC_DEFAULT):
+    o = qs_options()
+    o.mode, o.fuse_k, o.chunk_m, o.precision = mode, fuse_k, chunk_m, precision
+    return o
+
+
+# ---- C-named wrappers -----------------------------------------------------------
+
+def qs_launch_count() -> int:
+    return int(load().qs_launch_count())
+
+
+def qs_version():
+    a, d = ctypes.c_int32(), ctypes.c_int32()
+    _check(load().qs_version(ctypes.byref(a), ctypes.byref(d)))
+    return a.value, d.value
+
+
+def qs_create(n_qubits: int, dtype: int = QS_C128):
+    h = _VP()
+    _check(load().qs_create(n_qubits, dtype, ctypes.byref(h)))
+    return h
+
+
+def qs_create_on(n_qubits: int, dtype: int, dev_ptr: int, nbytes: int, stream: int = 0):
+    h = _VP()
+    _check(load().qs_create_on(n_qubits, dtype, dev_ptr, nbytes, stream, ctypes.byref(h)))
+    return h
+
+
+def qs_destroy(h):
+    _check(load().qs_destroy(h))
+
+
+def qs_set_stream(h, stream: int):
+    _check(load().qs_set_stream(h, stream))
+
+
+def qs_synchronize(h):
+    _check(load().qs_synchronize(h))
+
+
+def qs_reset(h):
+    _check(load().qs_reset(h))
+
+
+def qs_info(h):
+    n, d, p = ctypes.c_int32(), ctypes.c_int32(), _VP()
+    _check(load().qs_info(h, ctypes.byref(n), ctypes.byref(d), ctypes.byref(p)))
+    return n.value, d.value, p.value
+
+
+def qs_apply_circuit(h, gates, opts=None):
+    recs = gates if isinstance(gates, ctypes.Array) else gate_records(gates)
+    n = len(gates)
+    o = opts if opts is not None else options()
+    _check(load().qs_apply_circuit(h, recs, n, ctypes.byref(o)))
+
+
+def qs_last_stats(h) -> dict:
+    s = qs_stats()
+    _check(load().qs_last_stats(h, ctypes.byref(s)))
+    return {f: getattr(s, f) for f, _ in qs_stats._fields_}
+
+
+def _np_dtype(h):
+    return np.complex128 if qs_info(h)[1] == QS_C128 else np.complex64
+
+
+def qs_set_amplitudes(h, host: np.ndarray, off: int = 0):
+    host = np.ascontiguousarray(host, dtype=_np_dtype(h))
+    _check(load().qs_set_amplitudes(h, off, host.size, host.ctypes.data))
+
+
+def qs_amplitudes(h, off: int = 0, cnt: int | None = None, out: np.ndarray | None = None):
+    n = qs_info(h)[0]
+    cnt = (1 << n) - off if cnt is None else cnt
+    if out is None:
+        out = np.empty(cnt, dtype=_np_dtype(h))
+    _check(load().qs_amplitudes(h, off, cnt, out.ctypes.data))
+    return out
+
+
+def qs_amplitudes_into(h, off: int, cnt: int, host_ptr: int):
+    _check(load().qs_amplitudes(h, off, cnt, host_ptr))
+
+
+def qs_set_amplitudes_from(h, off: int, cnt: int, host_ptr: int):
+    _check(load().qs_set_amplitudes(h, off, cnt, host_ptr))
+
+
+def qs_norm(h) -> float:
+    v = ctypes.c_double()
+    _check(load().qs_norm(h, ctypes.byref(v)))
+    return v.value
+
+
+def qs_expectation_z(h):
+    n = qs_info(h)[0]
+    out = np.zeros(n)
+    nrm = ctypes.c_double()
+    _check(load().qs_expectation_z(h, out.ctypes.data_as(_DP), ctypes.byref(nrm)))
+    return out, nrm.value
+
+
+def qs_top_amplitudes(h, k: int):
+    idx = np.zeros(k, dtype=np.uint64)
+    amp = np.zeros(k, dtype=np.complex128)
+    _check(load().qs_top_amplitudes(h, k, idx.ctypes.data_as(_U64P), amp.ctypes.data_as(_DP)))
+    return idx, amp
+
+
+def qs_renormalize(h) -> float:
+    v = ctypes.c_double()
+    _check(load().qs_renormalize(h, ctypes.byref(v)))
+    return v.value
+
+
+class State:
+    """Owning wrapper: ``with State(n, QS_C128) as s: s.apply(gates)``."""
+
+    def __init__(self, n: int, dtype: int = QS_C128):
+        self.n, self.dtype = n, dtype
+        self.h = qs_create(n, dtype)
+
+    def apply(self, gates, mode=QS_MODE_AUTO, **kw):
+        qs_apply_circuit(self.h, gates, options(mode=mode, **kw))
+        return self
+
+    def set(self, psi):
+        qs_set_amplitudes(self.h, psi)
+        return self
+
+    def get(self):
+        return qs_amplitudes(self.h)
+
+    def sync(self):
+        qs_synchronize(self.h)
+
+    def close(self):
+        if self.h:
+            qs_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,200 @@
+"""GPU parity of the streaming path (one kernel launch per gate) and the reductions,
+through the C ABI, against the FP64 CPU oracle on identical seeded inputs."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2409_14697_gb300 import inputs
+from tests.gpu_util import TOL_C128, TOL_C64, fidelity_gap, require_gpu
+
+pytestmark = pytest.mark.gpu
+
+ALL_1Q = ["h", "x", "y", "z", "s", "t", "rx", "ry", "rz", "p", "u3"]
+ALL_2Q = ["cnot", "cz", "swap", "cu3", "cp", "rzz"]
+
+
+@pytest.fixture(scope="module")
+def qs():
+    require_gpu()
+    from paper_2409_14697_gb300 import qs as q
+    q.load()
+    return q
+
+
+def run_gpu(qs, n, dtype, psi0, gates, mode, **kw):
+    h = qs.qs_create(n, dtype)
+    try:
+        qs.qs_set_amplitudes(h, psi0)
+        qs.qs_apply_circuit(h, gates, qs.options(mode=mode, **kw))
+        return qs.qs_amplitudes(h).astype(np.complex128)
+    finally:
+        qs.qs_destroy(h)
+
+
+def check(got, want, dtype):
+    err = np.max(np.abs(got - want))
+    if dtype == 2:
+        assert err <= TOL_C128, err
+    else:
+        assert err <= TOL_C64, err
+
+
+@pytest.mark.parametrize("dtype", [2, 1])
+@pytest.mark.parametrize("n", [1, 2, 3, 5, 8])
+def test_every_gate_every_target(qs, n, dtype):
+    psi0 = inputs.gaussian_state(n, seed=n)
+    if dtype == 1:
+        psi0 = psi0.astype(np.complex64)
+    r = np.random.default_rng(n)
+    gates = []
+    for name in ALL_1Q:
+        for q in range(n):
+            gates.append((name, (q,), tuple(r.uniform(0, 2 * math.pi, inputs.n_params(name)))))
+    if n >= 2:
+        for name in ALL_2Q:
+            for a in range(n):
+                for b in range(n):
+                    if a != b:
+                        gates.append((name, (a, b), tuple(r.uniform(0, 2 * math.pi, inputs.n_params(name)))))
+    # one gate per call, each compared with the oracle
+    h = qs.qs_create(n, dtype)
+    try:
+        qs.qs_set_amplitudes(h, psi0)
+        want = psi0.astype(np.complex128)
+        for g in gates:
+            qs.qs_apply_circuit(h, [g], qs.options(mode=qs.QS_MODE_GATE))
+            oracle.run(want, n, [g])
+            got = qs.qs_amplitudes(h).astype(np.complex128)
+            err = np.max(np.abs(got - want))
+            assert err <= (TOL_C128 if dtype == 2 else TOL_C64), (g, err)
+            if dtype == 1:   # keep the comparison per gate: restart from the GPU state
+                want = got.copy()
+    finally:
+        qs.qs_destroy(h)
+
+
+@pytest.mark.parametrize("dtype", [2, 1])
+def test_brickwork_12q(qs, dtype):
+    """20 layers of U3 on every qubit + CZ brickwork from |0...0>, all 4096 amplitudes."""
+    n = 12
+    gates = inputs.brickwork(n, 20, seed=1)
+    want = oracle.run(oracle.zero_state(n), n, gates)
+    psi0 = oracle.zero_state(n).astype(np.complex64 if dtype == 1 else np.complex128)
+    got = run_gpu(qs, n, dtype, psi0, gates, qs.QS_MODE_GATE)
+    check(got, want, dtype)
+    if dtype == 1:
+        assert fidelity_gap(got, want) < 1e-6
+
+
+@pytest.mark.parametrize("k", [1, 2, 3, 4, 5, 6])
+@pytest.mark.parametrize("dtype", [2, 1])
+def test_dense_blocks(qs, k, dtype):
+    n = 10
+    r = np.random.default_rng(k)
+    gates = []
+    for i in range(6):
+        qubits = tuple(int(x) for x in r.choice(n, size=k, replace=False))
+        gates.append(("dense", qubits, inputs.random_unitary(k, seed=10 * k + i)))
+    psi0 = inputs.gaussian_state(n, seed=3)
+    want = oracle.run(psi0.copy(), n, gates)
+    if dtype == 1:
+        psi0 = psi0.astype(np.complex64)
+    got = run_gpu(qs, n, dtype, psi0, gates, qs.QS_MODE_GATE)
+    check(got, want, dtype)
+
+
+@pytest.mark.parametrize("dtype", [2, 1])
+@pytest.mark.parametrize("fk", [2, 3, 4, 5])
+def test_fused_mode(qs, dtype, fk):
+    n = 11
+    gates = inputs.random_circuit(n, 120, seed=fk) + inputs.brickwork(n, 4, seed=fk)
+    psi0 = inputs.gaussian_state(n, seed=fk)
+    want = oracle.run(psi0.copy(), n, gates)
+    if dtype == 1:
+        psi0 = psi0.astype(np.complex64)
+    got = run_gpu(qs, n, dtype, psi0, gates, qs.QS_MODE_FUSED, fuse_k=fk)
+    check(got, want, dtype)
+
+
+@pytest.mark.parametrize("dtype", [2, 1])
+@pytest.mark.parametrize("n", [1, 3, 9, 13, 16, 21])
+def test_norm_expz(qs, n, dtype):
+    psi = inputs.gaussian_state(n, seed=100 + n)
+    psi = psi * 1.7  # not normalised on purpose
+    if dtype == 1:
+        psi = psi.astype(np.complex64)
+    ref = psi.astype(np.complex128)
+    h = qs.qs_create(n, dtype)
+    try:
+        qs.qs_set_amplitudes(h, psi)
+        ez, nrm = qs.qs_expectation_z(h)
+        nrm2 = qs.qs_norm(h)
+    finally:
+        qs.qs_destroy(h)
+    want_n = oracle.norm(ref, n)
+    want_z = oracle.expz(ref, n)
+    assert abs(nrm - want_n) <= 1e-13 * want_n
+    assert nrm2 == nrm
+    assert np.max(np.abs(ez - want_z)) <= 1e-13 * want_n
+
+
+@pytest.mark.parametrize("dtype", [2, 1])
+@pytest.mark.parametrize("n,k", [(4, 16), (10, 1), (10, 37), (14, 1024), (18, 1024), (20, 4096)])
+def test_top_k(qs, n, k, dtype):
+    psi = inputs.gaussian_state(n, seed=200 + n)
+    if dtype == 1:
+        psi = psi.astype(np.complex64)
+    ref = psi.astype(np.complex128)
+    h = qs.qs_create(n, dtype)
+    try:
+        qs.qs_set_amplitudes(h, psi)
+        idx, amp = qs.qs_top_amplitudes(h, k)
+    finally:
+        qs.qs_destroy(h)
+    widx, wamp = oracle.top_k(ref, n, k)
+    # probabilities are computed in FP64 on both sides from identical stored values,
+    # so the selection and the tie order are identical
+    assert np.array_equal(idx, widx)
+    assert np.array_equal(amp, wamp)
+
+
+def test_top_k_ties_uniform(qs):
+    n = 12
+    h = qs.qs_create(n, 2)
+    try:
+        qs.qs_apply_circuit(h, [("h", (q,), ()) for q in range(n)], qs.options(mode=qs.QS_MODE_GATE))
+        idx, amp = qs.qs_top_amplitudes(h, 100)
+    finally:
+        qs.qs_destroy(h)
+    assert list(idx) == list(range(100))   # all equal: lowest indices first
+
+
+def test_invalid_records(qs):
+    h = qs.qs_create(4, 2)
+    try:
+        for bad in [[("cnot", (1, 1), ())], [("h", (4,), ())], [("h", (-1,), ())]]:
+            with pytest.raises(qs.QsError) as e:
+                qs.qs_apply_circuit(h, bad)
+            assert e.value.code == qs.QS_ERR_INVALID
+        with pytest.raises(qs.QsError):
+            qs.qs_amplitudes(h, 10, 10)
+    finally:
+        qs.qs_destroy(h)
+
+
+def test_reset_and_renormalize(qs):
+    n = 9
+    h = qs.qs_create(n, 2)
+    try:
+        psi = inputs.gaussian_state(n, seed=5) * 3.0
+        qs.qs_set_amplitudes(h, psi)
+        old = qs.qs_renormalize(h)
+        assert abs(old - 9.0) < 1e-12
+        assert abs(qs.qs_norm(h) - 1.0) < 1e-14
+        qs.qs_reset(h)
+        got = qs.qs_amplitudes(h)
+        assert got[0] == 1 and np.count_nonzero(got) == 1
+    finally:
+        qs.qs_destroy(h)
