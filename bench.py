@@ -45,7 +45,9 @@ def parse():
     ap.add_argument("--dtype", default="c128", choices=["c128", "c64"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--cpu-sample-gates", type=int, default=3)
+    ap.add_argument("--cpu-sample-gates", type=int, default=2)
+    ap.add_argument("--no-extra", action="store_true",
+                    help="skip the context rows (planned circuits, the other dtype)")
     return ap.parse_args()
 
 
@@ -221,6 +223,9 @@ def run_ours(args, rank, world, local):
     e2e = None
     if not args.no_e2e:
         e2e = run_e2e(qs, h, host_in, recs, opts, n, B, n_gates, world)
+    extra = {}
+    if not args.no_extra:
+        extra["planned"] = time_planned(qs, h, stream, recs, n, B)
     qs.qs_destroy(h)
     del host_in
 
@@ -242,6 +247,30 @@ def run_ours(args, rank, world, local):
     }
     if e2e:
         out["e2e"] = e2e
+    out.update(extra)
+    return out
+
+
+def time_planned(qs, h, stream, recs, n, B):
+    """Context row: each gate type's 30 gates as ONE planned circuit (in-cache chunk
+    passes, QS_MODE_AUTO).  Reports ms per 30 gates, passes, and effective gate GB/s
+    (30 x a full pass of bytes / time: may exceed the roofline, that is what fusion buys)."""
+    import torch
+    out = {}
+    opts = qs.options(mode=qs.QS_MODE_AUTO)
+    for name in GATE_TYPES:
+        qs.qs_apply_circuit(h, recs[name], opts)   # warm-up
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(3):
+            qs.qs_apply_circuit(h, recs[name], opts)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / 3
+        st = qs.qs_last_stats(h)
+        out[name] = {"ms_per_30": round(ms, 3), "passes": int(st["passes"]),
+                     "alg_GBps": round(st["bytes"] / (ms * 1e-3) / 1e9, 1),
+                     "effective_gate_GBps": round(30 * 2 * B * (1 << n) / (ms * 1e-3) / 1e9, 1)}
     return out
 
 

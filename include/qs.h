@@ -162,6 +162,15 @@ int qs_apply_circuit(qs_state *s, const qs_gate *gates, size_t n_gates, const qs
 /* Statistics of the last qs_apply_circuit on s. */
 int qs_last_stats(const qs_state *s, qs_stats *out);
 
+/* Host-only dry run of the chunk planner of QS_MODE_AUTO (Sec. II-B "Qubit Reordering"
+ * and "In-cache Operations"; Sec. III-A tier 4): no GPU is touched.  For an n-qubit state
+ * of dtype dt, writes for each gate the index of the pass that executes it into
+ * pass_of_gate[n_gates]; for each pass p < *n_passes (at most n_gates passes), its local
+ * qubit mask into pass_lmask[p] (0 for a pass run by the streaming kernel).  The caller
+ * allocates both arrays with n_gates entries.  Errors as qs_apply_circuit. */
+int qs_plan(int n_qubits, qs_dtype dt, const qs_gate *gates, size_t n_gates, const qs_options *opt,
+            int32_t *pass_of_gate, uint64_t *pass_lmask, int64_t *n_passes);
+
 /* ---- amplitudes and reductions -------------------------------------------------- */
 
 /* Copies cnt amplitudes [off, off+cnt) from host memory (the state's dtype, interleaved)
@@ -180,6 +189,47 @@ int qs_expectation_z(qs_state *s, double *out, double *norm_out);
 int qs_top_amplitudes(qs_state *s, uint32_t k, uint64_t *idx, double *amp);
 /* Scales the state by 1/sqrt(norm) (norm computed in FP64); returns the old norm. */
 int qs_renormalize(qs_state *s, double *old_norm);
+
+/* ---- batched execution: many small circuits in one persistent launch ------------ */
+
+typedef struct qs_batch qs_batch;  /* opaque */
+
+/* One circuit of a batch: its qubit count and its gate records (copied at creation). */
+typedef struct {
+    int32_t n_qubits;
+    int32_t reserved;
+    const qs_gate *gates;
+    uint64_t n_gates;
+} qs_circuit;
+
+typedef struct {
+    int64_t circuits;
+    int64_t passes;       /* tile passes over all circuits */
+    int64_t work_items;   /* tiles handed out by the persistent kernel per run */
+    int64_t grid;         /* persistent CTAs */
+    uint64_t state_bytes; /* device bytes of all states together */
+} qs_batch_stats;
+
+/* Plans every circuit (gate semantics of Eq. 2 / Eq. 3; passes and fusion as in
+ * qs_apply_circuit, Sec. II-B / III-A), lays all states out in one device arena (every
+ * circuit starts from |0...0>), uploads every table and captures one CUDA graph holding a
+ * single persistent kernel launch.  All circuits share dtype dt.  Options: chunk_m (tile
+ * width), fuse_k (fusion width inside a pass); reserved[0] = wait limit of the kernel's
+ * dependency waits in microseconds (0: 2 s); reserved[1] = 1 is a test hook that makes one
+ * dependency unsatisfiable, so that a run ends with QS_ERR_TIMEOUT instead of hanging.
+ * QS_ERR_UNSUPPORTED for dense blocks wider than 4 qubits. */
+int qs_batch_create(const qs_circuit *circuits, size_t count, qs_dtype dt, const qs_options *opt,
+                    qs_batch **out);
+/* Replays the graph (all circuits from |0...0>) on the batch's stream; asynchronous. */
+int qs_batch_run(qs_batch *b);
+/* Waits for the batch's stream; QS_ERR_TIMEOUT if a bounded device wait gave up. */
+int qs_batch_synchronize(qs_batch *b);
+/* Makes later runs use `stream` (cudaStream_t). */
+int qs_batch_set_stream(qs_batch *b, void *stream);
+/* Copies amplitudes [off, off+cnt) of circuit i (batch dtype, interleaved) to host memory. */
+int qs_batch_amplitudes(qs_batch *b, uint64_t i, uint64_t off, uint64_t cnt, void *host_dst);
+int qs_batch_info(const qs_batch *b, qs_batch_stats *out);
+int qs_batch_destroy(qs_batch *b);
 
 #ifdef __cplusplus
 }

@@ -4,6 +4,7 @@
 #include <cstring>
 #include <mutex>
 
+#include "capi_util.h"
 #include "plan.h"
 #include "qs_internal.h"
 
@@ -16,8 +17,8 @@ struct qs_state {
 
 namespace qs {
 
-namespace {
 thread_local std::string g_last_error;
+namespace {
 std::atomic<uint64_t> g_launches{0};
 }  // namespace
 
@@ -96,6 +97,18 @@ void *upload_params(DeviceState &st, const void *host, size_t bytes) {
     return dst;
 }
 
+// Waits for the state's stream, then reports (and clears) a device-side timeout.
+void sync_and_check(DeviceState &d) {
+    QS_CUDA(cudaStreamSynchronize(d.stream));
+    if (!d.dev_err) return;
+    int e = 0;
+    QS_CUDA(cudaMemcpy(&e, d.dev_err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (e != 0) {
+        QS_CUDA(cudaMemset(d.dev_err, 0, sizeof(int)));
+        fail(e, "a bounded device-side wait gave up (kernel returned early)");
+    }
+}
+
 static size_t amp_bytes(int dtype) { return dtype == QS_C128 ? 16 : 8; }
 
 static void destroy_state(qs_state *s) {
@@ -107,6 +120,7 @@ static void destroy_state(qs_state *s) {
         if (d.arena_ev[c]) cudaEventDestroy(d.arena_ev[c]);
     }
     if (d.scratch) cudaFree(d.scratch);
+    if (d.dev_err) cudaFree(d.dev_err);
     if (s->owns_memory && d.psi) cudaFree(d.psi);
     if (s->owns_stream && d.stream) cudaStreamDestroy(d.stream);
     delete s;
@@ -150,25 +164,6 @@ static void execute(qs_state *s, const std::vector<Op> &ops, const qs_options &o
 }  // namespace qs
 
 using namespace qs;
-
-#define QS_API_BEGIN try {
-#define QS_API_END                                  \
-    }                                               \
-    catch (const qs::Error &e) {                    \
-        qs::g_last_error = e.msg;                   \
-        return e.code;                              \
-    }                                               \
-    catch (const std::bad_alloc &) {                \
-        qs::g_last_error = "host allocation failed"; \
-        return QS_ERR_NOMEM;                        \
-    }                                               \
-    catch (const std::exception &e) {               \
-        qs::g_last_error = e.what();                \
-        return QS_ERR_CUDA;                         \
-    }                                               \
-    qs::g_last_error.clear();                       \
-    return QS_OK;
-
 extern "C" {
 
 const char *qs_last_error(void) { return qs::g_last_error.c_str(); }
@@ -208,6 +203,8 @@ int qs_create(int n_qubits, qs_dtype dt, qs_state **out) {
             s->d.psi = nullptr;
             fail(QS_ERR_NOMEM, "cannot allocate " + std::to_string(bytes) + " bytes of device memory");
         }
+        QS_CUDA(cudaMalloc(&s->d.dev_err, sizeof(int)));
+        QS_CUDA(cudaMemsetAsync(s->d.dev_err, 0, sizeof(int), s->d.stream));
         launch_set_zero_state(s->d);
         QS_CUDA(cudaStreamSynchronize(s->d.stream));
     } catch (...) {
@@ -232,6 +229,13 @@ int qs_create_on(int n_qubits, qs_dtype dt, void *dev_ptr, uint64_t bytes, void 
     s->d.stream = (cudaStream_t)stream;
     s->owns_memory = false;
     s->owns_stream = false;
+    try {
+        QS_CUDA(cudaMalloc(&s->d.dev_err, sizeof(int)));
+        QS_CUDA(cudaMemset(s->d.dev_err, 0, sizeof(int)));
+    } catch (...) {
+        destroy_state(s);
+        throw;
+    }
     *out = s;
     QS_API_END
 }
@@ -256,7 +260,7 @@ int qs_set_stream(qs_state *s, void *stream) {
 int qs_synchronize(qs_state *s) {
     QS_API_BEGIN
     if (!s) fail(QS_ERR_INVALID, "state is NULL");
-    QS_CUDA(cudaStreamSynchronize(s->d.stream));
+    sync_and_check(s->d);
     QS_API_END
 }
 
@@ -296,6 +300,36 @@ int qs_apply_circuit(qs_state *s, const qs_gate *gates, size_t n_gates, const qs
     QS_API_END
 }
 
+int qs_plan(int n_qubits, qs_dtype dt, const qs_gate *gates, size_t n_gates, const qs_options *opt,
+            int32_t *pass_of_gate, uint64_t *pass_lmask, int64_t *n_passes) {
+    QS_API_BEGIN
+    if (n_qubits < 1 || n_qubits > QS_MAX_QUBITS) fail(QS_ERR_INVALID, "n_qubits out of range");
+    if (dt != QS_C64 && dt != QS_C128) fail(QS_ERR_INVALID, "unknown dtype");
+    if (n_gates && (!gates || !pass_of_gate || !pass_lmask)) fail(QS_ERR_INVALID, "NULL argument");
+    if (!n_passes) fail(QS_ERR_INVALID, "NULL argument");
+    qs_options o{};
+    if (opt) o = *opt;
+    std::vector<Op> ops;
+    for (size_t i = 0; i < n_gates; i++) {
+        try {
+            validate_gate(gates[i], n_qubits);
+        } catch (const Error &e) {
+            fail(e.code, "gate " + std::to_string(i) + ": " + e.msg);
+        }
+        ops.push_back(lower_gate(gates[i]));
+    }
+    DeviceState d;
+    d.n = n_qubits;
+    d.dtype = dt;
+    const std::vector<Pass> plan = make_plan(ops, n_qubits, plan_params(d, o));
+    for (size_t p = 0; p < plan.size(); p++) {
+        pass_lmask[p] = plan[p].stream ? 0 : plan[p].lmask;
+        for (int i : plan[p].ops) pass_of_gate[i] = (int32_t)p;
+    }
+    *n_passes = (int64_t)plan.size();
+    QS_API_END
+}
+
 int qs_last_stats(const qs_state *s, qs_stats *out) {
     QS_API_BEGIN
     if (!s || !out) fail(QS_ERR_INVALID, "NULL argument");
@@ -320,6 +354,7 @@ int qs_amplitudes(qs_state *s, uint64_t off, uint64_t cnt, void *host_dst) {
     const uint64_t N = 1ull << s->d.n;
     if (off > N || cnt > N - off) fail(QS_ERR_INVALID, "amplitude range out of bounds");
     const size_t B = amp_bytes(s->d.dtype);
+    sync_and_check(s->d);
     QS_CUDA(cudaMemcpyAsync(host_dst, (const char *)s->d.psi + off * B, cnt * B, cudaMemcpyDeviceToHost, s->d.stream));
     QS_CUDA(cudaStreamSynchronize(s->d.stream));
     QS_API_END

@@ -185,13 +185,27 @@ bool is_diagonal(const Op &op) { return op.kind == K_DIAG1 || op.kind == K_DIAG;
 
 }  // namespace
 
-std::vector<Op> fuse_ops(const std::vector<Op> &ops, int fuse_k) {
+double op_flops(const Op &op) {
+    switch (op.kind) {
+    case K_H: return 4.0;
+    case K_PERM1: case K_SWAP: return 0.0;
+    case K_DIAG1: return op.m[0] == cd(1.0) ? 2.0 : 4.0;
+    case K_DENSE1: return 8.0;
+    case K_CTRL1: return 4.0;
+    case K_DIAG: return 4.0;
+    case K_DENSE: return 4.0 * (double)(1 << op.k);
+    }
+    return 8.0;
+}
+
+std::vector<Op> fuse_ops(const std::vector<Op> &ops, int fuse_k, double sweep_flops) {
     if (fuse_k <= 1) return ops;
     std::vector<Op> out;
     std::vector<int> Q;                  // qubits of the current block, Q[0] most significant
     std::vector<cd> U;                   // its matrix
     std::vector<const Op *> members;     // ops absorbed into the current block
     bool diag = true;
+    double member_flops = 0.0;           // flops/amplitude of the members applied one by one
 
     auto flush = [&]() {
         if (members.empty()) return;
@@ -216,6 +230,7 @@ std::vector<Op> fuse_ops(const std::vector<Op> &ops, int fuse_k) {
         Q.clear();
         U.clear();
         diag = true;
+        member_flops = 0.0;
     };
 
     for (const Op &op : ops) {
@@ -225,7 +240,15 @@ std::vector<Op> fuse_ops(const std::vector<Op> &ops, int fuse_k) {
             for (int x : nQ) have |= x == op.q[j];
             if (!have) nQ.push_back(op.q[j]);
         }
-        if ((int)nQ.size() > fuse_k) {
+        bool fits = (int)nQ.size() <= fuse_k;
+        if (fits && !members.empty() && sweep_flops >= 0.0) {
+            // cost gate: the fused block may not cost more flops per amplitude than its
+            // members one by one plus the saved shared-memory sweep
+            const bool ndiag = diag && is_diagonal(op);
+            const double fused = ndiag ? 4.0 : 4.0 * (double)(1 << nQ.size());
+            fits = fused <= member_flops + op_flops(op) + sweep_flops;
+        }
+        if (!fits) {
             flush();
             nQ.assign(op.q, op.q + op.k);
         }
@@ -254,6 +277,7 @@ std::vector<Op> fuse_ops(const std::vector<Op> &ops, int fuse_k) {
         Q = nQ;
         U = std::move(newU);
         members.push_back(&op);
+        member_flops += op_flops(op);
         diag = diag && is_diagonal(op);
     }
     flush();

@@ -1,0 +1,129 @@
+// K2: in-shared-memory chunk pass ("in-cache operations", QueenV2 Sec. II-B; the
+// block-by-block all-in-cache module, Sec. III-B).
+//
+// A pass owns a set L of m "local" qubits: bits 0..c0-1 (contiguous runs of 2^c0
+// amplitudes in HBM) plus m - c0 higher bits chosen by the planner.  Every CTA takes
+// tiles t in [0, 2^(n-m)): the tile is the 2^m amplitudes whose non-local bits spell t
+// (the non-local bits are deposited from t, the local ones from the in-tile index, the
+// PDEP/PEXT-style addressing of Sec. III-B).  The tile is staged into shared memory by
+// TMA bulk copies (cp.async.bulk, one per contiguous run, completion on an mbarrier),
+// every op of the pass is applied on tile-local bit positions (Eq. 2 / Eq. 3 groups),
+// and the tile is written back once by TMA bulk stores.  One full HBM read + write per
+// pass, however many ops it holds.
+#include <algorithm>
+
+#include "chunk.h"
+#include "kops.cuh"
+#include "ptx.cuh"
+#include "tile_ops.cuh"
+
+namespace qs {
+namespace {
+
+constexpr int kChunkThreads = 256;
+constexpr long long kWaitLimit = 1ll << 26;  // bounded mbarrier spin (seconds, never hit)
+
+template <typename T>
+__global__ void __launch_bounds__(kChunkThreads)
+k_chunk(typename C2T<T>::type *__restrict__ psi, const ChunkArgs a, const KOp *__restrict__ ops,
+        const T *__restrict__ mats, int *__restrict__ err) {
+    using V = typename C2T<T>::type;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    V *tile = (V *)smem_raw;
+    __shared__ uint64_t bar;
+    __shared__ int abort_flag;
+    __shared__ KOp s_op;
+    __shared__ T s_m[kMaxOpReals];
+    const uint32_t nruns = 1u << (a.m - a.c0);
+    const uint32_t run_bytes = (uint32_t)sizeof(V) << a.c0;
+    const uint32_t tile_bytes = (uint32_t)sizeof(V) << a.m;
+    if (threadIdx.x == 0) {
+        ptx::mbar_init(&bar, 1);
+        ptx::fence_mbar_init();
+        abort_flag = 0;
+    }
+    __syncthreads();
+    uint32_t phase = 0;
+    for (uint64_t t = blockIdx.x; t < a.n_tiles; t += gridDim.x) {
+        uint64_t base = t << a.c0;
+        for (int j = 0; j < a.nlh; j++) {
+            const int b = a.lhigh[j];
+            base = ((base >> b) << (b + 1)) | (base & ((1ull << b) - 1ull));
+        }
+        if (threadIdx.x == 0) ptx::mbar_arrive_expect_tx(&bar, tile_bytes);
+        __syncthreads();
+        for (uint32_t r = threadIdx.x; r < nruns; r += blockDim.x) {
+            uint64_t off = 0;
+            for (int j = 0; j < a.nlh; j++) off |= (uint64_t)((r >> j) & 1u) << a.lhigh[j];
+            ptx::bulk_g2s(tile + ((uint64_t)r << a.c0), psi + (base | off), run_bytes, &bar);
+        }
+        long long spins = 0;
+        while (!ptx::mbar_try_wait(&bar, phase)) {
+            if (++spins > kWaitLimit) {
+                abort_flag = 1;
+                break;
+            }
+        }
+        phase ^= 1u;
+        __syncthreads();
+        if (abort_flag) {
+            if (threadIdx.x == 0) atomicExch(err, QS_ERR_TIMEOUT);
+            break;
+        }
+        apply_ops_tile<T>(tile, ops, a.n_ops, mats, a.m, s_op, s_m);
+        ptx::fence_proxy_async_smem();
+        __syncthreads();
+        for (uint32_t r = threadIdx.x; r < nruns; r += blockDim.x) {
+            uint64_t off = 0;
+            for (int j = 0; j < a.nlh; j++) off |= (uint64_t)((r >> j) & 1u) << a.lhigh[j];
+            ptx::bulk_s2g(psi + (base | off), tile + ((uint64_t)r << a.c0), run_bytes);
+        }
+        ptx::bulk_commit();
+        ptx::bulk_wait_read_all();
+        __syncthreads();
+    }
+    ptx::bulk_wait_all();
+}
+
+template <typename T>
+void launch_t(DeviceState &st, const ChunkArgs &a, const std::vector<KOp> &kops, const std::vector<double> &mats) {
+    std::vector<T> tm(std::max<size_t>(mats.size(), 2));
+    for (size_t i = 0; i < mats.size(); i++) tm[i] = (T)mats[i];
+    const KOp *d_ops = (const KOp *)upload_params(st, kops.data(), kops.size() * sizeof(KOp));
+    const T *d_m = (const T *)upload_params(st, tm.data(), tm.size() * sizeof(T));
+    using V = typename C2T<T>::type;
+    const size_t smem = sizeof(V) << a.m;
+    auto kern = k_chunk<T>;
+    static bool attr_set[2] = {false, false};
+    if (!attr_set[sizeof(T) == 8]) {
+        QS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+        attr_set[sizeof(T) == 8] = true;
+    }
+    const int grid = persistent_grid((const void *)kern, kChunkThreads, smem, a.n_tiles);
+    kern<<<grid, kChunkThreads, smem, st.stream>>>((V *)st.psi, a, d_ops, d_m, st.dev_err);
+    QS_CUDA(cudaGetLastError());
+    count_launch();
+}
+
+}  // namespace
+
+void launch_chunk_pass(DeviceState &st, uint64_t lmask, const std::vector<KOp> &kops,
+                       const std::vector<double> &mats) {
+    ChunkArgs a{};
+    const int n = st.n;
+    a.m = __builtin_popcountll(lmask);
+    a.c0 = 0;
+    while (a.c0 < n && ((lmask >> a.c0) & 1ull)) a.c0++;
+    a.nlh = 0;
+    for (int b = a.c0; b < n; b++)
+        if ((lmask >> b) & 1ull) a.lhigh[a.nlh++] = b;
+    a.n_tiles = 1ull << (n - a.m);
+    a.n_ops = (int)kops.size();
+    const size_t B = st.dtype == QS_C128 ? 16 : 8;
+    if ((B << a.c0) % 16 != 0) fail(QS_ERR_INVALID, "chunk runs must be multiples of 16 bytes");
+    if ((B << a.m) > 200 * 1024) fail(QS_ERR_INVALID, "chunk tile exceeds shared memory");
+    if (st.dtype == QS_C128) launch_t<double>(st, a, kops, mats);
+    else launch_t<float>(st, a, kops, mats);
+}
+
+}  // namespace qs

@@ -1,0 +1,143 @@
+// Kernel-side form of one operation ("KOp") and the functors that apply it to the
+// touched amplitudes of one group.  Shared by the streaming kernel (K1, groups over the
+// whole state in HBM) and the chunk kernel (K2, groups over a tile in shared memory).
+//
+// Group structure (Eq. 2 / Eq. 3 of QueenV2, generalised): every group is one base index
+// with the nf fixed bits fb[] cleared and the set_mask bits forced to one; the op reads
+// and writes the nt elements at base | off[t].  Structure-specific kinds avoid touching
+// amplitudes a gate leaves unchanged (controls, phases) and avoid arithmetic for
+// permutations.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+namespace qs {
+
+enum FKind : int32_t {
+    F_H = 0,     // (a+b, a-b)/sqrt2, nt = 2
+    F_SWAP,      // exchange two elements, nt = 2
+    F_DENSE1,    // 2x2 matrix, nt = 2 (m: 8 reals)
+    F_DIAG1,     // diag(d0, d1), nt = 2 (m: 4 reals)
+    F_PHASE,     // one element times e^{i a}, nt = 1 (m: 2 reals)
+    F_NEG,       // one element times -1, nt = 1
+    F_DIAG2,     // four phases, nt = 4 (m: 8 reals)
+    F_DENSE2,    // 4x4 matrix, nt = 4 (m: 32 reals)
+    F_DIAGK,     // diagonal on k qubits at positions pos[] (m: 2^(k+1) reals), every element
+    F_DENSEK,    // dense 2^k x 2^k on positions pos[] (m: 2^(2k+1) reals), k = 3..6
+};
+
+// Host+device description of one op in a given index space (HBM amplitude/element
+// indices for K1, tile-local indices for K2).
+struct KOp {
+    int32_t fkind;
+    int32_t nf;         // fixed bits (F_H..F_DENSE2)
+    int32_t fb[3];      // fixed bits ascending
+    int32_t nt;         // touched elements per group
+    uint64_t set_mask;  // forced-one bits
+    uint64_t off[4];    // touched element offsets
+    int32_t k;          // operand count (F_DIAGK / F_DENSEK)
+    int32_t pos[8];     // operand positions, first = most significant (F_DIAGK / F_DENSEK)
+    int32_t mat;        // offset of the op's reals in the parameter array
+    int32_t nmat;       // number of reals
+};
+
+#ifdef __CUDACC__
+
+template <typename T> struct C2T;
+template <> struct C2T<double> { using type = double2; };
+template <> struct C2T<float> { using type = float2; };
+
+template <typename T, int L> struct Amp { T r[L], i[L]; };
+
+// y = m0 * x0 + m1 * x1 (complex), 8 real multiply-adds.
+template <typename T>
+__device__ __forceinline__ void cdot2(T &yr, T &yi, T m0r, T m0i, T x0r, T x0i, T m1r, T m1i,
+                                      T x1r, T x1i) {
+    yr = m0r * x0r;
+    yr = fma(-m0i, x0i, yr);
+    yr = fma(m1r, x1r, yr);
+    yr = fma(-m1i, x1i, yr);
+    yi = m0r * x0i;
+    yi = fma(m0i, x0r, yi);
+    yi = fma(m1r, x1i, yi);
+    yi = fma(m1i, x1r, yi);
+}
+
+template <typename T, int L>
+__device__ __forceinline__ void f_h(Amp<T, L> *v, T r) {
+#pragma unroll
+    for (int l = 0; l < L; l++) {
+        const T ar = v[0].r[l], ai = v[0].i[l], br = v[1].r[l], bi = v[1].i[l];
+        v[0].r[l] = (ar + br) * r; v[0].i[l] = (ai + bi) * r;
+        v[1].r[l] = (ar - br) * r; v[1].i[l] = (ai - bi) * r;
+    }
+}
+template <typename T, int L>
+__device__ __forceinline__ void f_swap(Amp<T, L> *v) {
+    const Amp<T, L> t = v[0];
+    v[0] = v[1];
+    v[1] = t;
+}
+template <typename T, int L>
+__device__ __forceinline__ void f_dense1(Amp<T, L> *v, const T *m) {
+#pragma unroll
+    for (int l = 0; l < L; l++) {
+        const T ar = v[0].r[l], ai = v[0].i[l], br = v[1].r[l], bi = v[1].i[l];
+        cdot2(v[0].r[l], v[0].i[l], m[0], m[1], ar, ai, m[2], m[3], br, bi);
+        cdot2(v[1].r[l], v[1].i[l], m[4], m[5], ar, ai, m[6], m[7], br, bi);
+    }
+}
+template <typename T, int L, int NT>
+__device__ __forceinline__ void f_diag(Amp<T, L> *v, const T *d) {
+#pragma unroll
+    for (int t = 0; t < NT; t++)
+#pragma unroll
+        for (int l = 0; l < L; l++) {
+            const T xr = v[t].r[l], xi = v[t].i[l];
+            v[t].r[l] = fma(d[2 * t], xr, -d[2 * t + 1] * xi);
+            v[t].i[l] = fma(d[2 * t], xi, d[2 * t + 1] * xr);
+        }
+}
+template <typename T, int L>
+__device__ __forceinline__ void f_neg(Amp<T, L> *v) {
+#pragma unroll
+    for (int l = 0; l < L; l++) {
+        v[0].r[l] = -v[0].r[l];
+        v[0].i[l] = -v[0].i[l];
+    }
+}
+template <typename T, int L>
+__device__ __forceinline__ void f_dense2(Amp<T, L> *v, const T *m) {
+#pragma unroll
+    for (int l = 0; l < L; l++) {
+        T xr[4], xi[4];
+#pragma unroll
+        for (int t = 0; t < 4; t++) { xr[t] = v[t].r[l]; xi[t] = v[t].i[l]; }
+#pragma unroll
+        for (int r = 0; r < 4; r++) {
+            T yr, yi, zr, zi;
+            cdot2(yr, yi, m[8 * r + 0], m[8 * r + 1], xr[0], xi[0], m[8 * r + 2], m[8 * r + 3], xr[1], xi[1]);
+            cdot2(zr, zi, m[8 * r + 4], m[8 * r + 5], xr[2], xi[2], m[8 * r + 6], m[8 * r + 7], xr[3], xi[3]);
+            v[r].r[l] = yr + zr;
+            v[r].i[l] = yi + zi;
+        }
+    }
+}
+
+// Inserts a zero bit at each of the nf sorted positions fb[] of x (runtime nf <= 3).
+__device__ __forceinline__ uint64_t insert_zero_bits(uint64_t x, int nf, const int32_t *fb) {
+#pragma unroll
+    for (int j = 0; j < 3; j++) {
+        if (j < nf) {
+            const int b = fb[j];
+            x = ((x >> b) << (b + 1)) | (x & ((1ull << b) - 1ull));
+        }
+    }
+    return x;
+}
+
+#endif  // __CUDACC__
+
+}  // namespace qs

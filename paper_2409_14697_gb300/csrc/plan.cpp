@@ -1,15 +1,147 @@
+// Chunk planner and executor (QueenV2 Sec. II-B "Qubit Reordering" and "In-cache
+// Operations"; Sec. III-A tiers 4-5 "In-Rank" gate blocks and general fusion).
+//
+// The planner partitions the op sequence into passes.  A pass owns a set L of m local
+// qubits that always contains the low c qubits (so every tile is made of contiguous
+// runs of 2^c amplitudes in HBM) plus high qubits claimed greedily, in circuit order,
+// by the ops it accepts.  An op joins the pass if none of its qubits is blocked by an
+// earlier op left for a later pass and its qubits fit in L; otherwise its qubits become
+// blocked (ops on disjoint qubits commute, so later ops on other qubits may still join).
+// Qubit reordering is logical: the pass's local qubits are mapped to tile positions by
+// a position table (the bidirectional qubit table of Sec. III-A) and the state is never
+// permuted in memory.  Inside a pass, consecutive ops are fused into dense blocks of at
+// most fuse_k qubits (FP64 host products) before the kernel applies them in shared
+// memory.  A pass holding a single op runs on the streaming kernel instead, which
+// touches only the amplitudes that op changes.
+#include <algorithm>
+
+#include "chunk.h"
+#include "kgeom.h"
 #include "plan.h"
 
 namespace qs {
 
-void run_planned(DeviceState &st, const std::vector<Op> &ops, const qs_options &o, qs_stats &stats) {
-    (void)o;
-    for (const Op &op : ops) {
-        launch_stream_op(st, op);
-        stats.passes++;
-        stats.bytes += stream_bytes(op, st.n, st.dtype);
+namespace {
+
+// Ops the shared-memory path applies: dense blocks up to 4 qubits (512 matrix reals)
+// and diagonals up to 8 qubits.
+bool chunkable(const Op &op) {
+    if (op.kind == K_DENSE) return op.k <= 4;
+    if (op.kind == K_DIAG) return op.k <= 8;
+    return true;
+}
+
+}  // namespace
+
+PlanParams plan_params(const DeviceState &st, const qs_options &o) {
+    PlanParams p;
+    const bool c128 = st.dtype == QS_C128;
+    p.m = o.chunk_m > 0 ? o.chunk_m : (c128 ? 12 : 13);
+    p.c = c128 ? 4 : 5;                  // runs of 256 bytes
+    // the shared-memory dense path applies blocks of at most 4 qubits
+    p.fuse_k = std::min(o.fuse_k > 0 ? o.fuse_k : 2, 4);
+    p.m = std::min(p.m, st.n);
+    p.c = std::min(p.c, p.m);
+    // FP64 is 1/72 of FP32 on GB300: for complex128 a fused block must not add flops;
+    // complex64 arithmetic is cheap next to a shared-memory sweep of the tile
+    p.sweep_flops = c128 ? 1.0 : 24.0;
+    return p;
+}
+
+std::vector<Pass> make_plan(const std::vector<Op> &ops, int n, const PlanParams &pp) {
+    std::vector<Pass> plan;
+    const uint64_t all = (n >= 64) ? ~0ull : ((1ull << n) - 1ull);
+    const uint64_t low = (1ull << pp.c) - 1ull;
+    std::vector<char> done(ops.size(), 0);
+    size_t first = 0;
+    while (first < ops.size()) {
+        while (first < ops.size() && done[first]) first++;
+        if (first >= ops.size()) break;
+        Pass pass;
+        uint64_t L = low, blocked = 0;
+        for (size_t i = first; i < ops.size(); i++) {
+            if (done[i]) continue;
+            const Op &op = ops[i];
+            const uint64_t qm = op.qmask();
+            if (!chunkable(op)) {
+                if (pass.ops.empty() && !(qm & blocked)) {
+                    pass.stream = true;
+                    pass.ops.push_back((int)i);
+                    done[i] = 1;
+                }
+                break;  // a non-chunkable op is a barrier for this pass
+            }
+            if (qm & blocked) {
+                blocked |= qm;
+            } else if (__builtin_popcountll(L | qm) <= pp.m) {
+                L |= qm;
+                pass.ops.push_back((int)i);
+                done[i] = 1;
+            } else {
+                blocked |= qm;
+            }
+            if ((blocked & all) == all) break;
+        }
+        if (pass.ops.empty()) {
+            // nothing fits next to the always-local low qubits (tiny m): stream the op
+            pass.stream = true;
+            pass.ops.push_back((int)first);
+            done[first] = 1;
+        }
+        if (!pass.stream) {
+            // pad with the lowest free qubits (longer contiguous runs)
+            for (int b = 0; b < n && __builtin_popcountll(L) < pp.m; b++) L |= 1ull << b;
+            pass.lmask = L & all;
+            if (pass.ops.size() == 1) pass.stream = true;
+        }
+        plan.push_back(std::move(pass));
     }
-    stats.ops_after_fuse = (int64_t)ops.size();
+    return plan;
+}
+
+void run_planned(DeviceState &st, const std::vector<Op> &ops, const qs_options &o, qs_stats &stats) {
+    const int n = st.n;
+    const PlanParams pp = plan_params(st, o);
+    const double B = st.dtype == QS_C128 ? 16.0 : 8.0;
+    // tiny states (no 128-byte runs): plain gate by gate
+    if (n < pp.c + 1 || (B * (double)(1ull << pp.c)) < 128.0) {
+        for (const Op &op : ops) {
+            launch_stream_op(st, op);
+            stats.passes++;
+            stats.bytes += stream_bytes(op, n, st.dtype);
+        }
+        stats.ops_after_fuse = (int64_t)ops.size();
+        return;
+    }
+    const std::vector<Pass> plan = make_plan(ops, n, pp);
+    int64_t n_ops = 0;
+    for (const Pass &p : plan) {
+        if (p.stream) {
+            for (int i : p.ops) {
+                launch_stream_op(st, ops[i]);
+                stats.bytes += stream_bytes(ops[i], n, st.dtype);
+                n_ops++;
+            }
+            stats.passes++;
+            continue;
+        }
+        std::vector<Op> pops;
+        pops.reserve(p.ops.size());
+        for (int i : p.ops) pops.push_back(ops[i]);
+        const std::vector<Op> fused = fuse_ops(pops, pp.fuse_k, pp.sweep_flops);
+        int pos[64] = {0};
+        int r = 0;
+        for (int b = 0; b < n; b++)
+            if ((p.lmask >> b) & 1ull) pos[b] = r++;
+        std::vector<KOp> kops;
+        std::vector<double> mats;
+        for (const Op &op : fused) kops.push_back(make_kop(op, pos, mats));
+        launch_chunk_pass(st, p.lmask, kops, mats);
+        stats.passes++;
+        stats.bytes += 2.0 * B * (double)(1ull << n);
+        n_ops += (int64_t)fused.size();
+    }
+    stats.ops_after_fuse = n_ops;
 }
 
 }  // namespace qs

@@ -1,10 +1,27 @@
-// Chunk planner + in-cache executor (Sec. II-B "Qubit Reordering", "In-cache Operations";
-// Sec. III-A tiers 4-5; Sec. III-B).
+// Chunk planner + in-cache executor (QueenV2 Sec. II-B "Qubit Reordering", "In-cache
+// Operations"; Sec. III-A tiers 4-5; Sec. III-B).
 #pragma once
+
 #include "qs_internal.h"
 
 namespace qs {
 
+struct PlanParams {
+    int m;       // local qubits per chunk pass
+    int c;       // low qubits always local (contiguous runs of 2^c amplitudes)
+    int fuse_k;  // fusion width inside a pass
+    double sweep_flops;  // fusion cost gate (see fuse_ops)
+};
+
+struct Pass {
+    bool stream = false;    // run the ops with the streaming kernel (one launch each)
+    uint64_t lmask = 0;     // local qubits of a chunk pass
+    std::vector<int> ops;   // indices into the op list, in order
+};
+
+PlanParams plan_params(const DeviceState &st, const qs_options &o);
+// Greedy dependency-respecting partition of ops into passes.
+std::vector<Pass> make_plan(const std::vector<Op> &ops, int n, const PlanParams &pp);
 // Plans `ops` into passes and launches them on st.stream, filling stats.
 void run_planned(DeviceState &st, const std::vector<Op> &ops, const qs_options &o, qs_stats &stats);
 

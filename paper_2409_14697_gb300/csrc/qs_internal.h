@@ -64,8 +64,14 @@ void validate_gate(const qs_gate &g, int n);
 Op lower_gate(const qs_gate &g);
 
 // Gate fusion (Sec. II-B "Gate Fusion", Sec. III-A tier 5): greedily merges runs of
-// consecutive ops into dense blocks on at most fuse_k qubits.  FP64 host products.
-std::vector<Op> fuse_ops(const std::vector<Op> &ops, int fuse_k);
+// consecutive ops into dense (or, if every member is diagonal, diagonal) blocks on at most
+// fuse_k qubits.  FP64 host products.  The paper leaves the merge decision to a cost
+// function; here, with sweep_flops >= 0, a merge is taken only if the fused block costs at
+// most the flops per amplitude of its members applied one by one plus sweep_flops (the
+// value of one saved pass over the tile).  sweep_flops < 0 merges whenever the width fits.
+std::vector<Op> fuse_ops(const std::vector<Op> &ops, int fuse_k, double sweep_flops = -1.0);
+// Real flops per amplitude of applying op alone (structure-aware).
+double op_flops(const Op &op);
 
 // ---------------------------------------------------------------------------------
 // Device-side geometry of a streaming application: each group is one base index with
@@ -96,6 +102,8 @@ struct DeviceState {
     size_t arena_used = 0;
     int arena_cur = 0;
     cudaEvent_t arena_ev[2] = {nullptr, nullptr};
+    // device error word written by bounded waits (QS_ERR_TIMEOUT), checked on sync
+    int *dev_err = nullptr;
 };
 
 // Launchers (kernels live in the .cu files).  All are asynchronous on st.stream.
@@ -109,9 +117,16 @@ void top_k(DeviceState &st, uint32_t k, uint64_t *idx, double *amp);
 // Algorithmic bytes of one streaming application of op on an n-qubit state.
 double stream_bytes(const Op &op, int n, int dtype);
 
+// Persistent grid: SMs x resident blocks of kernel fn at this block size / smem, capped
+// by the number of work blocks.
+int persistent_grid(const void *fn, int threads, size_t smem, uint64_t work_blocks);
+
 // Copies `bytes` of host data into the state's device parameter arena (asynchronously,
 // ordered on st.stream before any later launch) and returns the device address.
 void *upload_params(DeviceState &st, const void *host, size_t bytes);
+
+// Waits for st.stream and raises QS_ERR_TIMEOUT if a kernel's bounded wait gave up.
+void sync_and_check(DeviceState &st);
 
 // Scratch helper: makes sure st.scratch holds at least `bytes`.
 void ensure_scratch(DeviceState &st, size_t bytes);

@@ -51,6 +51,16 @@ class qs_stats(ctypes.Structure):
                 ("passes", ctypes.c_int64), ("launches", ctypes.c_int64), ("bytes", ctypes.c_double)]
 
 
+class qs_circuit(ctypes.Structure):
+    _fields_ = [("n_qubits", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("gates", ctypes.POINTER(qs_gate)), ("n_gates", ctypes.c_uint64)]
+
+
+class qs_batch_stats(ctypes.Structure):
+    _fields_ = [("circuits", ctypes.c_int64), ("passes", ctypes.c_int64), ("work_items", ctypes.c_int64),
+                ("grid", ctypes.c_int64), ("state_bytes", ctypes.c_uint64)]
+
+
 _lib = None
 _VP = ctypes.c_void_p
 _DP = ctypes.POINTER(ctypes.c_double)
@@ -70,12 +80,23 @@ _SIGS = {
     "qs_info": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(_VP)]),
     "qs_apply_circuit": (ctypes.c_int, [_VP, ctypes.POINTER(qs_gate), ctypes.c_size_t, ctypes.POINTER(qs_options)]),
     "qs_last_stats": (ctypes.c_int, [_VP, ctypes.POINTER(qs_stats)]),
+    "qs_plan": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.POINTER(qs_gate), ctypes.c_size_t,
+                               ctypes.POINTER(qs_options), ctypes.POINTER(ctypes.c_int32), _U64P,
+                               ctypes.POINTER(ctypes.c_int64)]),
     "qs_set_amplitudes": (ctypes.c_int, [_VP, ctypes.c_uint64, ctypes.c_uint64, _VP]),
     "qs_amplitudes": (ctypes.c_int, [_VP, ctypes.c_uint64, ctypes.c_uint64, _VP]),
     "qs_norm": (ctypes.c_int, [_VP, _DP]),
     "qs_expectation_z": (ctypes.c_int, [_VP, _DP, _DP]),
     "qs_top_amplitudes": (ctypes.c_int, [_VP, ctypes.c_uint32, _U64P, _DP]),
     "qs_renormalize": (ctypes.c_int, [_VP, _DP]),
+    "qs_batch_create": (ctypes.c_int, [ctypes.POINTER(qs_circuit), ctypes.c_size_t, ctypes.c_int,
+                                       ctypes.POINTER(qs_options), ctypes.POINTER(_VP)]),
+    "qs_batch_run": (ctypes.c_int, [_VP]),
+    "qs_batch_synchronize": (ctypes.c_int, [_VP]),
+    "qs_batch_set_stream": (ctypes.c_int, [_VP, _VP]),
+    "qs_batch_amplitudes": (ctypes.c_int, [_VP, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint64, _VP]),
+    "qs_batch_info": (ctypes.c_int, [_VP, ctypes.POINTER(qs_batch_stats)]),
+    "qs_batch_destroy": (ctypes.c_int, [_VP]),
 }
 
 
@@ -191,6 +212,20 @@ def qs_last_stats(h) -> dict:
     return {f: getattr(s, f) for f, _ in qs_stats._fields_}
 
 
+def qs_plan(n_qubits: int, dtype: int, gates, opts=None):
+    """Host-only planner dry run: (pass index per gate, local-qubit mask per pass)."""
+    recs = gates if isinstance(gates, ctypes.Array) else gate_records(gates)
+    ng = len(gates)
+    pog = np.zeros(max(ng, 1), dtype=np.int32)
+    lm = np.zeros(max(ng, 1), dtype=np.uint64)
+    npass = ctypes.c_int64()
+    o = opts if opts is not None else options()
+    _check(load().qs_plan(n_qubits, dtype, recs, ng, ctypes.byref(o),
+                          pog.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), lm.ctypes.data_as(_U64P),
+                          ctypes.byref(npass)))
+    return pog[:ng], lm[:npass.value]
+
+
 def _np_dtype(h):
     return np.complex128 if qs_info(h)[1] == QS_C128 else np.complex64
 
@@ -242,6 +277,52 @@ def qs_renormalize(h) -> float:
     v = ctypes.c_double()
     _check(load().qs_renormalize(h, ctypes.byref(v)))
     return v.value
+
+
+# ---- batched execution ----------------------------------------------------------
+
+def qs_batch_create(circuits, dtype: int = QS_C64, opts=None):
+    """circuits: list of (n_qubits, gates).  Returns an opaque batch handle."""
+    arr = (qs_circuit * len(circuits))()
+    keep = []
+    for i, (n, gates) in enumerate(circuits):
+        recs = gate_records(gates)
+        keep.append(recs)
+        arr[i].n_qubits = n
+        arr[i].gates = ctypes.cast(recs, ctypes.POINTER(qs_gate))
+        arr[i].n_gates = len(gates)
+    h = _VP()
+    o = opts if opts is not None else options()
+    _check(load().qs_batch_create(arr, len(circuits), dtype, ctypes.byref(o), ctypes.byref(h)))
+    return h
+
+
+def qs_batch_run(b):
+    _check(load().qs_batch_run(b))
+
+
+def qs_batch_synchronize(b):
+    _check(load().qs_batch_synchronize(b))
+
+
+def qs_batch_set_stream(b, stream: int):
+    _check(load().qs_batch_set_stream(b, stream))
+
+
+def qs_batch_amplitudes(b, i: int, n: int, dtype: int = QS_C64):
+    out = np.empty(1 << n, dtype=np.complex64 if dtype == QS_C64 else np.complex128)
+    _check(load().qs_batch_amplitudes(b, i, 0, out.size, out.ctypes.data))
+    return out
+
+
+def qs_batch_info(b) -> dict:
+    s = qs_batch_stats()
+    _check(load().qs_batch_info(b, ctypes.byref(s)))
+    return {f: getattr(s, f) for f, _ in qs_batch_stats._fields_}
+
+
+def qs_batch_destroy(b):
+    _check(load().qs_batch_destroy(b))
 
 
 class State:

@@ -1,0 +1,136 @@
+"""GPU parity of the planned in-cache path (chunk kernel, TMA-staged tiles) against
+the FP64 oracle, and kernel-selection equivalence at sizes beyond the oracle's reach."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2409_14697_gb300 import inputs
+from tests.gpu_util import TOL_C128, TOL_C64, fidelity_gap, require_gpu
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def qs():
+    require_gpu()
+    from paper_2409_14697_gb300 import qs as q
+    q.load()
+    return q
+
+
+def run_gpu(qs, n, dtype, psi0, gates, mode, **kw):
+    h = qs.qs_create(n, dtype)
+    try:
+        if psi0 is not None:
+            qs.qs_set_amplitudes(h, psi0)
+        qs.qs_apply_circuit(h, gates, qs.options(mode=mode, **kw))
+        stats = qs.qs_last_stats(h)
+        return qs.qs_amplitudes(h).astype(np.complex128), stats
+    finally:
+        qs.qs_destroy(h)
+
+
+def tol(dtype):
+    return TOL_C128 if dtype == 2 else TOL_C64
+
+
+@pytest.mark.parametrize("dtype", [2, 1])
+@pytest.mark.parametrize("n,m", [(5, 0), (8, 6), (12, 0), (14, 8), (16, 10), (17, 0), (20, 12)])
+def test_random_circuits_chunked(qs, n, m, dtype):
+    gates = inputs.random_circuit(n, 200, seed=n + m) + inputs.brickwork(n, 6, seed=n)
+    psi0 = inputs.gaussian_state(n, seed=n)
+    want = oracle.run(psi0.copy(), n, gates)
+    if dtype == 1:
+        psi0 = psi0.astype(np.complex64)
+    got, st = run_gpu(qs, n, dtype, psi0, gates, qs.QS_MODE_AUTO, chunk_m=m)
+    assert np.max(np.abs(got - want)) <= tol(dtype)
+    assert st["passes"] <= len(gates)
+
+
+@pytest.mark.parametrize("dtype", [2, 1])
+@pytest.mark.parametrize("fk", [1, 2, 3, 4])
+def test_fusion_inside_passes(qs, dtype, fk):
+    n = 16
+    gates = inputs.brickwork(n, 8, seed=5) + inputs.random_circuit(n, 60, seed=fk)
+    psi0 = inputs.gaussian_state(n, seed=6)
+    want = oracle.run(psi0.copy(), n, gates)
+    if dtype == 1:
+        psi0 = psi0.astype(np.complex64)
+    got, _ = run_gpu(qs, n, dtype, psi0, gates, qs.QS_MODE_AUTO, fuse_k=fk, chunk_m=9)
+    assert np.max(np.abs(got - want)) <= tol(dtype)
+
+
+@pytest.mark.parametrize("dtype", [2, 1])
+def test_dense_user_blocks_in_passes(qs, dtype):
+    n = 15
+    gates = []
+    for i, k in enumerate([1, 2, 3, 4, 5, 6, 3, 4]):
+        r = np.random.default_rng(i)
+        qubits = tuple(int(x) for x in r.choice(n, size=k, replace=False))
+        gates.append(("dense", qubits, inputs.random_unitary(k, seed=i)))
+        gates += inputs.random_circuit(n, 10, seed=100 + i)
+    psi0 = inputs.gaussian_state(n, seed=8)
+    want = oracle.run(psi0.copy(), n, gates)
+    if dtype == 1:
+        psi0 = psi0.astype(np.complex64)
+    got, _ = run_gpu(qs, n, dtype, psi0, gates, qs.QS_MODE_AUTO, chunk_m=10)
+    assert np.max(np.abs(got - want)) <= tol(dtype)
+
+
+@pytest.mark.parametrize("dtype", [2, 1])
+@pytest.mark.parametrize("family", ["qaoa", "tfim", "qft", "ghz"])
+def test_circuit_families(qs, dtype, family):
+    n = 18
+    if family == "qaoa":
+        gates = inputs.qaoa_3regular(n, p=4, seed=1)
+    elif family == "tfim":
+        gates = inputs.tfim(n, steps=20, dt=0.05)
+    elif family == "qft":
+        gates = inputs.qft(n)
+    else:
+        gates = [("h", (0,), ())] + [("cnot", (q, q + 1), ()) for q in range(n - 1)]
+    want = oracle.run(oracle.zero_state(n), n, gates)
+    psi0 = oracle.zero_state(n).astype(np.complex64 if dtype == 1 else np.complex128)
+    got, st = run_gpu(qs, n, dtype, psi0, gates, qs.QS_MODE_AUTO)
+    assert np.max(np.abs(got - want)) <= tol(dtype)
+    if dtype == 1:
+        assert fidelity_gap(got, want) <= 1e-6
+
+
+@pytest.mark.parametrize("dtype", [2, 1])
+def test_config1_brickwork_12q_auto(qs, dtype):
+    """The 12-qubit workload: one tile holds the whole state, one pass for 350 gates."""
+    n = 12
+    gates = inputs.brickwork(n, 20, seed=1)
+    want = oracle.run(oracle.zero_state(n), n, gates)
+    psi0 = oracle.zero_state(n).astype(np.complex64 if dtype == 1 else np.complex128)
+    got, st = run_gpu(qs, n, dtype, psi0, gates, qs.QS_MODE_AUTO)
+    assert np.max(np.abs(got - want)) <= tol(dtype)
+    assert st["passes"] == 1
+
+
+@pytest.mark.parametrize("dtype", [2, 1])
+def test_mode_equivalence_24q(qs, dtype):
+    """GATE, AUTO and FUSED agree at 24 qubits on a brickwork + sweep circuit."""
+    n = 24
+    gates = inputs.brickwork(n, 6, seed=2) + inputs.sweep_all(n, seed=3, count=n)
+    psi0 = inputs.gaussian_state(n, seed=9)
+    if dtype == 1:
+        psi0 = psi0.astype(np.complex64)
+    a, _ = run_gpu(qs, n, dtype, psi0, gates, qs.QS_MODE_GATE)
+    b, sb = run_gpu(qs, n, dtype, psi0, gates, qs.QS_MODE_AUTO)
+    c, _ = run_gpu(qs, n, dtype, psi0, gates, qs.QS_MODE_FUSED, fuse_k=3)
+    t = 1e-12 if dtype == 2 else 2e-5
+    assert np.max(np.abs(a - b)) <= t
+    assert np.max(np.abs(a - c)) <= t
+    assert sb["passes"] < len(gates) / 3
+
+
+def test_inverse_returns_initial_26q(qs):
+    """circuit followed by its inverse returns the initial state (complex128, 26 qubits)."""
+    n = 26
+    gates = inputs.brickwork(n, 8, seed=4) + inputs.sweep_all(n, seed=4, count=n)
+    full = gates + inputs.inverse(gates)
+    psi0 = inputs.gaussian_state(n, seed=10)
+    got, _ = run_gpu(qs, n, 2, psi0, full, qs.QS_MODE_AUTO)
+    assert np.max(np.abs(got - psi0)) <= 1e-12

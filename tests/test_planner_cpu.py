@@ -1,0 +1,87 @@
+"""CPU tests of the chunk planner's host logic (qs_plan dry run, no GPU)."""
+import numpy as np
+import pytest
+
+from paper_2409_14697_gb300 import inputs, qs
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_2409_14697_gb300 import build
+    build.build()
+
+
+def qmask(g):
+    m = 0
+    for q in g[1]:
+        m |= 1 << q
+    return m
+
+
+def check_plan(n, dtype, gates, chunk_m=0):
+    pog, lm = qs.qs_plan(n, dtype, gates, qs.options(chunk_m=chunk_m))
+    m = chunk_m or (12 if dtype == qs.QS_C128 else 13)
+    m = min(m, n)
+    c = min(4 if dtype == qs.QS_C128 else 5, m)
+    assert len(pog) == len(gates)
+    assert (pog >= 0).all() and (pog < len(lm)).all()
+    # every gate of a chunk pass lies inside the pass's local qubits
+    for i, g in enumerate(gates):
+        L = int(lm[pog[i]])
+        if L:
+            assert qmask(g) & ~L == 0
+            assert bin(L).count("1") == m
+            assert L & ((1 << c) - 1) == (1 << c) - 1
+    # dependencies: gates sharing a qubit keep their order across passes
+    last = {}
+    for i, g in enumerate(gates):
+        for q in g[1]:
+            if q in last:
+                assert pog[last[q]] <= pog[i]
+            last[q] = i
+    return pog, lm
+
+
+@pytest.mark.parametrize("n", [6, 12, 20, 30, 33])
+@pytest.mark.parametrize("dtype", [qs.QS_C128, qs.QS_C64])
+def test_brickwork_plan_valid(n, dtype):
+    gates = inputs.brickwork(n, 10, seed=1)
+    pog, lm = check_plan(n, dtype, gates)
+    if n <= 12:
+        assert len(lm) == 1           # the whole state is one tile: one pass
+    else:
+        assert len(lm) < len(gates) / 4
+
+
+@pytest.mark.parametrize("n", [14, 25, 33])
+def test_qaoa_tfim_qft_plans_valid(n):
+    for gates in (inputs.qaoa_3regular(n, p=2), inputs.tfim(n, steps=5), inputs.qft(min(n, 20))):
+        check_plan(min(n, 20) if len(gates) and max(max(g[1]) for g in gates) < 20 else n,
+                   qs.QS_C64, gates)
+
+
+def test_random_and_dense_plans_valid():
+    n = 18
+    gates = inputs.random_circuit(n, 300, seed=3)
+    gates.insert(50, ("dense", (17, 3, 9, 1, 0), inputs.random_unitary(5, 1)))
+    gates.insert(120, ("dense", (2, 16), inputs.random_unitary(2, 2)))
+    pog, lm = check_plan(n, qs.QS_C128, gates, chunk_m=10)
+    assert lm[pog[50]] == 0           # a 5-qubit dense block is streamed on its own
+    assert (pog == pog[50]).sum() == 1
+
+
+def test_plan_rejects_invalid():
+    with pytest.raises(qs.QsError):
+        qs.qs_plan(4, qs.QS_C128, [("cz", (0, 4), ())])
+
+
+@pytest.mark.parametrize("dtype", [qs.QS_C128, qs.QS_C64])
+@pytest.mark.parametrize("n,m", [(8, 6), (8, 5), (10, 4), (14, 6), (6, 6)])
+def test_small_chunk_width_always_progresses(n, m, dtype):
+    """With few free local slots some ops cannot join any pass: they are streamed, and
+    the planner still assigns every gate exactly once (no empty passes)."""
+    gates = inputs.random_circuit(n, 200, seed=n + m) + inputs.brickwork(n, 6, seed=n)
+    pog, lm = check_plan(n, dtype, gates, chunk_m=m)
+    assert len(lm) <= len(gates)
+    counts = np.bincount(pog, minlength=len(lm))
+    assert (counts >= 1).all()
