@@ -190,6 +190,26 @@ int qs_top_amplitudes(qs_state *s, uint32_t k, uint64_t *idx, double *amp);
 /* Scales the state by 1/sqrt(norm) (norm computed in FP64); returns the old norm. */
 int qs_renormalize(qs_state *s, double *old_norm);
 
+/* Allocation-free <Z_q> and squared norm.  The paper has no counterpart: this exists for
+ * callers that cannot call cudaMalloc, e.g. a host program that has handed all device
+ * memory to its own pool allocator, or a latency-critical loop that cannot afford
+ * cudaMalloc's implicit device synchronisation.  Same results as qs_expectation_z (FP64,
+ * fixed summation order; the block split differs, so the last bits may differ).
+ *   dev_psi   device pointer to 2^n_qubits amplitudes of dtype dt (caller's memory,
+ *             16-byte aligned), left unchanged;
+ *   stream    cudaStream_t to run on (NULL: legacy default stream); the call waits for it;
+ *   out_expz  host array of n_qubits doubles (or NULL), out_norm host double (or NULL).
+ * Scratch: a file-scope device array of about 2.5 MB that every GPU loading this library
+ * holds until process exit; nothing is allocated per call.  The first call on a device
+ * looks up that array's device address (cudaGetSymbolAddress), so make it before any
+ * stream capture.  All calls share the one array and it keeps the last call's contents;
+ * every value a call reads it has written itself, so nothing needs clearing, but calls
+ * that overlap on the GPU (on different streams or host threads) race.
+ * Errors: QS_ERR_INVALID for NULL pointers, an unknown dtype or n_qubits outside 1..32
+ * (the scratch's limit); QS_ERR_CUDA if a launch or copy fails. */
+int qs_expectation_z_noalloc(const void *dev_psi, int n_qubits, qs_dtype dt, void *stream,
+                             double *out_expz, double *out_norm);
+
 /* ---- batched execution: many small circuits in one persistent launch ------------ */
 
 typedef struct qs_batch qs_batch;  /* opaque */

@@ -12,7 +12,9 @@
 //    the elements above it and of the lowest-index ties, then one-block bitonic sort.
 //  * |0...0> and scaling.
 #include <algorithm>
+#include <mutex>
 
+#include "capi_util.h"
 #include "qs_internal.h"
 
 namespace qs {
@@ -418,4 +420,81 @@ void top_k(DeviceState &st, uint32_t K, uint64_t *idx, double *amp) {
     QS_CUDA(cudaStreamSynchronize(st.stream));
 }
 
+
+// ---------------------------------------------------------------------------------
+// Allocation-free variant of the norm / <Z_q> reduction.
+//
+// Some callers cannot call cudaMalloc: for example a host program that has handed all of
+// the device's memory to its own pool allocator, or a latency-critical loop that cannot
+// afford the implicit device synchronisation and unbounded latency of cudaMalloc.  This
+// entry point allocates nothing.  Its scratch is the file-scope device array below, of a
+// fixed size (kNoAllocScratchDoubles doubles, about 2.5 MB), which every GPU that loads
+// the library holds until the process exits.  The reduction kernels are the same as
+// above; only the block size is chosen so that at most 2^14 blocks write partial sums.
+
+namespace {
+
+constexpr int kNoAllocMaxQubits = 32;
+constexpr int kNoAllocMaxBlockBits = 14;
+// partials: 2^14 blocks x (cb + 1 <= 19) doubles, then the n + 1 outputs
+constexpr size_t kNoAllocScratchDoubles = ((size_t)1 << kNoAllocMaxBlockBits) * 19 + 64;
+
+__device__ __align__(256) double g_noalloc_scratch[kNoAllocScratchDoubles];
+
+std::mutex g_noalloc_mu;
+double *g_noalloc_ptr[64] = {nullptr};
+
+// Device address of g_noalloc_scratch on the current device (looked up once per device).
+double *noalloc_scratch() {
+    int dev = 0;
+    QS_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) fail(QS_ERR_UNSUPPORTED, "device index above 63");
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+        void *p = nullptr;
+        QS_CUDA(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+        g_noalloc_ptr[dev] = (double *)p;
+    }
+    return g_noalloc_ptr[dev];
+}
+
+}  // namespace
+
 }  // namespace qs
+
+extern "C" int qs_expectation_z_noalloc(const void *dev_psi, int n_qubits, qs_dtype dt, void *stream,
+                                        double *out_expz, double *out_norm) {
+    using namespace qs;
+    QS_API_BEGIN
+    if (!dev_psi || (!out_expz && !out_norm)) fail(QS_ERR_INVALID, "NULL argument");
+    if (dt != QS_C64 && dt != QS_C128) fail(QS_ERR_INVALID, "unknown dtype");
+    if (n_qubits < 1 || n_qubits > kNoAllocMaxQubits)
+        fail(QS_ERR_INVALID, "qs_expectation_z_noalloc takes 1 to 32 qubits (fixed static scratch of " +
+                                 std::to_string(kNoAllocScratchDoubles) + " doubles)");
+    const int n = n_qubits;
+    const int cb = std::min(n, std::max(chunk_bits(n), n - kNoAllocMaxBlockBits));
+    const int tb = std::min(cb, 8);
+    const uint64_t nblk = 1ull << (n - cb);
+    const size_t part_elems = nblk * (cb + 1);
+    if (part_elems + n + 1 > kNoAllocScratchDoubles) fail(QS_ERR_INVALID, "static scratch too small");
+    double *part = noalloc_scratch();
+    double *out = part + part_elems;
+    cudaStream_t st = (cudaStream_t)stream;
+    // every partial the second stage reads is written by the first: nothing to clear
+    if (dt == QS_C128)
+        k_expz_part<double2><<<(unsigned)nblk, 1 << tb, 0, st>>>((const double2 *)dev_psi, cb, tb, 1, part);
+    else
+        k_expz_part<float2><<<(unsigned)nblk, 1 << tb, 0, st>>>((const float2 *)dev_psi, cb, tb, 1, part);
+    QS_CUDA(cudaGetLastError());
+    k_expz_final<<<n + 1, 256, 0, st>>>(part, nblk, cb, n, out);
+    QS_CUDA(cudaGetLastError());
+    count_launch(2);
+    double h[kNoAllocMaxQubits + 1];
+    QS_CUDA(cudaMemcpyAsync(h, out, sizeof(double) * (n + 1), cudaMemcpyDeviceToHost, st));
+    QS_CUDA(cudaStreamSynchronize(st));
+    if (out_norm) *out_norm = h[0];
+    if (out_expz)
+        for (int q = 0; q < n; q++) out_expz[q] = h[1 + q];
+    QS_API_END
+}
+

@@ -89,6 +89,7 @@ _SIGS = {
     "qs_expectation_z": (ctypes.c_int, [_VP, _DP, _DP]),
     "qs_top_amplitudes": (ctypes.c_int, [_VP, ctypes.c_uint32, _U64P, _DP]),
     "qs_renormalize": (ctypes.c_int, [_VP, _DP]),
+    "qs_expectation_z_noalloc": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int, _VP, _DP, _DP]),
     "qs_batch_create": (ctypes.c_int, [ctypes.POINTER(qs_circuit), ctypes.c_size_t, ctypes.c_int,
                                        ctypes.POINTER(qs_options), ctypes.POINTER(_VP)]),
     "qs_batch_run": (ctypes.c_int, [_VP]),
@@ -271,6 +272,15 @@ def qs_top_amplitudes(h, k: int):
     amp = np.zeros(k, dtype=np.complex128)
     _check(load().qs_top_amplitudes(h, k, idx.ctypes.data_as(_U64P), amp.ctypes.data_as(_DP)))
     return idx, amp
+
+
+def qs_expectation_z_noalloc(dev_ptr: int, n_qubits: int, dtype: int, stream: int = 0):
+    """Allocation-free <Z_q> and squared norm of a state at device address dev_ptr."""
+    out = np.zeros(n_qubits)
+    nrm = ctypes.c_double()
+    _check(load().qs_expectation_z_noalloc(dev_ptr, n_qubits, dtype, stream, out.ctypes.data_as(_DP),
+                                           ctypes.byref(nrm)))
+    return out, nrm.value
 
 
 def qs_renormalize(h) -> float:
