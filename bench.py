@@ -48,6 +48,12 @@ def parse():
     ap.add_argument("--cpu-sample-gates", type=int, default=2)
     ap.add_argument("--no-extra", action="store_true",
                     help="skip the context rows (planned circuits, the other dtype)")
+    ap.add_argument("--workload", default="gates30",
+                    choices=["gates30", "circuit12", "circuits33", "batched", "served"],
+                    help="gates30: the headline benchmark; the others print their own JSON line")
+    ap.add_argument("--count", type=int, default=0, help="circuits/requests for batched/served")
+    ap.add_argument("--fuse-k", type=int, default=5)
+    ap.add_argument("--rate", type=float, default=2000.0)
     return ap.parse_args()
 
 
@@ -214,9 +220,18 @@ def run_ours(args, rank, world, local):
                           "share": round(per_type_ms[name] / total_ms, 3)}
     dom = max(GATE_TYPES, key=lambda k: per_type_ms[k])
     traffic = load_traffic(dom, n, args.dtype)
-    roof = {"kernel": f"k_stream[{dom}]", "bound": "hbm", "achieved": per_gate[dom]["GBps"],
-            "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
-            "frac": round(per_gate[dom]["GBps"] / peak, 3), "traffic": traffic}
+    hbm = {"achieved": per_gate[dom]["GBps"], "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
+           "frac": round(per_gate[dom]["GBps"] / peak, 3)}
+    fp64 = fp64_roof(dom, n, B, per_type_ms[dom] / (args.steps * len(sweeps[dom])))
+    if fp64 and fp64["frac"] > hbm["frac"]:
+        roof = {"kernel": f"k_stream[{dom}]", "bound": "alu", "achieved": fp64["achieved"],
+                "peak": fp64["peak"], "unit": fp64["unit"], "frac": fp64["frac"],
+                "peak_source": fp64["peak_source"], "traffic": traffic, "hbm": hbm}
+    else:
+        roof = {"kernel": f"k_stream[{dom}]", "bound": "hbm", "achieved": hbm["achieved"], "peak": peak,
+                "peak_kind": peak_kind, "unit": "GB/s", "frac": hbm["frac"], "traffic": traffic}
+        if fp64:
+            roof["fp64"] = fp64
     all_bytes = sum(per_gate[k]["alg_bytes"] * len(sweeps[k]) for k in GATE_TYPES)
     agg_gbps = all_bytes / (ms_per_step * 1e-3) / 1e9
 
@@ -226,6 +241,8 @@ def run_ours(args, rank, world, local):
     extra = {}
     if not args.no_extra:
         extra["planned"] = time_planned(qs, h, stream, recs, n, B)
+        if B == 16:
+            extra["df32"] = time_df32(qs, h, stream, recs, n, sweeps, peak)
     qs.qs_destroy(h)
     del host_in
 
@@ -249,6 +266,32 @@ def run_ours(args, rank, world, local):
         out["e2e"] = e2e
     out.update(extra)
     return out
+
+
+def time_df32(qs, h, stream, recs, n, sweeps, peak):
+    """Context row: the same gate-by-gate sweep with complex128 double-float arithmetic
+    (QS_PREC_DF32: IEEE-double storage, FP32-pair compensated arithmetic)."""
+    import torch
+    opts = qs.options(mode=qs.QS_MODE_GATE, precision=qs.QS_PREC_DF32)
+    for name in GATE_TYPES:
+        qs.qs_apply_circuit(h, recs[name], opts)
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(len(GATE_TYPES) + 1)]
+    for i, name in enumerate(GATE_TYPES):
+        evs[i].record(stream)
+        qs.qs_apply_circuit(h, recs[name], opts)
+    evs[-1].record(stream)
+    torch.cuda.synchronize()
+    per, tot = {}, 0.0
+    for i, name in enumerate(GATE_TYPES):
+        ms = evs[i].elapsed_time(evs[i + 1])
+        tot += ms
+        byts = float(np.mean([alg_bytes_per_gate(name, g[1], n, 16) for g in sweeps[name]]))
+        per[name] = {"ms": round(ms / len(sweeps[name]), 4),
+                     "GBps": round(byts / (ms / len(sweeps[name]) * 1e-3) / 1e9, 1)}
+        per[name]["frac_of_measured_hbm"] = round(per[name]["GBps"] / peak, 3)
+    n_g = sum(len(g) for g in sweeps.values())
+    return {"value": round(n_g / (tot * 1e-3), 2), "unit": "gates/s", "ms_per_step": round(tot, 3),
+            "per_gate": per}
 
 
 def time_planned(qs, h, stream, recs, n, B):
@@ -295,13 +338,30 @@ def run_e2e(qs, h, host_in, recs, opts, n, B, n_gates, world):
             "ms_per_step": round(dt * 1e3, 2), "steps": reps}
 
 
+# FP64 instructions per amplitude (FMA-class issues, one FP64 pipe slot each) of the
+# complex128 streaming updates; the other gate types issue none on the FP64 pipe.
+FP64_INSTR_PER_AMP = {"h": 4, "rz": 4, "u3": 8, "cu3": 4}
+# FP64 pipe peak: 2 FP64 instructions per clock per SM (ncu: the U3 kernel at 0.526e12/s
+# keeps the FP64 pipe 83.8 % busy) x 152 SMs x 2.07 GHz max SM clock = 1.26 TFLOP/s.
+FP64_PEAK_TINSTR = 2 * 152 * 2.07e9 / 1e12
+
+
+def fp64_roof(name, n, B, launch_ms):
+    if B != 16 or name not in FP64_INSTR_PER_AMP:
+        return None
+    ach = FP64_INSTR_PER_AMP[name] * (1 << n) / (launch_ms * 1e-3) / 1e12
+    return {"achieved": round(ach, 4), "peak": round(FP64_PEAK_TINSTR, 4), "unit": "T FP64 instr/s",
+            "frac": round(ach / FP64_PEAK_TINSTR, 3),
+            "peak_source": "2 FP64 instr/clk/SM x 152 SMs x 2.07 GHz (ncu-confirmed pipe rate)"}
+
+
 def load_traffic(kernel_gate, n, dtype):
     """Per-launch DRAM bytes from the committed ncu summary, if one matches."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(p) as f:
             t = json.load(f)
-        return t.get(f"{kernel_gate}:{n}:{dtype}")
+        return t.get(f"k_stream[{kernel_gate}]:{n}:{dtype}")
     except Exception:
         return None
 
@@ -348,9 +408,239 @@ def run_reference(args, rank, world):
             "e2e": {"value": round(v, 4), "unit": "gates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
+# ---- other workloads (each prints its own JSON line) ---------------------------------
+
+def _event_ms(stream, fn, reps=1):
+    import torch
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def wl_circuit12(args):
+    """12-qubit random brickwork (20 layers, complex128) from |0...0>, planned path: the
+    whole 64 KiB state is one tile, 350 gates in one pass."""
+    import torch
+    import oracle
+    from paper_2409_14697_gb300 import inputs, qs
+    n = 12
+    gates = inputs.brickwork(n, 20, seed=1)
+    recs = qs.gate_records(gates)
+    stream = torch.cuda.Stream()
+    h = qs.qs_create(n, qs.QS_C128)
+    qs.qs_set_stream(h, stream.cuda_stream)
+    opts = qs.options()
+
+    def once():
+        qs.qs_reset(h)
+        qs.qs_apply_circuit(h, recs, opts)
+    for _ in range(max(args.warmup, 3)):
+        once()
+    reps = max(args.steps, 20)
+    ms = _event_ms(stream, once, reps)
+    got = qs.qs_amplitudes(h)
+    want = oracle.run(oracle.zero_state(n), n, gates)
+    st = qs.qs_last_stats(h)
+    qs.qs_destroy(h)
+    return {"workload": "12-qubit brickwork, 20 layers, complex128, planned", "metric": "circuits/s",
+            "value": round(1e3 / ms, 1), "gates_per_s": round(len(gates) * 1e3 / ms, 1), "ms_per_circuit": round(ms, 4),
+            "passes": st["passes"], "max_abs_err_vs_oracle": float(np.max(np.abs(got - want))), "reps": reps}
+
+
+def wl_circuits33(args):
+    """33-qubit complex64 circuits (64 GiB state) with fused blocks of fuse_k qubits on the
+    tensor cores: brickwork 40 layers, QAOA p=4 on a 3-regular graph, TFIM 50 steps.
+    Checks at full size: norm, and 1 - |<0|C^-1 C|0>|^2 (circuit then inverse)."""
+    import torch
+    from paper_2409_14697_gb300 import inputs, qs
+    n = args.qubits if args.qubits != N_QUBITS else 33
+    stream = torch.cuda.Stream()
+    h = qs.qs_create(n, qs.QS_C64)
+    qs.qs_set_stream(h, stream.cuda_stream)
+    out = {"workload": f"{n}-qubit circuits, complex64, fused k={args.fuse_k} (tensor cores)", "qubits": n,
+           "state_bytes": 8 << n, "circuits": {}}
+    opts = qs.options(fuse_k=args.fuse_k)
+    fams = {"brickwork40": inputs.brickwork(n, 40, seed=3), "qaoa_p4": inputs.qaoa_3regular(n, p=4, seed=3),
+            "tfim50": inputs.tfim(n, steps=50, dt=0.05)}
+    for name, gates in fams.items():
+        recs = qs.gate_records(gates)
+        inv = qs.gate_records(inputs.inverse(gates))
+        qs.qs_reset(h)
+        qs.qs_apply_circuit(h, recs, opts)      # warm-up (also plans)
+        qs.qs_synchronize(h)
+        qs.qs_reset(h)
+        ms = _event_ms(stream, lambda: qs.qs_apply_circuit(h, recs, opts))
+        st = qs.qs_last_stats(h)
+        nrm = qs.qs_norm(h)
+        qs.qs_apply_circuit(h, inv, opts)
+        a0 = qs.qs_amplitudes(h, 0, 1)[0]
+        out["circuits"][name] = {"gates": len(gates), "ms": round(ms, 2), "passes": st["passes"],
+                                 "ops_after_fuse": st["ops_after_fuse"],
+                                 "gates_per_s": round(len(gates) * 1e3 / ms, 1),
+                                 "pass_GBps": round(st["bytes"] / (ms * 1e-3) / 1e9, 1),
+                                 "norm_minus_1": nrm - 1.0, "inverse_infidelity": 1.0 - abs(complex(a0)) ** 2}
+    qs.qs_destroy(h)
+    return out
+
+
+def wl_batched(args):
+    """4096 independent random U3+CZ brickwork circuits (n ~ U{8..20}, depth ~ U{10..60}),
+    complex64, all in ONE graph-captured persistent launch; against one circuit at a time
+    through qs_apply_circuit on the same GPU."""
+    import torch
+    import oracle
+    from paper_2409_14697_gb300 import inputs, qs
+    count = args.count or 4096
+    circs = inputs.batched_circuits(count, seed=10)
+    t0 = time.perf_counter()
+    b = qs.qs_batch_create(circs, qs.QS_C64, qs.options(fuse_k=2))
+    build_s = time.perf_counter() - t0
+    stream = torch.cuda.Stream()
+    qs.qs_batch_set_stream(b, stream.cuda_stream)
+    for _ in range(max(args.warmup, 3)):
+        qs.qs_batch_run(b)
+    qs.qs_batch_synchronize(b)
+    reps = max(args.steps, 3)
+    ms = _event_ms(stream, lambda: qs.qs_batch_run(b), reps)
+    qs.qs_batch_synchronize(b)
+    info = qs.qs_batch_info(b)
+    # per-circuit error vs the FP64 oracle on a seeded sample of the smaller circuits
+    rs = np.random.default_rng(1)
+    small = [i for i, (n, g) in enumerate(circs) if n <= 12]
+    sample = sorted(rs.choice(small, size=min(12, len(small)), replace=False).tolist())
+    errs, infid = [], []
+    for i in sample:
+        n, g = circs[i]
+        got = qs.qs_batch_amplitudes(b, i, n, qs.QS_C64).astype(np.complex128)
+        want = oracle.run(oracle.zero_state(n), n, g)
+        errs.append(float(np.max(np.abs(got - want))))
+        infid.append(float(1 - abs(np.vdot(want, got)) ** 2 / (np.vdot(got, got).real * np.vdot(want, want).real)))
+    qs.qs_batch_destroy(b)
+    # one at a time on a subset, scaled to the whole batch by gate count
+    sub = circs[: min(256, count)]
+    hs = {}
+    t_one = 0.0
+    for n, g in sub:
+        if n not in hs:
+            hs[n] = qs.qs_create(n, qs.QS_C64)
+            qs.qs_set_stream(hs[n], stream.cuda_stream)
+        recs = qs.gate_records(g)
+        qs.qs_reset(hs[n])
+        qs.qs_apply_circuit(hs[n], recs, qs.options(fuse_k=2))
+    torch.cuda.synchronize()
+    for n, g in sub:
+        recs = qs.gate_records(g)
+
+        def one(h=hs[n], r=recs):
+            qs.qs_reset(h)
+            qs.qs_apply_circuit(h, r, qs.options(fuse_k=2))
+        t_one += _event_ms(stream, one)
+    for h in hs.values():
+        qs.qs_destroy(h)
+    one_cps = len(sub) / (t_one * 1e-3)
+    return {"workload": f"batched: {count} random U3+CZ circuits, n 8-20, depth 10-60, complex64, one graph launch",
+            "metric": "circuits/s", "value": round(count / (ms * 1e-3), 1), "ms_per_batch": round(ms, 3),
+            "one_at_a_time_circuits_per_s": round(one_cps, 1), "one_at_a_time_sample": len(sub),
+            "speedup_vs_one_at_a_time": round(count / (ms * 1e-3) / one_cps, 2),
+            "passes": info["passes"], "work_items": info["work_items"], "grid": info["grid"],
+            "state_bytes": info["state_bytes"], "host_build_s": round(build_s, 2),
+            "oracle_sample": sample, "max_abs_err": max(errs), "max_infidelity": max(infid)}
+
+
+def wl_served(args):
+    """Poisson stream (mean rate --rate req/s) of circuits with n log-uniform in 10..30,
+    complex64 or complex128, each returning <Z_i> for all qubits and the top 1024
+    amplitudes; admission by an HBM budget of 150 GB; against the plain sequential path."""
+    import torch
+    from paper_2409_14697_gb300 import inputs, qs
+    count = args.count or 300
+    reqs = inputs.served_stream(count, rate_hz=args.rate, seed=11)
+    init_cache = {}
+
+    def init_for(r):
+        if not r["init_seed"]:
+            return None, r["gates"]
+        if r["n"] > 24:   # reading: large sweep requests start from H^n|0> built on the device
+            return None, [("h", (q,), ()) for q in range(r["n"])] + r["gates"]
+        key = (r["n"], r["dtype"])
+        if key not in init_cache:
+            init_cache[key] = inputs.gaussian_state(r["n"], seed=r["n"]).astype(
+                np.complex128 if r["dtype"] == "c128" else np.complex64)
+        return init_cache[key], r["gates"]
+    prepared = []
+    for r in reqs:
+        init, gates = init_for(r)
+        dt = qs.QS_C128 if r["dtype"] == "c128" else qs.QS_C64
+        prepared.append((r["t"], r["n"], dt, qs.gate_records(gates), len(gates), init, min(1024, 1 << r["n"])))
+    sv = qs.qs_server_create(150 * 10 ** 9, max_slots=8)
+    lat, tickets = [], []
+    t0 = time.perf_counter()
+    pending = {}
+    i = 0
+    while i < len(prepared) or pending:
+        now = time.perf_counter() - t0
+        while i < len(prepared) and prepared[i][0] <= now:
+            t_arr, n, dt, recs, ng, init, k = prepared[i]
+            tk = qs.qs_submit(sv, n, dt, recs, top_k=k, init=init)
+            pending[tk] = (n, k)
+            i += 1
+        done = []
+        for tk, (n, k) in pending.items():
+            r = qs.qs_poll(sv, tk, n, k)
+            if r is not None:
+                lat.append(r["latency_s"])
+                done.append(tk)
+        for tk in done:
+            del pending[tk]
+        if not done:
+            time.sleep(0.0002)
+    wall = time.perf_counter() - t0
+    st = qs.qs_server_stats(sv)
+    qs.qs_server_destroy(sv)
+    # the plain sequential path: one request after the other through qs_apply_circuit
+    hs = {}
+    t1 = time.perf_counter()
+    for t_arr, n, dt, recs, ng, init, k in prepared:
+        key = (n, dt)
+        if key not in hs:
+            hs[key] = qs.qs_create(n, dt)
+        h = hs[key]
+        if init is None:
+            qs.qs_reset(h)
+        else:
+            qs.qs_set_amplitudes(h, init)
+        qs.qs_apply_circuit(h, recs)
+        qs.qs_expectation_z(h)
+        qs.qs_top_amplitudes(h, k)
+    seq_wall = time.perf_counter() - t1
+    for h in hs.values():
+        qs.qs_destroy(h)
+    lat = np.array(lat)
+    return {"workload": f"served: {count} Poisson requests at {args.rate:g} req/s, n 10-30 log-uniform, "
+                        f"c64/c128, <Z_i> + top-1024, 150 GB budget, 8 slots",
+            "metric": "requests/s", "value": round(count / wall, 2), "p50_latency_s": round(float(np.percentile(lat, 50)), 4),
+            "p99_latency_s": round(float(np.percentile(lat, 99)), 4), "mean_latency_s": round(float(lat.mean()), 4),
+            "wall_s": round(wall, 2), "sequential_requests_per_s": round(count / seq_wall, 2),
+            "sequential_wall_s": round(seq_wall, 2), "peak_bytes": st["peak_bytes"], "failed": st["failed"]}
+
+
+def run_workload(args):
+    fn = {"circuit12": wl_circuit12, "circuits33": wl_circuits33,
+          "batched": wl_batched, "served": wl_served}[args.workload]
+    print(json.dumps(fn(args)))
+
+
 def main():
     args = parse()
     rank, world, local = dist_env()
+    if args.workload != "gates30" and args.impl == "ours":
+        if rank == 0:
+            run_workload(args)
+        return
     if args.impl == "reference":
         if rank != 0:
             return

@@ -95,10 +95,15 @@ enum {
     QS_MODE_CHUNK = 2,    /* every gate through in-shared-memory chunk passes */
     QS_MODE_FUSED = 3     /* fuse to dense k-qubit blocks, one full pass per block */
 };
-/* Arithmetic used for complex128 gate updates. */
+/* Arithmetic used for complex128 gate updates (complex64 always uses FP32).  The state
+ * is stored as IEEE doubles in every mode. */
 enum {
     QS_PREC_DEFAULT = 0,  /* native FP64 */
-    QS_PREC_FP64 = 1      /* native FP64 */
+    QS_PREC_FP64 = 1,     /* native FP64 instructions */
+    QS_PREC_DF32 = 2      /* double-float: FP32 pairs with compensated products and sums
+                             (TwoProd/TwoSum); each update is within ~2^-46 of the sum of
+                             |matrix entry x amplitude| of the exact value.  Applies to
+                             the streaming and the in-cache (chunk) passes. */
 };
 
 /* Options for qs_apply_circuit; pass NULL for defaults.  Zero fields mean "choose". */
@@ -209,6 +214,53 @@ int qs_renormalize(qs_state *s, double *old_norm);
  * (the scratch's limit); QS_ERR_CUDA if a launch or copy fails. */
 int qs_expectation_z_noalloc(const void *dev_psi, int n_qubits, qs_dtype dt, void *stream,
                              double *out_expz, double *out_norm);
+
+/* ---- serving: continuous batching of circuit requests -------------------------- */
+/* The paper has no serving layer; this is the request loop around the operation of
+ * Eq. 1-3.  Requests enter a FIFO queue; a worker thread admits the queue head when a
+ * slot is free and the admitted states' bytes (2^n x bytes per amplitude) stay within
+ * hbm_budget_bytes.  Every slot has its own CUDA stream, so admitted requests overlap on
+ * the device.  A request runs its circuit (QS_MODE_* of `mode`, planned by default) from
+ * |0...0> or from the caller's amplitudes, then returns <Z_q> for every qubit, the squared
+ * norm and its top_k amplitudes.  Results are bitwise identical whatever else runs. */
+
+typedef struct {
+    uint64_t hbm_budget_bytes;  /* admission budget for the states in flight */
+    int32_t max_slots;          /* requests in flight at once (1..256) */
+    int32_t reserved[5];
+} qs_server_config;
+
+typedef struct {
+    int32_t n_qubits;
+    int32_t dtype;                 /* QS_C64 or QS_C128 */
+    const qs_gate *gates;          /* copied by qs_submit */
+    uint64_t n_gates;
+    const void *init_amplitudes;   /* 2^n amplitudes of dtype (copied), or NULL for |0...0> */
+    uint32_t top_k;                /* amplitudes to return, <= min(2^n, 4096) */
+    int32_t mode;                  /* QS_MODE_* for the circuit */
+} qs_request;
+
+typedef struct {
+    int64_t submitted, completed, failed, queued, in_flight;
+    uint64_t bytes_in_use, peak_bytes;
+} qs_server_stats_t;
+
+/* Creates the server on the current CUDA device and starts its worker thread. */
+int qs_server_create(const qs_server_config *cfg, qs_server **out);
+/* Queues a request and returns its ticket.  QS_ERR_NOMEM only if the request can never
+ * fit the budget; QS_ERR_INVALID for bad records (nothing is queued). */
+int qs_submit(qs_server *sv, const qs_request *req, uint64_t *ticket);
+/* QS_NOT_READY while the request runs; QS_OK once done, copying <Z_q> (n doubles),
+ * the squared norm, top_k indices and 2*top_k doubles (interleaved amplitudes) and the
+ * latency from submission to completion in seconds (any pointer may be NULL).  A ticket
+ * is returned once; afterwards (or never issued) it is QS_ERR_INVALID. */
+int qs_poll(qs_server *sv, uint64_t ticket, double *expz, double *norm, uint64_t *top_idx,
+            double *top_amp, double *latency_s);
+int qs_server_stats(qs_server *sv, qs_server_stats_t *out);
+/* Waits until every submitted request has completed; QS_ERR_TIMEOUT after timeout_s. */
+int qs_server_drain(qs_server *sv, double timeout_s);
+/* QS_ERR_BUSY while requests are queued or in flight. */
+int qs_server_destroy(qs_server *sv);
 
 /* ---- batched execution: many small circuits in one persistent launch ------------ */
 

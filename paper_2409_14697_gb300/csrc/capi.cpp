@@ -5,6 +5,7 @@
 #include <mutex>
 
 #include "capi_util.h"
+#include "chunk.h"
 #include "plan.h"
 #include "qs_internal.h"
 
@@ -62,13 +63,20 @@ void ensure_scratch(DeviceState &st, size_t bytes) {
 // Parameter arena: two halves used alternately by successive qs_apply_circuit calls.
 // Before a half is reused, the event recorded after its last copy is waited on, so the
 // pinned staging memory is never rewritten while a copy from it may still be pending.
-static void arena_begin(DeviceState &st) {
+void arena_begin(DeviceState &st) {
     st.arena_cur ^= 1;
     st.arena_used = 0;
-    if (st.arena_ev[st.arena_cur]) QS_CUDA(cudaEventSynchronize(st.arena_ev[st.arena_cur]));
+    const int c = st.arena_cur;
+    if (st.arena_ev[c]) QS_CUDA(cudaEventSynchronize(st.arena_ev[c]));
+    // buffers this half outgrew during its last use are idle now
+    for (auto &r : st.arena_retired[c]) {
+        if (r.first) cudaFree(r.first);
+        if (r.second) cudaFreeHost(r.second);
+    }
+    st.arena_retired[c].clear();
 }
 
-static void arena_end(DeviceState &st) {
+void arena_end(DeviceState &st) {
     if (!st.arena_ev[st.arena_cur])
         QS_CUDA(cudaEventCreateWithFlags(&st.arena_ev[st.arena_cur], cudaEventDisableTiming));
     QS_CUDA(cudaEventRecord(st.arena_ev[st.arena_cur], st.stream));
@@ -78,10 +86,10 @@ void *upload_params(DeviceState &st, const void *host, size_t bytes) {
     const int c = st.arena_cur;
     const size_t need = ((st.arena_used + 255) & ~size_t(255)) + bytes;
     if (need > st.arena_cap[c]) {
-        // grow: nothing queued may still read the old half
-        QS_CUDA(cudaStreamSynchronize(st.stream));
-        if (st.arena_dev[c]) QS_CUDA(cudaFree(st.arena_dev[c]));
-        if (st.arena_host[c]) QS_CUDA(cudaFreeHost(st.arena_host[c]));
+        // grow: earlier uploads of this call (and queued copies from the pinned staging)
+        // still refer to the old buffers, so they are retired, not freed; arena_begin frees
+        // them once this half's event shows that nothing uses them
+        st.arena_retired[c].push_back({st.arena_dev[c], st.arena_host[c]});
         st.arena_dev[c] = st.arena_host[c] = nullptr;
         const size_t cap = std::max<size_t>(need * 2, 1 << 16);
         QS_CUDA(cudaMalloc(&st.arena_dev[c], cap));
@@ -113,52 +121,86 @@ static size_t amp_bytes(int dtype) { return dtype == QS_C128 ? 16 : 8; }
 
 static void destroy_state(qs_state *s) {
     DeviceState &d = s->d;
-    if (d.stream) cudaStreamSynchronize(d.stream);
-    for (int c = 0; c < 2; c++) {
-        if (d.arena_dev[c]) cudaFree(d.arena_dev[c]);
-        if (d.arena_host[c]) cudaFreeHost(d.arena_host[c]);
-        if (d.arena_ev[c]) cudaEventDestroy(d.arena_ev[c]);
-    }
-    if (d.scratch) cudaFree(d.scratch);
-    if (d.dev_err) cudaFree(d.dev_err);
+    free_device_state(d);
     if (s->owns_memory && d.psi) cudaFree(d.psi);
     if (s->owns_stream && d.stream) cudaStreamDestroy(d.stream);
     delete s;
 }
 
-// Runs the executor for one circuit (validated, lowered).
-static void execute(qs_state *s, const std::vector<Op> &ops, const qs_options &o) {
-    DeviceState &d = s->d;
-    qs_stats st{};
+// Runs the executor for one circuit (validated, lowered) on d.stream.
+void run_circuit(DeviceState &d, const std::vector<Op> &ops, const qs_options &o, qs_stats &st) {
+    st = qs_stats{};
     st.gates_in = (int64_t)ops.size();
+    if (o.precision != QS_PREC_DEFAULT && o.precision != QS_PREC_FP64 && o.precision != QS_PREC_DF32)
+        fail(QS_ERR_INVALID, "unknown precision mode");
+    d.prec = o.precision == QS_PREC_DF32 ? QS_PREC_DF32 : QS_PREC_FP64;
     const uint64_t l0 = g_launches.load();
     arena_begin(d);
-    int mode = o.mode;
-    if (mode == QS_MODE_GATE) {
-        for (const Op &op : ops) {
-            launch_stream_op(d, op);
-            st.passes++;
-            st.bytes += stream_bytes(op, d.n, d.dtype);
+    const int mode = o.mode;
+    try {
+        if (mode == QS_MODE_GATE) {
+            for (const Op &op : ops) {
+                launch_stream_op(d, op);
+                st.passes++;
+                st.bytes += stream_bytes(op, d.n, d.dtype);
+            }
+            st.ops_after_fuse = (int64_t)ops.size();
+        } else if (mode == QS_MODE_FUSED) {
+            const int k = o.fuse_k > 0 ? o.fuse_k : 3;
+            const std::vector<Op> fused = fuse_ops(ops, std::min(k, 6));
+            const int m_tc = std::min(d.n, 13);
+            for (const Op &op : fused) {
+                if (d.dtype == QS_C64 && op.kind == K_DENSE && tc_available(m_tc, op.k)) {
+                    // one full pass per block on the tensor cores: local qubits = the
+                    // block's qubits plus the lowest others up to 2^13 amplitudes
+                    uint64_t L = op.qmask();
+                    for (int b = 0; b < d.n && __builtin_popcountll(L) < m_tc; b++) L |= 1ull << b;
+                    launch_pass_ops(d, L, {op}, true);
+                    st.bytes += 2.0 * 8.0 * (double)(1ull << d.n);
+                } else {
+                    launch_stream_op(d, op);
+                    st.bytes += stream_bytes(op, d.n, d.dtype);
+                }
+                st.passes++;
+            }
+            st.ops_after_fuse = (int64_t)fused.size();
+        } else if (mode == QS_MODE_AUTO || mode == QS_MODE_CHUNK) {
+            run_planned(d, ops, o, st);
+        } else {
+            fail(QS_ERR_INVALID, "unknown mode");
         }
-        st.ops_after_fuse = (int64_t)ops.size();
-    } else if (mode == QS_MODE_FUSED) {
-        const int k = o.fuse_k > 0 ? o.fuse_k : 3;
-        const std::vector<Op> fused = fuse_ops(ops, std::min(k, 6));
-        for (const Op &op : fused) {
-            launch_stream_op(d, op);
-            st.passes++;
-            st.bytes += stream_bytes(op, d.n, d.dtype);
-        }
-        st.ops_after_fuse = (int64_t)fused.size();
-    } else if (mode == QS_MODE_AUTO || mode == QS_MODE_CHUNK) {
-        run_planned(d, ops, o, st);
-    } else {
+    } catch (...) {
         arena_end(d);
-        fail(QS_ERR_INVALID, "unknown mode");
+        throw;
     }
     arena_end(d);
     st.launches = (int64_t)(g_launches.load() - l0);
-    s->stats = st;
+}
+
+void free_device_state(DeviceState &d) {
+    if (d.stream) cudaStreamSynchronize(d.stream);
+    for (int c = 0; c < 2; c++) {
+        if (d.arena_dev[c]) cudaFree(d.arena_dev[c]);
+        if (d.arena_host[c]) cudaFreeHost(d.arena_host[c]);
+        for (auto &r : d.arena_retired[c]) {
+            if (r.first) cudaFree(r.first);
+            if (r.second) cudaFreeHost(r.second);
+        }
+        d.arena_retired[c].clear();
+        if (d.arena_ev[c]) cudaEventDestroy(d.arena_ev[c]);
+        d.arena_dev[c] = d.arena_host[c] = nullptr;
+        d.arena_ev[c] = nullptr;
+        d.arena_cap[c] = 0;
+    }
+    if (d.scratch) cudaFree(d.scratch);
+    if (d.dev_err) cudaFree(d.dev_err);
+    d.scratch = nullptr;
+    d.scratch_bytes = 0;
+    d.dev_err = nullptr;
+}
+
+static void execute(qs_state *s, const std::vector<Op> &ops, const qs_options &o) {
+    run_circuit(s->d, ops, o, s->stats);
 }
 
 }  // namespace qs

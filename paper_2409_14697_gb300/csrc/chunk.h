@@ -20,4 +20,13 @@ struct ChunkArgs {
 void launch_chunk_pass(DeviceState &st, uint64_t lmask, const std::vector<KOp> &kops,
                        const std::vector<double> &mats);
 
+// Tensor-core variant (complex64): ops of kind F_TC index bmats (B operands built by
+// build_tc_operand; b_floats = largest B part of the pass, in floats).
+void launch_chunk_pass_tc(DeviceState &st, uint64_t lmask, const std::vector<KOp> &kops,
+                          const std::vector<double> &mats, const std::vector<float> &bmats, uint32_t b_floats);
+// True if a k-qubit block can run on the tensor cores in a tile of 2^m amplitudes.
+bool tc_available(int m, int k);
+// Appends the TF32 hi/lo B operand of the complex D x D block G (D = 2^k) to out.
+void build_tc_operand(const std::vector<cd> &G, int k, std::vector<float> &out, int &off, int &count);
+
 }  // namespace qs

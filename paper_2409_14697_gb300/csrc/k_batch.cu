@@ -36,11 +36,7 @@ __device__ __forceinline__ void red_release_add(unsigned int *p, unsigned int v)
 __device__ __forceinline__ void fence_proxy_async_global() {
     asm volatile("fence.proxy.async.global;" ::: "memory");
 }
-__device__ __forceinline__ uint64_t globaltimer_ns() {
-    uint64_t t;
-    asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
-    return t;
-}
+using ptx::globaltimer_ns;
 
 template <typename T>
 __global__ void __launch_bounds__(kBatchThreads)

@@ -21,9 +21,9 @@ namespace qs {
 namespace {
 
 constexpr int kChunkThreads = 256;
-constexpr long long kWaitLimit = 1ll << 26;  // bounded mbarrier spin (seconds, never hit)
 
-template <typename T>
+// DF: complex128 with double-float arithmetic; mats then holds (hi, lo) float pairs.
+template <typename T, bool DF>
 __global__ void __launch_bounds__(kChunkThreads)
 k_chunk(typename C2T<T>::type *__restrict__ psi, const ChunkArgs a, const KOp *__restrict__ ops,
         const T *__restrict__ mats, int *__restrict__ err) {
@@ -34,6 +34,7 @@ k_chunk(typename C2T<T>::type *__restrict__ psi, const ChunkArgs a, const KOp *_
     __shared__ int abort_flag;
     __shared__ KOp s_op;
     __shared__ T s_m[kMaxOpReals];
+    __shared__ double s_fb[DF ? kMaxOpReals : 1];
     const uint32_t nruns = 1u << (a.m - a.c0);
     const uint32_t run_bytes = (uint32_t)sizeof(V) << a.c0;
     const uint32_t tile_bytes = (uint32_t)sizeof(V) << a.m;
@@ -57,12 +58,10 @@ k_chunk(typename C2T<T>::type *__restrict__ psi, const ChunkArgs a, const KOp *_
             for (int j = 0; j < a.nlh; j++) off |= (uint64_t)((r >> j) & 1u) << a.lhigh[j];
             ptx::bulk_g2s(tile + ((uint64_t)r << a.c0), psi + (base | off), run_bytes, &bar);
         }
-        long long spins = 0;
-        while (!ptx::mbar_try_wait(&bar, phase)) {
-            if (++spins > kWaitLimit) {
-                abort_flag = 1;
-                break;
-            }
+        if (!ptx::mbar_wait_bounded(&bar, phase, ptx::kWaitLimitNs)) {
+            abort_flag = 1;
+            // copies may still be in flight: one more bounded wait before leaving
+            ptx::mbar_wait_bounded(&bar, phase, ptx::kWaitLimitNs);
         }
         phase ^= 1u;
         __syncthreads();
@@ -70,7 +69,20 @@ k_chunk(typename C2T<T>::type *__restrict__ psi, const ChunkArgs a, const KOp *_
             if (threadIdx.x == 0) atomicExch(err, QS_ERR_TIMEOUT);
             break;
         }
-        apply_ops_tile<T>(tile, ops, a.n_ops, mats, a.m, s_op, s_m);
+        if constexpr (DF) {
+            const df::F2 *mp = (const df::F2 *)mats;
+            df::F2 *sp = (df::F2 *)s_m;
+            for (int i = 0; i < a.n_ops; i++) {
+                if (threadIdx.x == 0) s_op = ops[i];
+                __syncthreads();
+                for (int j = threadIdx.x; j < s_op.nmat; j += blockDim.x) sp[j] = mp[s_op.mat + j];
+                __syncthreads();
+                apply_op_smem_df((double2 *)tile, s_op, sp, s_fb, a.m);
+                __syncthreads();
+            }
+        } else {
+            apply_ops_tile<T>(tile, ops, a.n_ops, mats, a.m, s_op, s_m);
+        }
         ptx::fence_proxy_async_smem();
         __syncthreads();
         for (uint32_t r = threadIdx.x; r < nruns; r += blockDim.x) {
@@ -85,19 +97,30 @@ k_chunk(typename C2T<T>::type *__restrict__ psi, const ChunkArgs a, const KOp *_
     ptx::bulk_wait_all();
 }
 
-template <typename T>
+template <typename T, bool DF>
 void launch_t(DeviceState &st, const ChunkArgs &a, const std::vector<KOp> &kops, const std::vector<double> &mats) {
-    std::vector<T> tm(std::max<size_t>(mats.size(), 2));
-    for (size_t i = 0; i < mats.size(); i++) tm[i] = (T)mats[i];
     const KOp *d_ops = (const KOp *)upload_params(st, kops.data(), kops.size() * sizeof(KOp));
-    const T *d_m = (const T *)upload_params(st, tm.data(), tm.size() * sizeof(T));
+    const T *d_m;
+    if constexpr (DF) {
+        // every real as a (hi, lo) float pair, same indices as the FP64 table
+        std::vector<float> pm(2 * std::max<size_t>(mats.size(), 1));
+        for (size_t i = 0; i < mats.size(); i++) {
+            pm[2 * i] = (float)mats[i];
+            pm[2 * i + 1] = (float)(mats[i] - (double)pm[2 * i]);
+        }
+        d_m = (const T *)upload_params(st, pm.data(), pm.size() * sizeof(float));
+    } else {
+        std::vector<T> tm(std::max<size_t>(mats.size(), 2));
+        for (size_t i = 0; i < mats.size(); i++) tm[i] = (T)mats[i];
+        d_m = (const T *)upload_params(st, tm.data(), tm.size() * sizeof(T));
+    }
     using V = typename C2T<T>::type;
     const size_t smem = sizeof(V) << a.m;
-    auto kern = k_chunk<T>;
-    static bool attr_set[2] = {false, false};
-    if (!attr_set[sizeof(T) == 8]) {
+    auto kern = k_chunk<T, DF>;
+    static bool attr_set = false;
+    if (!attr_set) {
         QS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-        attr_set[sizeof(T) == 8] = true;
+        attr_set = true;
     }
     const int grid = persistent_grid((const void *)kern, kChunkThreads, smem, a.n_tiles);
     kern<<<grid, kChunkThreads, smem, st.stream>>>((V *)st.psi, a, d_ops, d_m, st.dev_err);
@@ -122,8 +145,12 @@ void launch_chunk_pass(DeviceState &st, uint64_t lmask, const std::vector<KOp> &
     const size_t B = st.dtype == QS_C128 ? 16 : 8;
     if ((B << a.c0) % 16 != 0) fail(QS_ERR_INVALID, "chunk runs must be multiples of 16 bytes");
     if ((B << a.m) > 200 * 1024) fail(QS_ERR_INVALID, "chunk tile exceeds shared memory");
-    if (st.dtype == QS_C128) launch_t<double>(st, a, kops, mats);
-    else launch_t<float>(st, a, kops, mats);
+    if (st.dtype == QS_C128) {
+        if (st.prec == QS_PREC_DF32) launch_t<double, true>(st, a, kops, mats);
+        else launch_t<double, false>(st, a, kops, mats);
+    } else {
+        launch_t<float, false>(st, a, kops, mats);
+    }
 }
 
 }  // namespace qs

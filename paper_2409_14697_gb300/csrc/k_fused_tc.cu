@@ -1,0 +1,302 @@
+// K3: fused dense blocks on the tensor cores (tcgen05), inside in-cache chunk passes.
+//
+// Gate fusion (QueenV2 Sec. II-B, Sec. III-A tier 5) merges runs of gates into one dense
+// 2^k x 2^k block; applying it to every group of 2^k amplitudes (Eq. 2/3 generalised) is a
+// complex matrix product over all groups.  Written over the reals with interleaved
+// (re, im) columns it is the real GEMM
+//     Y[g][2r + c] = sum_{s, c'} X[g][2s + c'] R[2r + c][2s + c'],
+//     R = [[Re G, -Im G], [Im G, Re G]] per complex entry,
+// with M = groups, N = K = 2^(k+1).  A complex64 chunk tile of 2^m amplitudes (m = 13)
+// holds 2^(m-k) groups, i.e. 2^(m-k-7) MMA row tiles of 128 groups.
+//
+// Per tile: every thread owns one group (one TMEM lane) and writes its 2^(k+1) reals into
+// TMEM with tcgen05.st, split into TF32 high and low parts (x = hi + lo, hi = x with the
+// low 13 mantissa bits cleared); one thread issues tcgen05.mma kind::tf32 with A in TMEM
+// and B = R (hi and lo parts, K-major canonical layout) in shared memory:
+// D = A_hi B_hi + A_hi B_lo + A_lo B_hi (3xTF32 split products, FP32 accumulation in TMEM);
+// the MMAs are committed to an mbarrier; each thread reads its row of D back with
+// tcgen05.ld and writes the group's new amplitudes into the tile.  TMEM: 512 columns
+// (A_hi, A_lo and D, 3 x 2^(m+1) / 128 <= 384 columns, rounded up), one CTA per SM.
+#include <algorithm>
+#include <cstring>
+
+#include "chunk.h"
+#include "kops.cuh"
+#include "ptx.cuh"
+#include "tc.cuh"
+#include "tile_ops.cuh"
+
+namespace qs {
+namespace {
+
+constexpr int kTcThreads = 256;
+constexpr uint32_t kTmemCols = 512;
+
+__device__ __forceinline__ uint32_t tf32_hi(float x) { return __float_as_uint(x) & 0xFFFFE000u; }
+
+// Applies one F_TC op to the tile.  bh/bl: B hi/lo parts in shared memory.
+__device__ void tc_apply(float2 *tile, const KOp &op, const float *bh, const float *bl, uint32_t tmem,
+                         uint64_t *bar, uint32_t &mma_phase, int m, int *abort_flag) {
+    const int k = op.k;
+    const int D = 1 << k;             // amplitudes per group
+    const int K2 = 2 * D;             // reals per group (GEMM K and N)
+    const int G = 1 << (m - k);       // groups in the tile
+    const int RT = G >> 7;            // 128-group row tiles
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int wg = warp >> 2, wq = warp & 3;
+    const uint32_t lane_off = (uint32_t)(32 * wq) << 16;
+    // TMEM column layout
+    const uint32_t col_ah = 0, col_al = (uint32_t)(RT * K2), col_d = (uint32_t)(2 * RT * K2);
+    int sorted[8];
+    for (int j = 0; j < k; j++) sorted[j] = op.pos[j];
+    for (int a = 1; a < k; a++)
+        for (int b = a; b > 0 && sorted[b - 1] > sorted[b]; b--) {
+            const int t = sorted[b]; sorted[b] = sorted[b - 1]; sorted[b - 1] = t;
+        }
+    auto group_base = [&](uint32_t g) {
+        uint32_t x = g;
+        for (int j = 0; j < k; j++) {
+            const int b = sorted[j];
+            x = ((x >> b) << (b + 1)) | (x & ((1u << b) - 1u));
+        }
+        return x;
+    };
+    auto amp_off = [&](int s) {
+        uint32_t o = 0;
+        for (int j = 0; j < k; j++) o |= (uint32_t)((s >> (k - 1 - j)) & 1) << op.pos[j];
+        return o;
+    };
+    // 1. A operand into TMEM (hi and lo parts)
+    for (int t = wg; t < RT; t += 2) {
+        const uint32_t base = group_base((uint32_t)(t * 128 + 32 * wq + lane));
+        for (int c = 0; c < K2 / 16; c++) {
+            uint32_t vh[16], vl[16];
+#pragma unroll
+            for (int i = 0; i < 8; i++) {
+                const float2 a = tile[base | amp_off(8 * c + i)];
+                const uint32_t hr = tf32_hi(a.x), hi = tf32_hi(a.y);
+                vh[2 * i] = hr;
+                vh[2 * i + 1] = hi;
+                vl[2 * i] = __float_as_uint(a.x - __uint_as_float(hr));
+                vl[2 * i + 1] = __float_as_uint(a.y - __uint_as_float(hi));
+            }
+            tc::st16(tmem + lane_off + col_ah + (uint32_t)(t * K2 + 16 * c), vh);
+            tc::st16(tmem + lane_off + col_al + (uint32_t)(t * K2 + 16 * c), vl);
+        }
+    }
+    tc::wait_st();
+    tc::fence_before();
+    __syncthreads();
+    tc::fence_after();
+    // 2. MMAs (one thread): D = Ah Bh + Ah Bl + Al Bh, K = 8 per instruction
+    if (threadIdx.x == 0) {
+        const uint32_t idesc = tc::idesc_tf32(128, K2);
+        const uint32_t lbo = 128, sbo = (uint32_t)(K2 / 4) * 128;
+        for (int t = 0; t < RT; t++) {
+            const uint32_t d = tmem + col_d + (uint32_t)(t * K2);
+            for (int s = 0; s < K2 / 8; s++) {
+                const uint32_t ah = tmem + col_ah + (uint32_t)(t * K2 + 8 * s);
+                const uint32_t al = tmem + col_al + (uint32_t)(t * K2 + 8 * s);
+                const uint64_t dbh = tc::sdesc(bh + 64 * s, lbo, sbo);  // 2 core matrices = 256 B per K-step
+                const uint64_t dbl = tc::sdesc(bl + 64 * s, lbo, sbo);
+                tc::mma_tf32_ta(d, ah, dbh, idesc, s > 0 ? 1u : 0u);
+                tc::mma_tf32_ta(d, ah, dbl, idesc, 1u);
+                tc::mma_tf32_ta(d, al, dbh, idesc, 1u);
+            }
+        }
+        tc::commit(bar);
+    }
+    if (!ptx::mbar_wait_bounded(bar, mma_phase, ptx::kWaitLimitNs)) {
+        *abort_flag = 1;
+        // MMAs may still be in flight: one more bounded wait before TMEM is released
+        ptx::mbar_wait_bounded(bar, mma_phase, ptx::kWaitLimitNs);
+    }
+    mma_phase ^= 1u;
+    tc::fence_after();
+    // 3. D back into the tile
+    for (int t = wg; t < RT; t += 2) {
+        const uint32_t base = group_base((uint32_t)(t * 128 + 32 * wq + lane));
+        for (int c = 0; c < K2 / 16; c++) {
+            uint32_t v[16];
+            tc::ld16(tmem + lane_off + col_d + (uint32_t)(t * K2 + 16 * c), v);
+            tc::wait_ld();
+#pragma unroll
+            for (int i = 0; i < 8; i++)
+                tile[base | amp_off(8 * c + i)] = make_float2(__uint_as_float(v[2 * i]), __uint_as_float(v[2 * i + 1]));
+        }
+    }
+    tc::fence_before();
+    __syncthreads();
+    tc::fence_after();
+}
+
+__global__ void __launch_bounds__(kTcThreads, 1)
+k_chunk_tc(float2 *__restrict__ psi, const ChunkArgs a, const KOp *__restrict__ ops, const float *__restrict__ mats,
+           const float *__restrict__ bmats, uint32_t b_floats, int *__restrict__ err) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    float2 *tile = (float2 *)smem_raw;
+    float *bh = (float *)(smem_raw + ((size_t)8 << a.m));
+    float *bl = bh + b_floats;
+    __shared__ uint64_t bar_load, bar_mma;
+    __shared__ uint32_t s_tmem;
+    __shared__ int abort_flag;
+    __shared__ int s_loaded;
+    __shared__ KOp s_op;
+    __shared__ float s_m[kMaxOpReals];
+    const uint32_t nruns = 1u << (a.m - a.c0);
+    const uint32_t run_bytes = 8u << a.c0;
+    const uint32_t tile_bytes = 8u << a.m;
+    if (threadIdx.x == 0) {
+        ptx::mbar_init(&bar_load, 1);
+        ptx::mbar_init(&bar_mma, 1);
+        ptx::fence_mbar_init();
+        abort_flag = 0;
+        s_loaded = -1;
+    }
+    if (threadIdx.x < 32) {
+        tc::alloc(&s_tmem, kTmemCols);
+        tc::relinquish();
+    }
+    tc::fence_before();
+    __syncthreads();
+    tc::fence_after();
+    const uint32_t tmem = s_tmem;
+    uint32_t load_phase = 0, mma_phase = 0;
+    for (uint64_t t = blockIdx.x; t < a.n_tiles; t += gridDim.x) {
+        uint64_t base = t << a.c0;
+        for (int j = 0; j < a.nlh; j++) {
+            const int b = a.lhigh[j];
+            base = ((base >> b) << (b + 1)) | (base & ((1ull << b) - 1ull));
+        }
+        if (threadIdx.x == 0) ptx::mbar_arrive_expect_tx(&bar_load, tile_bytes);
+        __syncthreads();
+        for (uint32_t r = threadIdx.x; r < nruns; r += blockDim.x) {
+            uint64_t off = 0;
+            for (int j = 0; j < a.nlh; j++) off |= (uint64_t)((r >> j) & 1u) << a.lhigh[j];
+            ptx::bulk_g2s(tile + ((uint64_t)r << a.c0), psi + (base | off), run_bytes, &bar_load);
+        }
+        if (!ptx::mbar_wait_bounded(&bar_load, load_phase, ptx::kWaitLimitNs)) {
+            abort_flag = 1;
+            ptx::mbar_wait_bounded(&bar_load, load_phase, ptx::kWaitLimitNs);
+        }
+        load_phase ^= 1u;
+        __syncthreads();
+        if (abort_flag) break;
+        for (int i = 0; i < a.n_ops; i++) {
+            if (threadIdx.x == 0) s_op = ops[i];
+            __syncthreads();
+            if (s_op.fkind == F_TC) {
+                if (s_loaded != i) {
+                    const float4 *src = (const float4 *)(bmats + s_op.mat);
+                    float4 *dst = (float4 *)bh;
+                    const int n4 = s_op.nmat / 4;   // hi then lo, contiguous
+                    for (int j = threadIdx.x; j < n4; j += blockDim.x) {
+                        const int half = j >= n4 / 2;
+                        float4 *d = half ? (float4 *)bl + (j - n4 / 2) : dst + j;
+                        *d = src[j];
+                    }
+                    ptx::fence_proxy_async_smem();  // generic writes -> read by the MMA (async proxy)
+                    __syncthreads();
+                    if (threadIdx.x == 0) s_loaded = i;
+                }
+                __syncthreads();
+                tc_apply(tile, s_op, bh, bl, tmem, &bar_mma, mma_phase, a.m, &abort_flag);
+                if (abort_flag) break;
+            } else {
+                for (int j = threadIdx.x; j < s_op.nmat; j += blockDim.x) s_m[j] = mats[s_op.mat + j];
+                __syncthreads();
+                apply_op_smem<float>(tile, s_op, s_m, a.m);
+                __syncthreads();
+            }
+        }
+        __syncthreads();
+        if (abort_flag) break;
+        ptx::fence_proxy_async_smem();
+        __syncthreads();
+        for (uint32_t r = threadIdx.x; r < nruns; r += blockDim.x) {
+            uint64_t off = 0;
+            for (int j = 0; j < a.nlh; j++) off |= (uint64_t)((r >> j) & 1u) << a.lhigh[j];
+            ptx::bulk_s2g(psi + (base | off), tile + ((uint64_t)r << a.c0), run_bytes);
+        }
+        ptx::bulk_commit();
+        ptx::bulk_wait_read_all();
+        __syncthreads();
+    }
+    ptx::bulk_wait_all();
+    if (abort_flag && threadIdx.x == 0) atomicExch(err, QS_ERR_TIMEOUT);
+    tc::fence_before();
+    __syncthreads();
+    tc::fence_after();
+    if (threadIdx.x < 32) tc::dealloc(tmem, kTmemCols);
+}
+
+}  // namespace
+
+bool tc_available(int m, int k) { return k >= 4 && k <= 6 && m >= k + 7 && m <= 13; }
+
+void launch_chunk_pass_tc(DeviceState &st, uint64_t lmask, const std::vector<KOp> &kops,
+                          const std::vector<double> &mats, const std::vector<float> &bmats, uint32_t b_floats) {
+    ChunkArgs a{};
+    const int n = st.n;
+    a.m = __builtin_popcountll(lmask);
+    a.c0 = 0;
+    while (a.c0 < n && ((lmask >> a.c0) & 1ull)) a.c0++;
+    a.nlh = 0;
+    for (int b = a.c0; b < n; b++)
+        if ((lmask >> b) & 1ull) a.lhigh[a.nlh++] = b;
+    a.n_tiles = 1ull << (n - a.m);
+    a.n_ops = (int)kops.size();
+    if (st.dtype != QS_C64) fail(QS_ERR_UNSUPPORTED, "tensor-core blocks run on complex64 states");
+    if ((8u << a.c0) % 16 != 0) fail(QS_ERR_INVALID, "chunk runs must be multiples of 16 bytes");
+    std::vector<float> tm(std::max<size_t>(mats.size(), 2));
+    for (size_t i = 0; i < mats.size(); i++) tm[i] = (float)mats[i];
+    const KOp *d_ops = (const KOp *)upload_params(st, kops.data(), kops.size() * sizeof(KOp));
+    const float *d_m = (const float *)upload_params(st, tm.data(), tm.size() * sizeof(float));
+    const float *d_b = (const float *)upload_params(st, bmats.data(), bmats.size() * sizeof(float));
+    // tile + B hi + B lo; at least 120 KB so that one CTA (and one TMEM owner) runs per SM
+    size_t smem = ((size_t)8 << a.m) + 2 * (size_t)b_floats * sizeof(float);
+    smem = std::max<size_t>(smem, 120 * 1024);
+    if (smem > 220 * 1024) fail(QS_ERR_INVALID, "tensor-core chunk pass exceeds shared memory");
+    static bool attr = false;
+    if (!attr) {
+        QS_CUDA(cudaFuncSetAttribute(k_chunk_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024));
+        attr = true;
+    }
+    const int grid = persistent_grid((const void *)k_chunk_tc, kTcThreads, smem, a.n_tiles);
+    k_chunk_tc<<<grid, kTcThreads, smem, st.stream>>>((float2 *)st.psi, a, d_ops, d_m, d_b, b_floats, st.dev_err);
+    QS_CUDA(cudaGetLastError());
+    count_launch();
+}
+
+// B = R (2D x 2D real form of the complex D x D block, interleaved re/im ordering) split
+// into TF32 hi and lo parts, each stored in the K-major canonical no-swizzle layout:
+// element (n, kk) at (n/8)*SBO + (kk/4)*128 + (n%8)*16 + (kk%4)*4 bytes, SBO = (2D/4)*128.
+void build_tc_operand(const std::vector<cd> &G, int k, std::vector<float> &out, int &off, int &count) {
+    const int D = 1 << k, K2 = 2 * D;
+    const size_t nf = (size_t)K2 * K2;
+    off = (int)out.size();
+    out.resize(out.size() + 2 * nf, 0.0f);
+    float *hi = out.data() + off, *lo = hi + nf;
+    const size_t sbo_f = (size_t)(K2 / 4) * 32;  // floats per 8-row group
+    for (int n = 0; n < K2; n++)
+        for (int kk = 0; kk < K2; kk++) {
+            const int r = n >> 1, cr = n & 1, s = kk >> 1, cs = kk & 1;
+            const cd g = G[(size_t)r * D + s];
+            double v;
+            if (cr == 0) v = cs == 0 ? g.real() : -g.imag();
+            else v = cs == 0 ? g.imag() : g.real();
+            const float f = (float)v;
+            uint32_t bits;
+            std::memcpy(&bits, &f, 4);
+            bits &= 0xFFFFE000u;
+            float h;
+            std::memcpy(&h, &bits, 4);
+            const float l = (float)(v - (double)h);
+            const size_t idx = (size_t)(n / 8) * sbo_f + (size_t)(kk / 4) * 32 + (size_t)(n % 8) * 4 + (kk % 4);
+            hi[idx] = h;
+            lo[idx] = l;
+        }
+    count = (int)(2 * nf);
+}
+
+}  // namespace qs

@@ -174,6 +174,13 @@ k_sel_hist(const V *__restrict__ psi, uint64_t n, const SelState *__restrict__ s
         if (h[i]) atomicAdd(&hist[i], (unsigned long long)h[i]);
 }
 
+__global__ void k_sel_init(SelState *st, unsigned long long K) {
+    st->prefix = 0ull;
+    st->need = K;
+    st->shift = 0;
+    st->pad = 0;
+}
+
 // Picks the digit holding the need-th largest key among the matching ones.
 __global__ void k_sel_pick(SelState *st, unsigned long long *hist, int shift) {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
@@ -320,24 +327,40 @@ void launch_scale(DeviceState &st, double f) {
     count_launch();
 }
 
-void reduce_expz(DeviceState &st, double *norm, double *expz) {
+size_t scratch_expz_bytes(int n) {
+    const int cb = chunk_bits(n);
+    const uint64_t nblk = 1ull << (n - cb);
+    return (nblk * (cb + 1) + n + 1) * sizeof(double);
+}
+
+// Norm and <Z_q> into out_dev (n + 1 doubles); the partials use st.scratch.
+static void expz_launch(DeviceState &st, bool bits, double *out_dev) {
     const int n = st.n;
     const int cb = chunk_bits(n);
     const int tb = std::min(cb, 8);
     const uint64_t nblk = 1ull << (n - cb);
-    const bool bits = expz != nullptr;
-    const size_t part_elems = nblk * (cb + 1);
-    ensure_scratch(st, (part_elems + n + 1) * sizeof(double));
+    ensure_scratch(st, scratch_expz_bytes(n));
     double *part = (double *)st.scratch;
-    double *out = part + part_elems;
     if (st.dtype == QS_C128)
         k_expz_part<double2><<<(unsigned)nblk, 1 << tb, 0, st.stream>>>((const double2 *)st.psi, cb, tb, bits, part);
     else
         k_expz_part<float2><<<(unsigned)nblk, 1 << tb, 0, st.stream>>>((const float2 *)st.psi, cb, tb, bits, part);
     QS_CUDA(cudaGetLastError());
-    k_expz_final<<<bits ? n + 1 : 1, 256, 0, st.stream>>>(part, nblk, cb, n, out);
+    k_expz_final<<<bits ? n + 1 : 1, 256, 0, st.stream>>>(part, nblk, cb, n, out_dev);
     QS_CUDA(cudaGetLastError());
     count_launch(2);
+}
+
+void reduce_expz_async(DeviceState &st, double *out_dev) { expz_launch(st, true, out_dev); }
+
+void reduce_expz(DeviceState &st, double *norm, double *expz) {
+    const int n = st.n;
+    const bool bits = expz != nullptr;
+    ensure_scratch(st, scratch_expz_bytes(n));
+    const int cb = chunk_bits(n);
+    const uint64_t nblk = 1ull << (n - cb);
+    double *out = (double *)st.scratch + nblk * (cb + 1);
+    expz_launch(st, bits, out);
     std::vector<double> h(n + 1);
     QS_CUDA(cudaMemcpyAsync(h.data(), out, sizeof(double) * (bits ? n + 1 : 1), cudaMemcpyDeviceToHost, st.stream));
     QS_CUDA(cudaStreamSynchronize(st.stream));
@@ -346,30 +369,48 @@ void reduce_expz(DeviceState &st, double *norm, double *expz) {
         for (int q = 0; q < n; q++) expz[q] = h[1 + q];
 }
 
-void top_k(DeviceState &st, uint32_t K, uint64_t *idx, double *amp) {
+namespace {
+struct TopkLayout {
+    size_t o_sel, o_hist, o_tie, o_gt, o_key, o_idx, o_oidx, o_oamp, total;
+};
+TopkLayout topk_layout(int n, uint32_t K) {
+    const int cb = std::min(n, 12);
+    const uint64_t nblk = (1ull << n) >> cb;
+    TopkLayout L{};
+    size_t off = 0;
+    auto carve = [&](size_t bytes) { size_t o = off; off += (bytes + 255) & ~size_t(255); return o; };
+    L.o_sel = carve(sizeof(SelState));
+    L.o_hist = carve(sizeof(unsigned long long) * kBins);
+    L.o_tie = carve(sizeof(unsigned int) * nblk);
+    L.o_gt = carve(sizeof(unsigned int));
+    L.o_key = carve(sizeof(unsigned long long) * K);
+    L.o_idx = carve(sizeof(unsigned long long) * K);
+    L.o_oidx = carve(sizeof(unsigned long long) * K);
+    L.o_oamp = carve(sizeof(double) * 2 * K);
+    L.total = off;
+    return L;
+}
+}  // namespace
+
+size_t scratch_topk_bytes(int n, uint32_t k) { return topk_layout(n, k).total; }
+
+// Launches the whole top-K pipeline; results to idx_dev / amp_dev (device).
+void top_k_async(DeviceState &st, uint32_t K, uint64_t *idx_dev, double *amp_dev) {
     const int n = st.n;
     const uint64_t N = 1ull << n;
     if (K == 0) return;
     if (K > N || K > 4096) fail(QS_ERR_INVALID, "top-k: k exceeds min(2^n, 4096)");
     const int cb = std::min(n, 12);
     const uint64_t nblk = N >> cb;
-    // scratch layout
-    size_t off = 0;
-    auto carve = [&](size_t bytes) { size_t o = off; off += (bytes + 255) & ~size_t(255); return o; };
-    const size_t o_sel = carve(sizeof(SelState));
-    const size_t o_hist = carve(sizeof(unsigned long long) * kBins);
-    const size_t o_tie = carve(sizeof(unsigned int) * nblk);
-    const size_t o_gt = carve(sizeof(unsigned int));
-    const size_t o_key = carve(sizeof(unsigned long long) * K);
-    const size_t o_idx = carve(sizeof(unsigned long long) * K);
-    const size_t o_oidx = carve(sizeof(unsigned long long) * K);
-    const size_t o_oamp = carve(sizeof(double) * 2 * K);
-    ensure_scratch(st, off);
+    const TopkLayout TL = topk_layout(n, K);
+    const size_t o_sel = TL.o_sel, o_hist = TL.o_hist, o_tie = TL.o_tie, o_gt = TL.o_gt, o_key = TL.o_key,
+                 o_idx = TL.o_idx;
+    ensure_scratch(st, TL.total);
     char *base = (char *)st.scratch;
     SelState *sel = (SelState *)(base + o_sel);
     unsigned long long *hist = (unsigned long long *)(base + o_hist);
-    SelState init{0ull, (unsigned long long)K, 0, 0};
-    QS_CUDA(cudaMemcpyAsync(sel, &init, sizeof(init), cudaMemcpyHostToDevice, st.stream));
+    k_sel_init<<<1, 1, 0, st.stream>>>(sel, (unsigned long long)K);
+    count_launch();
     QS_CUDA(cudaMemsetAsync(hist, 0, sizeof(unsigned long long) * kBins, st.stream));
     QS_CUDA(cudaMemsetAsync(base + o_gt, 0, sizeof(unsigned int), st.stream));
     const int grid = (int)std::min<uint64_t>((N + 255) / 256, (uint64_t)device_sm_count() * 8);
@@ -402,8 +443,8 @@ void top_k(DeviceState &st, uint32_t K, uint64_t *idx, double *amp) {
     while (P < (int)K) P <<= 1;
     P = std::max(P, 2);
     const size_t smem = sizeof(unsigned long long) * 2 * P;
-    unsigned long long *oidx = (unsigned long long *)(base + o_oidx);
-    double *oamp = (double *)(base + o_oamp);
+    unsigned long long *oidx = (unsigned long long *)idx_dev;
+    double *oamp = amp_dev;
     if (st.dtype == QS_C128) {
         auto kern = k_topk_sort<double2>;
         QS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -415,11 +456,21 @@ void top_k(DeviceState &st, uint32_t K, uint64_t *idx, double *amp) {
     }
     QS_CUDA(cudaGetLastError());
     count_launch(4);
+}
+
+void top_k(DeviceState &st, uint32_t K, uint64_t *idx, double *amp) {
+    if (K == 0) return;
+    if ((uint64_t)K > (1ull << st.n) || K > 4096) fail(QS_ERR_INVALID, "top-k: k exceeds min(2^n, 4096)");
+    const TopkLayout TL = topk_layout(st.n, K);
+    ensure_scratch(st, TL.total);
+    char *base = (char *)st.scratch;
+    uint64_t *oidx = (uint64_t *)(base + TL.o_oidx);
+    double *oamp = (double *)(base + TL.o_oamp);
+    top_k_async(st, K, oidx, oamp);
     QS_CUDA(cudaMemcpyAsync(idx, oidx, sizeof(uint64_t) * K, cudaMemcpyDeviceToHost, st.stream));
     QS_CUDA(cudaMemcpyAsync(amp, oamp, sizeof(double) * 2 * K, cudaMemcpyDeviceToHost, st.stream));
     QS_CUDA(cudaStreamSynchronize(st.stream));
 }
-
 
 // ---------------------------------------------------------------------------------
 // Allocation-free variant of the norm / <Z_q> reduction.

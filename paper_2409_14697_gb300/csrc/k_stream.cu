@@ -17,6 +17,7 @@
 #include <map>
 #include <tuple>
 
+#include "dfmath.cuh"
 #include "kgeom.h"
 #include "kops.cuh"
 #include "qs_internal.h"
@@ -86,6 +87,106 @@ template <typename T> struct FDense2 {
     T m[32];
     template <int L> __device__ void operator()(Amp<T, L> *v) const { f_dense2<T, L>(v, m); }
 };
+
+// ---- complex128 functors with double-float (FP32 pair) arithmetic ---------------
+// Matrix entries arrive as (hi, lo) float pairs split on the host; amplitudes are split
+// and re-joined in the kernel (dfmath.cuh).  Same group structure as the FP64 functors.
+using df::F2;
+
+__device__ __forceinline__ F2 neg(F2 a) { return F2{-a.h, -a.l}; }
+
+// y = m0 * x0 + m1 * x1, complex, compensated
+__device__ __forceinline__ void df_cdot2(double &yr, double &yi, const F2 *m0, F2 x0r, F2 x0i, const F2 *m1,
+                                         F2 x1r, F2 x1i) {
+    df::Acc a = df::mul(m0[0], x0r);
+    df::mac(a, neg(m0[1]), x0i);
+    df::mac(a, m1[0], x1r);
+    df::mac(a, neg(m1[1]), x1i);
+    df::Acc b = df::mul(m0[0], x0i);
+    df::mac(b, m0[1], x0r);
+    df::mac(b, m1[0], x1i);
+    df::mac(b, m1[1], x1r);
+    yr = df::result(a);
+    yi = df::result(b);
+}
+
+// y = d * x, complex, compensated
+__device__ __forceinline__ void df_cmul(double &yr, double &yi, const F2 *d, F2 xr, F2 xi) {
+    df::Acc a = df::mul(d[0], xr);
+    df::mac(a, neg(d[1]), xi);
+    df::Acc b = df::mul(d[0], xi);
+    df::mac(b, d[1], xr);
+    yr = df::result(a);
+    yi = df::result(b);
+}
+
+struct FHDF {
+    static constexpr int NT = 2;
+    F2 r;
+    template <int L> __device__ void operator()(Amp<double, L> *v) const {
+        const F2 ar = df::split(v[0].r[0]), ai = df::split(v[0].i[0]);
+        const F2 br = df::split(v[1].r[0]), bi = df::split(v[1].i[0]);
+        v[0].r[0] = df::result(df::scale(df::add(ar, br), r));
+        v[0].i[0] = df::result(df::scale(df::add(ai, bi), r));
+        v[1].r[0] = df::result(df::scale(df::sub(ar, br), r));
+        v[1].i[0] = df::result(df::scale(df::sub(ai, bi), r));
+    }
+};
+struct FDense1DF {
+    static constexpr int NT = 2;
+    F2 m[8];
+    template <int L> __device__ void operator()(Amp<double, L> *v) const {
+        const F2 x0r = df::split(v[0].r[0]), x0i = df::split(v[0].i[0]);
+        const F2 x1r = df::split(v[1].r[0]), x1i = df::split(v[1].i[0]);
+        df_cdot2(v[0].r[0], v[0].i[0], m + 0, x0r, x0i, m + 2, x1r, x1i);
+        df_cdot2(v[1].r[0], v[1].i[0], m + 4, x0r, x0i, m + 6, x1r, x1i);
+    }
+};
+template <int NTT> struct FDiagDF {
+    static constexpr int NT = NTT;
+    F2 d[2 * NTT];
+    template <int L> __device__ void operator()(Amp<double, L> *v) const {
+#pragma unroll
+        for (int t = 0; t < NTT; t++) {
+            const F2 xr = df::split(v[t].r[0]), xi = df::split(v[t].i[0]);
+            df_cmul(v[t].r[0], v[t].i[0], d + 2 * t, xr, xi);
+        }
+    }
+};
+struct FDense2DF {
+    static constexpr int NT = 4;
+    F2 m[32];
+    template <int L> __device__ void operator()(Amp<double, L> *v) const {
+        F2 xr[4], xi[4];
+#pragma unroll
+        for (int t = 0; t < 4; t++) {
+            xr[t] = df::split(v[t].r[0]);
+            xi[t] = df::split(v[t].i[0]);
+        }
+#pragma unroll
+        for (int r = 0; r < 4; r++) {
+            const F2 *row = m + 8 * r;
+            df::Acc a = df::mul(row[0], xr[0]);
+            df::Acc b = df::mul(row[0], xi[0]);
+            df::mac(a, neg(row[1]), xi[0]);
+            df::mac(b, row[1], xr[0]);
+#pragma unroll
+            for (int c = 1; c < 4; c++) {
+                df::mac(a, row[2 * c], xr[c]);
+                df::mac(a, neg(row[2 * c + 1]), xi[c]);
+                df::mac(b, row[2 * c], xi[c]);
+                df::mac(b, row[2 * c + 1], xr[c]);
+            }
+            v[r].r[0] = df::result(a);
+            v[r].i[0] = df::result(b);
+        }
+    }
+};
+
+void split_host(double v, F2 &o) {
+    o.h = (float)v;
+    o.l = (float)(v - (double)o.h);
+}
 
 constexpr int kThreads = 256;
 
@@ -262,6 +363,29 @@ void load_m(T *dst, const std::vector<double> &mats, const KOp &k) {
     for (int i = 0; i < k.nmat; i++) dst[i] = (T)mats[k.mat + i];
 }
 
+template <typename F, int N>
+void load_pairs(F &f, F2 (&dst)[N], const std::vector<double> &mats, const KOp &k) {
+    for (int i = 0; i < k.nmat && i < N; i++) split_host(mats[k.mat + i], dst[i]);
+}
+
+// complex128 with double-float arithmetic; returns false for kinds it does not cover
+bool launch_df(DeviceState &st, const KOp &k, const std::vector<double> &mats) {
+    switch (k.fkind) {
+    case F_H: {
+        FHDF f;
+        split_host(1.0 / std::sqrt(2.0), f.r);
+        dispatch_elem<double>(st, k, f);
+        return true;
+    }
+    case F_DENSE1: { FDense1DF f; load_pairs(f, f.m, mats, k); dispatch_elem<double>(st, k, f); return true; }
+    case F_DIAG1: { FDiagDF<2> f; load_pairs(f, f.d, mats, k); dispatch_elem<double>(st, k, f); return true; }
+    case F_PHASE: { FDiagDF<1> f; load_pairs(f, f.d, mats, k); dispatch_elem<double>(st, k, f); return true; }
+    case F_DIAG2: { FDiagDF<4> f; load_pairs(f, f.d, mats, k); dispatch_elem<double>(st, k, f); return true; }
+    case F_DENSE2: { FDense2DF f; load_pairs(f, f.m, mats, k); dispatch_elem<double>(st, k, f); return true; }
+    default: return false;
+    }
+}
+
 template <typename T>
 void launch_typed(DeviceState &st, const Op &op) {
     const int n = st.n;
@@ -269,6 +393,9 @@ void launch_typed(DeviceState &st, const Op &op) {
     for (int i = 0; i < 64; i++) ident[i] = i;
     std::vector<double> mats;
     const KOp k = make_kop(op, ident.data(), mats);
+    if constexpr (std::is_same<T, double>::value) {
+        if (st.prec == QS_PREC_DF32 && launch_df(st, k, mats)) return;
+    }
     switch (k.fkind) {
     case F_H: {
         FH<T> f;

@@ -25,13 +25,47 @@ namespace {
 
 // Ops the shared-memory path applies: dense blocks up to 4 qubits (512 matrix reals)
 // and diagonals up to 8 qubits.
-bool chunkable(const Op &op) {
-    if (op.kind == K_DENSE) return op.k <= 4;
+bool chunkable(const Op &op, const PlanParams &pp) {
+    if (op.kind == K_DENSE) return op.k <= 4 || (pp.tc && tc_available(pp.m, op.k));
     if (op.kind == K_DIAG) return op.k <= 8;
     return true;
 }
 
 }  // namespace
+
+// Launches one chunk pass over lmask applying `fused` (tensor cores where allowed).
+void launch_pass_ops(DeviceState &st, uint64_t lmask, const std::vector<Op> &fused, bool use_tc) {
+    const int n = st.n;
+    int pos[64] = {0};
+    int r = 0;
+    for (int b = 0; b < n; b++)
+        if ((lmask >> b) & 1ull) pos[b] = r++;
+    const int m = r;
+    std::vector<KOp> kops;
+    std::vector<double> mats;
+    std::vector<float> bmats;
+    uint32_t b_floats = 0;
+    bool any_tc = false;
+    for (const Op &op : fused) {
+        if (use_tc && op.kind == K_DENSE && tc_available(m, op.k)) {
+            KOp k{};
+            k.fkind = F_TC;
+            k.k = op.k;
+            for (int j = 0; j < op.k; j++) k.pos[j] = pos[op.q[j]];
+            int off = 0, cnt = 0;
+            build_tc_operand(op.m, op.k, bmats, off, cnt);
+            k.mat = off;
+            k.nmat = cnt;
+            b_floats = std::max<uint32_t>(b_floats, (uint32_t)(cnt / 2));
+            kops.push_back(k);
+            any_tc = true;
+        } else {
+            kops.push_back(make_kop(op, pos, mats));
+        }
+    }
+    if (any_tc) launch_chunk_pass_tc(st, lmask, kops, mats, bmats, b_floats);
+    else launch_chunk_pass(st, lmask, kops, mats);
+}
 
 PlanParams plan_params(const DeviceState &st, const qs_options &o) {
     PlanParams p;
@@ -45,6 +79,12 @@ PlanParams plan_params(const DeviceState &st, const qs_options &o) {
     // FP64 is 1/72 of FP32 on GB300: for complex128 a fused block must not add flops;
     // complex64 arithmetic is cheap next to a shared-memory sweep of the tile
     p.sweep_flops = c128 ? 1.0 : 24.0;
+    // complex64 with fusion width 4..6: dense blocks go to the tensor cores (K3)
+    p.tc = !c128 && o.fuse_k >= 4 && tc_available(p.m, std::min(o.fuse_k, 6));
+    if (p.tc) {
+        p.fuse_k = std::min(o.fuse_k, 6);
+        p.sweep_flops = 1e30;  // fuse whenever the block fits: its cost is on the tensor pipe
+    }
     return p;
 }
 
@@ -63,7 +103,7 @@ std::vector<Pass> make_plan(const std::vector<Op> &ops, int n, const PlanParams 
             if (done[i]) continue;
             const Op &op = ops[i];
             const uint64_t qm = op.qmask();
-            if (!chunkable(op)) {
+            if (!chunkable(op, pp)) {
                 if (pass.ops.empty() && !(qm & blocked)) {
                     pass.stream = true;
                     pass.ops.push_back((int)i);
@@ -129,14 +169,7 @@ void run_planned(DeviceState &st, const std::vector<Op> &ops, const qs_options &
         pops.reserve(p.ops.size());
         for (int i : p.ops) pops.push_back(ops[i]);
         const std::vector<Op> fused = fuse_ops(pops, pp.fuse_k, pp.sweep_flops);
-        int pos[64] = {0};
-        int r = 0;
-        for (int b = 0; b < n; b++)
-            if ((p.lmask >> b) & 1ull) pos[b] = r++;
-        std::vector<KOp> kops;
-        std::vector<double> mats;
-        for (const Op &op : fused) kops.push_back(make_kop(op, pos, mats));
-        launch_chunk_pass(st, p.lmask, kops, mats);
+        launch_pass_ops(st, p.lmask, fused, pp.tc);
         stats.passes++;
         stats.bytes += 2.0 * B * (double)(1ull << n);
         n_ops += (int64_t)fused.size();

@@ -11,6 +11,7 @@ struct PlanParams {
     int c;       // low qubits always local (contiguous runs of 2^c amplitudes)
     int fuse_k;  // fusion width inside a pass
     double sweep_flops;  // fusion cost gate (see fuse_ops)
+    bool tc;             // complex64 blocks of 4..6 qubits run on the tensor cores
 };
 
 struct Pass {
@@ -22,6 +23,8 @@ struct Pass {
 PlanParams plan_params(const DeviceState &st, const qs_options &o);
 // Greedy dependency-respecting partition of ops into passes.
 std::vector<Pass> make_plan(const std::vector<Op> &ops, int n, const PlanParams &pp);
+// One chunk pass over lmask applying ops already fused (tensor cores if use_tc).
+void launch_pass_ops(DeviceState &st, uint64_t lmask, const std::vector<Op> &fused, bool use_tc);
 // Plans `ops` into passes and launches them on st.stream, filling stats.
 void run_planned(DeviceState &st, const std::vector<Op> &ops, const qs_options &o, qs_stats &stats);
 

@@ -7,6 +7,15 @@
 namespace qs {
 namespace ptx {
 
+__device__ __forceinline__ uint64_t globaltimer_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Default limit of every device-side wait: about two seconds of wall time.
+constexpr long long kWaitLimitNs = 2000000000ll;
+
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
     return (uint32_t)__cvta_generic_to_shared(p);
 }
@@ -35,6 +44,15 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
         : "r"(smem_u32(bar)), "r"(parity)
         : "memory");
     return ok != 0;
+}
+
+// Waits for the phase with this parity; false if it did not complete within limit_ns.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity, long long limit_ns) {
+    const uint64_t t0 = globaltimer_ns();
+    while (!mbar_try_wait(bar, parity)) {
+        if ((long long)(globaltimer_ns() - t0) > limit_ns) return false;
+    }
+    return true;
 }
 
 // Global -> shared bulk copy; completion is signalled on `bar` as transaction bytes.

@@ -7,6 +7,7 @@
 #include <cstdint>
 #include <string>
 #include <type_traits>
+#include <utility>
 #include <vector>
 
 #include "qs.h"
@@ -90,6 +91,7 @@ struct DeviceState {
     void *psi = nullptr;  // amplitudes
     int n = 0;            // qubits
     int dtype = QS_C128;
+    int prec = QS_PREC_FP64;  // complex128 arithmetic: QS_PREC_FP64 or QS_PREC_DF32
     cudaStream_t stream = nullptr;
     // scratch for reductions (owned by the state)
     void *scratch = nullptr;
@@ -102,9 +104,17 @@ struct DeviceState {
     size_t arena_used = 0;
     int arena_cur = 0;
     cudaEvent_t arena_ev[2] = {nullptr, nullptr};
+    std::vector<std::pair<void *, void *>> arena_retired[2];  // outgrown (device, pinned) buffers
     // device error word written by bounded waits (QS_ERR_TIMEOUT), checked on sync
     int *dev_err = nullptr;
 };
+
+// Executor: runs one lowered circuit on d.stream (mode, fusion and planning from o).
+void run_circuit(DeviceState &d, const std::vector<Op> &ops, const qs_options &o, qs_stats &st);
+// Frees everything DeviceState owns except psi and the stream.
+void free_device_state(DeviceState &d);
+void arena_begin(DeviceState &st);
+void arena_end(DeviceState &st);
 
 // Launchers (kernels live in the .cu files).  All are asynchronous on st.stream.
 void launch_stream_op(DeviceState &st, const Op &op);           // K1, one op, one pass
@@ -113,6 +123,14 @@ void launch_scale(DeviceState &st, double f);                   // psi *= f
 // Reductions (K4).  expz may be null (norm only).  Results are copied to host.
 void reduce_expz(DeviceState &st, double *norm, double *expz);
 void top_k(DeviceState &st, uint32_t k, uint64_t *idx, double *amp);
+// Asynchronous forms (no host wait): results land in device memory.  reduce_expz_async
+// writes out_dev[0] = squared norm, out_dev[1 + q] = <Z_q>; top_k_async writes k indices
+// and 2k doubles.  Scratch must have been sized by the caller (scratch_expz_bytes /
+// scratch_topk_bytes) before any capture or concurrent use.
+void reduce_expz_async(DeviceState &st, double *out_dev);
+void top_k_async(DeviceState &st, uint32_t k, uint64_t *idx_dev, double *amp_dev);
+size_t scratch_expz_bytes(int n);
+size_t scratch_topk_bytes(int n, uint32_t k);
 
 // Algorithmic bytes of one streaming application of op on an n-qubit state.
 double stream_bytes(const Op &op, int n, int dtype);

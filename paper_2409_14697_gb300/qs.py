@@ -20,7 +20,7 @@ QS_C64, QS_C128 = 1, 2
 QS_OK, QS_NOT_READY = 0, 1
 QS_ERR_INVALID, QS_ERR_NOMEM, QS_ERR_CUDA, QS_ERR_TIMEOUT, QS_ERR_BUSY, QS_ERR_UNSUPPORTED = -1, -2, -3, -4, -5, -6
 QS_MODE_AUTO, QS_MODE_GATE, QS_MODE_CHUNK, QS_MODE_FUSED = 0, 1, 2, 3
-QS_PREC_DEFAULT, QS_PREC_FP64 = 0, 1
+QS_PREC_DEFAULT, QS_PREC_FP64, QS_PREC_DF32 = 0, 1, 2
 
 GATE_TYPES = {
     "h": 0, "x": 1, "y": 2, "z": 3, "s": 4, "t": 5,
@@ -61,6 +61,23 @@ class qs_batch_stats(ctypes.Structure):
                 ("grid", ctypes.c_int64), ("state_bytes", ctypes.c_uint64)]
 
 
+class qs_server_config(ctypes.Structure):
+    _fields_ = [("hbm_budget_bytes", ctypes.c_uint64), ("max_slots", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 5)]
+
+
+class qs_request(ctypes.Structure):
+    _fields_ = [("n_qubits", ctypes.c_int32), ("dtype", ctypes.c_int32),
+                ("gates", ctypes.POINTER(qs_gate)), ("n_gates", ctypes.c_uint64),
+                ("init_amplitudes", ctypes.c_void_p), ("top_k", ctypes.c_uint32), ("mode", ctypes.c_int32)]
+
+
+class qs_server_stats_t(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_int64), ("completed", ctypes.c_int64), ("failed", ctypes.c_int64),
+                ("queued", ctypes.c_int64), ("in_flight", ctypes.c_int64),
+                ("bytes_in_use", ctypes.c_uint64), ("peak_bytes", ctypes.c_uint64)]
+
+
 _lib = None
 _VP = ctypes.c_void_p
 _DP = ctypes.POINTER(ctypes.c_double)
@@ -90,6 +107,12 @@ _SIGS = {
     "qs_top_amplitudes": (ctypes.c_int, [_VP, ctypes.c_uint32, _U64P, _DP]),
     "qs_renormalize": (ctypes.c_int, [_VP, _DP]),
     "qs_expectation_z_noalloc": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int, _VP, _DP, _DP]),
+    "qs_server_create": (ctypes.c_int, [ctypes.POINTER(qs_server_config), ctypes.POINTER(_VP)]),
+    "qs_submit": (ctypes.c_int, [_VP, ctypes.POINTER(qs_request), ctypes.POINTER(ctypes.c_uint64)]),
+    "qs_poll": (ctypes.c_int, [_VP, ctypes.c_uint64, _DP, _DP, _U64P, _DP, _DP]),
+    "qs_server_stats": (ctypes.c_int, [_VP, ctypes.POINTER(qs_server_stats_t)]),
+    "qs_server_drain": (ctypes.c_int, [_VP, ctypes.c_double]),
+    "qs_server_destroy": (ctypes.c_int, [_VP]),
     "qs_batch_create": (ctypes.c_int, [ctypes.POINTER(qs_circuit), ctypes.c_size_t, ctypes.c_int,
                                        ctypes.POINTER(qs_options), ctypes.POINTER(_VP)]),
     "qs_batch_run": (ctypes.c_int, [_VP]),
@@ -287,6 +310,62 @@ def qs_renormalize(h) -> float:
     v = ctypes.c_double()
     _check(load().qs_renormalize(h, ctypes.byref(v)))
     return v.value
+
+
+# ---- serving ----------------------------------------------------------------------
+
+def qs_server_create(hbm_budget_bytes: int, max_slots: int = 8):
+    cfg = qs_server_config()
+    cfg.hbm_budget_bytes = int(hbm_budget_bytes)
+    cfg.max_slots = max_slots
+    h = _VP()
+    _check(load().qs_server_create(ctypes.byref(cfg), ctypes.byref(h)))
+    return h
+
+
+def qs_submit(sv, n_qubits: int, dtype: int, gates, top_k: int = 0, init=None, mode: int = QS_MODE_AUTO):
+    """Queues a request; returns its ticket (the library copies gates and init)."""
+    recs = gates if isinstance(gates, ctypes.Array) else gate_records(gates)
+    r = qs_request()
+    r.n_qubits, r.dtype = n_qubits, dtype
+    r.gates = ctypes.cast(recs, ctypes.POINTER(qs_gate))
+    r.n_gates = len(gates)
+    if init is not None:
+        init = np.ascontiguousarray(init, dtype=np.complex64 if dtype == QS_C64 else np.complex128)
+        r.init_amplitudes = init.ctypes.data
+    r.top_k, r.mode = top_k, mode
+    t = ctypes.c_uint64()
+    _check(load().qs_submit(sv, ctypes.byref(r), ctypes.byref(t)))
+    return t.value
+
+
+def qs_poll(sv, ticket: int, n_qubits: int, top_k: int):
+    """None while running; else dict(expz, norm, top_idx, top_amp, latency_s)."""
+    ez = np.zeros(max(n_qubits, 1))
+    nrm = ctypes.c_double()
+    idx = np.zeros(max(top_k, 1), dtype=np.uint64)
+    amp = np.zeros(max(top_k, 1), dtype=np.complex128)
+    lat = ctypes.c_double()
+    rc = _check(load().qs_poll(sv, ticket, ez.ctypes.data_as(_DP), ctypes.byref(nrm), idx.ctypes.data_as(_U64P),
+                               amp.ctypes.data_as(_DP), ctypes.byref(lat)))
+    if rc == QS_NOT_READY:
+        return None
+    return {"expz": ez[:n_qubits], "norm": nrm.value, "top_idx": idx[:top_k], "top_amp": amp[:top_k],
+            "latency_s": lat.value}
+
+
+def qs_server_stats(sv) -> dict:
+    s = qs_server_stats_t()
+    _check(load().qs_server_stats(sv, ctypes.byref(s)))
+    return {f: getattr(s, f) for f, _ in qs_server_stats_t._fields_}
+
+
+def qs_server_drain(sv, timeout_s: float = 600.0):
+    _check(load().qs_server_drain(sv, timeout_s))
+
+
+def qs_server_destroy(sv):
+    _check(load().qs_server_destroy(sv))
 
 
 # ---- batched execution ----------------------------------------------------------
