@@ -54,6 +54,8 @@ def parse():
     ap.add_argument("--count", type=int, default=0, help="circuits/requests for batched/served")
     ap.add_argument("--fuse-k", type=int, default=5)
     ap.add_argument("--rate", type=float, default=2000.0)
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "df32"],
+                    help="complex128 arithmetic of the served workload")
     return ap.parse_args()
 
 
@@ -340,7 +342,7 @@ def run_e2e(qs, h, host_in, recs, opts, n, B, n_gates, world):
 
 # FP64 instructions per amplitude (FMA-class issues, one FP64 pipe slot each) of the
 # complex128 streaming updates; the other gate types issue none on the FP64 pipe.
-FP64_INSTR_PER_AMP = {"h": 4, "rz": 4, "u3": 8, "cu3": 4}
+FP64_INSTR_PER_AMP = {"h": 3, "rz": 4, "u3": 8, "cu3": 4}
 # FP64 pipe peak: 2 FP64 instructions per clock per SM (ncu: the U3 kernel at 0.526e12/s
 # keeps the FP64 pipe 83.8 % busy) x 152 SMs x 2.07 GHz max SM clock = 1.26 TFLOP/s.
 FP64_PEAK_TINSTR = 2 * 152 * 2.07e9 / 1e12
@@ -461,7 +463,8 @@ def wl_circuits33(args):
     stream = torch.cuda.Stream()
     h = qs.qs_create(n, qs.QS_C64)
     qs.qs_set_stream(h, stream.cuda_stream)
-    out = {"workload": f"{n}-qubit circuits, complex64, fused k={args.fuse_k} (tensor cores)", "qubits": n,
+    tc = "tensor cores" if args.fuse_k >= 4 else "SIMT"
+    out = {"workload": f"{n}-qubit circuits, complex64, fused k={args.fuse_k} ({tc})", "qubits": n,
            "state_bytes": 8 << n, "circuits": {}}
     opts = qs.options(fuse_k=args.fuse_k)
     fams = {"brickwork40": inputs.brickwork(n, 40, seed=3), "qaoa_p4": inputs.qaoa_3regular(n, p=4, seed=3),
@@ -478,11 +481,13 @@ def wl_circuits33(args):
         nrm = qs.qs_norm(h)
         qs.qs_apply_circuit(h, inv, opts)
         a0 = qs.qs_amplitudes(h, 0, 1)[0]
+        nrm2 = qs.qs_norm(h)
         out["circuits"][name] = {"gates": len(gates), "ms": round(ms, 2), "passes": st["passes"],
                                  "ops_after_fuse": st["ops_after_fuse"],
                                  "gates_per_s": round(len(gates) * 1e3 / ms, 1),
                                  "pass_GBps": round(st["bytes"] / (ms * 1e-3) / 1e9, 1),
-                                 "norm_minus_1": nrm - 1.0, "inverse_infidelity": 1.0 - abs(complex(a0)) ** 2}
+                                 "norm_minus_1": nrm - 1.0, "inverse_infidelity": 1.0 - abs(complex(a0)) ** 2,
+                                 "inverse_infidelity_normalised": 1.0 - abs(complex(a0)) ** 2 / nrm2}
     qs.qs_destroy(h)
     return out
 
@@ -494,10 +499,16 @@ def wl_batched(args):
     import torch
     import oracle
     from paper_2409_14697_gb300 import inputs, qs
+    from paper_2409_14697_gb300 import autotune
     count = args.count or 4096
     circs = inputs.batched_circuits(count, seed=10)
+    # autotune chunk width and fusion width on a 256-circuit sample of the same mix
+    tt0 = time.perf_counter()
+    best, table = autotune.tune_batch(circs[:256], qs.QS_C64, path=os.path.join(
+        os.environ.get("TMPDIR", "/tmp"), "qsim_autotune_bench.json"))
+    tune_s = time.perf_counter() - tt0
     t0 = time.perf_counter()
-    b = qs.qs_batch_create(circs, qs.QS_C64, qs.options(fuse_k=2))
+    b = qs.qs_batch_create(circs, qs.QS_C64, qs.options(chunk_m=best["chunk_m"], fuse_k=best["fuse_k"]))
     build_s = time.perf_counter() - t0
     stream = torch.cuda.Stream()
     qs.qs_batch_set_stream(b, stream.cuda_stream)
@@ -530,14 +541,14 @@ def wl_batched(args):
             qs.qs_set_stream(hs[n], stream.cuda_stream)
         recs = qs.gate_records(g)
         qs.qs_reset(hs[n])
-        qs.qs_apply_circuit(hs[n], recs, qs.options(fuse_k=2))
+        qs.qs_apply_circuit(hs[n], recs, qs.options(fuse_k=best["fuse_k"]))
     torch.cuda.synchronize()
     for n, g in sub:
         recs = qs.gate_records(g)
 
         def one(h=hs[n], r=recs):
             qs.qs_reset(h)
-            qs.qs_apply_circuit(h, r, qs.options(fuse_k=2))
+            qs.qs_apply_circuit(h, r, qs.options(fuse_k=best["fuse_k"]))
         t_one += _event_ms(stream, one)
     for h in hs.values():
         qs.qs_destroy(h)
@@ -548,6 +559,8 @@ def wl_batched(args):
             "speedup_vs_one_at_a_time": round(count / (ms * 1e-3) / one_cps, 2),
             "passes": info["passes"], "work_items": info["work_items"], "grid": info["grid"],
             "state_bytes": info["state_bytes"], "host_build_s": round(build_s, 2),
+            "autotuned": best, "autotune_s": round(tune_s, 1),
+            "autotune_table_ms": {f"m{t['chunk_m']}k{t['fuse_k']}": t["ms"] for t in table},
             "oracle_sample": sample, "max_abs_err": max(errs), "max_infidelity": max(infid)}
 
 
@@ -576,6 +589,7 @@ def wl_served(args):
         init, gates = init_for(r)
         dt = qs.QS_C128 if r["dtype"] == "c128" else qs.QS_C64
         prepared.append((r["t"], r["n"], dt, qs.gate_records(gates), len(gates), init, min(1024, 1 << r["n"])))
+    prec = qs.QS_PREC_DF32 if args.precision == "df32" else qs.QS_PREC_FP64
     sv = qs.qs_server_create(150 * 10 ** 9, max_slots=8)
     lat, tickets = [], []
     t0 = time.perf_counter()
@@ -585,7 +599,7 @@ def wl_served(args):
         now = time.perf_counter() - t0
         while i < len(prepared) and prepared[i][0] <= now:
             t_arr, n, dt, recs, ng, init, k = prepared[i]
-            tk = qs.qs_submit(sv, n, dt, recs, top_k=k, init=init)
+            tk = qs.qs_submit(sv, n, dt, recs, top_k=k, init=init, precision=prec)
             pending[tk] = (n, k)
             i += 1
         done = []
@@ -613,7 +627,7 @@ def wl_served(args):
             qs.qs_reset(h)
         else:
             qs.qs_set_amplitudes(h, init)
-        qs.qs_apply_circuit(h, recs)
+        qs.qs_apply_circuit(h, recs, qs.options(precision=prec))
         qs.qs_expectation_z(h)
         qs.qs_top_amplitudes(h, k)
     seq_wall = time.perf_counter() - t1
@@ -621,7 +635,7 @@ def wl_served(args):
         qs.qs_destroy(h)
     lat = np.array(lat)
     return {"workload": f"served: {count} Poisson requests at {args.rate:g} req/s, n 10-30 log-uniform, "
-                        f"c64/c128, <Z_i> + top-1024, 150 GB budget, 8 slots",
+                        f"c64/c128 ({args.precision} for c128), <Z_i> + top-1024, 150 GB budget, 8 slots",
             "metric": "requests/s", "value": round(count / wall, 2), "p50_latency_s": round(float(np.percentile(lat, 50)), 4),
             "p99_latency_s": round(float(np.percentile(lat, 99)), 4), "mean_latency_s": round(float(lat.mean()), 4),
             "wall_s": round(wall, 2), "sequential_requests_per_s": round(count / seq_wall, 2),

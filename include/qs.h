@@ -112,6 +112,10 @@ typedef struct {
     int32_t fuse_k;       /* max qubits of a fused block (0: choose; 1 disables fusion) */
     int32_t chunk_m;      /* local qubits of a chunk pass (0: choose) */
     int32_t precision;    /* QS_PREC_* */
+    /* reserved[0], reserved[1]: batched-launch wait limit and test hook (qs_batch_create);
+     * reserved[2] = 1 turns off the norm-preserving correction after complex64 circuits that
+     * used tensor-core blocks (default on: the squared norm before the circuit is restored,
+     * which removes the small systematic shrink of FP32 accumulation inside the MMA). */
     int32_t reserved[4];
 } qs_options;
 
@@ -238,6 +242,8 @@ typedef struct {
     const void *init_amplitudes;   /* 2^n amplitudes of dtype (copied), or NULL for |0...0> */
     uint32_t top_k;                /* amplitudes to return, <= min(2^n, 4096) */
     int32_t mode;                  /* QS_MODE_* for the circuit */
+    int32_t precision;             /* QS_PREC_* for complex128 requests */
+    int32_t reserved;
 } qs_request;
 
 typedef struct {

@@ -194,6 +194,8 @@ void free_device_state(DeviceState &d) {
     }
     if (d.scratch) cudaFree(d.scratch);
     if (d.dev_err) cudaFree(d.dev_err);
+    if (d.dev_norms) cudaFree(d.dev_norms);
+    d.dev_norms = nullptr;
     d.scratch = nullptr;
     d.scratch_bytes = 0;
     d.dev_err = nullptr;

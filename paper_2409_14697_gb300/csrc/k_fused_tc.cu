@@ -32,11 +32,40 @@ namespace {
 constexpr int kTcThreads = 256;
 constexpr uint32_t kTmemCols = 512;
 
-__device__ __forceinline__ uint32_t tf32_hi(float x) { return __float_as_uint(x) & 0xFFFFE000u; }
+// Round a float to the nearest TF32 value (10 explicit mantissa bits; ties to even).
+// The tensor cores read only the top 19 bits of a TF32 operand, i.e. they truncate; an
+// operand that is already a TF32 value is read exactly, so rounding here keeps the split
+// x = hi + lo unbiased (truncation would bias every product toward zero and the state's
+// norm would drift over many blocks).
+__device__ __forceinline__ uint32_t tf32_rn(float x) {
+    const uint32_t b = __float_as_uint(x);
+    return (b + 0x0FFFu + ((b >> 13) & 1u)) & 0xFFFFE000u;
+}
 
-// Applies one F_TC op to the tile.  bh/bl: B hi/lo parts in shared memory.
-__device__ void tc_apply(float2 *tile, const KOp &op, const float *bh, const float *bl, uint32_t tmem,
-                         uint64_t *bar, uint32_t &mma_phase, int m, int *abort_flag) {
+// Rotates 8 complex values: out[j] = in[(j + sh) & 7] for sh in 0..7 (3 select stages).
+__device__ __forceinline__ void rot8(float2 (&v)[8], int sh) {
+#pragma unroll
+    for (int b = 0; b < 3; b++) {
+        const int k = 1 << b;
+        if ((sh >> b) & 1) {
+            float2 t[8];
+#pragma unroll
+            for (int j = 0; j < 8; j++) t[j] = v[(j + k) & 7];
+#pragma unroll
+            for (int j = 0; j < 8; j++) v[j] = t[j];
+        }
+    }
+}
+
+// Applies one F_TC op to the tile.  bh/bl: B hi/lo parts in shared memory; aoff: the op's
+// 2^k amplitude offsets inside a group (shared memory).
+//
+// Shared-memory access: lane l of a warp owns group g and visits the 8 amplitudes of each
+// chunk starting at (l & 7), so the 32 lanes of a warp touch 8 different offsets at a time
+// instead of 32 times the same bank when groups sit 2^k amplitudes apart; a 3-stage select
+// network puts the values back in column order for tcgen05.st (and the reverse for D).
+__device__ void tc_apply(float2 *tile, const KOp &op, const float *bh, const float *bl, const uint32_t *aoff,
+                         uint32_t tmem, uint64_t *bar, uint32_t &mma_phase, int m, int *abort_flag) {
     const int k = op.k;
     const int D = 1 << k;             // amplitudes per group
     const int K2 = 2 * D;             // reals per group (GEMM K and N)
@@ -45,40 +74,38 @@ __device__ void tc_apply(float2 *tile, const KOp &op, const float *bh, const flo
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int wg = warp >> 2, wq = warp & 3;
     const uint32_t lane_off = (uint32_t)(32 * wq) << 16;
+    const int rsh = lane & 7;
     // TMEM column layout
     const uint32_t col_ah = 0, col_al = (uint32_t)(RT * K2), col_d = (uint32_t)(2 * RT * K2);
+    // work split: with one row tile both warpgroups share it (even / odd column chunks)
+    const int t0 = RT >= 2 ? wg : 0, tstep = RT >= 2 ? 2 : 1;
+    const int c0 = RT >= 2 ? 0 : wg, cstep = RT >= 2 ? 1 : 2;
     int sorted[8];
     for (int j = 0; j < k; j++) sorted[j] = op.pos[j];
     for (int a = 1; a < k; a++)
         for (int b = a; b > 0 && sorted[b - 1] > sorted[b]; b--) {
             const int t = sorted[b]; sorted[b] = sorted[b - 1]; sorted[b - 1] = t;
         }
-    auto group_base = [&](uint32_t g) {
-        uint32_t x = g;
+    // 1. A operand into TMEM (hi and lo parts)
+    for (int t = t0; t < RT; t += tstep) {
+        uint32_t base = (uint32_t)(t * 128 + 32 * wq + lane);
         for (int j = 0; j < k; j++) {
             const int b = sorted[j];
-            x = ((x >> b) << (b + 1)) | (x & ((1u << b) - 1u));
+            base = ((base >> b) << (b + 1)) | (base & ((1u << b) - 1u));
         }
-        return x;
-    };
-    auto amp_off = [&](int s) {
-        uint32_t o = 0;
-        for (int j = 0; j < k; j++) o |= (uint32_t)((s >> (k - 1 - j)) & 1) << op.pos[j];
-        return o;
-    };
-    // 1. A operand into TMEM (hi and lo parts)
-    for (int t = wg; t < RT; t += 2) {
-        const uint32_t base = group_base((uint32_t)(t * 128 + 32 * wq + lane));
-        for (int c = 0; c < K2 / 16; c++) {
+        for (int c = c0; c < K2 / 16; c += cstep) {
+            float2 a[8];
+#pragma unroll
+            for (int i = 0; i < 8; i++) a[i] = tile[base | aoff[8 * c + ((i + rsh) & 7)]];
+            rot8(a, (8 - rsh) & 7);
             uint32_t vh[16], vl[16];
 #pragma unroll
             for (int i = 0; i < 8; i++) {
-                const float2 a = tile[base | amp_off(8 * c + i)];
-                const uint32_t hr = tf32_hi(a.x), hi = tf32_hi(a.y);
+                const uint32_t hr = tf32_rn(a[i].x), hi = tf32_rn(a[i].y);
                 vh[2 * i] = hr;
                 vh[2 * i + 1] = hi;
-                vl[2 * i] = __float_as_uint(a.x - __uint_as_float(hr));
-                vl[2 * i + 1] = __float_as_uint(a.y - __uint_as_float(hi));
+                vl[2 * i] = tf32_rn(__fsub_rn(a[i].x, __uint_as_float(hr)));
+                vl[2 * i + 1] = tf32_rn(__fsub_rn(a[i].y, __uint_as_float(hi)));
             }
             tc::st16(tmem + lane_off + col_ah + (uint32_t)(t * K2 + 16 * c), vh);
             tc::st16(tmem + lane_off + col_al + (uint32_t)(t * K2 + 16 * c), vl);
@@ -114,15 +141,22 @@ __device__ void tc_apply(float2 *tile, const KOp &op, const float *bh, const flo
     mma_phase ^= 1u;
     tc::fence_after();
     // 3. D back into the tile
-    for (int t = wg; t < RT; t += 2) {
-        const uint32_t base = group_base((uint32_t)(t * 128 + 32 * wq + lane));
-        for (int c = 0; c < K2 / 16; c++) {
+    for (int t = t0; t < RT; t += tstep) {
+        uint32_t base = (uint32_t)(t * 128 + 32 * wq + lane);
+        for (int j = 0; j < k; j++) {
+            const int b = sorted[j];
+            base = ((base >> b) << (b + 1)) | (base & ((1u << b) - 1u));
+        }
+        for (int c = c0; c < K2 / 16; c += cstep) {
             uint32_t v[16];
             tc::ld16(tmem + lane_off + col_d + (uint32_t)(t * K2 + 16 * c), v);
             tc::wait_ld();
+            float2 a[8];
 #pragma unroll
-            for (int i = 0; i < 8; i++)
-                tile[base | amp_off(8 * c + i)] = make_float2(__uint_as_float(v[2 * i]), __uint_as_float(v[2 * i + 1]));
+            for (int i = 0; i < 8; i++) a[i] = make_float2(__uint_as_float(v[2 * i]), __uint_as_float(v[2 * i + 1]));
+            rot8(a, rsh);
+#pragma unroll
+            for (int i = 0; i < 8; i++) tile[base | aoff[8 * c + ((i + rsh) & 7)]] = a[i];
         }
     }
     tc::fence_before();
@@ -132,7 +166,7 @@ __device__ void tc_apply(float2 *tile, const KOp &op, const float *bh, const flo
 
 __global__ void __launch_bounds__(kTcThreads, 1)
 k_chunk_tc(float2 *__restrict__ psi, const ChunkArgs a, const KOp *__restrict__ ops, const float *__restrict__ mats,
-           const float *__restrict__ bmats, uint32_t b_floats, int *__restrict__ err) {
+           const float *__restrict__ bmats, uint32_t b_floats, int b_resident, int *__restrict__ err) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     float2 *tile = (float2 *)smem_raw;
     float *bh = (float *)(smem_raw + ((size_t)8 << a.m));
@@ -143,6 +177,7 @@ k_chunk_tc(float2 *__restrict__ psi, const ChunkArgs a, const KOp *__restrict__ 
     __shared__ int s_loaded;
     __shared__ KOp s_op;
     __shared__ float s_m[kMaxOpReals];
+    __shared__ uint32_t s_aoff[64];
     const uint32_t nruns = 1u << (a.m - a.c0);
     const uint32_t run_bytes = 8u << a.c0;
     const uint32_t tile_bytes = 8u << a.m;
@@ -156,6 +191,13 @@ k_chunk_tc(float2 *__restrict__ psi, const ChunkArgs a, const KOp *__restrict__ 
     if (threadIdx.x < 32) {
         tc::alloc(&s_tmem, kTmemCols);
         tc::relinquish();
+    }
+    if (b_resident) {
+        // every B operand of the pass stays in shared memory for the whole kernel
+        const float4 *src = (const float4 *)bmats;
+        float4 *dst = (float4 *)bh;
+        for (uint32_t j = threadIdx.x; j < b_floats / 4; j += blockDim.x) dst[j] = src[j];
+        ptx::fence_proxy_async_smem();
     }
     tc::fence_before();
     __syncthreads();
@@ -186,7 +228,7 @@ k_chunk_tc(float2 *__restrict__ psi, const ChunkArgs a, const KOp *__restrict__ 
             if (threadIdx.x == 0) s_op = ops[i];
             __syncthreads();
             if (s_op.fkind == F_TC) {
-                if (s_loaded != i) {
+                if (!b_resident && s_loaded != i) {
                     const float4 *src = (const float4 *)(bmats + s_op.mat);
                     float4 *dst = (float4 *)bh;
                     const int n4 = s_op.nmat / 4;   // hi then lo, contiguous
@@ -199,8 +241,15 @@ k_chunk_tc(float2 *__restrict__ psi, const ChunkArgs a, const KOp *__restrict__ 
                     __syncthreads();
                     if (threadIdx.x == 0) s_loaded = i;
                 }
+                if (threadIdx.x < (1 << s_op.k)) {
+                    uint32_t o = 0;
+                    for (int j = 0; j < s_op.k; j++) o |= (uint32_t)((threadIdx.x >> (s_op.k - 1 - j)) & 1) << s_op.pos[j];
+                    s_aoff[threadIdx.x] = o;
+                }
                 __syncthreads();
-                tc_apply(tile, s_op, bh, bl, tmem, &bar_mma, mma_phase, a.m, &abort_flag);
+                const float *obh = b_resident ? bh + s_op.mat : bh;
+                const float *obl = b_resident ? obh + s_op.nmat / 2 : bl;
+                tc_apply(tile, s_op, obh, obl, s_aoff, tmem, &bar_mma, mma_phase, a.m, &abort_flag);
                 if (abort_flag) break;
             } else {
                 for (int j = threadIdx.x; j < s_op.nmat; j += blockDim.x) s_m[j] = mats[s_op.mat + j];
@@ -253,8 +302,13 @@ void launch_chunk_pass_tc(DeviceState &st, uint64_t lmask, const std::vector<KOp
     const KOp *d_ops = (const KOp *)upload_params(st, kops.data(), kops.size() * sizeof(KOp));
     const float *d_m = (const float *)upload_params(st, tm.data(), tm.size() * sizeof(float));
     const float *d_b = (const float *)upload_params(st, bmats.data(), bmats.size() * sizeof(float));
-    // tile + B hi + B lo; at least 120 KB so that one CTA (and one TMEM owner) runs per SM
-    size_t smem = ((size_t)8 << a.m) + 2 * (size_t)b_floats * sizeof(float);
+    // B operands: all resident if they fit next to the tile, else one op's at a time
+    const size_t tile_bytes = (size_t)8 << a.m;
+    const size_t all_b = bmats.size() * sizeof(float);
+    const int resident = tile_bytes + all_b <= 200 * 1024 ? 1 : 0;
+    const uint32_t bf = resident ? (uint32_t)bmats.size() : b_floats;
+    // tile + B; at least 120 KB so that one CTA (and one TMEM owner) runs per SM
+    size_t smem = tile_bytes + (resident ? all_b : 2 * (size_t)b_floats * sizeof(float));
     smem = std::max<size_t>(smem, 120 * 1024);
     if (smem > 220 * 1024) fail(QS_ERR_INVALID, "tensor-core chunk pass exceeds shared memory");
     static bool attr = false;
@@ -263,9 +317,20 @@ void launch_chunk_pass_tc(DeviceState &st, uint64_t lmask, const std::vector<KOp
         attr = true;
     }
     const int grid = persistent_grid((const void *)k_chunk_tc, kTcThreads, smem, a.n_tiles);
-    k_chunk_tc<<<grid, kTcThreads, smem, st.stream>>>((float2 *)st.psi, a, d_ops, d_m, d_b, b_floats, st.dev_err);
+    k_chunk_tc<<<grid, kTcThreads, smem, st.stream>>>((float2 *)st.psi, a, d_ops, d_m, d_b, bf, resident,
+                                                       st.dev_err);
     QS_CUDA(cudaGetLastError());
     count_launch();
+}
+
+// Nearest TF32 value of a float (ties to even), as on the device.
+static float tf32_round_host(float x) {
+    uint32_t b;
+    std::memcpy(&b, &x, 4);
+    b = (b + 0x0FFFu + ((b >> 13) & 1u)) & 0xFFFFE000u;
+    float r;
+    std::memcpy(&r, &b, 4);
+    return r;
 }
 
 // B = R (2D x 2D real form of the complex D x D block, interleaved re/im ordering) split
@@ -285,13 +350,8 @@ void build_tc_operand(const std::vector<cd> &G, int k, std::vector<float> &out, 
             double v;
             if (cr == 0) v = cs == 0 ? g.real() : -g.imag();
             else v = cs == 0 ? g.imag() : g.real();
-            const float f = (float)v;
-            uint32_t bits;
-            std::memcpy(&bits, &f, 4);
-            bits &= 0xFFFFE000u;
-            float h;
-            std::memcpy(&h, &bits, 4);
-            const float l = (float)(v - (double)h);
+            const float h = tf32_round_host((float)v);
+            const float l = tf32_round_host((float)(v - (double)h));
             const size_t idx = (size_t)(n / 8) * sbo_f + (size_t)(kk / 4) * 32 + (size_t)(n % 8) * 4 + (kk % 4);
             hi[idx] = h;
             lo[idx] = l;

@@ -126,6 +126,20 @@ __global__ void k_set_one(void *psi, int is_c128) {
     else ((float2 *)psi)[0] = make_float2(1.0f, 0.0f);
 }
 
+// psi *= sqrt(norms[0] / norms[1]) (both squared norms in device memory, FP64)
+template <typename V>
+__global__ void __launch_bounds__(256) k_scale_ratio(V *__restrict__ psi, uint64_t n, const double *__restrict__ norms) {
+    const double a = norms[0], b = norms[1];
+    if (!(a > 0.0) || !(b > 0.0)) return;
+    const double f = sqrt(a / b);
+    for (uint64_t i = (uint64_t)blockIdx.x * 256 + threadIdx.x; i < n; i += (uint64_t)gridDim.x * 256) {
+        V v = psi[i];
+        v.x = (decltype(v.x))((double)v.x * f);
+        v.y = (decltype(v.y))((double)v.y * f);
+        psi[i] = v;
+    }
+}
+
 template <typename V, typename S>
 __global__ void __launch_bounds__(256) k_scale(V *__restrict__ psi, uint64_t n, S f) {
     for (uint64_t i = (uint64_t)blockIdx.x * 256 + threadIdx.x; i < n; i += (uint64_t)gridDim.x * 256) {
@@ -352,6 +366,17 @@ static void expz_launch(DeviceState &st, bool bits, double *out_dev) {
 }
 
 void reduce_expz_async(DeviceState &st, double *out_dev) { expz_launch(st, true, out_dev); }
+
+void reduce_norm_async(DeviceState &st, double *out_dev) { expz_launch(st, false, out_dev); }
+
+void launch_scale_ratio(DeviceState &st, const double *norms_dev) {
+    const uint64_t n = 1ull << st.n;
+    const int grid = (int)std::min<uint64_t>((n + 255) / 256, (uint64_t)device_sm_count() * 8);
+    if (st.dtype == QS_C128) k_scale_ratio<double2><<<grid, 256, 0, st.stream>>>((double2 *)st.psi, n, norms_dev);
+    else k_scale_ratio<float2><<<grid, 256, 0, st.stream>>>((float2 *)st.psi, n, norms_dev);
+    QS_CUDA(cudaGetLastError());
+    count_launch();
+}
 
 void reduce_expz(DeviceState &st, double *norm, double *expz) {
     const int n = st.n;

@@ -154,6 +154,14 @@ void run_planned(DeviceState &st, const std::vector<Op> &ops, const qs_options &
         return;
     }
     const std::vector<Pass> plan = make_plan(ops, n, pp);
+    // Tensor-core blocks accumulate in FP32 inside the MMA with truncation toward zero, a
+    // small systematic shrink per block.  The circuit is unitary, so the FP64 squared norm
+    // before it is restored afterwards (three extra read passes and one write pass).
+    const bool correct_norm = pp.tc && o.reserved[2] == 0;
+    if (correct_norm) {
+        if (!st.dev_norms) QS_CUDA(cudaMalloc(&st.dev_norms, 2 * sizeof(double)));
+        reduce_norm_async(st, st.dev_norms);
+    }
     int64_t n_ops = 0;
     for (const Pass &p : plan) {
         if (p.stream) {
@@ -173,6 +181,11 @@ void run_planned(DeviceState &st, const std::vector<Op> &ops, const qs_options &
         stats.passes++;
         stats.bytes += 2.0 * B * (double)(1ull << n);
         n_ops += (int64_t)fused.size();
+    }
+    if (correct_norm) {
+        reduce_norm_async(st, st.dev_norms + 1);
+        launch_scale_ratio(st, st.dev_norms);
+        stats.bytes += 4.0 * B * (double)(1ull << n);
     }
     stats.ops_after_fuse = n_ops;
 }

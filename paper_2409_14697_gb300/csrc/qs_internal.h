@@ -107,6 +107,8 @@ struct DeviceState {
     std::vector<std::pair<void *, void *>> arena_retired[2];  // outgrown (device, pinned) buffers
     // device error word written by bounded waits (QS_ERR_TIMEOUT), checked on sync
     int *dev_err = nullptr;
+    // two FP64 squared norms (before / after) for the norm-preserving correction
+    double *dev_norms = nullptr;
 };
 
 // Executor: runs one lowered circuit on d.stream (mode, fusion and planning from o).
@@ -128,6 +130,9 @@ void top_k(DeviceState &st, uint32_t k, uint64_t *idx, double *amp);
 // and 2k doubles.  Scratch must have been sized by the caller (scratch_expz_bytes /
 // scratch_topk_bytes) before any capture or concurrent use.
 void reduce_expz_async(DeviceState &st, double *out_dev);
+// Squared norm into out_dev[0] (asynchronous); psi *= sqrt(norms[0] / norms[1]).
+void reduce_norm_async(DeviceState &st, double *out_dev);
+void launch_scale_ratio(DeviceState &st, const double *norms_dev);
 void top_k_async(DeviceState &st, uint32_t k, uint64_t *idx_dev, double *amp_dev);
 size_t scratch_expz_bytes(int n);
 size_t scratch_topk_bytes(int n, uint32_t k);

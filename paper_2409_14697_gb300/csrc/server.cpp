@@ -334,6 +334,7 @@ int qs_submit(qs_server *p, const qs_request *req, uint64_t *ticket) {
     r.top_k = req->top_k;
     r.opt = qs_options{};
     r.opt.mode = req->mode;
+    r.opt.precision = req->precision;
     r.t_submit = Clock::now();
     std::lock_guard<std::mutex> lk(S.mu);
     if (S.stop) fail(QS_ERR_BUSY, "server is shutting down");

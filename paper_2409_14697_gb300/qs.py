@@ -69,7 +69,8 @@ class qs_server_config(ctypes.Structure):
 class qs_request(ctypes.Structure):
     _fields_ = [("n_qubits", ctypes.c_int32), ("dtype", ctypes.c_int32),
                 ("gates", ctypes.POINTER(qs_gate)), ("n_gates", ctypes.c_uint64),
-                ("init_amplitudes", ctypes.c_void_p), ("top_k", ctypes.c_uint32), ("mode", ctypes.c_int32)]
+                ("init_amplitudes", ctypes.c_void_p), ("top_k", ctypes.c_uint32), ("mode", ctypes.c_int32),
+                ("precision", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class qs_server_stats_t(ctypes.Structure):
@@ -323,7 +324,8 @@ def qs_server_create(hbm_budget_bytes: int, max_slots: int = 8):
     return h
 
 
-def qs_submit(sv, n_qubits: int, dtype: int, gates, top_k: int = 0, init=None, mode: int = QS_MODE_AUTO):
+def qs_submit(sv, n_qubits: int, dtype: int, gates, top_k: int = 0, init=None, mode: int = QS_MODE_AUTO,
+              precision: int = QS_PREC_DEFAULT):
     """Queues a request; returns its ticket (the library copies gates and init)."""
     recs = gates if isinstance(gates, ctypes.Array) else gate_records(gates)
     r = qs_request()
@@ -333,7 +335,7 @@ def qs_submit(sv, n_qubits: int, dtype: int, gates, top_k: int = 0, init=None, m
     if init is not None:
         init = np.ascontiguousarray(init, dtype=np.complex64 if dtype == QS_C64 else np.complex128)
         r.init_amplitudes = init.ctypes.data
-    r.top_k, r.mode = top_k, mode
+    r.top_k, r.mode, r.precision = top_k, mode, precision
     t = ctypes.c_uint64()
     _check(load().qs_submit(sv, ctypes.byref(r), ctypes.byref(t)))
     return t.value
