@@ -54,6 +54,8 @@ def parse():
     ap.add_argument("--count", type=int, default=0, help="circuits/requests for batched/served")
     ap.add_argument("--fuse-k", type=int, default=5)
     ap.add_argument("--rate", type=float, default=2000.0)
+    ap.add_argument("--no-rgroups", action="store_true",
+                    help="complex64 passes: one shared-memory sweep per op (no register groups)")
     ap.add_argument("--precision", default="fp64", choices=["fp64", "df32"],
                     help="complex128 arithmetic of the served workload")
     return ap.parse_args()
@@ -467,6 +469,9 @@ def wl_circuits33(args):
     out = {"workload": f"{n}-qubit circuits, complex64, fused k={args.fuse_k} ({tc})", "qubits": n,
            "state_bytes": 8 << n, "circuits": {}}
     opts = qs.options(fuse_k=args.fuse_k)
+    if args.no_rgroups:
+        opts.reserved[3] = 1
+        out["workload"] += ", no register groups"
     fams = {"brickwork40": inputs.brickwork(n, 40, seed=3), "qaoa_p4": inputs.qaoa_3regular(n, p=4, seed=3),
             "tfim50": inputs.tfim(n, steps=50, dt=0.05)}
     for name, gates in fams.items():
@@ -508,7 +513,10 @@ def wl_batched(args):
         os.environ.get("TMPDIR", "/tmp"), "qsim_autotune_bench.json"))
     tune_s = time.perf_counter() - tt0
     t0 = time.perf_counter()
-    b = qs.qs_batch_create(circs, qs.QS_C64, qs.options(chunk_m=best["chunk_m"], fuse_k=best["fuse_k"]))
+    bo = qs.options(chunk_m=best["chunk_m"], fuse_k=best["fuse_k"])
+    if args.no_rgroups:
+        bo.reserved[3] = 1
+    b = qs.qs_batch_create(circs, qs.QS_C64, bo)
     build_s = time.perf_counter() - t0
     stream = torch.cuda.Stream()
     qs.qs_batch_set_stream(b, stream.cuda_stream)

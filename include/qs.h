@@ -115,7 +115,8 @@ typedef struct {
     /* reserved[0], reserved[1]: batched-launch wait limit and test hook (qs_batch_create);
      * reserved[2] = 1 turns off the norm-preserving correction after complex64 circuits that
      * used tensor-core blocks (default on: the squared norm before the circuit is restored,
-     * which removes the small systematic shrink of FP32 accumulation inside the MMA). */
+     * which removes the small systematic shrink of FP32 accumulation inside the MMA);
+     * reserved[3] = 1 turns off register grouping of small ops in complex64 passes. */
     int32_t reserved[4];
 } qs_options;
 

@@ -134,6 +134,7 @@ void run_circuit(DeviceState &d, const std::vector<Op> &ops, const qs_options &o
     if (o.precision != QS_PREC_DEFAULT && o.precision != QS_PREC_FP64 && o.precision != QS_PREC_DF32)
         fail(QS_ERR_INVALID, "unknown precision mode");
     d.prec = o.precision == QS_PREC_DF32 ? QS_PREC_DF32 : QS_PREC_FP64;
+    d.reg_groups = o.reserved[3] == 0;
     const uint64_t l0 = g_launches.load();
     arena_begin(d);
     const int mode = o.mode;

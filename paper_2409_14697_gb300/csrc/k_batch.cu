@@ -39,7 +39,7 @@ __device__ __forceinline__ void fence_proxy_async_global() {
 using ptx::globaltimer_ns;
 
 template <typename T>
-__global__ void __launch_bounds__(kBatchThreads)
+__global__ void __launch_bounds__(kBatchThreads, 2)
 k_batch(typename C2T<T>::type *__restrict__ states, const BatchPass *__restrict__ passes, int n_passes,
         uint64_t total_items, const KOp *__restrict__ ops, const T *__restrict__ mats,
         unsigned long long *__restrict__ counter, unsigned int *__restrict__ done, int *__restrict__ err,
@@ -230,6 +230,7 @@ void batch_build(Batch &b, const std::vector<std::vector<Op>> &circ_ops, const s
             std::vector<KOp> ko;
             std::vector<double> mt;
             for (const Op &op : fused) ko.push_back(make_kop(op, pos, mt));
+            if (!c128 && o.reserved[3] == 0) ko = group_registers(ko, mt, __builtin_popcountll(L));
             cp.kops.push_back(std::move(ko));
             cp.mats.push_back(std::move(mt));
             cp.lm.push_back(L);

@@ -24,7 +24,7 @@ constexpr int kChunkThreads = 256;
 
 // DF: complex128 with double-float arithmetic; mats then holds (hi, lo) float pairs.
 template <typename T, bool DF>
-__global__ void __launch_bounds__(kChunkThreads)
+__global__ void __launch_bounds__(kChunkThreads, 2)
 k_chunk(typename C2T<T>::type *__restrict__ psi, const ChunkArgs a, const KOp *__restrict__ ops,
         const T *__restrict__ mats, int *__restrict__ err) {
     using V = typename C2T<T>::type;

@@ -1,5 +1,6 @@
 // Host: lowered Op -> kernel-side KOp in a given index space, plus algorithmic bytes.
 #include <algorithm>
+#include <cmath>
 
 #include "kgeom.h"
 
@@ -137,6 +138,130 @@ KOp make_kop(const Op &op, const int *pos, std::vector<double> &mats) {
     }
     }
     fail(QS_ERR_INVALID, "unknown op kind");
+}
+
+namespace {
+
+bool rg_eligible(const KOp &k) {
+    switch (k.fkind) {
+    case F_H: case F_SWAP: case F_DENSE1: case F_DIAG1: case F_PHASE: case F_NEG: case F_DIAG2: case F_DENSE2:
+        return k.nf == 1 || k.nf == 2;
+    default:
+        return false;
+    }
+}
+
+// The op as a dense 2^nf x 2^nf matrix on its fixed bits (sub-index bit j <-> fb[j]),
+// obtained by applying it to every basis vector of one group.
+std::vector<cd> member_matrix(const KOp &k, const std::vector<double> &mats) {
+    const int nb = k.nf, D = 1 << nb;
+    auto sub = [&](uint64_t x) {
+        int s = 0;
+        for (int j = 0; j < nb; j++) s |= (int)((x >> k.fb[j]) & 1ull) << j;
+        return s;
+    };
+    auto mc = [&](int i) { return cd(mats[k.mat + 2 * i], mats[k.mat + 2 * i + 1]); };
+    std::vector<cd> M((size_t)D * D, 0.0);
+    for (int s0 = 0; s0 < D; s0++) {
+        std::vector<cd> v(D, 0.0);
+        v[s0] = 1.0;
+        cd a[4];
+        int idx[4];
+        for (int t = 0; t < k.nt; t++) {
+            idx[t] = sub(k.off[t] | k.set_mask);
+            a[t] = v[idx[t]];
+        }
+        cd y[4];
+        switch (k.fkind) {
+        case F_H: {
+            const double r = 1.0 / std::sqrt(2.0);
+            y[0] = (a[0] + a[1]) * r;
+            y[1] = (a[0] - a[1]) * r;
+            break;
+        }
+        case F_SWAP: y[0] = a[1]; y[1] = a[0]; break;
+        case F_DENSE1:
+            y[0] = mc(0) * a[0] + mc(1) * a[1];
+            y[1] = mc(2) * a[0] + mc(3) * a[1];
+            break;
+        case F_DIAG1: y[0] = mc(0) * a[0]; y[1] = mc(1) * a[1]; break;
+        case F_PHASE: y[0] = mc(0) * a[0]; break;
+        case F_NEG: y[0] = -a[0]; break;
+        case F_DIAG2:
+            for (int t = 0; t < 4; t++) y[t] = mc(t) * a[t];
+            break;
+        case F_DENSE2:
+            for (int r = 0; r < 4; r++) {
+                y[r] = 0.0;
+                for (int c = 0; c < 4; c++) y[r] += mc(4 * r + c) * a[c];
+            }
+            break;
+        default:
+            break;
+        }
+        for (int t = 0; t < k.nt; t++) v[idx[t]] = y[t];
+        for (int r = 0; r < D; r++) M[(size_t)r * D + s0] = v[r];
+    }
+    return M;
+}
+
+}  // namespace
+
+std::vector<KOp> group_registers(const std::vector<KOp> &in, std::vector<double> &mats, int m) {
+    if (m < 5) return in;
+    std::vector<KOp> out;
+    std::vector<const KOp *> members;
+    uint32_t pos_mask = 0;
+    int floats = 1;
+    constexpr int kBudget = 500;  // block floats (kMaxOpReals = 512)
+    auto flush = [&]() {
+        if (members.size() >= 2) {
+            KOp g{};
+            g.fkind = F_RGROUP;
+            g.k = 4;
+            uint32_t S = pos_mask;
+            for (int b = m - 1; b >= 0 && __builtin_popcount(S) < 4; b--) S |= 1u << b;  // pad from the top
+            int np = 0;
+            for (int b = 0; b < m; b++)
+                if ((S >> b) & 1u) g.pos[np++] = b;
+            g.mat = (int32_t)mats.size();
+            mats.push_back((double)members.size());
+            for (const KOp *k : members) {
+                int bits[2] = {0, 0};
+                for (int j = 0; j < k->nf; j++)
+                    for (int t = 0; t < 4; t++)
+                        if (g.pos[t] == k->fb[j]) bits[j] = t;
+                mats.push_back((double)(k->nf + 4 * bits[0] + 16 * bits[1]));
+                for (const cd &z : member_matrix(*k, mats)) {
+                    mats.push_back(z.real());
+                    mats.push_back(z.imag());
+                }
+            }
+            g.nmat = (int32_t)mats.size() - g.mat;
+            out.push_back(g);
+        } else {
+            for (const KOp *k : members) out.push_back(*k);
+        }
+        members.clear();
+        pos_mask = 0;
+        floats = 1;
+    };
+    for (const KOp &k : in) {
+        if (!rg_eligible(k)) {
+            flush();
+            out.push_back(k);
+            continue;
+        }
+        uint32_t km = 0;
+        for (int j = 0; j < k.nf; j++) km |= 1u << k.fb[j];
+        const int cost = 1 + 2 * (1 << (2 * k.nf));
+        if (__builtin_popcount(pos_mask | km) > 4 || floats + cost > kBudget) flush();
+        members.push_back(&k);
+        pos_mask |= km;
+        floats += cost;
+    }
+    flush();
+    return out;
 }
 
 double kop_touched_fraction(const KOp &k, int sector_bits) {

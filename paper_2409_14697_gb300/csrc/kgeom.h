@@ -11,6 +11,11 @@ namespace qs {
 // op's matrix entries are appended to `mats` (as re, im doubles; KOp.mat indexes them).
 KOp make_kop(const Op &op, const int *pos, std::vector<double> &mats);
 
+// complex64 passes: replaces runs of consecutive one- and two-bit ops whose positions fit
+// in 4 tile positions by F_RGROUP ops (applied in registers, one shared-memory sweep per
+// run); member matrices are appended to `mats`.  m = tile bits.
+std::vector<KOp> group_registers(const std::vector<KOp> &in, std::vector<double> &mats, int m);
+
 // Fraction of the state's bytes one streaming application reads and writes, counting
 // whole DRAM sectors of 2^sector_bits elements.
 double kop_touched_fraction(const KOp &k, int sector_bits);

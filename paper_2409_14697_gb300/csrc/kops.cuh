@@ -27,6 +27,7 @@ enum FKind : int32_t {
     F_DIAGK,     // diagonal on k qubits at positions pos[] (m: 2^(k+1) reals), every element
     F_DENSEK,    // dense 2^k x 2^k on positions pos[] (m: 2^(2k+1) reals), k = 3..6
     F_TC,        // dense block on the tensor cores (k = 4..6; mat/nmat index the B operand)
+    F_RGROUP,    // run of one- and two-bit ops inside 4 positions pos[0..3], applied in registers
 };
 
 // Host+device description of one op in a given index space (HBM amplitude/element

@@ -3,10 +3,12 @@
 //
 // The planner partitions the op sequence into passes.  A pass owns a set L of m local
 // qubits that always contains the low c qubits (so every tile is made of contiguous
-// runs of 2^c amplitudes in HBM) plus high qubits claimed greedily, in circuit order,
-// by the ops it accepts.  An op joins the pass if none of its qubits is blocked by an
-// earlier op left for a later pass and its qubits fit in L; otherwise its qubits become
-// blocked (ops on disjoint qubits commute, so later ops on other qubits may still join).
+// runs of 2^c amplitudes in HBM) plus high qubits taken by the ops it accepts.  An op
+// joins the pass if none of its qubits is blocked by an earlier op left for a later pass
+// and its qubits fit in L; otherwise its qubits become blocked (ops on disjoint qubits
+// commute, so later ops on other qubits may still join).  Several candidate passes are
+// built: unrestricted (high qubits claimed in circuit order) and restricted to each
+// window of m - c consecutive high qubits; the one that executes the most ops is kept.
 // Qubit reordering is logical: the pass's local qubits are mapped to tile positions by
 // a position table (the bidirectional qubit table of Sec. III-A) and the state is never
 // permuted in memory.  Inside a pass, consecutive ops are fused into dense blocks of at
@@ -63,6 +65,7 @@ void launch_pass_ops(DeviceState &st, uint64_t lmask, const std::vector<Op> &fus
             kops.push_back(make_kop(op, pos, mats));
         }
     }
+    if (st.dtype == QS_C64 && st.reg_groups) kops = group_registers(kops, mats, m);
     if (any_tc) launch_chunk_pass_tc(st, lmask, kops, mats, bmats, b_floats);
     else launch_chunk_pass(st, lmask, kops, mats);
 }
@@ -88,47 +91,80 @@ PlanParams plan_params(const DeviceState &st, const qs_options &o) {
     return p;
 }
 
+namespace {
+
+// One greedy pass from the first open op, local qubits restricted to low | allowed.
+// Returns the ops it takes (in order) and its local mask (unpadded).
+struct Trial {
+    std::vector<int> ops;
+    uint64_t L = 0;
+    bool stream = false;
+};
+
+Trial greedy_pass(const std::vector<Op> &ops, const std::vector<char> &done, size_t first, int n,
+                  const PlanParams &pp, uint64_t allowed) {
+    const uint64_t all = (n >= 64) ? ~0ull : ((1ull << n) - 1ull);
+    const uint64_t low = (1ull << pp.c) - 1ull;
+    Trial tr;
+    uint64_t L = low, blocked = 0;
+    for (size_t i = first; i < ops.size(); i++) {
+        if (done[i]) continue;
+        const Op &op = ops[i];
+        const uint64_t qm = op.qmask();
+        if (!chunkable(op, pp)) {
+            if (tr.ops.empty() && !(qm & blocked)) {
+                tr.stream = true;
+                tr.ops.push_back((int)i);
+            }
+            break;  // a non-chunkable op is a barrier for this pass
+        }
+        if (qm & blocked) {
+            blocked |= qm;
+        } else if ((qm & ~(low | allowed)) == 0 && __builtin_popcountll(L | qm) <= pp.m) {
+            L |= qm;
+            tr.ops.push_back((int)i);
+        } else {
+            blocked |= qm;
+        }
+        if ((blocked & all) == all) break;
+    }
+    tr.L = L;
+    return tr;
+}
+
+}  // namespace
+
 std::vector<Pass> make_plan(const std::vector<Op> &ops, int n, const PlanParams &pp) {
     std::vector<Pass> plan;
     const uint64_t all = (n >= 64) ? ~0ull : ((1ull << n) - 1ull);
-    const uint64_t low = (1ull << pp.c) - 1ull;
+    const int free_slots = pp.m - pp.c;
     std::vector<char> done(ops.size(), 0);
     size_t first = 0;
     while (first < ops.size()) {
         while (first < ops.size() && done[first]) first++;
         if (first >= ops.size()) break;
-        Pass pass;
-        uint64_t L = low, blocked = 0;
-        for (size_t i = first; i < ops.size(); i++) {
-            if (done[i]) continue;
-            const Op &op = ops[i];
-            const uint64_t qm = op.qmask();
-            if (!chunkable(op, pp)) {
-                if (pass.ops.empty() && !(qm & blocked)) {
-                    pass.stream = true;
-                    pass.ops.push_back((int)i);
-                    done[i] = 1;
-                }
-                break;  // a non-chunkable op is a barrier for this pass
+        // candidates: unrestricted greedy, and greedy restricted to each window of
+        // free_slots consecutive high qubits (chains and brickwork advance further when the
+        // local window is chosen, not claimed by the first gates in circuit order)
+        Trial best = greedy_pass(ops, done, first, n, pp, all);
+        if (!best.stream && free_slots > 0 && n > pp.m) {
+            for (int s = pp.c; s + free_slots <= n; s++) {
+                const uint64_t win = ((1ull << free_slots) - 1ull) << s;
+                Trial t = greedy_pass(ops, done, first, n, pp, win);
+                if (!t.stream && t.ops.size() > best.ops.size()) best = std::move(t);
             }
-            if (qm & blocked) {
-                blocked |= qm;
-            } else if (__builtin_popcountll(L | qm) <= pp.m) {
-                L |= qm;
-                pass.ops.push_back((int)i);
-                done[i] = 1;
-            } else {
-                blocked |= qm;
-            }
-            if ((blocked & all) == all) break;
         }
+        Pass pass;
+        pass.ops = best.ops;
+        pass.stream = best.stream;
         if (pass.ops.empty()) {
             // nothing fits next to the always-local low qubits (tiny m): stream the op
             pass.stream = true;
             pass.ops.push_back((int)first);
-            done[first] = 1;
         }
+        for (int i : pass.ops) done[i] = 1;
         if (!pass.stream) {
+            uint64_t L = best.L;
             // pad with the lowest free qubits (longer contiguous runs)
             for (int b = 0; b < n && __builtin_popcountll(L) < pp.m; b++) L |= 1ull << b;
             pass.lmask = L & all;

@@ -2,6 +2,8 @@
 // Shared by the chunk kernel (K2) and the batched persistent kernel (K6).
 #pragma once
 
+#include <type_traits>
+
 #include "dfmath.cuh"
 #include "kops.cuh"
 
@@ -116,6 +118,151 @@ __device__ __forceinline__ void dense_k_smem(typename C2T<T>::type *tile, const 
     }
 }
 
+// F_RGROUP (complex64): every thread owns groups of 16 amplitudes spanned by the 4
+// positions pos[0..3] and applies a run of one- and two-bit ops to them in registers, one
+// shared-memory sweep for the whole run.  Lane l keeps amplitude r ^ L (L = l & 15) in
+// register r, so the 32 lanes of a warp touch different banks even when the 4 positions
+// are the lowest ones; each member's matrix is read with its row and column indices XORed
+// by L's bits on that member's positions, which is the same operator in that order.
+// Block layout in sm: [member count, then per member: code, 2^(2 nb) complex entries],
+// code = nb + 4 b0 + 16 b1 (nb in {1,2}; b0 < b1 register bits; sub-index s = bit b0 +
+// 2 bit b1), entries row-major (re, im).
+// Member matrices are copied into registers once per member, already permuted for this
+// lane (entry (r, c) of the register copy is M[r ^ x][c ^ x]), so that the multiply-adds
+// use uniform register operands.
+template <int B0, int G>
+__device__ __forceinline__ void rg_one(float2 (&v)[G][16], const float *M, int L) {
+    const int x = (L >> B0) & 1;
+    float m[8];
+#pragma unroll
+    for (int r = 0; r < 2; r++)
+#pragma unroll
+        for (int c = 0; c < 2; c++) {
+            m[4 * r + 2 * c] = M[4 * (r ^ x) + 2 * (c ^ x)];
+            m[4 * r + 2 * c + 1] = M[4 * (r ^ x) + 2 * (c ^ x) + 1];
+        }
+#pragma unroll
+    for (int g = 0; g < G; g++)
+#pragma unroll
+        for (int r = 0; r < 16; r++) {
+            if (r & (1 << B0)) continue;
+            const float2 a = v[g][r], b = v[g][r | (1 << B0)];
+#pragma unroll
+            for (int so = 0; so < 2; so++) {
+                const float *row = m + 4 * so;
+                float yr = row[0] * a.x;
+                yr = fmaf(-row[1], a.y, yr);
+                yr = fmaf(row[2], b.x, yr);
+                yr = fmaf(-row[3], b.y, yr);
+                float yi = row[0] * a.y;
+                yi = fmaf(row[1], a.x, yi);
+                yi = fmaf(row[2], b.y, yi);
+                yi = fmaf(row[3], b.x, yi);
+                v[g][so ? (r | (1 << B0)) : r] = make_float2(yr, yi);
+            }
+        }
+}
+template <int B0, int B1, int G>
+__device__ __forceinline__ void rg_two(float2 (&v)[G][16], const float *M, int L) {
+    const int xm = ((L >> B0) & 1) | (((L >> B1) & 1) << 1);
+    float m[32];
+#pragma unroll
+    for (int r = 0; r < 4; r++)
+#pragma unroll
+        for (int c = 0; c < 4; c++) {
+            m[8 * r + 2 * c] = M[8 * (r ^ xm) + 2 * (c ^ xm)];
+            m[8 * r + 2 * c + 1] = M[8 * (r ^ xm) + 2 * (c ^ xm) + 1];
+        }
+#pragma unroll
+    for (int g = 0; g < G; g++)
+#pragma unroll
+        for (int r = 0; r < 16; r++) {
+            if (r & ((1 << B0) | (1 << B1))) continue;
+            float2 a[4];
+#pragma unroll
+            for (int s = 0; s < 4; s++) a[s] = v[g][r | ((s & 1) << B0) | ((s >> 1) << B1)];
+#pragma unroll
+            for (int so = 0; so < 4; so++) {
+                const float *row = m + 8 * so;
+                float yr = 0.f, yi = 0.f;
+#pragma unroll
+                for (int s = 0; s < 4; s++) {
+                    yr = fmaf(row[2 * s], a[s].x, yr);
+                    yr = fmaf(-row[2 * s + 1], a[s].y, yr);
+                    yi = fmaf(row[2 * s], a[s].y, yi);
+                    yi = fmaf(row[2 * s + 1], a[s].x, yi);
+                }
+                v[g][r | ((so & 1) << B0) | ((so >> 1) << B1)] = make_float2(yr, yi);
+            }
+        }
+}
+
+// G groups of 16 per thread stay in registers while every member is applied.
+template <int G>
+__device__ __forceinline__ void rgroup_run(float2 *tile, const KOp &op, const float *sm, uint32_t g0, uint32_t gstep) {
+    const uint32_t p0 = 1u << op.pos[0], p1 = 1u << op.pos[1], p2 = 1u << op.pos[2], p3 = 1u << op.pos[3];
+    const int L = threadIdx.x & 15;
+    const uint32_t dL = ((L & 1) ? p0 : 0u) | ((L & 2) ? p1 : 0u) | ((L & 4) ? p2 : 0u) | ((L & 8) ? p3 : 0u);
+    float2 v[G][16];
+    uint32_t base[G];
+#pragma unroll
+    for (int gi = 0; gi < G; gi++) {
+        uint32_t b = g0 + gi * gstep;
+#pragma unroll
+        for (int j = 0; j < 4; j++) {
+            const int q = op.pos[j];
+            b = ((b >> q) << (q + 1)) | (b & ((1u << q) - 1u));
+        }
+        base[gi] = b;
+#pragma unroll
+        for (int r = 0; r < 16; r++) {
+            const uint32_t d = ((r & 1) ? p0 : 0u) | ((r & 2) ? p1 : 0u) | ((r & 4) ? p2 : 0u) | ((r & 8) ? p3 : 0u);
+            v[gi][r] = tile[b | (d ^ dL)];
+        }
+    }
+    const int nmem = (int)sm[0];
+    int o = 1;
+    for (int mi = 0; mi < nmem; mi++) {
+        const int code = (int)sm[o];
+        const float *M = sm + o + 1;
+        if ((code & 3) == 1) {
+            switch ((code >> 2) & 3) {
+            case 0: rg_one<0, G>(v, M, L); break;
+            case 1: rg_one<1, G>(v, M, L); break;
+            case 2: rg_one<2, G>(v, M, L); break;
+            default: rg_one<3, G>(v, M, L); break;
+            }
+            o += 9;
+        } else {
+            switch (code >> 2) {
+            case 0 + 4 * 1: rg_two<0, 1, G>(v, M, L); break;
+            case 0 + 4 * 2: rg_two<0, 2, G>(v, M, L); break;
+            case 0 + 4 * 3: rg_two<0, 3, G>(v, M, L); break;
+            case 1 + 4 * 2: rg_two<1, 2, G>(v, M, L); break;
+            case 1 + 4 * 3: rg_two<1, 3, G>(v, M, L); break;
+            default: rg_two<2, 3, G>(v, M, L); break;
+            }
+            o += 33;
+        }
+    }
+#pragma unroll
+    for (int gi = 0; gi < G; gi++)
+#pragma unroll
+        for (int r = 0; r < 16; r++) {
+            const uint32_t d = ((r & 1) ? p0 : 0u) | ((r & 2) ? p1 : 0u) | ((r & 4) ? p2 : 0u) | ((r & 8) ? p3 : 0u);
+            tile[base[gi] | (d ^ dL)] = v[gi][r];
+        }
+}
+
+__device__ __forceinline__ void rgroup_apply(float2 *tile, const KOp &op, const float *sm, int m) {
+    const uint32_t ng = 1u << (m - 4);
+    if (ng == 2u * blockDim.x) {
+        rgroup_run<2>(tile, op, sm, threadIdx.x, blockDim.x);
+    } else {
+        for (uint32_t g = threadIdx.x; g < ng; g += blockDim.x) rgroup_run<1>(tile, op, sm, g, 0);
+    }
+}
+
 // Applies one op to the tile; op and its matrix entries are in shared memory.
 template <typename T>
 __device__ __forceinline__ void apply_op_smem(typename C2T<T>::type *tile, const KOp &op, const T *sm, int m) {
@@ -143,6 +290,9 @@ __device__ __forceinline__ void apply_op_smem(typename C2T<T>::type *tile, const
     case F_DENSEK:
         if (op.k == 3) dense_k_smem<T, 3>(tile, op, sm, m);
         else if (op.k == 4) dense_k_smem<T, 4>(tile, op, sm, m);
+        break;
+    case F_RGROUP:
+        if constexpr (std::is_same<T, float>::value) rgroup_apply(tile, op, sm, m);
         break;
     default:
         break;

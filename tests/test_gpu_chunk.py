@@ -134,3 +134,27 @@ def test_inverse_returns_initial_26q(qs):
     psi0 = inputs.gaussian_state(n, seed=10)
     got, _ = run_gpu(qs, n, 2, psi0, full, qs.QS_MODE_AUTO)
     assert np.max(np.abs(got - psi0)) <= 1e-12
+
+
+@pytest.mark.parametrize("fk", [1, 2, 3])
+def test_register_groups_match_plain_sweeps(qs, fk):
+    """complex64 passes with runs of small ops applied in registers (default) against
+    the same passes with one shared-memory sweep per op (grouping off) and the oracle."""
+    n = 17
+    gates = inputs.brickwork(n, 10, seed=fk) + inputs.random_circuit(n, 200, seed=40 + fk) + \
+        inputs.qaoa_3regular(n, p=1, seed=fk)
+    psi0 = inputs.gaussian_state(n, seed=fk).astype(np.complex64)
+    want = oracle.run(psi0.astype(np.complex128), n, gates)
+    a, _ = run_gpu(qs, n, 1, psi0, gates, qs.QS_MODE_AUTO, fuse_k=fk)
+    h = qs.qs_create(n, 1)
+    try:
+        qs.qs_set_amplitudes(h, psi0)
+        o = qs.options(fuse_k=fk)
+        o.reserved[3] = 1
+        qs.qs_apply_circuit(h, gates, o)
+        b = qs.qs_amplitudes(h).astype(np.complex128)
+    finally:
+        qs.qs_destroy(h)
+    assert np.max(np.abs(a - want)) <= TOL_C64
+    assert np.max(np.abs(b - want)) <= TOL_C64
+    assert fidelity_gap(a, want) <= 1e-6

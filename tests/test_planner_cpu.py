@@ -85,3 +85,14 @@ def test_small_chunk_width_always_progresses(n, m, dtype):
     assert len(lm) <= len(gates)
     counts = np.bincount(pog, minlength=len(lm))
     assert (counts >= 1).all()
+
+
+def test_window_search_cuts_passes():
+    """The windowed local-set search executes brickwork and TFIM chains in far fewer
+    passes than claiming local qubits in circuit order (85 / 197 before the search)."""
+    g = inputs.brickwork(33, 40, seed=3)
+    pog, lm = check_plan(33, qs.QS_C64, g)
+    assert len(lm) <= 40
+    g = inputs.tfim(33, 50)
+    pog, lm = check_plan(33, qs.QS_C64, g)
+    assert len(lm) <= 90
