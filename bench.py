@@ -61,6 +61,25 @@ def parse():
     return ap.parse_args()
 
 
+def max_over_ranks(x: float, world: int) -> float:
+    """Max of x over all ranks (replicas are timed independently; the slowest rank sets
+    the job's step time).  Works with the nccl (CUDA tensor) and gloo (CPU tensor)
+    backends."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate_rate(units_per_rank: int, ms_per_step: float, world: int) -> float:
+    """Whole-job throughput: every rank processed units_per_rank per step."""
+    return world * units_per_rank / (ms_per_step * 1e-3)
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -205,13 +224,8 @@ def run_ours(args, rank, world, local):
             d = evs[s][i].elapsed_time(evs[s][i + 1])
             per_type_ms[name] += d
             total_ms += d
-    ms_per_step = total_ms / args.steps
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms_per_step], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_per_step = float(t.item())
-    value = world * n_gates / (ms_per_step * 1e-3)
+    ms_per_step = max_over_ranks(total_ms / args.steps, world)
+    value = aggregate_rate(n_gates, ms_per_step, world)
 
     peak, peak_kind = load_peaks()
     per_gate = {}

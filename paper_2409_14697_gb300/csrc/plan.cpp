@@ -84,6 +84,7 @@ PlanParams plan_params(const DeviceState &st, const qs_options &o) {
     p.sweep_flops = c128 ? 1.0 : 24.0;
     // complex64 with fusion width 4..6: dense blocks go to the tensor cores (K3)
     p.tc = !c128 && o.fuse_k >= 4 && tc_available(p.m, std::min(o.fuse_k, 6));
+    p.force_chunk = o.mode == QS_MODE_CHUNK;
     if (p.tc) {
         p.fuse_k = std::min(o.fuse_k, 6);
         p.sweep_flops = 1e30;  // fuse whenever the block fits: its cost is on the tensor pipe
@@ -168,7 +169,7 @@ std::vector<Pass> make_plan(const std::vector<Op> &ops, int n, const PlanParams 
             // pad with the lowest free qubits (longer contiguous runs)
             for (int b = 0; b < n && __builtin_popcountll(L) < pp.m; b++) L |= 1ull << b;
             pass.lmask = L & all;
-            if (pass.ops.size() == 1) pass.stream = true;
+            if (pass.ops.size() == 1 && !pp.force_chunk) pass.stream = true;
         }
         plan.push_back(std::move(pass));
     }

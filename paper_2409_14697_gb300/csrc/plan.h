@@ -12,6 +12,7 @@ struct PlanParams {
     int fuse_k;  // fusion width inside a pass
     double sweep_flops;  // fusion cost gate (see fuse_ops)
     bool tc;             // complex64 blocks of 4..6 qubits run on the tensor cores
+    bool force_chunk;    // QS_MODE_CHUNK: single-op passes also run as chunk passes
 };
 
 struct Pass {
