@@ -54,8 +54,8 @@ def parse():
     ap.add_argument("--count", type=int, default=0, help="circuits/requests for batched/served")
     ap.add_argument("--fuse-k", type=int, default=5)
     ap.add_argument("--rate", type=float, default=2000.0)
-    ap.add_argument("--no-rgroups", action="store_true",
-                    help="complex64 passes: one shared-memory sweep per op (no register groups)")
+    ap.add_argument("--no-rphases", action="store_true",
+                    help="complex64 passes: one shared-memory sweep per op (no register phases)")
     ap.add_argument("--precision", default="fp64", choices=["fp64", "df32"],
                     help="complex128 arithmetic of the served workload")
     return ap.parse_args()
@@ -358,7 +358,7 @@ def run_e2e(qs, h, host_in, recs, opts, n, B, n_gates, world):
 
 # FP64 instructions per amplitude (FMA-class issues, one FP64 pipe slot each) of the
 # complex128 streaming updates; the other gate types issue none on the FP64 pipe.
-FP64_INSTR_PER_AMP = {"h": 3, "rz": 4, "u3": 8, "cu3": 4}
+FP64_INSTR_PER_AMP = {"h": 3, "rz": 4, "u3": 7, "cu3": 3.5}
 # FP64 pipe peak: 2 FP64 instructions per clock per SM (ncu: the U3 kernel at 0.526e12/s
 # keeps the FP64 pipe 83.8 % busy) x 152 SMs x 2.07 GHz max SM clock = 1.26 TFLOP/s.
 FP64_PEAK_TINSTR = 2 * 152 * 2.07e9 / 1e12
@@ -479,13 +479,12 @@ def wl_circuits33(args):
     stream = torch.cuda.Stream()
     h = qs.qs_create(n, qs.QS_C64)
     qs.qs_set_stream(h, stream.cuda_stream)
-    tc = "tensor cores" if args.fuse_k >= 4 else "SIMT"
+    tc = "tensor cores" if args.fuse_k >= 4 else ("SIMT" if args.no_rphases else "SIMT, register phases")
     out = {"workload": f"{n}-qubit circuits, complex64, fused k={args.fuse_k} ({tc})", "qubits": n,
            "state_bytes": 8 << n, "circuits": {}}
     opts = qs.options(fuse_k=args.fuse_k)
-    if args.no_rgroups:
+    if args.no_rphases:
         opts.reserved[3] = 1
-        out["workload"] += ", no register groups"
     fams = {"brickwork40": inputs.brickwork(n, 40, seed=3), "qaoa_p4": inputs.qaoa_3regular(n, p=4, seed=3),
             "tfim50": inputs.tfim(n, steps=50, dt=0.05)}
     for name, gates in fams.items():
@@ -503,6 +502,7 @@ def wl_circuits33(args):
         nrm2 = qs.qs_norm(h)
         out["circuits"][name] = {"gates": len(gates), "ms": round(ms, 2), "passes": st["passes"],
                                  "ops_after_fuse": st["ops_after_fuse"],
+                                 "tile_sweeps": st["tile_sweeps"],
                                  "gates_per_s": round(len(gates) * 1e3 / ms, 1),
                                  "pass_GBps": round(st["bytes"] / (ms * 1e-3) / 1e9, 1),
                                  "norm_minus_1": nrm - 1.0, "inverse_infidelity": 1.0 - abs(complex(a0)) ** 2,
@@ -528,7 +528,7 @@ def wl_batched(args):
     tune_s = time.perf_counter() - tt0
     t0 = time.perf_counter()
     bo = qs.options(chunk_m=best["chunk_m"], fuse_k=best["fuse_k"])
-    if args.no_rgroups:
+    if args.no_rphases:
         bo.reserved[3] = 1
     b = qs.qs_batch_create(circs, qs.QS_C64, bo)
     build_s = time.perf_counter() - t0

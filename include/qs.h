@@ -116,7 +116,10 @@ typedef struct {
      * reserved[2] = 1 turns off the norm-preserving correction after complex64 circuits that
      * used tensor-core blocks (default on: the squared norm before the circuit is restored,
      * which removes the small systematic shrink of FP32 accumulation inside the MMA);
-     * reserved[3] = 1 turns off register grouping of small ops in complex64 passes. */
+     * reserved[3] = 1 turns off register phases in complex64 passes over 2^13-amplitude tiles
+     * (every op then takes its own shared-memory sweep of the tile; default on: runs of
+     * one-qubit, controlled and at most two-qubit diagonal gates are applied to amplitudes
+     * held in registers, one sweep per run). */
     int32_t reserved[4];
 } qs_options;
 
@@ -127,6 +130,8 @@ typedef struct {
     int64_t passes;        /* full state-vector passes launched (each = 1 read + 1 write) */
     int64_t launches;      /* kernel launches */
     double bytes;          /* algorithmic HBM bytes of those launches */
+    int64_t tile_sweeps;   /* shared-memory sweeps of the tiles in chunk passes, summed over
+                              passes (a register phase is one sweep for all its ops) */
 } qs_stats;
 
 /* ---- library ------------------------------------------------------------------ */

@@ -61,8 +61,9 @@ def signature(kind: str, n, dtype: int, gates_or_circuits) -> str:
 
 
 def candidates(dtype: int, n: int, kind: str = "circuit"):
-    """Candidate option sets: chunk width, fusion width (tensor cores for complex64 when
-    k >= 4), and for complex128 the arithmetic (native FP64 or double-float)."""
+    """Candidate option sets: chunk width, fusion width (complex64: k = 1 applies gates
+    unfused, in register phases on 2^13-amplitude tiles; tensor cores when k >= 4), and for
+    complex128 the arithmetic (native FP64 or double-float)."""
     from . import qs
     out = []
     ms = [m for m in ((10, 11, 12) if dtype == qs.QS_C128 else (11, 12, 13)) if m <= max(n, 1)] or [0]
@@ -74,7 +75,7 @@ def candidates(dtype: int, n: int, kind: str = "circuit"):
                     out.append({"chunk_m": m, "fuse_k": k, "precision": prec})
     else:
         for m in ms:
-            for k in (2, 3, 4, 5, 6):
+            for k in (1, 2, 3, 4, 5, 6):
                 if kind == "batch" and k > 4:
                     continue
                 out.append({"chunk_m": m, "fuse_k": k, "precision": 0})

@@ -134,7 +134,7 @@ void run_circuit(DeviceState &d, const std::vector<Op> &ops, const qs_options &o
     if (o.precision != QS_PREC_DEFAULT && o.precision != QS_PREC_FP64 && o.precision != QS_PREC_DF32)
         fail(QS_ERR_INVALID, "unknown precision mode");
     d.prec = o.precision == QS_PREC_DF32 ? QS_PREC_DF32 : QS_PREC_FP64;
-    d.reg_groups = o.reserved[3] == 0;
+    d.reg_phases = o.reserved[3] == 0;
     const uint64_t l0 = g_launches.load();
     arena_begin(d);
     const int mode = o.mode;
@@ -156,7 +156,7 @@ void run_circuit(DeviceState &d, const std::vector<Op> &ops, const qs_options &o
                     // block's qubits plus the lowest others up to 2^13 amplitudes
                     uint64_t L = op.qmask();
                     for (int b = 0; b < d.n && __builtin_popcountll(L) < m_tc; b++) L |= 1ull << b;
-                    launch_pass_ops(d, L, {op}, true);
+                    st.tile_sweeps += launch_pass_ops(d, L, {op}, true);
                     st.bytes += 2.0 * 8.0 * (double)(1ull << d.n);
                 } else {
                     launch_stream_op(d, op);

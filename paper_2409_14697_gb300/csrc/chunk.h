@@ -13,6 +13,10 @@ struct ChunkArgs {
     int32_t lhigh[24];  // global positions of the other local bits, ascending
     int32_t n_ops;
     uint64_t n_tiles;   // 2^(n-m)
+    // staged = 1: the pass's ops and reals are copied once per CTA into dynamic shared
+    // memory after the tile, at byte offsets ops_off and reals_off
+    int32_t staged;
+    uint32_t ops_off, reals_off, n_reals;
 };
 
 // One pass over the state: tiles over the local bit set `lmask`, applying `kops`

@@ -23,7 +23,7 @@
 namespace qs {
 namespace {
 
-constexpr int kBatchThreads = 256;
+constexpr int kBatchThreads = kTileThreads;
 
 __device__ __forceinline__ unsigned int ld_acquire(const unsigned int *p) {
     unsigned int v;
@@ -98,8 +98,8 @@ k_batch(typename C2T<T>::type *__restrict__ states, const BatchPass *__restrict_
         if (s_stop) break;
         const BatchPass &bp = s_pass;
         const uint64_t t = s_w - bp.tile_start;
-        const uint32_t nruns = 1u << (bp.m - bp.c0);
-        const uint32_t run_bytes = (uint32_t)sizeof(V) << bp.c0;
+        uint32_t nruns = 1u << (bp.m - bp.c0);
+        uint32_t run_bytes = (uint32_t)sizeof(V) << bp.c0;
         const uint32_t tile_amps = 1u << bp.m;
         uint64_t base = t << bp.c0;
         for (int j = 0; j < bp.nlh; j++) {
@@ -147,6 +147,17 @@ k_batch(typename C2T<T>::type *__restrict__ states, const BatchPass *__restrict_
         apply_ops_tile<T>(tile, ops + bp.ops_off, bp.n_ops, mats + bp.mats_off, bp.m, s_op, s_m);
         ptx::fence_proxy_async_smem();
         __syncthreads();
+        // the write-back addresses are rebuilt from shared memory instead of being kept live
+        // through the ops (register pressure of the complex64 register phases)
+        asm volatile("" ::: "memory");
+        base = (s_w - bp.tile_start) << bp.c0;
+        for (int j = 0; j < bp.nlh; j++) {
+            const int b = bp.lhigh[j];
+            base = ((base >> b) << (b + 1)) | (base & ((1ull << b) - 1ull));
+        }
+        psi = states + bp.state_off;
+        nruns = 1u << (bp.m - bp.c0);
+        run_bytes = (uint32_t)sizeof(V) << bp.c0;
         for (uint32_t r = threadIdx.x; r < nruns; r += blockDim.x) {
             uint64_t off = 0;
             for (int j = 0; j < bp.nlh; j++) off |= (uint64_t)((r >> j) & 1u) << bp.lhigh[j];
@@ -201,6 +212,7 @@ void batch_build(Batch &b, const std::vector<std::vector<Op>> &circ_ops, const s
         DeviceState d;
         d.n = n;
         d.dtype = b.dtype;
+        d.reg_phases = o.reserved[3] == 0;
         qs_options oc = o;
         oc.chunk_m = std::min(m_max, n);
         PlanParams pp = plan_params(d, oc);
@@ -229,8 +241,12 @@ void batch_build(Batch &b, const std::vector<std::vector<Op>> &circ_ops, const s
                 if ((L >> bit) & 1ull) pos[bit] = r++;
             std::vector<KOp> ko;
             std::vector<double> mt;
-            for (const Op &op : fused) ko.push_back(make_kop(op, pos, mt));
-            if (!c128 && o.reserved[3] == 0) ko = group_registers(ko, mt, __builtin_popcountll(L));
+            const int m = __builtin_popcountll(L);
+            if (!c128 && d.reg_phases && rphase_applicable(m, kTileThreadBits)) {
+                ko = build_register_phases(fused, pos, m, kTileThreadBits, mt);
+            } else {
+                for (const Op &op : fused) ko.push_back(make_kop(op, pos, mt));
+            }
             cp.kops.push_back(std::move(ko));
             cp.mats.push_back(std::move(mt));
             cp.lm.push_back(L);

@@ -20,7 +20,9 @@
 namespace qs {
 namespace {
 
-constexpr int kChunkThreads = 256;
+constexpr int kChunkThreads = kTileThreads;
+// Dynamic shared memory of a staged pass (tile + program): two CTAs per SM must fit.
+constexpr size_t kStagedSmemLimit = 104 * 1024;
 
 // DF: complex128 with double-float arithmetic; mats then holds (hi, lo) float pairs.
 template <typename T, bool DF>
@@ -42,6 +44,18 @@ k_chunk(typename C2T<T>::type *__restrict__ psi, const ChunkArgs a, const KOp *_
         ptx::mbar_init(&bar, 1);
         ptx::fence_mbar_init();
         abort_flag = 0;
+    }
+    // staged: the whole pass program is copied once per CTA (tiles then need one barrier
+    // per op instead of three, and no global reads of ops)
+    const KOp *st_ops = (const KOp *)(smem_raw + a.ops_off);
+    const T *st_m = (const T *)(smem_raw + a.reals_off);
+    if (a.staged) {
+        const uint32_t *src = (const uint32_t *)ops;
+        uint32_t *dst = (uint32_t *)(smem_raw + a.ops_off);
+        const uint32_t nw = (uint32_t)a.n_ops * (uint32_t)(sizeof(KOp) / 4);
+        for (uint32_t j = threadIdx.x; j < nw; j += blockDim.x) dst[j] = src[j];
+        T *dm = (T *)(smem_raw + a.reals_off);
+        for (uint32_t j = threadIdx.x; j < a.n_reals; j += blockDim.x) dm[j] = mats[j];
     }
     __syncthreads();
     uint32_t phase = 0;
@@ -69,22 +83,35 @@ k_chunk(typename C2T<T>::type *__restrict__ psi, const ChunkArgs a, const KOp *_
             if (threadIdx.x == 0) atomicExch(err, QS_ERR_TIMEOUT);
             break;
         }
-        if constexpr (DF) {
-            const df::F2 *mp = (const df::F2 *)mats;
-            df::F2 *sp = (df::F2 *)s_m;
-            for (int i = 0; i < a.n_ops; i++) {
+        // one call site of the op code (it is large: register phases)
+        for (int i = 0; i < a.n_ops; i++) {
+            const KOp *op;
+            const T *om;
+            if (a.staged) {
+                op = st_ops + i;
+                om = st_m + op->mat;
+            } else {
                 if (threadIdx.x == 0) s_op = ops[i];
                 __syncthreads();
-                for (int j = threadIdx.x; j < s_op.nmat; j += blockDim.x) sp[j] = mp[s_op.mat + j];
+                for (int j = threadIdx.x; j < s_op.nmat; j += blockDim.x) s_m[j] = mats[s_op.mat + j];
                 __syncthreads();
-                apply_op_smem_df((double2 *)tile, s_op, sp, s_fb, a.m);
-                __syncthreads();
+                op = &s_op;
+                om = s_m;
             }
-        } else {
-            apply_ops_tile<T>(tile, ops, a.n_ops, mats, a.m, s_op, s_m);
+            if constexpr (DF) apply_op_smem_df((double2 *)tile, *op, (const df::F2 *)om, s_fb, a.m);
+            else apply_op_smem<T>(tile, *op, om, a.m);
+            __syncthreads();
         }
         ptx::fence_proxy_async_smem();
         __syncthreads();
+        // the write-back addresses are rebuilt rather than kept live through the ops
+        // (register pressure of the complex64 register phases)
+        asm volatile("" ::: "memory");
+        base = t << a.c0;
+        for (int j = 0; j < a.nlh; j++) {
+            const int b = a.lhigh[j];
+            base = ((base >> b) << (b + 1)) | (base & ((1ull << b) - 1ull));
+        }
         for (uint32_t r = threadIdx.x; r < nruns; r += blockDim.x) {
             uint64_t off = 0;
             for (int j = 0; j < a.nlh; j++) off |= (uint64_t)((r >> j) & 1u) << a.lhigh[j];
@@ -115,7 +142,17 @@ void launch_t(DeviceState &st, const ChunkArgs &a, const std::vector<KOp> &kops,
         d_m = (const T *)upload_params(st, tm.data(), tm.size() * sizeof(T));
     }
     using V = typename C2T<T>::type;
-    const size_t smem = sizeof(V) << a.m;
+    // stage the pass program after the tile when two CTAs per SM still fit
+    ChunkArgs ca = a;
+    const size_t tile_bytes = sizeof(V) << a.m;
+    const size_t ops_bytes = kops.size() * sizeof(KOp);
+    const size_t reals_bytes = (DF ? 2 * sizeof(float) : sizeof(T)) * mats.size();
+    size_t smem = tile_bytes;
+    ca.ops_off = (uint32_t)tile_bytes;
+    ca.reals_off = (uint32_t)(tile_bytes + ops_bytes);
+    ca.n_reals = (uint32_t)mats.size();
+    ca.staged = tile_bytes + ops_bytes + reals_bytes <= kStagedSmemLimit ? 1 : 0;
+    if (ca.staged) smem = (tile_bytes + ops_bytes + reals_bytes + 15) / 16 * 16;
     auto kern = k_chunk<T, DF>;
     static bool attr_set = false;
     if (!attr_set) {
@@ -123,7 +160,7 @@ void launch_t(DeviceState &st, const ChunkArgs &a, const std::vector<KOp> &kops,
         attr_set = true;
     }
     const int grid = persistent_grid((const void *)kern, kChunkThreads, smem, a.n_tiles);
-    kern<<<grid, kChunkThreads, smem, st.stream>>>((V *)st.psi, a, d_ops, d_m, st.dev_err);
+    kern<<<grid, kChunkThreads, smem, st.stream>>>((V *)st.psi, ca, d_ops, d_m, st.dev_err);
     QS_CUDA(cudaGetLastError());
     count_launch();
 }

@@ -63,6 +63,11 @@ template <typename T> struct FDense1 {
     T m[8];
     template <int L> __device__ void operator()(Amp<T, L> *v) const { f_dense1<T, L>(v, m); }
 };
+template <typename T> struct FDense1R0 {
+    static constexpr int NT = 2;
+    T m[8];
+    template <int L> __device__ void operator()(Amp<T, L> *v) const { f_dense1_r0<T, L>(v, m); }
+};
 template <typename T> struct FDiag1 {
     static constexpr int NT = 2;
     T d[4];
@@ -405,7 +410,18 @@ void launch_typed(DeviceState &st, const Op &op) {
     }
     case F_SWAP: dispatch_elem<T>(st, k, FSwap<T>{}); return;
     case F_NEG: dispatch_elem<T>(st, k, FNeg<T>{}); return;
-    case F_DENSE1: { FDense1<T> f; load_m(f.m, mats, k); dispatch_elem<T>(st, k, f); return; }
+    case F_DENSE1: {
+        if (std::is_same<T, double>::value && mats[k.mat + 1] == 0.0) {
+            FDense1R0<T> f;  // real first entry (U3, CU3, RX, RY): 7 FP64 ops per amplitude
+            load_m(f.m, mats, k);
+            dispatch_elem<T>(st, k, f);
+        } else {
+            FDense1<T> f;
+            load_m(f.m, mats, k);
+            dispatch_elem<T>(st, k, f);
+        }
+        return;
+    }
     case F_DIAG1: { FDiag1<T> f; load_m(f.d, mats, k); dispatch_elem<T>(st, k, f); return; }
     case F_PHASE: { FPhase<T> f; load_m(f.d, mats, k); dispatch_elem<T>(st, k, f); return; }
     case F_DIAG2: { FDiag2<T> f; load_m(f.d, mats, k); dispatch_elem<T>(st, k, f); return; }

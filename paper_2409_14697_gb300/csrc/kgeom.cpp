@@ -142,125 +142,231 @@ KOp make_kop(const Op &op, const int *pos, std::vector<double> &mats) {
 
 namespace {
 
-bool rg_eligible(const KOp &k) {
-    switch (k.fkind) {
-    case F_H: case F_SWAP: case F_DENSE1: case F_DIAG1: case F_PHASE: case F_NEG: case F_DIAG2: case F_DENSE2:
-        return k.nf == 1 || k.nf == 2;
+// One op as a register-phase member (tile positions); false if a phase cannot hold it.
+struct RpMember {
+    int type = 0;
+    int tgt = -1;       // register-slot operand (a position the phase must hold in registers)
+    int a = -1, b = -1; // position operands (-1: bit 1 for every amplitude, -2: bit 0)
+    double pay[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+};
+
+bool rp_member(const Op &op, const int *pos, RpMember &mb) {
+    auto P = [&](int j) { return pos[op.q[j]]; };
+    auto put = [&](int i, cd z) {
+        mb.pay[2 * i] = z.real();
+        mb.pay[2 * i + 1] = z.imag();
+    };
+    auto mat = [&](cd m00, cd m01, cd m10, cd m11) {
+        put(0, m00); put(1, m01); put(2, m10); put(3, m11);
+    };
+    // diagonal on positions (a, b), entry index 2 x_a + x_b
+    auto diag = [&](int a, int b, cd d0, cd d1, cd d2, cd d3) {
+        mb.a = a;
+        mb.b = b;
+        if (is_one(d0) && is_one(d1) && is_one(d2)) {
+            if (is_minus_one(d3)) {
+                mb.type = RP_NEG;
+            } else {
+                mb.type = RP_PH;
+                put(0, d3);
+            }
+        } else if (d0 == d3 && d1 == d2) {
+            mb.type = RP_PARITY;  // depends on x_a xor x_b only (RZZ)
+            put(0, d0); put(1, d1);
+        } else {
+            mb.type = RP_DIAG;
+            put(0, d0); put(1, d1); put(2, d2); put(3, d3);
+        }
+    };
+    // diagonal diag(d0, d1) on one position a
+    auto diag1 = [&](int a, cd d0, cd d1) {
+        mb.a = a;
+        mb.b = a;
+        if (is_one(d0) && is_minus_one(d1)) {
+            mb.type = RP_NEG;
+        } else if (is_one(d0)) {
+            mb.type = RP_PH;
+            put(0, d1);
+        } else {
+            mb.type = RP_PARITY;  // x_a xor 0 = x_a
+            mb.b = -2;
+            put(0, d0); put(1, d1);
+        }
+    };
+    switch (op.kind) {
+    case K_H: {
+        const double r = 1.0 / std::sqrt(2.0);
+        mb.type = RP_M1;
+        mb.tgt = P(0);
+        mat(r, r, r, -r);
+        return true;
+    }
+    case K_PERM1:
+        mb.type = RP_X;
+        mb.tgt = P(0);
+        return true;
+    case K_DENSE1:
+        mb.type = RP_M1;
+        mb.tgt = P(0);
+        mat(op.m[0], op.m[1], op.m[2], op.m[3]);
+        return true;
+    case K_DIAG1:
+        diag1(P(0), op.m[0], op.m[1]);
+        return true;
+    case K_CTRL1: {
+        const std::vector<cd> &u = op.m;
+        if (u[1] == cd(0.0) && u[2] == cd(0.0)) {
+            diag(P(0), P(1), 1.0, 1.0, u[0], u[3]);
+            return true;
+        }
+        mb.tgt = P(1);
+        mb.a = P(0);
+        if (u[0] == cd(0.0) && u[3] == cd(0.0) && is_one(u[1]) && is_one(u[2])) {
+            mb.type = RP_X;
+        } else {
+            mb.type = RP_C1;
+            mat(u[0], u[1], u[2], u[3]);
+        }
+        return true;
+    }
+    case K_DIAG:
+        if (op.k == 1) {
+            diag1(P(0), op.m[0], op.m[1]);
+            return true;
+        }
+        if (op.k == 2) {
+            diag(P(0), P(1), op.m[0], op.m[1], op.m[2], op.m[3]);
+            return true;
+        }
+        return false;
     default:
         return false;
     }
 }
 
-// The op as a dense 2^nf x 2^nf matrix on its fixed bits (sub-index bit j <-> fb[j]),
-// obtained by applying it to every basis vector of one group.
-std::vector<cd> member_matrix(const KOp &k, const std::vector<double> &mats) {
-    const int nb = k.nf, D = 1 << nb;
-    auto sub = [&](uint64_t x) {
-        int s = 0;
-        for (int j = 0; j < nb; j++) s |= (int)((x >> k.fb[j]) & 1ull) << j;
-        return s;
-    };
-    auto mc = [&](int i) { return cd(mats[k.mat + 2 * i], mats[k.mat + 2 * i + 1]); };
-    std::vector<cd> M((size_t)D * D, 0.0);
-    for (int s0 = 0; s0 < D; s0++) {
-        std::vector<cd> v(D, 0.0);
-        v[s0] = 1.0;
-        cd a[4];
-        int idx[4];
-        for (int t = 0; t < k.nt; t++) {
-            idx[t] = sub(k.off[t] | k.set_mask);
-            a[t] = v[idx[t]];
-        }
-        cd y[4];
-        switch (k.fkind) {
-        case F_H: {
-            const double r = 1.0 / std::sqrt(2.0);
-            y[0] = (a[0] + a[1]) * r;
-            y[1] = (a[0] - a[1]) * r;
-            break;
-        }
-        case F_SWAP: y[0] = a[1]; y[1] = a[0]; break;
-        case F_DENSE1:
-            y[0] = mc(0) * a[0] + mc(1) * a[1];
-            y[1] = mc(2) * a[0] + mc(3) * a[1];
-            break;
-        case F_DIAG1: y[0] = mc(0) * a[0]; y[1] = mc(1) * a[1]; break;
-        case F_PHASE: y[0] = mc(0) * a[0]; break;
-        case F_NEG: y[0] = -a[0]; break;
-        case F_DIAG2:
-            for (int t = 0; t < 4; t++) y[t] = mc(t) * a[t];
-            break;
-        case F_DENSE2:
-            for (int r = 0; r < 4; r++) {
-                y[r] = 0.0;
-                for (int c = 0; c < 4; c++) y[r] += mc(4 * r + c) * a[c];
-            }
-            break;
-        default:
-            break;
-        }
-        for (int t = 0; t < k.nt; t++) v[idx[t]] = y[t];
-        for (int r = 0; r < D; r++) M[(size_t)r * D + s0] = v[r];
-    }
-    return M;
+uint32_t tile_mask(const Op &op, const int *pos) {
+    uint32_t r = 0;
+    for (int j = 0; j < op.k; j++) r |= 1u << pos[op.q[j]];
+    return r;
 }
 
 }  // namespace
 
-std::vector<KOp> group_registers(const std::vector<KOp> &in, std::vector<double> &mats, int m) {
-    if (m < 5) return in;
-    std::vector<KOp> out;
-    std::vector<const KOp *> members;
-    uint32_t pos_mask = 0;
-    int floats = 1;
-    constexpr int kBudget = 500;  // block floats (kMaxOpReals = 512)
-    auto flush = [&]() {
-        if (members.size() >= 2) {
-            KOp g{};
-            g.fkind = F_RGROUP;
-            g.k = 4;
-            uint32_t S = pos_mask;
-            for (int b = m - 1; b >= 0 && __builtin_popcount(S) < 4; b--) S |= 1u << b;  // pad from the top
-            int np = 0;
-            for (int b = 0; b < m; b++)
-                if ((S >> b) & 1u) g.pos[np++] = b;
-            g.mat = (int32_t)mats.size();
-            mats.push_back((double)members.size());
-            for (const KOp *k : members) {
-                int bits[2] = {0, 0};
-                for (int j = 0; j < k->nf; j++)
-                    for (int t = 0; t < 4; t++)
-                        if (g.pos[t] == k->fb[j]) bits[j] = t;
-                mats.push_back((double)(k->nf + 4 * bits[0] + 16 * bits[1]));
-                for (const cd &z : member_matrix(*k, mats)) {
-                    mats.push_back(z.real());
-                    mats.push_back(z.imag());
-                }
+bool rphase_applicable(int m, int thread_bits) { return m - thread_bits == kRpBits; }
+
+std::vector<KOp> build_register_phases(const std::vector<Op> &ops, const int *pos, int m, int thread_bits,
+                                       std::vector<double> &mats, int *n_phases) {
+    if (!rphase_applicable(m, thread_bits)) fail(QS_ERR_INVALID, "register phases need m = thread bits + 5");
+    const size_t N = ops.size();
+    std::vector<RpMember> mb(N);
+    std::vector<char> ok(N), done(N, 0);
+    std::vector<uint32_t> touch(N);
+    for (size_t i = 0; i < N; i++) {
+        ok[i] = rp_member(ops[i], pos, mb[i]);
+        touch[i] = tile_mask(ops[i], pos);
+    }
+    const uint32_t all = (1u << m) - 1u;
+    // One greedy phase from `first`: an op joins if none of its positions is blocked by an
+    // earlier op left out, its register operand fits in R (at most kRpBits positions,
+    // within `allowed`) and the program has room; otherwise its positions become blocked.
+    auto trial = [&](size_t first, uint32_t allowed, std::vector<int> &taken) {
+        uint32_t R = 0, blocked = 0;
+        taken.clear();
+        for (size_t i = first; i < N; i++) {
+            if (done[i]) continue;
+            const uint32_t tm = touch[i];
+            bool take = ok[i] && !(tm & blocked) && (int)taken.size() < kRpMaxMembers;
+            if (take && mb[i].tgt >= 0) {
+                const uint32_t need = 1u << mb[i].tgt;
+                take = (need & ~allowed) == 0 && __builtin_popcount(R | need) <= kRpBits;
+                if (take) R |= need;
             }
-            g.nmat = (int32_t)mats.size() - g.mat;
-            out.push_back(g);
-        } else {
-            for (const KOp *k : members) out.push_back(*k);
+            if (take) taken.push_back((int)i);
+            else blocked |= tm;
+            if ((blocked & all) == all) break;
         }
-        members.clear();
-        pos_mask = 0;
-        floats = 1;
+        return R;
     };
-    for (const KOp &k : in) {
-        if (!rg_eligible(k)) {
-            flush();
-            out.push_back(k);
+    std::vector<KOp> out;
+    int phases = 0;
+    size_t first = 0;
+    std::vector<int> best, cand;
+    while (true) {
+        while (first < N && done[first]) first++;
+        if (first >= N) break;
+        if (!ok[first]) {
+            out.push_back(make_kop(ops[first], pos, mats));
+            done[first] = 1;
             continue;
         }
-        uint32_t km = 0;
-        for (int j = 0; j < k.nf; j++) km |= 1u << k.fb[j];
-        const int cost = 1 + 2 * (1 << (2 * k.nf));
-        if (__builtin_popcount(pos_mask | km) > 4 || floats + cost > kBudget) flush();
-        members.push_back(&k);
-        pos_mask |= km;
-        floats += cost;
+        // candidates: unrestricted, and register positions within each window of kRpBits
+        // consecutive positions; keep the one that takes most ops
+        uint32_t R = trial(first, all, best);
+        for (int w = 0; w + kRpBits <= m; w++) {
+            const uint32_t Rw = trial(first, ((1u << kRpBits) - 1u) << w, cand);
+            if (cand.size() > best.size()) {
+                best.swap(cand);
+                R = Rw;
+            }
+        }
+        // pad R with the highest free positions
+        for (int p = m - 1; p >= 0 && __builtin_popcount(R) < kRpBits; p--) R |= 1u << p;
+        KOp k{};
+        k.fkind = F_RPHASE;
+        k.k = kRpBits;
+        int slot_of[32], tbit_of[32];
+        int ns = 0, nt = 0;
+        uint64_t tpos = 0;
+        for (int p = 0; p < m; p++) {
+            if ((R >> p) & 1u) {
+                k.pos[ns] = p;
+                slot_of[p] = ns++;
+            } else {
+                tpos |= (uint64_t)p << (4 * nt);
+                tbit_of[p] = nt++;
+            }
+        }
+        k.nt = nt;
+        k.off[0] = tpos;
+        auto enc = [&](int p) {
+            if (p == -1) return kRpAlways;
+            if (p == -2) return kRpNever;
+            return ((R >> p) & 1u) ? 16 + slot_of[p] : tbit_of[p];
+        };
+        k.mat = (int32_t)mats.size();
+        mats.push_back(0.0);  // member count
+        int count = 0, last = -1, last_pairs = 0;
+        for (int i : best) {
+            const RpMember &e = mb[i];
+            done[i] = 1;
+            const double pair = (double)(enc(e.a) | enc(e.b) << 5);
+            if (e.type == RP_NEG && last >= 0 && last_pairs < 8) {
+                // consecutive sign flips commute: one member, the patterns XORed
+                mats[(size_t)last + 1 + last_pairs] = pair;
+                last_pairs++;
+                mats[(size_t)last] = (double)(RP_NEG | (last_pairs - 1) << 3);
+                continue;
+            }
+            const int slot = e.tgt >= 0 ? slot_of[e.tgt] : 0;
+            const size_t at = mats.size();
+            mats.push_back((double)(e.type | slot << 3 | enc(e.a) << 6 | enc(e.b) << 11));
+            for (int j = 0; j < 8; j++) mats.push_back(e.pay[j]);
+            if (e.type == RP_NEG) {
+                mats[at] = (double)RP_NEG;  // one pattern, held as payload real 0
+                mats[at + 1] = pair;
+                last = (int)at;
+                last_pairs = 1;
+            } else {
+                last = -1;
+            }
+            count++;
+        }
+        mats[(size_t)k.mat] = (double)count;
+        k.nmat = (int32_t)mats.size() - k.mat;
+        out.push_back(k);
+        phases++;
     }
-    flush();
+    if (n_phases) *n_phases = phases;
     return out;
 }
 

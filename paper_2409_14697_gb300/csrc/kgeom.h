@@ -11,10 +11,15 @@ namespace qs {
 // op's matrix entries are appended to `mats` (as re, im doubles; KOp.mat indexes them).
 KOp make_kop(const Op &op, const int *pos, std::vector<double> &mats);
 
-// complex64 passes: replaces runs of consecutive one- and two-bit ops whose positions fit
-// in 4 tile positions by F_RGROUP ops (applied in registers, one shared-memory sweep per
-// run); member matrices are appended to `mats`.  m = tile bits.
-std::vector<KOp> group_registers(const std::vector<KOp> &in, std::vector<double> &mats, int m);
+// complex64 tiles of 2^m amplitudes with 2^thread_bits threads: true if register phases
+// apply (m = thread_bits + kRpBits).
+bool rphase_applicable(int m, int thread_bits);
+// Packs the pass's ops (logical qubits, tile position of qubit q = pos[q]) into register
+// phases (F_RPHASE KOps; their programs appended to `mats`).  Ops no phase can hold
+// (swaps, wider dense or diagonal blocks) become ordinary KOps in their place in the
+// order.  n_phases (optional) receives the number of phases.
+std::vector<KOp> build_register_phases(const std::vector<Op> &ops, const int *pos, int m, int thread_bits,
+                                       std::vector<double> &mats, int *n_phases = nullptr);
 
 // Fraction of the state's bytes one streaming application reads and writes, counting
 // whole DRAM sectors of 2^sector_bits elements.

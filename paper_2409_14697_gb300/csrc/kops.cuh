@@ -27,7 +27,30 @@ enum FKind : int32_t {
     F_DIAGK,     // diagonal on k qubits at positions pos[] (m: 2^(k+1) reals), every element
     F_DENSEK,    // dense 2^k x 2^k on positions pos[] (m: 2^(2k+1) reals), k = 3..6
     F_TC,        // dense block on the tensor cores (k = 4..6; mat/nmat index the B operand)
-    F_RGROUP,    // run of one- and two-bit ops inside 4 positions pos[0..3], applied in registers
+    F_RPHASE,    // complex64 register phase: a run of ops on 2^5 amplitudes per thread in registers
+};
+
+// Reals staged in shared memory per op (dense 4-qubit block: 2 * 16 * 16).
+constexpr int kMaxOpReals = 512;
+// Threads per CTA of the tile kernels (chunk pass, batched launch).
+constexpr int kTileThreadBits = 8;
+constexpr int kTileThreads = 1 << kTileThreadBits;
+
+// Register phases (F_RPHASE, complex64): kRpBits tile positions per thread in registers,
+// so tiles of 2^(kTileThreadBits + kRpBits) amplitudes.  Member types of a phase program:
+constexpr int kRpBits = 5;
+constexpr int kRpAlways = 31;     // position operand whose bit is 1 for every amplitude
+constexpr int kRpNever = 30;      // position operand whose bit is 0 for every amplitude
+constexpr int kRpMaxMembers = 56; // 1 + 9 * 56 reals <= kMaxOpReals
+enum RpType : int {
+    RP_M1 = 0,  // 2x2 matrix (row-major re, im) on register slot `slot`
+    RP_C1,      // the same, only where the bit at position a is 1
+    RP_X,       // exchange on `slot` where the bit at position a is 1
+    RP_DIAG,    // multiply by d[2 x_a + x_b] (one position: a = b, d1 = d2 unused)
+    RP_NEG,     // negate where an odd number of slot + 1 patterns x_a x_b hold; the pairs
+                // (a | b << 5) are payload reals 0..slot
+    RP_PH,      // multiply by payload[0] + i payload[1] where x_a = x_b = 1
+    RP_PARITY,  // multiply by payload (0, 1) where x_a = x_b, by payload (2, 3) elsewhere
 };
 
 // Host+device description of one op in a given index space (HBM amplitude/element
@@ -44,6 +67,9 @@ struct KOp {
     int32_t mat;        // offset of the op's reals in the parameter array
     int32_t nmat;       // number of reals
 };
+
+// KOp arrays are copied into shared memory in 4-byte words, followed by reals.
+static_assert(sizeof(KOp) % 16 == 0, "KOp size keeps the reals after a KOp array aligned");
 
 #ifdef __CUDACC__
 
@@ -92,6 +118,23 @@ __device__ __forceinline__ void f_dense1(Amp<T, L> *v, const T *m) {
         const T ar = v[0].r[l], ai = v[0].i[l], br = v[1].r[l], bi = v[1].i[l];
         cdot2(v[0].r[l], v[0].i[l], m[0], m[1], ar, ai, m[2], m[3], br, bi);
         cdot2(v[1].r[l], v[1].i[l], m[4], m[5], ar, ai, m[6], m[7], br, bi);
+    }
+}
+// The same when m[0] has no imaginary part (U3, CU3, RX, RY: cos(theta/2) first): the first
+// row takes 6 multiply-adds instead of 8, 7 per amplitude in all (complex128 U3 is bound
+// by the FP64 pipe on this GPU).
+template <typename T, int L>
+__device__ __forceinline__ void f_dense1_r0(Amp<T, L> *v, const T *m) {
+#pragma unroll
+    for (int l = 0; l < L; l++) {
+        const T ar = v[0].r[l], ai = v[0].i[l], br = v[1].r[l], bi = v[1].i[l];
+        T pr = m[2] * br;
+        pr = fma(-m[3], bi, pr);
+        T pi = m[2] * bi;
+        pi = fma(m[3], br, pi);
+        cdot2(v[1].r[l], v[1].i[l], m[4], m[5], ar, ai, m[6], m[7], br, bi);
+        v[0].r[l] = fma(m[0], ar, pr);
+        v[0].i[l] = fma(m[0], ai, pi);
     }
 }
 template <typename T, int L, int NT>

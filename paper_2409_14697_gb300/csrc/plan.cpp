@@ -35,8 +35,9 @@ bool chunkable(const Op &op, const PlanParams &pp) {
 
 }  // namespace
 
-// Launches one chunk pass over lmask applying `fused` (tensor cores where allowed).
-void launch_pass_ops(DeviceState &st, uint64_t lmask, const std::vector<Op> &fused, bool use_tc) {
+// Launches one chunk pass over lmask applying `fused` (tensor cores where allowed);
+// returns the number of tile sweeps.
+int launch_pass_ops(DeviceState &st, uint64_t lmask, const std::vector<Op> &fused, bool use_tc) {
     const int n = st.n;
     int pos[64] = {0};
     int r = 0;
@@ -45,6 +46,11 @@ void launch_pass_ops(DeviceState &st, uint64_t lmask, const std::vector<Op> &fus
     const int m = r;
     std::vector<KOp> kops;
     std::vector<double> mats;
+    if (!use_tc && st.dtype == QS_C64 && st.reg_phases && rphase_applicable(m, kTileThreadBits)) {
+        const std::vector<KOp> kp = build_register_phases(fused, pos, m, kTileThreadBits, mats);
+        launch_chunk_pass(st, lmask, kp, mats);
+        return (int)kp.size();
+    }
     std::vector<float> bmats;
     uint32_t b_floats = 0;
     bool any_tc = false;
@@ -65,9 +71,9 @@ void launch_pass_ops(DeviceState &st, uint64_t lmask, const std::vector<Op> &fus
             kops.push_back(make_kop(op, pos, mats));
         }
     }
-    if (st.dtype == QS_C64 && st.reg_groups) kops = group_registers(kops, mats, m);
     if (any_tc) launch_chunk_pass_tc(st, lmask, kops, mats, bmats, b_floats);
     else launch_chunk_pass(st, lmask, kops, mats);
+    return (int)kops.size();
 }
 
 PlanParams plan_params(const DeviceState &st, const qs_options &o) {
@@ -75,10 +81,12 @@ PlanParams plan_params(const DeviceState &st, const qs_options &o) {
     const bool c128 = st.dtype == QS_C128;
     p.m = o.chunk_m > 0 ? o.chunk_m : (c128 ? 12 : 13);
     p.c = c128 ? 4 : 5;                  // runs of 256 bytes
-    // the shared-memory dense path applies blocks of at most 4 qubits
-    p.fuse_k = std::min(o.fuse_k > 0 ? o.fuse_k : 2, 4);
     p.m = std::min(p.m, st.n);
     p.c = std::min(p.c, p.m);
+    // the shared-memory dense path applies blocks of at most 4 qubits; complex64 register
+    // phases apply gates unfused (a fused block costs more flops than its members there)
+    const bool phases = !c128 && st.reg_phases && rphase_applicable(p.m, kTileThreadBits);
+    p.fuse_k = std::min(o.fuse_k > 0 ? o.fuse_k : (phases ? 1 : 2), 4);
     // FP64 is 1/72 of FP32 on GB300: for complex128 a fused block must not add flops;
     // complex64 arithmetic is cheap next to a shared-memory sweep of the tile
     p.sweep_flops = c128 ? 1.0 : 24.0;
@@ -214,7 +222,7 @@ void run_planned(DeviceState &st, const std::vector<Op> &ops, const qs_options &
         pops.reserve(p.ops.size());
         for (int i : p.ops) pops.push_back(ops[i]);
         const std::vector<Op> fused = fuse_ops(pops, pp.fuse_k, pp.sweep_flops);
-        launch_pass_ops(st, p.lmask, fused, pp.tc);
+        stats.tile_sweeps += launch_pass_ops(st, p.lmask, fused, pp.tc);
         stats.passes++;
         stats.bytes += 2.0 * B * (double)(1ull << n);
         n_ops += (int64_t)fused.size();

@@ -25,7 +25,7 @@ PlanParams plan_params(const DeviceState &st, const qs_options &o);
 // Greedy dependency-respecting partition of ops into passes.
 std::vector<Pass> make_plan(const std::vector<Op> &ops, int n, const PlanParams &pp);
 // One chunk pass over lmask applying ops already fused (tensor cores if use_tc).
-void launch_pass_ops(DeviceState &st, uint64_t lmask, const std::vector<Op> &fused, bool use_tc);
+int launch_pass_ops(DeviceState &st, uint64_t lmask, const std::vector<Op> &fused, bool use_tc);
 // Plans `ops` into passes and launches them on st.stream, filling stats.
 void run_planned(DeviceState &st, const std::vector<Op> &ops, const qs_options &o, qs_stats &stats);
 

@@ -92,7 +92,7 @@ struct DeviceState {
     int n = 0;            // qubits
     int dtype = QS_C128;
     int prec = QS_PREC_FP64;  // complex128 arithmetic: QS_PREC_FP64 or QS_PREC_DF32
-    bool reg_groups = true;   // complex64 chunk passes: apply runs of small ops in registers
+    bool reg_phases = true;   // complex64 chunk passes: register phases (2^13-amplitude tiles)
     cudaStream_t stream = nullptr;
     // scratch for reductions (owned by the state)
     void *scratch = nullptr;

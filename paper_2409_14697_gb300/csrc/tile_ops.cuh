@@ -9,7 +9,6 @@
 
 namespace qs {
 
-constexpr int kMaxOpReals = 512;  // dense 4-qubit block: 2 * 16 * 16 reals
 
 template <typename T>
 __device__ __forceinline__ void ld_amp(const typename C2T<T>::type *p, Amp<T, 1> &a) {
@@ -118,148 +117,309 @@ __device__ __forceinline__ void dense_k_smem(typename C2T<T>::type *tile, const 
     }
 }
 
-// F_RGROUP (complex64): every thread owns groups of 16 amplitudes spanned by the 4
-// positions pos[0..3] and applies a run of one- and two-bit ops to them in registers, one
-// shared-memory sweep for the whole run.  Lane l keeps amplitude r ^ L (L = l & 15) in
-// register r, so the 32 lanes of a warp touch different banks even when the 4 positions
-// are the lowest ones; each member's matrix is read with its row and column indices XORed
-// by L's bits on that member's positions, which is the same operator in that order.
-// Block layout in sm: [member count, then per member: code, 2^(2 nb) complex entries],
-// code = nb + 4 b0 + 16 b1 (nb in {1,2}; b0 < b1 register bits; sub-index s = bit b0 +
-// 2 bit b1), entries row-major (re, im).
-// Member matrices are copied into registers once per member, already permuted for this
-// lane (entry (r, c) of the register copy is M[r ^ x][c ^ x]), so that the multiply-adds
-// use uniform register operands.
-template <int B0, int G>
-__device__ __forceinline__ void rg_one(float2 (&v)[G][16], const float *M, int L) {
-    const int x = (L >> B0) & 1;
-    float m[8];
-#pragma unroll
-    for (int r = 0; r < 2; r++)
-#pragma unroll
-        for (int c = 0; c < 2; c++) {
-            m[4 * r + 2 * c] = M[4 * (r ^ x) + 2 * (c ^ x)];
-            m[4 * r + 2 * c + 1] = M[4 * (r ^ x) + 2 * (c ^ x) + 1];
-        }
-#pragma unroll
-    for (int g = 0; g < G; g++)
-#pragma unroll
-        for (int r = 0; r < 16; r++) {
-            if (r & (1 << B0)) continue;
-            const float2 a = v[g][r], b = v[g][r | (1 << B0)];
-#pragma unroll
-            for (int so = 0; so < 2; so++) {
-                const float *row = m + 4 * so;
-                float yr = row[0] * a.x;
-                yr = fmaf(-row[1], a.y, yr);
-                yr = fmaf(row[2], b.x, yr);
-                yr = fmaf(-row[3], b.y, yr);
-                float yi = row[0] * a.y;
-                yi = fmaf(row[1], a.x, yi);
-                yi = fmaf(row[2], b.y, yi);
-                yi = fmaf(row[3], b.x, yi);
-                v[g][so ? (r | (1 << B0)) : r] = make_float2(yr, yi);
-            }
-        }
+// ---- complex64 register phases (F_RPHASE) ---------------------------------------------
+// A phase keeps the 2^kRpBits amplitudes spanned by kRpBits tile positions R (pos[0..4],
+// register slot j <-> position pos[j]) in every thread's registers while a run of ops
+// ("members") is applied to them, so the tile is read and written once per phase instead
+// of once per op.  The other nt = m - kRpBits positions (off[0]: 4 bits each, ascending)
+// are spelled by the thread index, bit i <-> i-th position; blockDim.x = 2^nt.
+//
+// Register r of lane l holds the amplitude whose R-bits are r ^ sigma(l).  sigma puts the
+// positions 0..3 that lie in R on the upper lane bits of each half-warp, so the 16 lanes
+// of an 8-byte shared-memory wavefront hit 16 different bank pairs whatever R is.  The
+// members see the same operator in that register order: a 2x2 matrix on slot j is
+// conjugated by X where bit j of sigma is set, and the bit masks of diagonals and controls
+// are complemented on those slots.
+//
+// Program (floats, staged in shared memory): member count, then 9 floats per member: a
+// code and 8 payload reals.  code = type | slot << 3 | a << 6 | b << 11, where a and b
+// name positions: 16 + slot for a register position, the thread-index bit for any other,
+// kRpAlways for "every amplitude".
+constexpr int kRpRegs = 1 << kRpBits;
+static_assert(kRpMaxMembers * 9 + 1 <= kMaxOpReals, "a phase program must fit the staged reals");
+
+__device__ __forceinline__ uint32_t rp_pattern(int j) {
+    switch (j) {  // bit r set iff bit j of r is set
+    case 0: return 0xAAAAAAAAu;
+    case 1: return 0xCCCCCCCCu;
+    case 2: return 0xF0F0F0F0u;
+    case 3: return 0xFF00FF00u;
+    default: return 0xFFFF0000u;
+    }
 }
-template <int B0, int B1, int G>
-__device__ __forceinline__ void rg_two(float2 (&v)[G][16], const float *M, int L) {
-    const int xm = ((L >> B0) & 1) | (((L >> B1) & 1) << 1);
-    float m[32];
+
+// Bit r of the result = the bit at operand position `enc` of the amplitude in register r.
+__device__ __forceinline__ uint32_t rp_mask(int enc, uint32_t sigma, uint32_t tid) {
+    if (enc == kRpAlways) return 0xFFFFFFFFu;
+    if (enc == kRpNever) return 0u;
+    if (enc & 16) {
+        const int j = enc & 15;
+        const uint32_t p = rp_pattern(j);
+        return ((sigma >> j) & 1u) ? ~p : p;
+    }
+    return ((tid >> enc) & 1u) ? 0xFFFFFFFFu : 0u;
+}
+
+// A mask that is the same for every register (an operand spelled by the thread index).
+__device__ __forceinline__ bool rp_uniform(uint32_t K) { return K == 0u || K == 0xFFFFFFFFu; }
+
+// Complex updates below are ordered so that every output's last multiply-add consumes the
+// input it replaces (the other terms first, as partial sums): each result can then take
+// its input's register, and the member loop needs no register copies.
+__device__ __forceinline__ float2 rp_cmul(float2 a, float br, float bi) {
+    const float pr = -a.y * bi, pi = a.x * bi;
+    return make_float2(fmaf(a.x, br, pr), fmaf(a.y, br, pi));
+}
+
+// rows (M0 + i M1, M2 + i M3) and (M4 + i M5, M6 + i M7) applied to (x, y)
+__device__ __forceinline__ void rp_2x2(const float (&M)[8], float2 &x, float2 &y) {
+    float p0r = -M[1] * x.y;
+    p0r = fmaf(M[2], y.x, p0r);
+    p0r = fmaf(-M[3], y.y, p0r);
+    float p0i = M[1] * x.x;
+    p0i = fmaf(M[2], y.y, p0i);
+    p0i = fmaf(M[3], y.x, p0i);
+    float p1r = M[4] * x.x;
+    p1r = fmaf(-M[5], x.y, p1r);
+    p1r = fmaf(-M[7], y.y, p1r);
+    float p1i = M[4] * x.y;
+    p1i = fmaf(M[5], x.x, p1i);
+    p1i = fmaf(M[7], y.x, p1i);
+    x.x = fmaf(M[0], x.x, p0r);
+    x.y = fmaf(M[0], x.y, p0i);
+    y.x = fmaf(M[6], y.x, p1r);
+    y.y = fmaf(M[6], y.y, p1i);
+}
+
+template <int J>
+__device__ __forceinline__ void rp_m1(float2 (&v)[kRpRegs], const float (&M)[8]) {
 #pragma unroll
-    for (int r = 0; r < 4; r++)
+    for (int r = 0; r < kRpRegs; r++) {
+        if (r & (1 << J)) continue;
+        rp_2x2(M, v[r], v[r | (1 << J)]);
+    }
+}
+
+template <int J>
+__device__ __forceinline__ void rp_c1(float2 (&v)[kRpRegs], const float (&M)[8], uint32_t K) {
 #pragma unroll
-        for (int c = 0; c < 4; c++) {
-            m[8 * r + 2 * c] = M[8 * (r ^ xm) + 2 * (c ^ xm)];
-            m[8 * r + 2 * c + 1] = M[8 * (r ^ xm) + 2 * (c ^ xm) + 1];
+    for (int r = 0; r < kRpRegs; r++) {
+        if (r & (1 << J)) continue;
+        float2 o0 = v[r], o1 = v[r | (1 << J)];
+        rp_2x2(M, o0, o1);
+        const bool c = (K >> r) & 1u;
+        v[r] = c ? o0 : v[r];
+        v[r | (1 << J)] = c ? o1 : v[r | (1 << J)];
+    }
+}
+
+template <int J>
+__device__ __forceinline__ void rp_x(float2 (&v)[kRpRegs], uint32_t K) {
+#pragma unroll
+    for (int r = 0; r < kRpRegs; r++) {
+        if (r & (1 << J)) continue;
+        const bool c = (K >> r) & 1u;
+        const float2 x = v[r], y = v[r | (1 << J)];
+        v[r] = c ? y : x;
+        v[r | (1 << J)] = c ? x : y;
+    }
+}
+
+__device__ __forceinline__ void rp_scale(float2 (&v)[kRpRegs], float dr, float di) {
+#pragma unroll
+    for (int r = 0; r < kRpRegs; r++) v[r] = rp_cmul(v[r], dr, di);
+}
+
+__device__ __forceinline__ void rp_diag(float2 (&v)[kRpRegs], const float (&d)[8], uint32_t Ka, uint32_t Kb) {
+    if (rp_uniform(Ka) && rp_uniform(Kb)) {
+        const bool xa = Ka != 0u, xb = Kb != 0u;
+        rp_scale(v, xa ? (xb ? d[6] : d[4]) : (xb ? d[2] : d[0]), xa ? (xb ? d[7] : d[5]) : (xb ? d[3] : d[1]));
+        return;
+    }
+#pragma unroll
+    for (int r = 0; r < kRpRegs; r++) {
+        const bool xa = (Ka >> r) & 1u, xb = (Kb >> r) & 1u;
+        const float dr = xa ? (xb ? d[6] : d[4]) : (xb ? d[2] : d[0]);
+        const float di = xa ? (xb ? d[7] : d[5]) : (xb ? d[3] : d[1]);
+        v[r] = rp_cmul(v[r], dr, di);
+    }
+}
+
+// multiply by f where bit r of K is set, by e elsewhere
+__device__ __forceinline__ void rp_two(float2 (&v)[kRpRegs], float er, float ei, float fr, float fi, uint32_t K) {
+    if (rp_uniform(K)) {
+        rp_scale(v, K ? fr : er, K ? fi : ei);
+        return;
+    }
+#pragma unroll
+    for (int r = 0; r < kRpRegs; r++) {
+        const bool c = (K >> r) & 1u;
+        v[r] = rp_cmul(v[r], c ? fr : er, c ? fi : ei);
+    }
+}
+
+// negate where bit r of K is set (sign by multiplication: the FMA pipe, not the ALU)
+__device__ __forceinline__ void rp_neg(float2 (&v)[kRpRegs], uint32_t K) {
+    if (K == 0u) return;
+#pragma unroll
+    for (int r = 0; r < kRpRegs; r++) {
+        const float s = __int_as_float(0x3f800000u | ((K << (31 - r)) & 0x80000000u));
+        v[r].x *= s;
+        v[r].y *= s;
+    }
+}
+
+__device__ __forceinline__ void rp_ph(float2 (&v)[kRpRegs], float pr, float pi, uint32_t K) {
+    if (K == 0u) return;
+    if (K == 0xFFFFFFFFu) {
+        rp_scale(v, pr, pi);
+        return;
+    }
+#pragma unroll
+    for (int r = 0; r < kRpRegs; r++) {
+        const float2 y = rp_cmul(v[r], pr, pi);
+        v[r] = ((K >> r) & 1u) ? y : v[r];
+    }
+}
+
+// Tile index of register 0 of this thread (register r: base ^ XOR of pb[j] over the bits
+// j of r), sigma and the per-slot position bits of phase ph.
+__device__ __forceinline__ void rp_geometry(const KOp &ph, uint32_t tid, uint32_t (&pb)[kRpBits], uint32_t &base,
+                                            uint32_t &sigma) {
+    const uint32_t lane = tid & 31u;
+    int nlow = 0;
+#pragma unroll
+    for (int j = 0; j < kRpBits; j++) {
+        pb[j] = 1u << ph.pos[j];
+        nlow += ph.pos[j] < 4 ? 1 : 0;
+    }
+    sigma = 0;
+    int li = 4 - nlow;
+#pragma unroll
+    for (int j = 0; j < kRpBits; j++)
+        if (ph.pos[j] < 4) {
+            sigma |= ((lane >> li) & 1u) << j;
+            li++;
         }
+    base = 0;
+    for (int i = 0; i < ph.nt; i++) base |= ((tid >> i) & 1u) << (uint32_t)((ph.off[0] >> (4 * i)) & 15u);
 #pragma unroll
-    for (int g = 0; g < G; g++)
+    for (int j = 0; j < kRpBits; j++) base ^= ((sigma >> j) & 1u) ? pb[j] : 0u;
+}
+
+template <int R>
+__device__ __forceinline__ uint32_t rp_index(uint32_t base, const uint32_t (&pb)[kRpBits]) {
+    uint32_t o = base;
 #pragma unroll
-        for (int r = 0; r < 16; r++) {
-            if (r & ((1 << B0) | (1 << B1))) continue;
-            float2 a[4];
-#pragma unroll
-            for (int s = 0; s < 4; s++) a[s] = v[g][r | ((s & 1) << B0) | ((s >> 1) << B1)];
-#pragma unroll
-            for (int so = 0; so < 4; so++) {
-                const float *row = m + 8 * so;
-                float yr = 0.f, yi = 0.f;
-#pragma unroll
-                for (int s = 0; s < 4; s++) {
-                    yr = fmaf(row[2 * s], a[s].x, yr);
-                    yr = fmaf(-row[2 * s + 1], a[s].y, yr);
-                    yi = fmaf(row[2 * s], a[s].y, yi);
-                    yi = fmaf(row[2 * s + 1], a[s].x, yi);
+    for (int j = 0; j < kRpBits; j++)
+        if (R & (1 << j)) o ^= pb[j];
+    return o;
+}
+
+template <int R>
+__device__ __forceinline__ void rp_load(float2 (&v)[kRpRegs], const float2 *tile, uint32_t base,
+                                        const uint32_t (&pb)[kRpBits]) {
+    if constexpr (R < kRpRegs) {
+        v[R] = tile[rp_index<R>(base, pb)];
+        rp_load<R + 1>(v, tile, base, pb);
+    }
+}
+template <int R>
+__device__ __forceinline__ void rp_store(const float2 (&v)[kRpRegs], float2 *tile, uint32_t base,
+                                         const uint32_t (&pb)[kRpBits]) {
+    if constexpr (R < kRpRegs) {
+        tile[rp_index<R>(base, pb)] = v[R];
+        rp_store<R + 1>(v, tile, base, pb);
+    }
+}
+
+// Runs one phase: every thread of the block must call this.
+__device__ __forceinline__ void rphase_run(float2 *tile, const KOp &ph, const float *prog) {
+    const uint32_t tid = threadIdx.x;
+    float2 v[kRpRegs];
+    uint32_t sigma;
+    {
+        uint32_t pb[kRpBits], base;
+        rp_geometry(ph, tid, pb, base, sigma);
+        rp_load<0>(v, tile, base, pb);
+    }
+    const int nmem = (int)prog[0];
+    for (int i = 0; i < nmem; i++) {
+        const float *mm = prog + 1 + 9 * i;
+        const int code = (int)mm[0];
+        const int type = code & 7, J = (code >> 3) & 7, ea = (code >> 6) & 31, eb = (code >> 11) & 31;
+        const float *P = mm + 1;
+        switch (type) {
+        case RP_M1:
+        case RP_C1: {
+            // X M X in this lane's register order where bit J of sigma is set: the rows and
+            // columns of the payload are read swapped
+            const int f = (int)((sigma >> J) & 1u);
+            float M[8];
+            M[0] = P[6 * f]; M[1] = P[6 * f + 1];
+            M[2] = P[2 + 2 * f]; M[3] = P[3 + 2 * f];
+            M[4] = P[4 - 2 * f]; M[5] = P[5 - 2 * f];
+            M[6] = P[6 - 6 * f]; M[7] = P[7 - 6 * f];
+            if (type == RP_M1) {
+                switch (J) {
+                case 0: rp_m1<0>(v, M); break;
+                case 1: rp_m1<1>(v, M); break;
+                case 2: rp_m1<2>(v, M); break;
+                case 3: rp_m1<3>(v, M); break;
+                default: rp_m1<4>(v, M); break;
                 }
-                v[g][r | ((so & 1) << B0) | ((so >> 1) << B1)] = make_float2(yr, yi);
+            } else {
+                const uint32_t K = rp_mask(ea, sigma, tid);
+                switch (J) {
+                case 0: rp_c1<0>(v, M, K); break;
+                case 1: rp_c1<1>(v, M, K); break;
+                case 2: rp_c1<2>(v, M, K); break;
+                case 3: rp_c1<3>(v, M, K); break;
+                default: rp_c1<4>(v, M, K); break;
+                }
             }
+            break;
         }
-}
-
-// G groups of 16 per thread stay in registers while every member is applied.
-template <int G>
-__device__ __forceinline__ void rgroup_run(float2 *tile, const KOp &op, const float *sm, uint32_t g0, uint32_t gstep) {
-    const uint32_t p0 = 1u << op.pos[0], p1 = 1u << op.pos[1], p2 = 1u << op.pos[2], p3 = 1u << op.pos[3];
-    const int L = threadIdx.x & 15;
-    const uint32_t dL = ((L & 1) ? p0 : 0u) | ((L & 2) ? p1 : 0u) | ((L & 4) ? p2 : 0u) | ((L & 8) ? p3 : 0u);
-    float2 v[G][16];
-    uint32_t base[G];
-#pragma unroll
-    for (int gi = 0; gi < G; gi++) {
-        uint32_t b = g0 + gi * gstep;
-#pragma unroll
-        for (int j = 0; j < 4; j++) {
-            const int q = op.pos[j];
-            b = ((b >> q) << (q + 1)) | (b & ((1u << q) - 1u));
+        case RP_X: {
+            const uint32_t K = rp_mask(ea, sigma, tid);
+            switch (J) {
+            case 0: rp_x<0>(v, K); break;
+            case 1: rp_x<1>(v, K); break;
+            case 2: rp_x<2>(v, K); break;
+            case 3: rp_x<3>(v, K); break;
+            default: rp_x<4>(v, K); break;
+            }
+            break;
         }
-        base[gi] = b;
+        case RP_DIAG: {
+            float M[8];
 #pragma unroll
-        for (int r = 0; r < 16; r++) {
-            const uint32_t d = ((r & 1) ? p0 : 0u) | ((r & 2) ? p1 : 0u) | ((r & 4) ? p2 : 0u) | ((r & 8) ? p3 : 0u);
-            v[gi][r] = tile[b | (d ^ dL)];
+            for (int e = 0; e < 8; e++) M[e] = P[e];
+            rp_diag(v, M, rp_mask(ea, sigma, tid), rp_mask(eb, sigma, tid));
+            break;
+        }
+        case RP_NEG: {
+            // J + 1 sign patterns x_a x_b, one (a | b << 5) per payload real: signs multiply
+            uint32_t K = 0;
+            for (int q = 0; q <= J; q++) {
+                const int e = (int)P[q];
+                K ^= rp_mask(e & 31, sigma, tid) & rp_mask(e >> 5, sigma, tid);
+            }
+            rp_neg(v, K);
+            break;
+        }
+        case RP_PARITY:
+            rp_two(v, P[0], P[1], P[2], P[3], rp_mask(ea, sigma, tid) ^ rp_mask(eb, sigma, tid));
+            break;
+        default: rp_ph(v, P[0], P[1], rp_mask(ea, sigma, tid) & rp_mask(eb, sigma, tid)); break;
         }
     }
-    const int nmem = (int)sm[0];
-    int o = 1;
-    for (int mi = 0; mi < nmem; mi++) {
-        const int code = (int)sm[o];
-        const float *M = sm + o + 1;
-        if ((code & 3) == 1) {
-            switch ((code >> 2) & 3) {
-            case 0: rg_one<0, G>(v, M, L); break;
-            case 1: rg_one<1, G>(v, M, L); break;
-            case 2: rg_one<2, G>(v, M, L); break;
-            default: rg_one<3, G>(v, M, L); break;
-            }
-            o += 9;
-        } else {
-            switch (code >> 2) {
-            case 0 + 4 * 1: rg_two<0, 1, G>(v, M, L); break;
-            case 0 + 4 * 2: rg_two<0, 2, G>(v, M, L); break;
-            case 0 + 4 * 3: rg_two<0, 3, G>(v, M, L); break;
-            case 1 + 4 * 2: rg_two<1, 2, G>(v, M, L); break;
-            case 1 + 4 * 3: rg_two<1, 3, G>(v, M, L); break;
-            default: rg_two<2, 3, G>(v, M, L); break;
-            }
-            o += 33;
-        }
-    }
-#pragma unroll
-    for (int gi = 0; gi < G; gi++)
-#pragma unroll
-        for (int r = 0; r < 16; r++) {
-            const uint32_t d = ((r & 1) ? p0 : 0u) | ((r & 2) ? p1 : 0u) | ((r & 4) ? p2 : 0u) | ((r & 8) ? p3 : 0u);
-            tile[base[gi] | (d ^ dL)] = v[gi][r];
-        }
-}
-
-__device__ __forceinline__ void rgroup_apply(float2 *tile, const KOp &op, const float *sm, int m) {
-    const uint32_t ng = 1u << (m - 4);
-    if (ng == 2u * blockDim.x) {
-        rgroup_run<2>(tile, op, sm, threadIdx.x, blockDim.x);
-    } else {
-        for (uint32_t g = threadIdx.x; g < ng; g += blockDim.x) rgroup_run<1>(tile, op, sm, g, 0);
+    // the addresses are rebuilt from shared memory rather than kept live through the members
+    asm volatile("" ::: "memory");
+    {
+        uint32_t pb[kRpBits], base, sg;
+        rp_geometry(ph, tid, pb, base, sg);
+        rp_store<0>(v, tile, base, pb);
     }
 }
 
@@ -291,8 +451,8 @@ __device__ __forceinline__ void apply_op_smem(typename C2T<T>::type *tile, const
         if (op.k == 3) dense_k_smem<T, 3>(tile, op, sm, m);
         else if (op.k == 4) dense_k_smem<T, 4>(tile, op, sm, m);
         break;
-    case F_RGROUP:
-        if constexpr (std::is_same<T, float>::value) rgroup_apply(tile, op, sm, m);
+    case F_RPHASE:
+        if constexpr (std::is_same<T, float>::value) rphase_run(tile, op, sm);
         break;
     default:
         break;

@@ -136,25 +136,50 @@ def test_inverse_returns_initial_26q(qs):
     assert np.max(np.abs(got - psi0)) <= 1e-12
 
 
-@pytest.mark.parametrize("fk", [1, 2, 3])
-def test_register_groups_match_plain_sweeps(qs, fk):
-    """complex64 passes with runs of small ops applied in registers (default) against
-    the same passes with one shared-memory sweep per op (grouping off) and the oracle."""
-    n = 17
-    gates = inputs.brickwork(n, 10, seed=fk) + inputs.random_circuit(n, 200, seed=40 + fk) + \
-        inputs.qaoa_3regular(n, p=1, seed=fk)
-    psi0 = inputs.gaussian_state(n, seed=fk).astype(np.complex64)
-    want = oracle.run(psi0.astype(np.complex128), n, gates)
-    a, _ = run_gpu(qs, n, 1, psi0, gates, qs.QS_MODE_AUTO, fuse_k=fk)
+def _run_c64(qs, n, psi0, gates, phases=True, **kw):
     h = qs.qs_create(n, 1)
     try:
         qs.qs_set_amplitudes(h, psi0)
-        o = qs.options(fuse_k=fk)
-        o.reserved[3] = 1
+        o = qs.options(**kw)
+        if not phases:
+            o.reserved[3] = 1
         qs.qs_apply_circuit(h, gates, o)
-        b = qs.qs_amplitudes(h).astype(np.complex128)
+        return qs.qs_amplitudes(h).astype(np.complex128), qs.qs_last_stats(h)
     finally:
         qs.qs_destroy(h)
+
+
+@pytest.mark.parametrize("n", [13, 14, 17])
+@pytest.mark.parametrize("fk", [1, 2])
+def test_register_phases_match_plain_sweeps(qs, n, fk):
+    """complex64 passes over 2^13-amplitude tiles with register phases (default) against
+    the same passes with one shared-memory sweep per op, and both against the oracle.  The
+    circuit mixes every gate type a phase holds (one-qubit dense, H, X, diagonals,
+    controlled gates with the control inside and outside the register positions, CZ, CP,
+    RZZ) with the ones it leaves to plain sweeps (SWAP, dense two-qubit blocks)."""
+    gates = inputs.brickwork(n, 10, seed=fk) + inputs.random_circuit(n, 300, seed=40 + fk + n) + \
+        inputs.qaoa_3regular(n, p=1, seed=fk) + inputs.qft(n)
+    gates.append(("dense", (3, n - 1), inputs.random_unitary(2, seed=fk)))
+    gates += inputs.random_circuit(n, 40, seed=7 + n)
+    psi0 = inputs.gaussian_state(n, seed=fk + n).astype(np.complex64)
+    want = oracle.run(psi0.astype(np.complex128), n, gates)
+    a, sa = _run_c64(qs, n, psi0, gates, True, fuse_k=fk)
+    b, sb = _run_c64(qs, n, psi0, gates, False, fuse_k=fk)
     assert np.max(np.abs(a - want)) <= TOL_C64
     assert np.max(np.abs(b - want)) <= TOL_C64
     assert fidelity_gap(a, want) <= 1e-6
+    # register phases take several ops per shared-memory sweep
+    assert sa["tile_sweeps"] <= sb["tile_sweeps"]
+    if fk == 1:
+        assert 2 * sa["tile_sweeps"] < sb["tile_sweeps"]
+
+
+def test_register_phases_brickwork_sweeps(qs):
+    """On brickwork, a phase holds many gates: far fewer tile sweeps than ops."""
+    n = 20
+    gates = inputs.brickwork(n, 12, seed=9)
+    psi0 = oracle.zero_state(n).astype(np.complex64)
+    want = oracle.run(oracle.zero_state(n), n, gates)
+    a, st = _run_c64(qs, n, psi0, gates, True, fuse_k=1)
+    assert np.max(np.abs(a - want)) <= TOL_C64
+    assert st["tile_sweeps"] * 4 <= st["ops_after_fuse"]
