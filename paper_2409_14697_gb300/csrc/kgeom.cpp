@@ -333,35 +333,65 @@ std::vector<KOp> build_register_phases(const std::vector<Op> &ops, const int *po
             if (p == -2) return kRpNever;
             return ((R >> p) & 1u) ? 16 + slot_of[p] : tbit_of[p];
         };
-        k.mat = (int32_t)mats.size();
-        mats.push_back(0.0);  // member count
-        int count = 0, last = -1, last_pairs = 0;
+        // members in order; consecutive sign flips merge (their patterns XOR), consecutive
+        // parity diagonals with equal factors merge (a count of odd patterns, one table)
+        struct Pending {
+            int type, slot, ea, eb;
+            std::vector<double> pay;
+            std::vector<int> pairs;
+            cd e, f;
+        };
+        std::vector<Pending> pend;
         for (int i : best) {
             const RpMember &e = mb[i];
             done[i] = 1;
-            const double pair = (double)(enc(e.a) | enc(e.b) << 5);
-            if (e.type == RP_NEG && last >= 0 && last_pairs < 8) {
-                // consecutive sign flips commute: one member, the patterns XORed
-                mats[(size_t)last + 1 + last_pairs] = pair;
-                last_pairs++;
-                mats[(size_t)last] = (double)(RP_NEG | (last_pairs - 1) << 3);
+            const int ea = enc(e.a), eb = enc(e.b), pair = ea | eb << 5;
+            Pending *last = pend.empty() ? nullptr : &pend.back();
+            if (e.type == RP_NEG) {
+                if (last && last->type == RP_NEG && last->pairs.size() < 8) last->pairs.push_back(pair);
+                else pend.push_back({RP_NEG, 0, 0, 0, {}, {pair}, 0.0, 0.0});
                 continue;
             }
-            const int slot = e.tgt >= 0 ? slot_of[e.tgt] : 0;
-            const size_t at = mats.size();
-            mats.push_back((double)(e.type | slot << 3 | enc(e.a) << 6 | enc(e.b) << 11));
-            for (int j = 0; j < 8; j++) mats.push_back(e.pay[j]);
-            if (e.type == RP_NEG) {
-                mats[at] = (double)RP_NEG;  // one pattern, held as payload real 0
-                mats[at + 1] = pair;
-                last = (int)at;
-                last_pairs = 1;
-            } else {
-                last = -1;
+            if (e.type == RP_PARITY) {
+                const cd ev(e.pay[0], e.pay[1]), fv(e.pay[2], e.pay[3]);
+                if (last && last->type == RP_PARITY && last->e == ev && last->f == fv &&
+                    (int)last->pairs.size() < kRpMaxParity)
+                    last->pairs.push_back(pair);
+                else pend.push_back({RP_PARITY, 0, 0, 0, {}, {pair}, ev, fv});
+                continue;
             }
-            count++;
+            Pending p{e.type, e.tgt >= 0 ? slot_of[e.tgt] : 0, ea, eb, {}, {}, 0.0, 0.0};
+            const int npay = e.type == RP_X ? 0 : e.type == RP_PH ? 2 : 8;
+            p.pay.assign(e.pay, e.pay + npay);
+            pend.push_back(std::move(p));
         }
-        mats[(size_t)k.mat] = (double)count;
+        k.mat = (int32_t)mats.size();
+        mats.push_back((double)pend.size());
+        auto emit = [&](int type, int slot, int ea, int eb, const std::vector<double> &pay) {
+            mats.push_back((double)(type | slot << 3 | ea << 6 | eb << 11 | (int)pay.size() << 16));
+            mats.insert(mats.end(), pay.begin(), pay.end());
+        };
+        for (const Pending &p : pend) {
+            if (p.type == RP_NEG) {
+                emit(RP_NEG, (int)p.pairs.size() - 1, 0, 0, std::vector<double>(p.pairs.begin(), p.pairs.end()));
+            } else if (p.type == RP_PARITY && p.pairs.size() == 1) {
+                emit(RP_PARITY, 0, p.pairs[0] & 31, p.pairs[0] >> 5,
+                     {p.e.real(), p.e.imag(), p.f.real(), p.f.imag()});
+            } else if (p.type == RP_PARITY) {
+                // factor for k odd patterns out of np: e^(np - k) f^k
+                const int np = (int)p.pairs.size();
+                std::vector<double> pay(p.pairs.begin(), p.pairs.end());
+                for (int kk = 0; kk <= np; kk++) {
+                    cd t = 1.0;
+                    for (int j = 0; j < np; j++) t *= j < kk ? p.f : p.e;
+                    pay.push_back(t.real());
+                    pay.push_back(t.imag());
+                }
+                emit(RP_PARITYN, 0, 0, 0, pay);
+            } else {
+                emit(p.type, p.slot, p.ea, p.eb, p.pay);
+            }
+        }
         k.nmat = (int32_t)mats.size() - k.mat;
         out.push_back(k);
         phases++;

@@ -41,7 +41,7 @@ constexpr int kTileThreads = 1 << kTileThreadBits;
 constexpr int kRpBits = 5;
 constexpr int kRpAlways = 31;     // position operand whose bit is 1 for every amplitude
 constexpr int kRpNever = 30;      // position operand whose bit is 0 for every amplitude
-constexpr int kRpMaxMembers = 56; // 1 + 9 * 56 reals <= kMaxOpReals
+constexpr int kRpMaxMembers = 56; // ops per phase: 1 + 9 * 56 reals <= kMaxOpReals
 enum RpType : int {
     RP_M1 = 0,  // 2x2 matrix (row-major re, im) on register slot `slot`
     RP_C1,      // the same, only where the bit at position a is 1
@@ -51,7 +51,10 @@ enum RpType : int {
                 // (a | b << 5) are payload reals 0..slot
     RP_PH,      // multiply by payload[0] + i payload[1] where x_a = x_b = 1
     RP_PARITY,  // multiply by payload (0, 1) where x_a = x_b, by payload (2, 3) elsewhere
+    RP_PARITYN, // np parity patterns (a | b << 5), then np + 1 factors (re, im) indexed by the
+                // number of patterns with x_a != x_b (equal-angle RZZ / RZ layers), np <= 15
 };
+constexpr int kRpMaxParity = 15;
 
 // Host+device description of one op in a given index space (HBM amplitude/element
 // indices for K1, tile-local indices for K2).

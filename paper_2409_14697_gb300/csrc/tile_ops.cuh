@@ -131,10 +131,14 @@ __device__ __forceinline__ void dense_k_smem(typename C2T<T>::type *tile, const 
 // conjugated by X where bit j of sigma is set, and the bit masks of diagonals and controls
 // are complemented on those slots.
 //
-// Program (floats, staged in shared memory): member count, then 9 floats per member: a
-// code and 8 payload reals.  code = type | slot << 3 | a << 6 | b << 11, where a and b
-// name positions: 16 + slot for a register position, the thread-index bit for any other,
-// kRpAlways for "every amplitude".
+// Program (floats, staged in shared memory): member count, then per member a code and
+// `len` payload reals.  code = type | slot << 3 | a << 6 | b << 11 | len << 16, where a
+// and b name positions: 16 + slot for a register position, the thread-index bit for any
+// other, kRpAlways / kRpNever for a bit that is 1 / 0 for every amplitude.
+//
+// An exchange (X, or CNOT whose control is not a register position) is not carried out:
+// it toggles bit `slot` of sigma, i.e. relabels which register holds which amplitude, and
+// every later member and the final store read the relabelled order.
 constexpr int kRpRegs = 1 << kRpBits;
 static_assert(kRpMaxMembers * 9 + 1 <= kMaxOpReals, "a phase program must fit the staged reals");
 
@@ -269,6 +273,23 @@ __device__ __forceinline__ void rp_neg(float2 (&v)[kRpRegs], uint32_t K) {
     }
 }
 
+// multiply register r by table[c(r)] (re, im pairs), c(r) = the 4-bit count whose bit j is
+// bit r of plane c_j
+__device__ __forceinline__ void rp_table(float2 (&v)[kRpRegs], const float *table, uint32_t c0, uint32_t c1,
+                                         uint32_t c2, uint32_t c3) {
+    if (rp_uniform(c0) && rp_uniform(c1) && rp_uniform(c2) && rp_uniform(c3)) {
+        const int k = (int)((c0 & 1u) | (c1 & 2u) | (c2 & 4u) | (c3 & 8u));
+        rp_scale(v, table[2 * k], table[2 * k + 1]);
+        return;
+    }
+#pragma unroll
+    for (int r = 0; r < kRpRegs; r++) {
+        const int k = (int)(((c0 >> r) & 1u) | (((c1 >> r) & 1u) << 1) | (((c2 >> r) & 1u) << 2) |
+                            (((c3 >> r) & 1u) << 3));
+        v[r] = rp_cmul(v[r], table[2 * k], table[2 * k + 1]);
+    }
+}
+
 __device__ __forceinline__ void rp_ph(float2 (&v)[kRpRegs], float pr, float pi, uint32_t K) {
     if (K == 0u) return;
     if (K == 0xFFFFFFFFu) {
@@ -344,11 +365,13 @@ __device__ __forceinline__ void rphase_run(float2 *tile, const KOp &ph, const fl
         rp_load<0>(v, tile, base, pb);
     }
     const int nmem = (int)prog[0];
+    const float *mm = prog + 1;
     for (int i = 0; i < nmem; i++) {
-        const float *mm = prog + 1 + 9 * i;
         const int code = (int)mm[0];
         const int type = code & 7, J = (code >> 3) & 7, ea = (code >> 6) & 31, eb = (code >> 11) & 31;
+        const int len = (code >> 16) & 255;
         const float *P = mm + 1;
+        mm += 1 + len;
         switch (type) {
         case RP_M1:
         case RP_C1: {
@@ -382,6 +405,10 @@ __device__ __forceinline__ void rphase_run(float2 *tile, const KOp &ph, const fl
         }
         case RP_X: {
             const uint32_t K = rp_mask(ea, sigma, tid);
+            if (rp_uniform(K)) {  // the same for every register: relabel instead of moving
+                sigma ^= (K & 1u) << J;
+                break;
+            }
             switch (J) {
             case 0: rp_x<0>(v, K); break;
             case 1: rp_x<1>(v, K); break;
@@ -411,14 +438,37 @@ __device__ __forceinline__ void rphase_run(float2 *tile, const KOp &ph, const fl
         case RP_PARITY:
             rp_two(v, P[0], P[1], P[2], P[3], rp_mask(ea, sigma, tid) ^ rp_mask(eb, sigma, tid));
             break;
+        case RP_PARITYN: {
+            // np parity patterns x_a xor x_b (one (a | b << 5) per payload real), then the
+            // np + 1 factors for 0..np odd patterns: the odd count of every register is
+            // kept in 4 bit planes (a ripple counter over the 32 registers at once)
+            const int np = (len - 2) / 3;
+            uint32_t c0 = 0, c1 = 0, c2 = 0, c3 = 0;
+            for (int q = 0; q < np; q++) {
+                const int e = (int)P[q];
+                const uint32_t M = rp_mask(e & 31, sigma, tid) ^ rp_mask(e >> 5, sigma, tid);
+                uint32_t cy = c0 & M;
+                c0 ^= M;
+                uint32_t cz = c1 & cy;
+                c1 ^= cy;
+                cy = c2 & cz;
+                c2 ^= cz;
+                c3 ^= cy;
+            }
+            rp_table(v, P + np, c0, c1, c2, c3);
+            break;
+        }
         default: rp_ph(v, P[0], P[1], rp_mask(ea, sigma, tid) & rp_mask(eb, sigma, tid)); break;
         }
     }
-    // the addresses are rebuilt from shared memory rather than kept live through the members
+    // the addresses are rebuilt from shared memory rather than kept live through the
+    // members; the register order is the final sigma (exchanges relabel it)
     asm volatile("" ::: "memory");
     {
         uint32_t pb[kRpBits], base, sg;
         rp_geometry(ph, tid, pb, base, sg);
+#pragma unroll
+        for (int j = 0; j < kRpBits; j++) base ^= (((sg ^ sigma) >> j) & 1u) ? pb[j] : 0u;
         rp_store<0>(v, tile, base, pb);
     }
 }
