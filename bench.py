@@ -49,7 +49,7 @@ def parse():
     ap.add_argument("--no-extra", action="store_true",
                     help="skip the context rows (planned circuits, the other dtype)")
     ap.add_argument("--workload", default="gates30",
-                    choices=["gates30", "circuit12", "circuits33", "batched", "served"],
+                    choices=["gates30", "circuit12", "circuits33", "batched", "served", "reductions", "paper"],
                     help="gates30: the headline benchmark; the others print their own JSON line")
     ap.add_argument("--count", type=int, default=0, help="circuits/requests for batched/served")
     ap.add_argument("--fuse-k", type=int, default=5)
@@ -484,7 +484,7 @@ def wl_circuits33(args):
            "state_bytes": 8 << n, "circuits": {}}
     opts = qs.options(fuse_k=args.fuse_k)
     if args.no_rphases:
-        opts.reserved[3] = 1
+        opts.flags |= qs.QS_OPT_NO_REG_PHASES
     fams = {"brickwork40": inputs.brickwork(n, 40, seed=3), "qaoa_p4": inputs.qaoa_3regular(n, p=4, seed=3),
             "tfim50": inputs.tfim(n, steps=50, dt=0.05)}
     for name, gates in fams.items():
@@ -529,7 +529,7 @@ def wl_batched(args):
     t0 = time.perf_counter()
     bo = qs.options(chunk_m=best["chunk_m"], fuse_k=best["fuse_k"])
     if args.no_rphases:
-        bo.reserved[3] = 1
+        bo.flags |= qs.QS_OPT_NO_REG_PHASES
     b = qs.qs_batch_create(circs, qs.QS_C64, bo)
     build_s = time.perf_counter() - t0
     stream = torch.cuda.Stream()
@@ -584,6 +584,99 @@ def wl_batched(args):
             "autotuned": best, "autotune_s": round(tune_s, 1),
             "autotune_table_ms": {f"m{t['chunk_m']}k{t['fuse_k']}": t["ms"] for t in table},
             "oracle_sample": sample, "max_abs_err": max(errs), "max_infidelity": max(infid)}
+
+
+def wl_reductions(args):
+    """Reductions on a seeded Gaussian state: squared norm, <Z_q> for every q (one FP64
+    pass), renormalisation (norm pass + scale pass) and top-1024 |a|^2 (radix select);
+    each timed with CUDA events on the state's stream, reported as algorithmic GB/s
+    against the measured HBM copy bandwidth."""
+    import torch
+    from paper_2409_14697_gb300 import inputs, qs
+    n = args.qubits
+    dt = qs.QS_C128 if args.dtype == "c128" else qs.QS_C64
+    B = 16 if dt == qs.QS_C128 else 8
+    npdt = np.complex128 if dt == qs.QS_C128 else np.complex64
+    stream = torch.cuda.Stream()
+    h = qs.qs_create(n, dt)
+    qs.qs_set_stream(h, stream.cuda_stream)
+    host = torch.empty((1 << n) * 2, dtype=torch.float64 if B == 16 else torch.float32, pin_memory=True)
+    hv = host.numpy().view(npdt)
+    inputs.gaussian_state(n, seed=7, out=hv)
+    qs.qs_set_amplitudes_from(h, 0, 1 << n, host.data_ptr())
+    state = B * (1 << n)
+    peak, peak_kind = load_peaks()
+    out = {"workload": f"reductions, {n} qubits, {args.dtype}", "state_bytes": state, "hbm_peak_GBps": peak,
+           "hbm_peak_kind": peak_kind, "ops": {}}
+    reps = max(args.steps, 5)
+    cases = {"norm": (lambda: qs.qs_norm(h), state),
+             "expectation_z_all": (lambda: qs.qs_expectation_z(h), state),
+             "renormalize": (lambda: qs.qs_renormalize(h), 3 * state),
+             "top_1024": (lambda: qs.qs_top_amplitudes(h, 1024), state)}
+    for name, (fn, nbytes) in cases.items():
+        for _ in range(max(args.warmup, 3)):
+            fn()
+        ms = _event_ms(stream, fn, reps)
+        gbps = nbytes / (ms * 1e-3) / 1e9
+        out["ops"][name] = {"ms": round(ms, 4), "alg_bytes": nbytes, "GBps": round(gbps, 1),
+                            "frac_of_measured_hbm": round(gbps / peak, 3)}
+    # spot checks against host sums of the same state (FP64)
+    ez, nrm = qs.qs_expectation_z(h)
+    p = np.abs(hv.astype(np.complex128)) ** 2
+    out["norm_vs_host"] = abs(nrm - float(p.sum()))
+    half = 1 << (n - 1)  # the top qubit is 0 on the first half of the indices
+    out["expz_top_qubit_vs_host"] = abs(ez[n - 1] - float(p[:half].sum() - p[half:].sum()))
+    out["alg_bytes_note"] = "norm, <Z>, top-K: one read of the state; renormalize: norm read + scale read/write"
+    qs.qs_destroy(h)
+    return out
+
+
+# QueenV2 Tables II-IV: seconds on an RTX 4090, complex128 (context, another GPU)
+PAPER_S = {"h": {23: 0.011, 24: 0.014, 25: 0.014, 26: 0.021, 27: 0.021, 28: 0.035, 29: 0.041, 30: 0.084},
+           "qft": {23: 0.011, 24: 0.014, 25: 0.024, 26: 0.041, 27: 0.064, 28: 0.124, 29: 0.252, 30: 0.519},
+           "qaoa_complete_p5": {23: 0.030, 24: 0.054, 25: 0.098, 26: 0.196, 27: 0.371, 28: 0.776, 29: 1.613,
+                                30: 3.391}}
+
+
+def wl_paper(args):
+    """The paper's own workloads, complex128, 23..30 qubits (or --qubits only): the Hadamard
+    benchmark (Table II; read both as one H gate and as H on every qubit), QFT (Table III)
+    and 5-level fully connected QAOA (Table IV), through qs_apply_circuit (QS_MODE_AUTO:
+    planner, fusion, merged diagonal runs).  Times beside the paper's RTX-4090 seconds."""
+    import torch
+    from paper_2409_14697_gb300 import inputs, qs
+    sizes = [args.qubits] if args.qubits != N_QUBITS else list(range(23, 31))
+    prec = qs.QS_PREC_DF32 if args.precision == "df32" else qs.QS_PREC_FP64
+    out = {"workload": f"paper tables II-IV, complex128 ({args.precision})", "sizes": {}}
+    stream = torch.cuda.Stream()
+    for n in sizes:
+        h = qs.qs_create(n, qs.QS_C128)
+        qs.qs_set_stream(h, stream.cuda_stream)
+        fams = {"h_one_gate": [("h", (n - 1,), ())], "h_all_qubits": [("h", (q,), ()) for q in range(n)],
+                "qft": inputs.qft(n), "qaoa_complete_p5": inputs.qaoa_complete(n, p=5, seed=n)}
+        row = {}
+        for name, gates in fams.items():
+            recs = qs.gate_records(gates)
+            o = qs.options(precision=prec)
+
+            def once():
+                qs.qs_reset(h)
+                qs.qs_apply_circuit(h, recs, o)
+            once()
+            reps = max(args.steps, 3)
+            ms = _event_ms(stream, once, reps)
+            st = qs.qs_last_stats(h)
+            nrm = qs.qs_norm(h)
+            paper = PAPER_S["h" if name.startswith("h_") else name].get(n)
+            row[name] = {"gates": len(gates), "s": round(ms * 1e-3, 5), "passes": st["passes"],
+                         "ops": st["ops_after_fuse"], "norm_minus_1": nrm - 1.0,
+                         "paper_rtx4090_s": paper,
+                         "paper_over_ours": round(paper / (ms * 1e-3), 2) if paper else None}
+        qs.qs_destroy(h)
+        out["sizes"][n] = row
+    out["note"] = ("times include qs_reset (|0..0>) and the host planning of each call; "
+                   "paper times are another GPU (RTX 4090, FP64), context only")
+    return out
 
 
 def wl_served(args):
@@ -666,7 +759,8 @@ def wl_served(args):
 
 def run_workload(args):
     fn = {"circuit12": wl_circuit12, "circuits33": wl_circuits33,
-          "batched": wl_batched, "served": wl_served}[args.workload]
+          "batched": wl_batched, "served": wl_served, "reductions": wl_reductions,
+          "paper": wl_paper}[args.workload]
     print(json.dumps(fn(args)))
 
 

@@ -41,7 +41,7 @@
 extern "C" {
 #endif
 
-#define QS_ABI_VERSION 1
+#define QS_ABI_VERSION 2
 #define QS_MAX_QUBITS 36      /* index arithmetic limit; memory is the real limit */
 #define QS_MAX_GATE_QUBITS 8  /* operands per gate record */
 
@@ -106,20 +106,30 @@ enum {
                              the streaming and the in-cache (chunk) passes. */
 };
 
+/* Bits of qs_options.flags (all off by default). */
+enum {
+    QS_OPT_NO_REG_PHASES = 1,   /* complex64 passes over 2^13-amplitude tiles: one shared-memory
+                                   sweep per op instead of register phases (runs of one-qubit,
+                                   controlled and at most two-qubit diagonal gates applied to
+                                   amplitudes held in registers, one sweep per run) */
+    QS_OPT_NO_DIAG_MERGE = 2,   /* QS_MODE_AUTO / QS_MODE_CHUNK: never merge runs of diagonal
+                                   gates into one phase-function pass (by default both plans are
+                                   built and the one with fewer passes over the state runs) */
+    QS_OPT_NO_TC_NORM_FIX = 4   /* no norm-preserving correction after complex64 circuits that
+                                   used tensor-core blocks (by default the squared norm before
+                                   the circuit is restored, removing the small systematic shrink
+                                   of FP32 accumulation inside the MMA) */
+};
+
 /* Options for qs_apply_circuit; pass NULL for defaults.  Zero fields mean "choose". */
 typedef struct {
     int32_t mode;         /* QS_MODE_* */
     int32_t fuse_k;       /* max qubits of a fused block (0: choose; 1 disables fusion) */
     int32_t chunk_m;      /* local qubits of a chunk pass (0: choose) */
     int32_t precision;    /* QS_PREC_* */
-    /* reserved[0], reserved[1]: batched-launch wait limit and test hook (qs_batch_create);
-     * reserved[2] = 1 turns off the norm-preserving correction after complex64 circuits that
-     * used tensor-core blocks (default on: the squared norm before the circuit is restored,
-     * which removes the small systematic shrink of FP32 accumulation inside the MMA);
-     * reserved[3] = 1 turns off register phases in complex64 passes over 2^13-amplitude tiles
-     * (every op then takes its own shared-memory sweep of the tile; default on: runs of
-     * one-qubit, controlled and at most two-qubit diagonal gates are applied to amplitudes
-     * held in registers, one sweep per run). */
+    uint32_t flags;       /* QS_OPT_* bits */
+    /* reserved[0], reserved[1]: batched-launch wait limit in microseconds and a test hook
+     * (qs_batch_create); reserved[2], reserved[3]: zero. */
     int32_t reserved[4];
 } qs_options;
 

@@ -134,7 +134,7 @@ void run_circuit(DeviceState &d, const std::vector<Op> &ops, const qs_options &o
     if (o.precision != QS_PREC_DEFAULT && o.precision != QS_PREC_FP64 && o.precision != QS_PREC_DF32)
         fail(QS_ERR_INVALID, "unknown precision mode");
     d.prec = o.precision == QS_PREC_DF32 ? QS_PREC_DF32 : QS_PREC_FP64;
-    d.reg_phases = o.reserved[3] == 0;
+    d.reg_phases = (o.flags & QS_OPT_NO_REG_PHASES) == 0;
     const uint64_t l0 = g_launches.load();
     arena_begin(d);
     const int mode = o.mode;
@@ -366,10 +366,19 @@ int qs_plan(int n_qubits, qs_dtype dt, const qs_gate *gates, size_t n_gates, con
     DeviceState d;
     d.n = n_qubits;
     d.dtype = dt;
-    const std::vector<Pass> plan = make_plan(ops, n_qubits, plan_params(d, o));
+    d.reg_phases = (o.flags & QS_OPT_NO_REG_PHASES) == 0;
+    std::vector<Op> merged;
+    std::vector<std::pair<size_t, size_t>> origin;
+    const std::vector<Pass> plan = choose_plan(ops, n_qubits, plan_params(d, o), o, merged, origin);
     for (size_t p = 0; p < plan.size(); p++) {
         pass_lmask[p] = plan[p].stream ? 0 : plan[p].lmask;
-        for (int i : plan[p].ops) pass_of_gate[i] = (int32_t)p;
+        for (int i : plan[p].ops) {
+            if (merged.empty()) {
+                pass_of_gate[i] = (int32_t)p;
+            } else {
+                for (size_t g = origin[i].first; g < origin[i].second; g++) pass_of_gate[g] = (int32_t)p;
+            }
+        }
     }
     *n_passes = (int64_t)plan.size();
     QS_API_END

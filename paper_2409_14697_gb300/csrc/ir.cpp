@@ -145,6 +145,7 @@ std::vector<cd> Op::full() const {
         for (size_t i = 0; i < d; i++) f[i * d + i] = m[i];
         break;
     case K_DENSE: f = m; break;
+    case K_PHASEFN: fail(QS_ERR_INVALID, "a phase function has no dense matrix");
     }
     return f;
 }
@@ -194,8 +195,124 @@ double op_flops(const Op &op) {
     case K_CTRL1: return 4.0;
     case K_DIAG: return 4.0;
     case K_DENSE: return 4.0 * (double)(1 << op.k);
+    case K_PHASEFN: return 6.0;
     }
     return 8.0;
+}
+
+namespace {
+
+// Diagonal entries of op on its own operands (first operand most significant), if it is
+// a diagonal (K_DIAG1, K_DIAG, or K_CTRL1 with a diagonal 2x2).
+bool diag_of(const Op &op, std::vector<cd> &d) {
+    switch (op.kind) {
+    case K_DIAG1:
+    case K_DIAG:
+        d = op.m;
+        return true;
+    case K_CTRL1:
+        if (op.m[1] != cd(0.0) || op.m[2] != cd(0.0)) return false;
+        d = {1.0, 1.0, op.m[0], op.m[3]};
+        return true;
+    default:
+        return false;
+    }
+}
+
+// FP64 operations per amplitude of one diagonal applied alone in a shared-memory sweep of
+// a complex128 tile: a complex multiply is 4, restricted to the fraction of elements it
+// changes; a sign flip is free.
+double diag_cost(const std::vector<cd> &d) {
+    size_t changed = 0;
+    bool neg_only = true;
+    for (const cd &z : d)
+        if (z != cd(1.0)) {
+            changed++;
+            neg_only = neg_only && z == cd(-1.0);
+        }
+    if (changed == 0 || neg_only) return 0.0;
+    // the kernels restrict work to the elements with the controls set (phase on |1..1>)
+    if (changed == 1 && d.back() != cd(1.0)) return 4.0 / (double)d.size();
+    return 4.0;
+}
+
+}  // namespace
+
+std::vector<Op> merge_tile_diagonals(const std::vector<Op> &ops, int max_k, double sweep_cost) {
+    std::vector<Op> out;
+    std::vector<int> Q;                  // block qubits, Q[0] most significant
+    std::vector<cd> D;                   // block diagonal over Q
+    std::vector<const Op *> members;
+    double member_cost = 0.0;
+    auto flush = [&]() {
+        if (members.empty()) return;
+        // controls: qubits on whose 0-half every entry is 1; the block then costs a complex
+        // multiply on the elements with all controls set
+        const int K = (int)Q.size();
+        int nctl = 0;
+        for (int j = 0; j < K; j++) {
+            const int bit = K - 1 - j;
+            bool ctl = true;
+            for (size_t x = 0; x < D.size() && ctl; x++)
+                if (!((x >> bit) & 1) && D[x] != cd(1.0)) ctl = false;
+            nctl += ctl;
+        }
+        bool identity = true;
+        for (const cd &z : D) identity = identity && z == cd(1.0);
+        const double merged = identity ? 0.0 : 4.0 / (double)(1u << nctl) + sweep_cost;
+        if (members.size() >= 2 && merged < member_cost) {
+            if (!identity) {
+                Op b;
+                b.kind = K_DIAG;
+                b.k = K;
+                for (int j = 0; j < K; j++) b.q[j] = Q[j];
+                b.m = D;
+                out.push_back(std::move(b));
+            }
+        } else {
+            for (const Op *m : members) out.push_back(*m);
+        }
+        members.clear();
+        Q.clear();
+        D.clear();
+        member_cost = 0.0;
+    };
+    for (const Op &op : ops) {
+        std::vector<cd> d;
+        if (!diag_of(op, d)) {
+            flush();
+            out.push_back(op);
+            continue;
+        }
+        std::vector<int> nQ = Q;
+        for (int j = 0; j < op.k; j++)
+            if (std::find(nQ.begin(), nQ.end(), op.q[j]) == nQ.end()) nQ.push_back(op.q[j]);
+        if ((int)nQ.size() > max_k) {
+            flush();
+            nQ.assign(op.q, op.q + op.k);
+        }
+        std::sort(nQ.begin(), nQ.end(), [](int a, int b) { return a > b; });
+        const int K = (int)nQ.size();
+        std::vector<cd> nD((size_t)1 << K, 1.0);
+        for (size_t x = 0; x < nD.size(); x++) {
+            auto bit_of = [&](int q) {
+                for (int t = 0; t < K; t++)
+                    if (nQ[t] == q) return (int)((x >> (K - 1 - t)) & 1);
+                return 0;
+            };
+            size_t xo = 0;  // index into the old block
+            for (size_t t = 0; t < Q.size(); t++) xo |= (size_t)bit_of(Q[t]) << (Q.size() - 1 - t);
+            size_t xm = 0;  // index into the op's own diagonal
+            for (int j = 0; j < op.k; j++) xm |= (size_t)bit_of(op.q[j]) << (op.k - 1 - j);
+            nD[x] = (members.empty() ? cd(1.0) : D[xo]) * d[xm];
+        }
+        Q = nQ;
+        D = std::move(nD);
+        members.push_back(&op);
+        member_cost += diag_cost(d) + sweep_cost;
+    }
+    flush();
+    return out;
 }
 
 std::vector<Op> fuse_ops(const std::vector<Op> &ops, int fuse_k, double sweep_flops) {

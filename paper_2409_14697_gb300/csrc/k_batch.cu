@@ -212,7 +212,7 @@ void batch_build(Batch &b, const std::vector<std::vector<Op>> &circ_ops, const s
         DeviceState d;
         d.n = n;
         d.dtype = b.dtype;
-        d.reg_phases = o.reserved[3] == 0;
+        d.reg_phases = (o.flags & QS_OPT_NO_REG_PHASES) == 0;
         qs_options oc = o;
         oc.chunk_m = std::min(m_max, n);
         PlanParams pp = plan_params(d, oc);

@@ -1,12 +1,14 @@
 // K4/K5: reductions and simple state kernels.
 //
 //  * norm and <Z_q> for every q in one read pass.  <Z_q> = sum_x |a_x|^2 (1 - 2 bit_q(x))
-//    = total - 2 S_q with S_q the probability mass on bit_q = 1.  Each block owns a
-//    contiguous chunk of 2^cb amplitudes, so every qubit >= cb is constant over the
-//    block and only the block total is needed for it; qubits < cb are split into
-//    thread bits and loop bits.  Everything is accumulated in FP64 in a fixed order
-//    (per-thread loop, fixed butterfly trees, fixed second stage), so results are
-//    bitwise reproducible whatever else runs on the GPU.
+//    = total - 2 S_q with S_q the probability mass on bit_q = 1.  Three levels: a block
+//    of the first level owns a contiguous chunk of 2^cb amplitudes, so every qubit >= cb
+//    is constant over it and only its total is needed for that qubit (qubits < cb are
+//    split into thread bits and loop bits); the second level combines groups of 256 such
+//    records, adding the 8 qubits spelled by the record index within the group; the last
+//    level combines the few second-level records.  Everything is accumulated in FP64 in a
+//    fixed order (per-thread loop, fixed butterfly trees, fixed upper levels), so results
+//    are bitwise reproducible whatever else runs on the GPU.
 //  * top-K |a|^2: exact radix select of the K-th largest key (the bit pattern of the
 //    non-negative probability, monotone in its value), then a deterministic gather of
 //    the elements above it and of the lowest-index ties, then one-block bitonic sort.
@@ -20,8 +22,6 @@
 namespace qs {
 namespace {
 
-constexpr int kMaxLoopBits = 10;
-
 __device__ __forceinline__ double prob(double2 a) {
     return __dadd_rn(__dmul_rn(a.x, a.x), __dmul_rn(a.y, a.y));
 }
@@ -29,6 +29,22 @@ __device__ __forceinline__ double prob(float2 a) {
     // products of floats are exact in double
     return __dadd_rn(__dmul_rn((double)a.x, (double)a.x), __dmul_rn((double)a.y, (double)a.y));
 }
+// Exact float -> double by integer bit operations (the hardware conversion runs on the
+// FP64 pipe); zero, subnormal and non-finite values take the hardware conversion.
+__device__ __forceinline__ double f2d_exact(float x) {
+    const uint32_t b = __float_as_uint(x);
+    const uint32_t e = (b >> 23) & 0xFFu;
+    if (e == 0u || e == 0xFFu) return (double)x;
+    const uint32_t hi = (b & 0x80000000u) | ((e + 896u) << 20) | ((b & 0x7FFFFFu) >> 3);
+    return __hiloint2double((int)hi, (int)((b & 7u) << 29));
+}
+// |a|^2 for sums (not keys): one FP64 multiply and one fused multiply-add
+__device__ __forceinline__ double prob_sum(double2 a) { return __fma_rn(a.x, a.x, __dmul_rn(a.y, a.y)); }
+__device__ __forceinline__ double prob_sum(float2 a) {
+    const double x = f2d_exact(a.x), y = f2d_exact(a.y);
+    return __fma_rn(x, x, __dmul_rn(y, y));
+}
+
 
 // Butterfly sum over a warp: fixed order, identical result in every lane.
 __device__ __forceinline__ double warp_sum(double v) {
@@ -37,72 +53,88 @@ __device__ __forceinline__ double warp_sum(double v) {
     return v;
 }
 
-// part[blk*(cb+1) + 0] = block total; part[blk*(cb+1) + 1 + q] = mass with bit q set, q < cb.
-template <typename V>
+// Level 1: part[blk*(cb+1) + 0] = block total; part[blk*(cb+1) + 1 + q] = mass with bit q
+// set, q < cb.  JB = loop bits per thread (cb = tb + JB); BITS = 0: totals only.
+template <typename V, int JB, int BITS>
 __global__ void __launch_bounds__(256)
-k_expz_part(const V *__restrict__ psi, int cb, int tb, int with_bits, double *__restrict__ part) {
+k_expz_part(const V *__restrict__ psi, int cb, int tb, double *__restrict__ part) {
     __shared__ double s_tot[256];
-    __shared__ double s_j[kMaxLoopBits][256];
+    __shared__ double s_j[JB > 0 ? JB : 1][256];
     const int T = 1 << tb, t = threadIdx.x;
-    const int jb = cb - tb, J = 1 << jb;
     const uint64_t start = (uint64_t)blockIdx.x << cb;
-    double tot = 0.0, jacc[kMaxLoopBits];
+    double tot = 0.0, jacc[JB > 0 ? JB : 1];
 #pragma unroll
-    for (int b = 0; b < kMaxLoopBits; b++) jacc[b] = 0.0;
-    for (int j = 0; j < J; j++) {
-        const double p = prob(psi[start + ((uint64_t)j << tb) + t]);
+    for (int b = 0; b < JB; b++) jacc[b] = 0.0;
+#pragma unroll 4
+    for (int j = 0; j < (1 << JB); j++) {
+        const double p = prob_sum(psi[start + ((uint64_t)j << tb) + t]);
         tot += p;
-        if (with_bits) {
+        if (BITS) {
 #pragma unroll
-            for (int b = 0; b < kMaxLoopBits; b++)
-                if (b < jb && ((j >> b) & 1)) jacc[b] += p;
+            for (int b = 0; b < JB; b++)
+                if ((j >> b) & 1) jacc[b] += p;
         }
     }
     s_tot[t] = tot;
-    if (with_bits)
-        for (int b = 0; b < jb; b++) s_j[b][t] = jacc[b];
+    if (BITS)
+#pragma unroll
+        for (int b = 0; b < JB; b++) s_j[b][t] = jacc[b];
     __syncthreads();
-    const int n_out = with_bits ? cb + 1 : 1;
+    const int n_out = BITS ? cb + 1 : 1;
     const int warp = t >> 5, lane = t & 31, nw = (T + 31) >> 5;
     for (int r = warp; r < n_out; r += nw) {
+        auto val = [&](int u) -> double {
+            if (r == 0) return s_tot[u];
+            if (r - 1 < tb) return ((u >> (r - 1)) & 1) ? s_tot[u] : 0.0;
+            return s_j[r - 1 - tb][u];
+        };
         double v = 0.0;
-        for (int u = lane; u < T; u += 32) {
-            double x;
-            if (r == 0) x = s_tot[u];
-            else if (r - 1 < tb) x = ((u >> (r - 1)) & 1) ? s_tot[u] : 0.0;
-            else x = s_j[r - 1 - tb][u];
-            v += x;
-        }
-        v = T >= 32 ? warp_sum(v) : v;
-        if (T < 32) {  // tiny blocks: lane 0 adds the T lanes in order
-            v = 0.0;
-            if (lane == 0)
-                for (int u = 0; u < T; u++) {
-                    double x;
-                    if (r == 0) x = s_tot[u];
-                    else if (r - 1 < tb) x = ((u >> (r - 1)) & 1) ? s_tot[u] : 0.0;
-                    else x = s_j[r - 1 - tb][u];
-                    v += x;
-                }
+        if (T >= 32) {
+            for (int u = lane; u < T; u += 32) v += val(u);
+            v = warp_sum(v);
+        } else if (lane == 0) {  // tiny blocks: lane 0 adds the T lanes in order
+            for (int u = 0; u < T; u++) v += val(u);
         }
         if (lane == 0) part[(uint64_t)blockIdx.x * (cb + 1) + r] = v;
     }
 }
 
-// out[0] = total, out[1 + q] = <Z_q> for q < n.  One block per output.
+// Level 2: one block per group of G = 2^gb consecutive level-1 records (G <= 256): record
+// layout [total, S_0 .. S_{cb-1}, S_cb .. S_{cb+gb-1}] (r2 = cb + 1 + gb doubles); the
+// last gb masses come from the totals of the records whose index in the group has that
+// bit set.  Each warp owns outputs; lane l adds records l, l + 32, ... in order, then a
+// fixed butterfly.
 __global__ void __launch_bounds__(256)
-k_expz_final(const double *__restrict__ part, uint64_t nblk, int cb, int n_out_q,
-             double *__restrict__ out) {
+k_expz_mid(const double *__restrict__ part, int cb, int gb, int bits, double *__restrict__ mid) {
+    const int G = 1 << gb, r1 = cb + 1, r2 = bits ? cb + 1 + gb : 1;
+    const uint64_t g0 = (uint64_t)blockIdx.x << gb;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int o = warp; o < r2; o += 8) {
+        double v = 0.0;
+        for (int u = lane; u < G; u += 32) {
+            const double *rec = part + (g0 + (uint64_t)u) * r1;
+            if (o < r1) v += rec[o];
+            else if ((u >> (o - r1)) & 1) v += rec[0];
+        }
+        v = warp_sum(v);
+        if (lane == 0) mid[(uint64_t)blockIdx.x * r2 + o] = v;
+    }
+}
+
+// Level 3: out[0] = total, out[1 + q] = <Z_q> for q < n.  One block per output, over the
+// nmid level-2 records (record width r2 = cb + 1 + gb; qubits >= cb + gb from totals).
+__global__ void __launch_bounds__(256)
+k_expz_final(const double *__restrict__ mid, uint64_t nmid, int qlo, int r2, double *__restrict__ out) {
     __shared__ double s[256];
     const int o = blockIdx.x;  // 0: total, 1+q: qubit q
     const int q = o - 1;
     double tot = 0.0, v = 0.0;
-    for (uint64_t b = threadIdx.x; b < nblk; b += 256) {
-        const double bt = part[b * (cb + 1)];
+    for (uint64_t b = threadIdx.x; b < nmid; b += 256) {
+        const double bt = mid[b * r2];
         tot += bt;
         if (q >= 0) {
-            if (q < cb) v += part[b * (cb + 1) + 1 + q];
-            else if ((b >> (q - cb)) & 1) v += bt;
+            if (q < qlo) v += mid[b * r2 + 1 + q];
+            else if ((b >> (q - qlo)) & 1) v += bt;
         }
     }
     // fixed-order tree over the 256 partials
@@ -118,7 +150,59 @@ k_expz_final(const double *__restrict__ part, uint64_t nblk, int cb, int n_out_q
         __syncthreads();
     }
     if (threadIdx.x == 0) out[o] = (q < 0) ? tot : tot - 2.0 * v;
-    (void)n_out_q;
+}
+
+template <typename V, int JB>
+void part_launch(const void *psi, uint64_t nblk, int cb, int tb, bool bits, double *part, cudaStream_t st) {
+    if (bits) k_expz_part<V, JB, 1><<<(unsigned)nblk, 1 << tb, 0, st>>>((const V *)psi, cb, tb, part);
+    else k_expz_part<V, JB, 0><<<(unsigned)nblk, 1 << tb, 0, st>>>((const V *)psi, cb, tb, part);
+}
+
+template <typename V>
+void part_dispatch(const void *psi, uint64_t nblk, int cb, int tb, bool bits, double *part, cudaStream_t st) {
+    switch (cb - tb) {
+    case 0: part_launch<V, 0>(psi, nblk, cb, tb, bits, part, st); break;
+    case 1: part_launch<V, 1>(psi, nblk, cb, tb, bits, part, st); break;
+    case 2: part_launch<V, 2>(psi, nblk, cb, tb, bits, part, st); break;
+    case 3: part_launch<V, 3>(psi, nblk, cb, tb, bits, part, st); break;
+    case 4: part_launch<V, 4>(psi, nblk, cb, tb, bits, part, st); break;
+    case 5: part_launch<V, 5>(psi, nblk, cb, tb, bits, part, st); break;
+    case 6: part_launch<V, 6>(psi, nblk, cb, tb, bits, part, st); break;
+    case 7: part_launch<V, 7>(psi, nblk, cb, tb, bits, part, st); break;
+    case 8: part_launch<V, 8>(psi, nblk, cb, tb, bits, part, st); break;
+    case 9: part_launch<V, 9>(psi, nblk, cb, tb, bits, part, st); break;
+    case 10: part_launch<V, 10>(psi, nblk, cb, tb, bits, part, st); break;
+    default: fail(QS_ERR_INVALID, "reduction block too large");
+    }
+}
+
+// Scratch doubles of the three-level pipeline for n qubits, first-level blocks of 2^cb.
+size_t expz_pipeline_doubles(int n, int cb) {
+    const uint64_t nblk = 1ull << (n - cb);
+    const int gb = (int)std::min<uint64_t>(8, (uint64_t)(n - cb));
+    const uint64_t nmid = nblk >> gb;
+    return nblk * (cb + 1) + nmid * (cb + 1 + gb) + n + 1;
+}
+
+// Norm (and <Z_q> if bits) of the state at psi into out (n + 1 doubles, device); scratch
+// holds expz_pipeline_doubles(n, cb) doubles (out may be its tail).
+void expz_pipeline(const void *psi, bool c128, int n, int cb, bool bits, double *scratch, double *out,
+                   cudaStream_t st) {
+    const int tb = std::min(cb, 8);
+    const uint64_t nblk = 1ull << (n - cb);
+    const int gb = (int)std::min<uint64_t>(8, (uint64_t)(n - cb));
+    const uint64_t nmid = nblk >> gb;
+    double *part = scratch;
+    double *mid = part + nblk * (cb + 1);
+    if (c128) part_dispatch<double2>(psi, nblk, cb, tb, bits, part, st);
+    else part_dispatch<float2>(psi, nblk, cb, tb, bits, part, st);
+    QS_CUDA(cudaGetLastError());
+    k_expz_mid<<<(unsigned)nmid, 256, 0, st>>>(part, cb, gb, bits ? 1 : 0, mid);
+    QS_CUDA(cudaGetLastError());
+    const int r2 = bits ? cb + 1 + gb : 1;
+    k_expz_final<<<bits ? n + 1 : 1, 256, 0, st>>>(mid, nmid, cb + gb, r2, out);
+    QS_CUDA(cudaGetLastError());
+    count_launch(3);
 }
 
 __global__ void k_set_one(void *psi, int is_c128) {
@@ -173,7 +257,8 @@ constexpr int kBins = 1 << kDigitBits;
 template <typename V>
 __global__ void __launch_bounds__(256)
 k_sel_hist(const V *__restrict__ psi, uint64_t n, const SelState *__restrict__ st, int hi_shift,
-           int shift, unsigned long long *__restrict__ hist) {
+           int shift, unsigned long long *__restrict__ hist, const int *__restrict__ skip) {
+    if (*skip) return;
     __shared__ unsigned int h[kBins];
     for (int i = threadIdx.x; i < kBins; i += 256) h[i] = 0;
     __syncthreads();
@@ -188,7 +273,8 @@ k_sel_hist(const V *__restrict__ psi, uint64_t n, const SelState *__restrict__ s
         if (h[i]) atomicAdd(&hist[i], (unsigned long long)h[i]);
 }
 
-__global__ void k_sel_init(SelState *st, unsigned long long K) {
+__global__ void k_sel_init(SelState *st, unsigned long long K, const int *skip) {
+    if (*skip) return;
     st->prefix = 0ull;
     st->need = K;
     st->shift = 0;
@@ -196,8 +282,8 @@ __global__ void k_sel_init(SelState *st, unsigned long long K) {
 }
 
 // Picks the digit holding the need-th largest key among the matching ones.
-__global__ void k_sel_pick(SelState *st, unsigned long long *hist, int shift) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+__global__ void k_sel_pick(SelState *st, unsigned long long *hist, int shift, const int *skip) {
+    if (threadIdx.x != 0 || blockIdx.x != 0 || *skip) return;
     unsigned long long need = st->need, acc = 0;
     int d = kBins - 1;
     for (; d > 0; d--) {
@@ -213,7 +299,8 @@ __global__ void k_sel_pick(SelState *st, unsigned long long *hist, int shift) {
 template <typename V>
 __global__ void __launch_bounds__(256)
 k_tie_count(const V *__restrict__ psi, int cb, const SelState *__restrict__ st,
-            unsigned int *__restrict__ cnt) {
+            unsigned int *__restrict__ cnt, const int *__restrict__ skip) {
+    if (*skip) return;
     __shared__ unsigned int c;
     if (threadIdx.x == 0) c = 0;
     __syncthreads();
@@ -227,8 +314,8 @@ k_tie_count(const V *__restrict__ psi, int cb, const SelState *__restrict__ st,
 }
 
 // Exclusive scan of the per-block tie counts (one block, fixed order).
-__global__ void k_tie_scan(unsigned int *cnt, uint64_t nblk) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+__global__ void k_tie_scan(unsigned int *cnt, uint64_t nblk, const int *skip) {
+    if (threadIdx.x != 0 || blockIdx.x != 0 || *skip) return;
     unsigned long long acc = 0;
     for (uint64_t b = 0; b < nblk; b++) {
         const unsigned int c = cnt[b];
@@ -243,7 +330,9 @@ template <typename V>
 __global__ void __launch_bounds__(256)
 k_gather(const V *__restrict__ psi, int cb, const SelState *__restrict__ st, unsigned int K,
          const unsigned int *__restrict__ tie_base, unsigned int *__restrict__ gt_count,
-         unsigned long long *__restrict__ out_key, unsigned long long *__restrict__ out_idx) {
+         unsigned long long *__restrict__ out_key, unsigned long long *__restrict__ out_idx,
+         const int *__restrict__ skip) {
+    if (*skip) return;
     __shared__ unsigned int warp_cnt[8];
     __shared__ unsigned int running;
     const unsigned long long T = st->prefix, need = st->need;
@@ -285,13 +374,18 @@ k_gather(const V *__restrict__ psi, int cb, const SelState *__restrict__ st, uns
 // entries beyond K are padding (key 0, idx max).  Writes idx and amplitudes (as doubles).
 template <typename V>
 __global__ void __launch_bounds__(1024)
-k_topk_sort(const V *__restrict__ psi, unsigned long long *key, unsigned long long *idx, int K,
-            int P, unsigned long long *__restrict__ out_idx, double *__restrict__ out_amp) {
+k_topk_sort(const V *__restrict__ psi, const unsigned long long *key, const unsigned long long *idx, int K,
+            int P, int n_in, const unsigned int *__restrict__ n_in_dev, unsigned long long *__restrict__ out_idx,
+            double *__restrict__ out_amp, const int *__restrict__ skip, int skip_when) {
+    // runs when *skip != skip_when: the exact pipeline's sort skips when the fast path ran,
+    // the fast path's sort skips when it did not
+    if ((*skip != 0) == (skip_when != 0)) return;
     extern __shared__ unsigned long long sm[];
     unsigned long long *sk = sm, *si = sm + P;
+    if (n_in < 0) n_in = (int)min(*n_in_dev, (unsigned int)P);  // candidate count (fast path)
     for (int i = threadIdx.x; i < P; i += blockDim.x) {
-        sk[i] = i < K ? key[i] : 0ull;
-        si[i] = i < K ? idx[i] : ~0ull;
+        sk[i] = i < n_in ? key[i] : 0ull;
+        si[i] = i < n_in ? idx[i] : ~0ull;
     }
     __syncthreads();
     for (int size = 2; size <= P; size <<= 1) {
@@ -320,6 +414,113 @@ k_topk_sort(const V *__restrict__ psi, unsigned long long *key, unsigned long lo
     }
 }
 
+// ---- top-K fast path: FP32 prefilter, exact FP64 keys for the candidates only ----------
+// p32 = |a|^2 in FP32 from the amplitude truncated to FP32 (complex128: by integer bit
+// operations, no FP64 instruction), relative error below 2^-20.  Its bits (sign 0) are
+// monotone in the value: coarse bin = bits >> 20 (exponent + 3 mantissa bits), fine bin =
+// (bits >> 9) & 2047 (fine bins are 2^-14 relative wide).  The K-th largest p32 lies in fine
+// bin T = (b1 << 11) | b2; every element of the exact top K has p32 at or above fine bin
+// T - 1 (the FP32 error is far below one fine bin), and every element below it has an exact
+// key below the K-th one, so sorting the candidates by (exact key desc, index asc) gives the
+// exact selection and tie order.
+constexpr int kTkBins = 2048;
+constexpr int kTkCap = 8192;  // candidates the one-block sort holds
+
+struct TkState {
+    int ok;                  // 1: fast path chosen (the exact pipeline then returns at once)
+    unsigned int cnt;        // candidates collected (must follow ok)
+    unsigned int b1, thr;    // coarse bin of the K-th value, threshold on bits >> 9
+    unsigned long long above1, need1;
+};
+
+__device__ __forceinline__ float trunc_f32(double x) {
+    const uint32_t hi = (uint32_t)__double2hiint(x), lo = (uint32_t)__double2loint(x);
+    const int e = (int)((hi >> 20) & 0x7FFu) - 1023 + 127;
+    if (e <= 0) return 0.0f;
+    if (e >= 255) return __int_as_float(0x7F7FFFFF);
+    return __uint_as_float((hi & 0x80000000u) | ((uint32_t)e << 23) | ((hi & 0xFFFFFu) << 3) | (lo >> 29));
+}
+__device__ __forceinline__ uint32_t p32_bits(double2 a) {
+    const float x = trunc_f32(a.x), y = trunc_f32(a.y);
+    return __float_as_uint(fmaf(x, x, y * y));
+}
+__device__ __forceinline__ uint32_t p32_bits(float2 a) { return __float_as_uint(fmaf(a.x, a.x, a.y * a.y)); }
+
+template <typename V, int LEVEL>
+__global__ void __launch_bounds__(256)
+k_tk_hist(const V *__restrict__ psi, uint64_t n, const TkState *__restrict__ ts,
+          unsigned long long *__restrict__ hist) {
+    __shared__ unsigned int h[kTkBins];
+    for (int i = threadIdx.x; i < kTkBins; i += 256) h[i] = 0;
+    __syncthreads();
+    const uint32_t b1 = LEVEL == 2 ? ts->b1 : 0u;
+    for (uint64_t i = (uint64_t)blockIdx.x * 256 + threadIdx.x; i < n; i += (uint64_t)gridDim.x * 256) {
+        const uint32_t b = p32_bits(psi[i]);
+        if (LEVEL == 1) atomicAdd(&h[b >> 20], 1u);
+        else if ((b >> 20) == b1) atomicAdd(&h[(b >> 9) & (kTkBins - 1)], 1u);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < kTkBins; i += 256)
+        if (h[i]) atomicAdd(&hist[i], (unsigned long long)h[i]);
+}
+
+__global__ void k_tk_plan1(const unsigned long long *__restrict__ h1, unsigned long long K, TkState *ts) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    unsigned long long acc = 0;
+    int b = kTkBins - 1;
+    for (; b > 0; b--) {
+        if (acc + h1[b] >= K) break;
+        acc += h1[b];
+    }
+    ts->b1 = (unsigned int)b;
+    ts->above1 = acc;
+    ts->need1 = K - acc;
+    ts->ok = 0;
+    ts->cnt = 0;
+}
+
+__global__ void k_tk_plan2(const unsigned long long *__restrict__ h1, const unsigned long long *__restrict__ h2,
+                           uint64_t n, TkState *ts) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    const unsigned long long need = ts->need1;
+    unsigned long long acc = 0;
+    int b2 = kTkBins - 1;
+    for (; b2 > 0; b2--) {
+        if (acc + h2[b2] >= need) break;
+        acc += h2[b2];
+    }
+    const uint32_t b1 = ts->b1, T = (b1 << 11) | (uint32_t)b2;
+    unsigned long long c;
+    if (b2 >= 1) {
+        c = ts->above1;
+        for (int f = b2 - 1; f < kTkBins; f++) c += h2[f];
+    } else if (b1 >= 1) {
+        c = ts->above1 + h1[b1] + h1[b1 - 1];  // bound: part of coarse bin b1 - 1 may join
+    } else {
+        c = n;
+    }
+    ts->thr = T >= 1 ? T - 1 : 0u;
+    ts->ok = c <= (unsigned long long)kTkCap ? 1 : 0;
+}
+
+template <typename V>
+__global__ void __launch_bounds__(256)
+k_tk_collect(const V *__restrict__ psi, uint64_t n, TkState *__restrict__ ts,
+             unsigned long long *__restrict__ ckey, unsigned long long *__restrict__ cidx) {
+    if (!ts->ok) return;
+    const uint32_t thr = ts->thr;
+    for (uint64_t i = (uint64_t)blockIdx.x * 256 + threadIdx.x; i < n; i += (uint64_t)gridDim.x * 256) {
+        const V a = psi[i];
+        if ((p32_bits(a) >> 9) >= thr) {
+            const unsigned int slot = atomicAdd(&ts->cnt, 1u);
+            if (slot < (unsigned int)kTkCap) {
+                ckey[slot] = key_of(a);
+                cidx[slot] = i;
+            }
+        }
+    }
+}
+
 int chunk_bits(int n) { return std::min(n, std::max(12, n - 18)); }
 
 }  // namespace
@@ -341,28 +542,13 @@ void launch_scale(DeviceState &st, double f) {
     count_launch();
 }
 
-size_t scratch_expz_bytes(int n) {
-    const int cb = chunk_bits(n);
-    const uint64_t nblk = 1ull << (n - cb);
-    return (nblk * (cb + 1) + n + 1) * sizeof(double);
-}
+size_t scratch_expz_bytes(int n) { return expz_pipeline_doubles(n, chunk_bits(n)) * sizeof(double); }
 
 // Norm and <Z_q> into out_dev (n + 1 doubles); the partials use st.scratch.
 static void expz_launch(DeviceState &st, bool bits, double *out_dev) {
-    const int n = st.n;
-    const int cb = chunk_bits(n);
-    const int tb = std::min(cb, 8);
-    const uint64_t nblk = 1ull << (n - cb);
-    ensure_scratch(st, scratch_expz_bytes(n));
-    double *part = (double *)st.scratch;
-    if (st.dtype == QS_C128)
-        k_expz_part<double2><<<(unsigned)nblk, 1 << tb, 0, st.stream>>>((const double2 *)st.psi, cb, tb, bits, part);
-    else
-        k_expz_part<float2><<<(unsigned)nblk, 1 << tb, 0, st.stream>>>((const float2 *)st.psi, cb, tb, bits, part);
-    QS_CUDA(cudaGetLastError());
-    k_expz_final<<<bits ? n + 1 : 1, 256, 0, st.stream>>>(part, nblk, cb, n, out_dev);
-    QS_CUDA(cudaGetLastError());
-    count_launch(2);
+    ensure_scratch(st, scratch_expz_bytes(st.n));
+    expz_pipeline(st.psi, st.dtype == QS_C128, st.n, chunk_bits(st.n), bits, (double *)st.scratch, out_dev,
+                  st.stream);
 }
 
 void reduce_expz_async(DeviceState &st, double *out_dev) { expz_launch(st, true, out_dev); }
@@ -382,9 +568,7 @@ void reduce_expz(DeviceState &st, double *norm, double *expz) {
     const int n = st.n;
     const bool bits = expz != nullptr;
     ensure_scratch(st, scratch_expz_bytes(n));
-    const int cb = chunk_bits(n);
-    const uint64_t nblk = 1ull << (n - cb);
-    double *out = (double *)st.scratch + nblk * (cb + 1);
+    double *out = (double *)st.scratch + expz_pipeline_doubles(n, chunk_bits(n)) - (n + 1);
     expz_launch(st, bits, out);
     std::vector<double> h(n + 1);
     QS_CUDA(cudaMemcpyAsync(h.data(), out, sizeof(double) * (bits ? n + 1 : 1), cudaMemcpyDeviceToHost, st.stream));
@@ -396,7 +580,7 @@ void reduce_expz(DeviceState &st, double *norm, double *expz) {
 
 namespace {
 struct TopkLayout {
-    size_t o_sel, o_hist, o_tie, o_gt, o_key, o_idx, o_oidx, o_oamp, total;
+    size_t o_sel, o_hist, o_tie, o_gt, o_key, o_idx, o_oidx, o_oamp, o_ts, o_h1, o_h2, o_ckey, o_cidx, total;
 };
 TopkLayout topk_layout(int n, uint32_t K) {
     const int cb = std::min(n, 12);
@@ -412,6 +596,11 @@ TopkLayout topk_layout(int n, uint32_t K) {
     L.o_idx = carve(sizeof(unsigned long long) * K);
     L.o_oidx = carve(sizeof(unsigned long long) * K);
     L.o_oamp = carve(sizeof(double) * 2 * K);
+    L.o_ts = carve(sizeof(TkState));
+    L.o_h1 = carve(sizeof(unsigned long long) * kTkBins);
+    L.o_h2 = carve(sizeof(unsigned long long) * kTkBins);
+    L.o_ckey = carve(sizeof(unsigned long long) * kTkCap);
+    L.o_cidx = carve(sizeof(unsigned long long) * kTkCap);
     L.total = off;
     return L;
 }
@@ -419,7 +608,10 @@ TopkLayout topk_layout(int n, uint32_t K) {
 
 size_t scratch_topk_bytes(int n, uint32_t k) { return topk_layout(n, k).total; }
 
-// Launches the whole top-K pipeline; results to idx_dev / amp_dev (device).
+// Launches the whole top-K pipeline; results to idx_dev / amp_dev (device).  The fast path
+// (two histogram passes, one collection pass, one sort) is enqueued first; the exact radix
+// pipeline follows and each of its kernels returns at once when the fast path was taken
+// (a device flag), so nothing waits on the host.
 void top_k_async(DeviceState &st, uint32_t K, uint64_t *idx_dev, double *amp_dev) {
     const int n = st.n;
     const uint64_t N = 1ull << n;
@@ -428,58 +620,79 @@ void top_k_async(DeviceState &st, uint32_t K, uint64_t *idx_dev, double *amp_dev
     const int cb = std::min(n, 12);
     const uint64_t nblk = N >> cb;
     const TopkLayout TL = topk_layout(n, K);
-    const size_t o_sel = TL.o_sel, o_hist = TL.o_hist, o_tie = TL.o_tie, o_gt = TL.o_gt, o_key = TL.o_key,
-                 o_idx = TL.o_idx;
     ensure_scratch(st, TL.total);
     char *base = (char *)st.scratch;
-    SelState *sel = (SelState *)(base + o_sel);
-    unsigned long long *hist = (unsigned long long *)(base + o_hist);
-    k_sel_init<<<1, 1, 0, st.stream>>>(sel, (unsigned long long)K);
+    const bool c128 = st.dtype == QS_C128;
+    const int grid = (int)std::min<uint64_t>((N + 255) / 256, (uint64_t)device_sm_count() * 8);
+    unsigned long long *oidx = (unsigned long long *)idx_dev;
+    double *oamp = amp_dev;
+    auto sort_launch = [&](const unsigned long long *key, const unsigned long long *idx, int P, int n_in,
+                           const unsigned int *n_in_dev, const int *flag, int skip_when) {
+        const size_t smem = sizeof(unsigned long long) * 2 * P;
+        if (c128) {
+            auto kern = k_topk_sort<double2>;
+            QS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            kern<<<1, 1024, smem, st.stream>>>((const double2 *)st.psi, key, idx, (int)K, P, n_in, n_in_dev, oidx,
+                                               oamp, flag, skip_when);
+        } else {
+            auto kern = k_topk_sort<float2>;
+            QS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            kern<<<1, 1024, smem, st.stream>>>((const float2 *)st.psi, key, idx, (int)K, P, n_in, n_in_dev, oidx,
+                                               oamp, flag, skip_when);
+        }
+        QS_CUDA(cudaGetLastError());
+    };
+    // ---- fast path
+    TkState *ts = (TkState *)(base + TL.o_ts);
+    unsigned long long *h1 = (unsigned long long *)(base + TL.o_h1), *h2 = (unsigned long long *)(base + TL.o_h2);
+    unsigned long long *ckey = (unsigned long long *)(base + TL.o_ckey), *cidx = (unsigned long long *)(base + TL.o_cidx);
+    QS_CUDA(cudaMemsetAsync(h1, 0, sizeof(unsigned long long) * kTkBins, st.stream));
+    QS_CUDA(cudaMemsetAsync(h2, 0, sizeof(unsigned long long) * kTkBins, st.stream));
+    if (c128) k_tk_hist<double2, 1><<<grid, 256, 0, st.stream>>>((const double2 *)st.psi, N, ts, h1);
+    else k_tk_hist<float2, 1><<<grid, 256, 0, st.stream>>>((const float2 *)st.psi, N, ts, h1);
+    k_tk_plan1<<<1, 1, 0, st.stream>>>(h1, (unsigned long long)K, ts);
+    if (c128) k_tk_hist<double2, 2><<<grid, 256, 0, st.stream>>>((const double2 *)st.psi, N, ts, h2);
+    else k_tk_hist<float2, 2><<<grid, 256, 0, st.stream>>>((const float2 *)st.psi, N, ts, h2);
+    k_tk_plan2<<<1, 1, 0, st.stream>>>(h1, h2, N, ts);
+    if (c128) k_tk_collect<double2><<<grid, 256, 0, st.stream>>>((const double2 *)st.psi, N, ts, ckey, cidx);
+    else k_tk_collect<float2><<<grid, 256, 0, st.stream>>>((const float2 *)st.psi, N, ts, ckey, cidx);
+    QS_CUDA(cudaGetLastError());
+    sort_launch(ckey, cidx, kTkCap, -1, &ts->cnt, &ts->ok, 0);
+    count_launch(6);
+    // ---- exact radix pipeline (returns at once when ts->ok)
+    const int *skip = &ts->ok;
+    SelState *sel = (SelState *)(base + TL.o_sel);
+    unsigned long long *hist = (unsigned long long *)(base + TL.o_hist);
+    k_sel_init<<<1, 1, 0, st.stream>>>(sel, (unsigned long long)K, skip);
     count_launch();
     QS_CUDA(cudaMemsetAsync(hist, 0, sizeof(unsigned long long) * kBins, st.stream));
-    QS_CUDA(cudaMemsetAsync(base + o_gt, 0, sizeof(unsigned int), st.stream));
-    const int grid = (int)std::min<uint64_t>((N + 255) / 256, (uint64_t)device_sm_count() * 8);
+    QS_CUDA(cudaMemsetAsync(base + TL.o_gt, 0, sizeof(unsigned int), st.stream));
     // keys are non-negative doubles: bit 63 is always 0, digits cover bits 62..0
     int hi = 64;
     for (int shift = 63 - kDigitBits; hi > 0; shift -= kDigitBits) {
         const int sh = std::max(shift, 0);
-        if (st.dtype == QS_C128)
-            k_sel_hist<double2><<<grid, 256, 0, st.stream>>>((const double2 *)st.psi, N, sel, hi, sh, hist);
-        else
-            k_sel_hist<float2><<<grid, 256, 0, st.stream>>>((const float2 *)st.psi, N, sel, hi, sh, hist);
-        k_sel_pick<<<1, 1, 0, st.stream>>>(sel, hist, sh);
+        if (c128) k_sel_hist<double2><<<grid, 256, 0, st.stream>>>((const double2 *)st.psi, N, sel, hi, sh, hist, skip);
+        else k_sel_hist<float2><<<grid, 256, 0, st.stream>>>((const float2 *)st.psi, N, sel, hi, sh, hist, skip);
+        k_sel_pick<<<1, 1, 0, st.stream>>>(sel, hist, sh, skip);
         count_launch(2);
         hi = sh;
     }
-    unsigned int *tie = (unsigned int *)(base + o_tie);
-    if (st.dtype == QS_C128)
-        k_tie_count<double2><<<(unsigned)nblk, 256, 0, st.stream>>>((const double2 *)st.psi, cb, sel, tie);
-    else
-        k_tie_count<float2><<<(unsigned)nblk, 256, 0, st.stream>>>((const float2 *)st.psi, cb, sel, tie);
-    k_tie_scan<<<1, 1, 0, st.stream>>>(tie, nblk);
-    unsigned long long *gkey = (unsigned long long *)(base + o_key), *gidx = (unsigned long long *)(base + o_idx);
-    if (st.dtype == QS_C128)
+    unsigned int *tie = (unsigned int *)(base + TL.o_tie);
+    if (c128) k_tie_count<double2><<<(unsigned)nblk, 256, 0, st.stream>>>((const double2 *)st.psi, cb, sel, tie, skip);
+    else k_tie_count<float2><<<(unsigned)nblk, 256, 0, st.stream>>>((const float2 *)st.psi, cb, sel, tie, skip);
+    k_tie_scan<<<1, 1, 0, st.stream>>>(tie, nblk, skip);
+    unsigned long long *gkey = (unsigned long long *)(base + TL.o_key), *gidx = (unsigned long long *)(base + TL.o_idx);
+    if (c128)
         k_gather<double2><<<(unsigned)nblk, 256, 0, st.stream>>>((const double2 *)st.psi, cb, sel, K, tie,
-                                                                   (unsigned int *)(base + o_gt), gkey, gidx);
+                                                                   (unsigned int *)(base + TL.o_gt), gkey, gidx, skip);
     else
         k_gather<float2><<<(unsigned)nblk, 256, 0, st.stream>>>((const float2 *)st.psi, cb, sel, K, tie,
-                                                                  (unsigned int *)(base + o_gt), gkey, gidx);
+                                                                  (unsigned int *)(base + TL.o_gt), gkey, gidx, skip);
+    QS_CUDA(cudaGetLastError());
     int P = 1;
     while (P < (int)K) P <<= 1;
     P = std::max(P, 2);
-    const size_t smem = sizeof(unsigned long long) * 2 * P;
-    unsigned long long *oidx = (unsigned long long *)idx_dev;
-    double *oamp = amp_dev;
-    if (st.dtype == QS_C128) {
-        auto kern = k_topk_sort<double2>;
-        QS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        kern<<<1, 1024, smem, st.stream>>>((const double2 *)st.psi, gkey, gidx, (int)K, P, oidx, oamp);
-    } else {
-        auto kern = k_topk_sort<float2>;
-        QS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        kern<<<1, 1024, smem, st.stream>>>((const float2 *)st.psi, gkey, gidx, (int)K, P, oidx, oamp);
-    }
-    QS_CUDA(cudaGetLastError());
+    sort_launch(gkey, gidx, P, (int)K, nullptr, skip, 1);
     count_launch(4);
 }
 
@@ -513,7 +726,7 @@ namespace {
 constexpr int kNoAllocMaxQubits = 32;
 constexpr int kNoAllocMaxBlockBits = 14;
 // partials: 2^14 blocks x (cb + 1 <= 19) doubles, then the n + 1 outputs
-constexpr size_t kNoAllocScratchDoubles = ((size_t)1 << kNoAllocMaxBlockBits) * 19 + 64;
+constexpr size_t kNoAllocScratchDoubles = ((size_t)1 << kNoAllocMaxBlockBits) * 19 + 2048 + 64;
 
 __device__ __align__(256) double g_noalloc_scratch[kNoAllocScratchDoubles];
 
@@ -549,22 +762,13 @@ extern "C" int qs_expectation_z_noalloc(const void *dev_psi, int n_qubits, qs_dt
                                  std::to_string(kNoAllocScratchDoubles) + " doubles)");
     const int n = n_qubits;
     const int cb = std::min(n, std::max(chunk_bits(n), n - kNoAllocMaxBlockBits));
-    const int tb = std::min(cb, 8);
-    const uint64_t nblk = 1ull << (n - cb);
-    const size_t part_elems = nblk * (cb + 1);
-    if (part_elems + n + 1 > kNoAllocScratchDoubles) fail(QS_ERR_INVALID, "static scratch too small");
-    double *part = noalloc_scratch();
-    double *out = part + part_elems;
+    const size_t need = expz_pipeline_doubles(n, cb);
+    if (need > kNoAllocScratchDoubles) fail(QS_ERR_INVALID, "static scratch too small");
+    double *scratch = noalloc_scratch();
+    double *out = scratch + need - (n + 1);
     cudaStream_t st = (cudaStream_t)stream;
-    // every partial the second stage reads is written by the first: nothing to clear
-    if (dt == QS_C128)
-        k_expz_part<double2><<<(unsigned)nblk, 1 << tb, 0, st>>>((const double2 *)dev_psi, cb, tb, 1, part);
-    else
-        k_expz_part<float2><<<(unsigned)nblk, 1 << tb, 0, st>>>((const float2 *)dev_psi, cb, tb, 1, part);
-    QS_CUDA(cudaGetLastError());
-    k_expz_final<<<n + 1, 256, 0, st>>>(part, nblk, cb, n, out);
-    QS_CUDA(cudaGetLastError());
-    count_launch(2);
+    // every partial a level reads is written by the level before: nothing to clear
+    expz_pipeline(dev_psi, dt == QS_C128, n, cb, true, scratch, out, st);
     double h[kNoAllocMaxQubits + 1];
     QS_CUDA(cudaMemcpyAsync(h, out, sizeof(double) * (n + 1), cudaMemcpyDeviceToHost, st));
     QS_CUDA(cudaStreamSynchronize(st));

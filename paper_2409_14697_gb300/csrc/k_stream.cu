@@ -68,6 +68,16 @@ template <typename T> struct FDense1R0 {
     T m[8];
     template <int L> __device__ void operator()(Amp<T, L> *v) const { f_dense1_r0<T, L>(v, m); }
 };
+template <typename T> struct FDense1Real {
+    static constexpr int NT = 2;
+    T m[8];
+    template <int L> __device__ void operator()(Amp<T, L> *v) const { f_dense1_real<T, L>(v, m); }
+};
+template <typename T> struct FDense1RX {
+    static constexpr int NT = 2;
+    T m[8];
+    template <int L> __device__ void operator()(Amp<T, L> *v) const { f_dense1_rx<T, L>(v, m); }
+};
 template <typename T> struct FDiag1 {
     static constexpr int NT = 2;
     T d[4];
@@ -411,8 +421,19 @@ void launch_typed(DeviceState &st, const Op &op) {
     case F_SWAP: dispatch_elem<T>(st, k, FSwap<T>{}); return;
     case F_NEG: dispatch_elem<T>(st, k, FNeg<T>{}); return;
     case F_DENSE1: {
-        if (std::is_same<T, double>::value && mats[k.mat + 1] == 0.0) {
-            FDense1R0<T> f;  // real first entry (U3, CU3, RX, RY): 7 FP64 ops per amplitude
+        // complex128 is bound by the FP64 pipe: use the cheapest form the matrix allows
+        // (complex64 is bound by HBM, every form takes the same time)
+        const int cls = std::is_same<T, double>::value ? k.k : (int)D1_GENERAL;
+        if (cls == D1_REAL) {
+            FDense1Real<T> f;
+            load_m(f.m, mats, k);
+            dispatch_elem<T>(st, k, f);
+        } else if (cls == D1_RX) {
+            FDense1RX<T> f;
+            load_m(f.m, mats, k);
+            dispatch_elem<T>(st, k, f);
+        } else if (cls == D1_R0) {
+            FDense1R0<T> f;
             load_m(f.m, mats, k);
             dispatch_elem<T>(st, k, f);
         } else {
@@ -497,6 +518,10 @@ int persistent_grid(const void *fn, int threads, size_t smem, uint64_t work_bloc
 }
 
 void launch_stream_op(DeviceState &st, const Op &op) {
+    if (op.kind == K_PHASEFN) {
+        launch_phasefn(st, op);
+        return;
+    }
     if (st.dtype == QS_C128) launch_typed<double>(st, op);
     else launch_typed<float>(st, op);
 }

@@ -9,6 +9,15 @@ namespace qs {
 namespace {
 
 bool is_one(cd z) { return z == cd(1.0, 0.0); }
+
+// D1_* class of a 2x2 matrix (row-major)
+int32_t d1_class(const std::vector<cd> &u) {
+    const bool real = u[0].imag() == 0.0 && u[1].imag() == 0.0 && u[2].imag() == 0.0 && u[3].imag() == 0.0;
+    if (real) return D1_REAL;
+    if (u[0].imag() == 0.0 && u[3].imag() == 0.0 && u[1].real() == 0.0 && u[2].real() == 0.0) return D1_RX;
+    if (u[0].imag() == 0.0) return D1_R0;
+    return D1_GENERAL;
+}
 bool is_minus_one(cd z) { return z == cd(-1.0, 0.0); }
 
 void push_c(std::vector<double> &mats, KOp &k, std::initializer_list<cd> vals) {
@@ -75,6 +84,7 @@ KOp make_kop(const Op &op, const int *pos, std::vector<double> &mats) {
     case K_DENSE1: {
         const int p = P(0);
         KOp k = base(F_DENSE1, {p}, 0, {0, 1ull << p});
+        k.k = d1_class(op.m);
         push_vec(mats, k, op.m);
         return k;
     }
@@ -91,6 +101,7 @@ KOp make_kop(const Op &op, const int *pos, std::vector<double> &mats) {
             return k;
         }
         KOp k = base(F_DENSE1, {c, t}, 1ull << c, {0, 1ull << t});
+        k.k = d1_class(u);
         push_vec(mats, k, u);
         return k;
     }
@@ -138,6 +149,43 @@ KOp make_kop(const Op &op, const int *pos, std::vector<double> &mats) {
     }
     }
     fail(QS_ERR_INVALID, "unknown op kind");
+}
+
+KOp make_tile_kop(const Op &op, const int *pos, std::vector<double> &mats) {
+    if (op.kind != K_DIAG || op.k < 3) return make_kop(op, pos, mats);
+    const int K = op.k;
+    std::vector<int> ctl, tab;  // operand indices
+    for (int j = 0; j < K; j++) {
+        const int bit = K - 1 - j;
+        bool c = true;
+        for (size_t x = 0; x < op.m.size() && c; x++)
+            if (!((x >> bit) & 1) && op.m[x] != cd(1.0)) c = false;
+        (c ? ctl : tab).push_back(j);
+    }
+    if (ctl.empty()) return make_kop(op, pos, mats);
+    KOp k{};
+    k.fkind = F_CDIAGK;
+    k.k = (int)tab.size();
+    for (int i = 0; i < k.k; i++) k.pos[i] = pos[op.q[tab[i]]];
+    std::vector<int> cp;
+    for (int j : ctl) cp.push_back(pos[op.q[j]]);
+    std::sort(cp.begin(), cp.end());
+    k.nf = (int)cp.size();
+    for (int i = 0; i < k.nf; i++) {
+        k.pos[k.k + i] = cp[i];
+        k.set_mask |= 1ull << cp[i];
+    }
+    k.mat = (int32_t)mats.size();
+    for (size_t s = 0; s < (1ull << k.k); s++) {
+        size_t x = 0;  // operand index with every control set and the table bits from s
+        for (int j : ctl) x |= (size_t)1 << (K - 1 - j);
+        for (int i = 0; i < k.k; i++)
+            if ((s >> (k.k - 1 - i)) & 1) x |= (size_t)1 << (K - 1 - tab[i]);
+        mats.push_back(op.m[x].real());
+        mats.push_back(op.m[x].imag());
+    }
+    k.nmat = (int32_t)mats.size() - k.mat;
+    return k;
 }
 
 namespace {
@@ -295,7 +343,7 @@ std::vector<KOp> build_register_phases(const std::vector<Op> &ops, const int *po
         while (first < N && done[first]) first++;
         if (first >= N) break;
         if (!ok[first]) {
-            out.push_back(make_kop(ops[first], pos, mats));
+            out.push_back(make_tile_kop(ops[first], pos, mats));
             done[first] = 1;
             continue;
         }
@@ -422,6 +470,7 @@ double kop_touched_fraction(const KOp &k, int sector_bits) {
 }
 
 double stream_bytes(const Op &op, int n, int dtype) {
+    if (op.kind == K_PHASEFN) return 2.0 * (dtype == QS_C128 ? 16.0 : 8.0) * (double)(1ull << n);
     std::vector<int> ident(64);
     for (int i = 0; i < 64; i++) ident[i] = i;
     std::vector<double> mats;

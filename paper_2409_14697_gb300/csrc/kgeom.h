@@ -11,6 +11,11 @@ namespace qs {
 // op's matrix entries are appended to `mats` (as re, im doubles; KOp.mat indexes them).
 KOp make_kop(const Op &op, const int *pos, std::vector<double> &mats);
 
+// The same for the shared-memory tile kernels: a diagonal on 3 or more qubits whose entries
+// are 1 unless some qubits ("controls") are set becomes F_CDIAGK, which touches only the
+// elements with every control set.
+KOp make_tile_kop(const Op &op, const int *pos, std::vector<double> &mats);
+
 // complex64 tiles of 2^m amplitudes with 2^thread_bits threads: true if register phases
 // apply (m = thread_bits + kRpBits).
 bool rphase_applicable(int m, int thread_bits);

@@ -28,7 +28,14 @@ enum FKind : int32_t {
     F_DENSEK,    // dense 2^k x 2^k on positions pos[] (m: 2^(2k+1) reals), k = 3..6
     F_TC,        // dense block on the tensor cores (k = 4..6; mat/nmat index the B operand)
     F_RPHASE,    // complex64 register phase: a run of ops on 2^5 amplitudes per thread in registers
+    F_CDIAGK,    // tile passes: diagonal over k table positions pos[0..k-1] on the elements whose
+                 // nf control positions pos[k..k+nf-1] (ascending, set_mask) are all set
 };
+
+// Structure of an F_DENSE1 matrix (FP64 operations per amplitude for complex128 work):
+// general 8, real first entry 7 (U3, CU3), real 4 (RY), real diagonal with imaginary
+// off-diagonal 4 (RX).
+enum D1Class : int32_t { D1_GENERAL = 0, D1_R0 = 1, D1_REAL = 2, D1_RX = 3 };
 
 // Reals staged in shared memory per op (dense 4-qubit block: 2 * 16 * 16).
 constexpr int kMaxOpReals = 512;
@@ -65,7 +72,7 @@ struct KOp {
     int32_t nt;         // touched elements per group
     uint64_t set_mask;  // forced-one bits
     uint64_t off[4];    // touched element offsets
-    int32_t k;          // operand count (F_DIAGK / F_DENSEK)
+    int32_t k;          // operand count (F_DIAGK / F_DENSEK); F_DENSE1: a D1_* structure class
     int32_t pos[8];     // operand positions, first = most significant (F_DIAGK / F_DENSEK)
     int32_t mat;        // offset of the op's reals in the parameter array
     int32_t nmat;       // number of reals
@@ -138,6 +145,30 @@ __device__ __forceinline__ void f_dense1_r0(Amp<T, L> *v, const T *m) {
         cdot2(v[1].r[l], v[1].i[l], m[4], m[5], ar, ai, m[6], m[7], br, bi);
         v[0].r[l] = fma(m[0], ar, pr);
         v[0].i[l] = fma(m[0], ai, pi);
+    }
+}
+// Real 2x2 (RY and other real rotations): 4 multiply-adds per amplitude.
+template <typename T, int L>
+__device__ __forceinline__ void f_dense1_real(Amp<T, L> *v, const T *m) {
+#pragma unroll
+    for (int l = 0; l < L; l++) {
+        const T ar = v[0].r[l], ai = v[0].i[l], br = v[1].r[l], bi = v[1].i[l];
+        v[0].r[l] = fma(m[0], ar, m[2] * br);
+        v[0].i[l] = fma(m[0], ai, m[2] * bi);
+        v[1].r[l] = fma(m[4], ar, m[6] * br);
+        v[1].i[l] = fma(m[4], ai, m[6] * bi);
+    }
+}
+// Real diagonal, imaginary off-diagonal (RX): 4 multiply-adds per amplitude.
+template <typename T, int L>
+__device__ __forceinline__ void f_dense1_rx(Amp<T, L> *v, const T *m) {
+#pragma unroll
+    for (int l = 0; l < L; l++) {
+        const T ar = v[0].r[l], ai = v[0].i[l], br = v[1].r[l], bi = v[1].i[l];
+        v[0].r[l] = fma(m[0], ar, -m[3] * bi);
+        v[0].i[l] = fma(m[0], ai, m[3] * br);
+        v[1].r[l] = fma(m[6], br, -m[5] * ai);
+        v[1].i[l] = fma(m[6], bi, m[5] * ar);
     }
 }
 template <typename T, int L, int NT>

@@ -19,15 +19,22 @@
 
 #include "chunk.h"
 #include "kgeom.h"
+#include "phasefn.h"
 #include "plan.h"
 
 namespace qs {
 
 namespace {
 
+// Shortest run of consecutive diagonal gates worth merging into a phase function.
+constexpr int kMinMergedRun = 4;
+// Widest diagonal block merged inside a tile pass (its table: 2^8 entries, 512 reals).
+constexpr int kTileDiagQubits = 8;
+
 // Ops the shared-memory path applies: dense blocks up to 4 qubits (512 matrix reals)
 // and diagonals up to 8 qubits.
 bool chunkable(const Op &op, const PlanParams &pp) {
+    if (op.kind == K_PHASEFN) return false;  // one streaming pass over the whole state
     if (op.kind == K_DENSE) return op.k <= 4 || (pp.tc && tc_available(pp.m, op.k));
     if (op.kind == K_DIAG) return op.k <= 8;
     return true;
@@ -68,7 +75,7 @@ int launch_pass_ops(DeviceState &st, uint64_t lmask, const std::vector<Op> &fuse
             kops.push_back(k);
             any_tc = true;
         } else {
-            kops.push_back(make_kop(op, pos, mats));
+            kops.push_back(make_tile_kop(op, pos, mats));
         }
     }
     if (any_tc) launch_chunk_pass_tc(st, lmask, kops, mats, bmats, b_floats);
@@ -184,6 +191,26 @@ std::vector<Pass> make_plan(const std::vector<Op> &ops, int n, const PlanParams 
     return plan;
 }
 
+std::vector<Pass> choose_plan(const std::vector<Op> &ops, int n, const PlanParams &pp, const qs_options &o,
+                              std::vector<Op> &merged, std::vector<std::pair<size_t, size_t>> &origin) {
+    // Merged diagonal runs (one phase-function pass each) help where a run reaches more
+    // qubits than a chunk pass holds (QAOA cost layers); chains of local diagonals are
+    // cheaper inside chunk passes (TFIM).  Both plans are built; the one with fewer passes
+    // over the state is run.
+    merged.clear();
+    origin.clear();
+    std::vector<Pass> plan = make_plan(ops, n, pp);
+    if ((o.flags & QS_OPT_NO_DIAG_MERGE) != 0 || !phasefn_supported(n)) return plan;
+    std::vector<std::pair<size_t, size_t>> org;
+    std::vector<Op> m = merge_diagonal_runs(ops, kMinMergedRun, &org);
+    if (m.size() >= ops.size()) return plan;
+    std::vector<Pass> alt = make_plan(m, n, pp);
+    if (alt.size() >= plan.size()) return plan;
+    merged = std::move(m);
+    origin = std::move(org);
+    return alt;
+}
+
 void run_planned(DeviceState &st, const std::vector<Op> &ops, const qs_options &o, qs_stats &stats) {
     const int n = st.n;
     const PlanParams pp = plan_params(st, o);
@@ -198,11 +225,14 @@ void run_planned(DeviceState &st, const std::vector<Op> &ops, const qs_options &
         stats.ops_after_fuse = (int64_t)ops.size();
         return;
     }
-    const std::vector<Pass> plan = make_plan(ops, n, pp);
+    std::vector<Op> merged;
+    std::vector<std::pair<size_t, size_t>> origin;
+    const std::vector<Pass> plan = choose_plan(ops, n, pp, o, merged, origin);
+    const std::vector<Op> &ops_r = merged.empty() ? ops : merged;
     // Tensor-core blocks accumulate in FP32 inside the MMA with truncation toward zero, a
     // small systematic shrink per block.  The circuit is unitary, so the FP64 squared norm
     // before it is restored afterwards (three extra read passes and one write pass).
-    const bool correct_norm = pp.tc && o.reserved[2] == 0;
+    const bool correct_norm = pp.tc && (o.flags & QS_OPT_NO_TC_NORM_FIX) == 0;
     if (correct_norm) {
         if (!st.dev_norms) QS_CUDA(cudaMalloc(&st.dev_norms, 2 * sizeof(double)));
         reduce_norm_async(st, st.dev_norms);
@@ -211,8 +241,8 @@ void run_planned(DeviceState &st, const std::vector<Op> &ops, const qs_options &
     for (const Pass &p : plan) {
         if (p.stream) {
             for (int i : p.ops) {
-                launch_stream_op(st, ops[i]);
-                stats.bytes += stream_bytes(ops[i], n, st.dtype);
+                launch_stream_op(st, ops_r[i]);
+                stats.bytes += stream_bytes(ops_r[i], n, st.dtype);
                 n_ops++;
             }
             stats.passes++;
@@ -220,8 +250,14 @@ void run_planned(DeviceState &st, const std::vector<Op> &ops, const qs_options &
         }
         std::vector<Op> pops;
         pops.reserve(p.ops.size());
-        for (int i : p.ops) pops.push_back(ops[i]);
-        const std::vector<Op> fused = fuse_ops(pops, pp.fuse_k, pp.sweep_flops);
+        for (int i : p.ops) pops.push_back(ops_r[i]);
+        std::vector<Op> fused = fuse_ops(pops, pp.fuse_k, pp.sweep_flops);
+        // runs of diagonal gates (e.g. a QFT target's controlled phases) as one diagonal
+        // block per up to 8 qubits, where that is cheaper; register phases already hold
+        // one- and two-qubit diagonals without a sweep
+        const bool phases = st.dtype == QS_C64 && st.reg_phases && !pp.tc &&
+                            rphase_applicable(__builtin_popcountll(p.lmask), kTileThreadBits);
+        if (!phases) fused = merge_tile_diagonals(fused, kTileDiagQubits, st.dtype == QS_C128 ? 0.5 : 4.0);
         stats.tile_sweeps += launch_pass_ops(st, p.lmask, fused, pp.tc);
         stats.passes++;
         stats.bytes += 2.0 * B * (double)(1ull << n);

@@ -24,6 +24,12 @@ struct Pass {
 PlanParams plan_params(const DeviceState &st, const qs_options &o);
 // Greedy dependency-respecting partition of ops into passes.
 std::vector<Pass> make_plan(const std::vector<Op> &ops, int n, const PlanParams &pp);
+// The plan QS_MODE_AUTO / CHUNK runs: the greedy plan of ops, or, if it needs fewer passes,
+// the plan of ops with runs of diagonal gates merged into phase functions (then `merged`
+// receives those ops and `origin` the input range each stands for; otherwise both are
+// left empty).
+std::vector<Pass> choose_plan(const std::vector<Op> &ops, int n, const PlanParams &pp, const qs_options &o,
+                              std::vector<Op> &merged, std::vector<std::pair<size_t, size_t>> &origin);
 // One chunk pass over lmask applying ops already fused (tensor cores if use_tc).
 int launch_pass_ops(DeviceState &st, uint64_t lmask, const std::vector<Op> &fused, bool use_tc);
 // Plans `ops` into passes and launches them on st.stream, filling stats.

@@ -5,6 +5,7 @@
 
 #include <complex>
 #include <cstdint>
+#include <memory>
 #include <string>
 #include <type_traits>
 #include <utility>
@@ -43,17 +44,22 @@ enum OpKind : int32_t {
     K_SWAP,        // exchange |01>,|10> of (q[0], q[1])
     K_DIAG,        // diagonal on k qubits: m holds the 2^k diagonal entries
     K_DENSE,       // dense 2^k x 2^k on k qubits (k >= 2), m row-major
+    K_PHASEFN,     // merged run of diagonal gates on any qubits (pf; k = 0, mask in wide_mask)
 };
+
+struct PhaseFn;
 
 struct Op {
     OpKind kind;
     int k = 0;          // operand count
     int q[8] = {0};     // operands
     std::vector<cd> m;  // K_DIAG1: 2 entries; K_DENSE1/K_CTRL1: 4; K_DIAG: 2^k; K_DENSE: 4^k
+    std::shared_ptr<const PhaseFn> pf;  // K_PHASEFN
+    uint64_t wide_mask = 0;             // K_PHASEFN: every qubit the function reads
     // The full 2^k x 2^k matrix of the op on q[0..k-1] (row-major).
     std::vector<cd> full() const;
     uint64_t qmask() const {
-        uint64_t r = 0;
+        uint64_t r = wide_mask;
         for (int j = 0; j < k; j++) r |= 1ull << q[j];
         return r;
     }
@@ -71,6 +77,12 @@ Op lower_gate(const qs_gate &g);
 // most the flops per amplitude of its members applied one by one plus sweep_flops (the
 // value of one saved pass over the tile).  sweep_flops < 0 merges whenever the width fits.
 std::vector<Op> fuse_ops(const std::vector<Op> &ops, int fuse_k, double sweep_flops = -1.0);
+// Merges runs of consecutive diagonal gates into diagonal blocks of at most max_k qubits
+// where that costs fewer FP64 operations per amplitude in a shared-memory pass (a block
+// multiplies only the elements whose "control" qubits, those on whose 0-half every entry
+// is 1, are set; sweep_cost is added per separate sweep).  FP64 host products; blocks
+// that come out as the identity are dropped.
+std::vector<Op> merge_tile_diagonals(const std::vector<Op> &ops, int max_k, double sweep_cost);
 // Real flops per amplitude of applying op alone (structure-aware).
 double op_flops(const Op &op);
 
@@ -121,6 +133,7 @@ void arena_end(DeviceState &st);
 
 // Launchers (kernels live in the .cu files).  All are asynchronous on st.stream.
 void launch_stream_op(DeviceState &st, const Op &op);           // K1, one op, one pass
+void launch_phasefn(DeviceState &st, const Op &op);             // merged diagonal run, one pass
 void launch_set_zero_state(DeviceState &st);                    // |0..0>
 void launch_scale(DeviceState &st, double f);                   // psi *= f
 // Reductions (K4).  expz may be null (norm only).  Results are copied to host.

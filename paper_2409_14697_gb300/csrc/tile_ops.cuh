@@ -52,6 +52,18 @@ template <typename T> struct SDense1 {
     const T *m;
     __device__ void operator()(Amp<T, 1> *v) const { f_dense1<T, 1>(v, m); }
 };
+template <typename T> struct SDense1R0 {
+    const T *m;
+    __device__ void operator()(Amp<T, 1> *v) const { f_dense1_r0<T, 1>(v, m); }
+};
+template <typename T> struct SDense1Real {
+    const T *m;
+    __device__ void operator()(Amp<T, 1> *v) const { f_dense1_real<T, 1>(v, m); }
+};
+template <typename T> struct SDense1RX {
+    const T *m;
+    __device__ void operator()(Amp<T, 1> *v) const { f_dense1_rx<T, 1>(v, m); }
+};
 template <typename T> struct SDense2 {
     const T *m;
     __device__ void operator()(Amp<T, 1> *v) const { f_dense2<T, 1>(v, m); }
@@ -479,7 +491,17 @@ __device__ __forceinline__ void apply_op_smem(typename C2T<T>::type *tile, const
     switch (op.fkind) {
     case F_H: groups_apply<T, 2>(tile, op, m, SH<T>{(T)0.70710678118654752440}); break;
     case F_SWAP: groups_apply<T, 2>(tile, op, m, SSwap<T>{}); break;
-    case F_DENSE1: groups_apply<T, 2>(tile, op, m, SDense1<T>{sm}); break;
+    case F_DENSE1:
+        if constexpr (std::is_same<T, double>::value) {
+            // complex128: the FP64 pipe is the limit, use the cheapest form
+            if (op.k == D1_REAL) groups_apply<T, 2>(tile, op, m, SDense1Real<T>{sm});
+            else if (op.k == D1_RX) groups_apply<T, 2>(tile, op, m, SDense1RX<T>{sm});
+            else if (op.k == D1_R0) groups_apply<T, 2>(tile, op, m, SDense1R0<T>{sm});
+            else groups_apply<T, 2>(tile, op, m, SDense1<T>{sm});
+        } else {
+            groups_apply<T, 2>(tile, op, m, SDense1<T>{sm});
+        }
+        break;
     case F_DIAG1: groups_apply<T, 2>(tile, op, m, SDiag<T, 2>{sm}); break;
     case F_PHASE: groups_apply<T, 1>(tile, op, m, SDiag<T, 1>{sm}); break;
     case F_NEG: groups_apply<T, 1>(tile, op, m, SNeg<T>{}); break;
@@ -490,6 +512,25 @@ __device__ __forceinline__ void apply_op_smem(typename C2T<T>::type *tile, const
         for (uint32_t x = threadIdx.x; x < N; x += blockDim.x) {
             uint32_t s = 0;
             for (int j = 0; j < op.k; j++) s |= ((x >> op.pos[j]) & 1u) << (op.k - 1 - j);
+            Amp<T, 1> v;
+            ld_amp<T>(tile + x, v);
+            f_diag<T, 1, 1>(&v, sm + 2 * s);
+            st_amp<T>(tile + x, v);
+        }
+        break;
+    }
+    case F_CDIAGK: {
+        const int kt = op.k, kc = op.nf;
+        const uint32_t ng = 1u << (m - kc);
+        for (uint32_t g = threadIdx.x; g < ng; g += blockDim.x) {
+            uint32_t x = g;
+            for (int j = 0; j < kc; j++) {
+                const int b = op.pos[kt + j];
+                x = ((x >> b) << (b + 1)) | (x & ((1u << b) - 1u));
+            }
+            x |= (uint32_t)op.set_mask;
+            uint32_t s = 0;
+            for (int j = 0; j < kt; j++) s |= ((x >> op.pos[j]) & 1u) << (kt - 1 - j);
             Amp<T, 1> v;
             ld_amp<T>(tile + x, v);
             f_diag<T, 1, 1>(&v, sm + 2 * s);

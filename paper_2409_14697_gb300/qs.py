@@ -21,6 +21,7 @@ QS_OK, QS_NOT_READY = 0, 1
 QS_ERR_INVALID, QS_ERR_NOMEM, QS_ERR_CUDA, QS_ERR_TIMEOUT, QS_ERR_BUSY, QS_ERR_UNSUPPORTED = -1, -2, -3, -4, -5, -6
 QS_MODE_AUTO, QS_MODE_GATE, QS_MODE_CHUNK, QS_MODE_FUSED = 0, 1, 2, 3
 QS_PREC_DEFAULT, QS_PREC_FP64, QS_PREC_DF32 = 0, 1, 2
+QS_OPT_NO_REG_PHASES, QS_OPT_NO_DIAG_MERGE, QS_OPT_NO_TC_NORM_FIX = 1, 2, 4
 
 GATE_TYPES = {
     "h": 0, "x": 1, "y": 2, "z": 3, "s": 4, "t": 5,
@@ -43,7 +44,7 @@ class qs_gate(ctypes.Structure):
 
 class qs_options(ctypes.Structure):
     _fields_ = [("mode", ctypes.c_int32), ("fuse_k", ctypes.c_int32), ("chunk_m", ctypes.c_int32),
-                ("precision", ctypes.c_int32), ("reserved", ctypes.c_int32 * 4)]
+                ("precision", ctypes.c_int32), ("flags", ctypes.c_uint32), ("reserved", ctypes.c_int32 * 4)]
 
 
 class qs_stats(ctypes.Structure):
@@ -173,9 +174,9 @@ def gate_records(gates):
     return arr
 
 
-def options(mode=QS_MODE_AUTO, fuse_k=0, chunk_m=0, precision=QS_PREC_DEFAULT):
+def options(mode=QS_MODE_AUTO, fuse_k=0, chunk_m=0, precision=QS_PREC_DEFAULT, flags=0):
     o = qs_options()
-    o.mode, o.fuse_k, o.chunk_m, o.precision = mode, fuse_k, chunk_m, precision
+    o.mode, o.fuse_k, o.chunk_m, o.precision, o.flags = mode, fuse_k, chunk_m, precision, flags
     return o
 
 

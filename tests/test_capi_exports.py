@@ -39,10 +39,10 @@ def test_version_without_gpu():
     from paper_2409_14697_gb300 import build as b, qs
     b.build()
     abi, ndev = qs.qs_version()
-    assert abi == 1 and ndev >= 0
+    assert abi == 2 and ndev >= 0
 
 
 def test_gate_record_layout():
     from paper_2409_14697_gb300 import qs
     assert ctypes.sizeof(qs.qs_gate) == 72
-    assert ctypes.sizeof(qs.qs_options) == 32
+    assert ctypes.sizeof(qs.qs_options) == 36

@@ -142,7 +142,7 @@ def _run_c64(qs, n, psi0, gates, phases=True, **kw):
         qs.qs_set_amplitudes(h, psi0)
         o = qs.options(**kw)
         if not phases:
-            o.reserved[3] = 1
+            o.flags |= qs.QS_OPT_NO_REG_PHASES
         qs.qs_apply_circuit(h, gates, o)
         return qs.qs_amplitudes(h).astype(np.complex128), qs.qs_last_stats(h)
     finally:
@@ -183,3 +183,19 @@ def test_register_phases_brickwork_sweeps(qs):
     a, st = _run_c64(qs, n, psi0, gates, True, fuse_k=1)
     assert np.max(np.abs(a - want)) <= TOL_C64
     assert st["tile_sweeps"] * 4 <= st["ops_after_fuse"]
+
+
+@pytest.mark.parametrize("dtype,flags", [(2, 0), (1, 1)])
+@pytest.mark.parametrize("n", [14, 20])
+def test_qft_merged_diagonal_blocks(qs, n, dtype, flags):
+    """QFT: each target's run of controlled phases is merged into diagonal blocks of up
+    to 8 qubits inside the tile passes (complex128, and complex64 without register phases);
+    against the oracle and the inverse QFT."""
+    gates = inputs.qft(n)
+    psi0 = inputs.gaussian_state(n, seed=n)
+    want = oracle.run(psi0.copy(), n, gates)
+    p0 = psi0.astype(np.complex64 if dtype == 1 else np.complex128)
+    got, st = run_gpu(qs, n, dtype, p0, gates, qs.QS_MODE_AUTO, **({"flags": flags} if flags else {}))
+    assert np.max(np.abs(got - want)) <= tol(dtype)
+    # fewer tile sweeps than ops: the controlled phases of a target share blocks
+    assert st["tile_sweeps"] < len(gates)

@@ -119,7 +119,7 @@ def test_fused_mode(qs, dtype, fk):
 
 
 @pytest.mark.parametrize("dtype", [2, 1])
-@pytest.mark.parametrize("n", [1, 3, 9, 13, 16, 21])
+@pytest.mark.parametrize("n", [1, 3, 9, 13, 16, 21, 24])
 def test_norm_expz(qs, n, dtype):
     psi = inputs.gaussian_state(n, seed=100 + n)
     psi = psi * 1.7  # not normalised on purpose
@@ -169,6 +169,58 @@ def test_top_k_ties_uniform(qs):
     finally:
         qs.qs_destroy(h)
     assert list(idx) == list(range(100))   # all equal: lowest indices first
+
+
+@pytest.mark.parametrize("n,k", [(14, 100), (15, 4096)])
+def test_top_k_ties_uniform_beyond_candidate_cap(qs, n, k):
+    """2^n equal probabilities (more than the fast path's 8192 candidates): the exact radix
+    pipeline runs and the lowest indices come first."""
+    h = qs.qs_create(n, 2)
+    try:
+        qs.qs_apply_circuit(h, [("h", (q,), ()) for q in range(n)], qs.options(mode=qs.QS_MODE_GATE))
+        idx, amp = qs.qs_top_amplitudes(h, k)
+    finally:
+        qs.qs_destroy(h)
+    assert list(idx) == list(range(k))
+
+
+@pytest.mark.parametrize("dtype", [2, 1])
+@pytest.mark.parametrize("n,k,levels", [(16, 1024, 5), (18, 333, 40), (20, 4096, 3)])
+def test_top_k_discrete_magnitudes(qs, n, k, levels, dtype):
+    """Probabilities from a few exact values (heavy ties at and around the K-th one)."""
+    r = np.random.default_rng(n + levels)
+    mags = r.uniform(0.1, 1.0, size=levels)[r.integers(levels, size=1 << n)]
+    psi = mags * np.array([1, 1j, -1, -1j])[r.integers(4, size=1 << n)]  # exact phases: exact ties
+    psi = psi.astype(np.complex64 if dtype == 1 else np.complex128)
+    ref = psi.astype(np.complex128)
+    h = qs.qs_create(n, dtype)
+    try:
+        qs.qs_set_amplitudes(h, psi)
+        idx, amp = qs.qs_top_amplitudes(h, k)
+    finally:
+        qs.qs_destroy(h)
+    widx, wamp = oracle.top_k(ref, n, k)
+    assert np.array_equal(idx, widx)
+    assert np.array_equal(amp, wamp)
+
+
+def test_top_k_sparse_state_zero_threshold(qs):
+    """Fewer nonzero amplitudes than K: the K-th probability is 0 (ties among zeros go to
+    the lowest indices)."""
+    n, k = 15, 2000
+    r = np.random.default_rng(4)
+    psi = np.zeros(1 << n, dtype=np.complex128)
+    nz = r.choice(1 << n, size=500, replace=False)
+    psi[nz] = r.standard_normal(500) + 1j * r.standard_normal(500)
+    h = qs.qs_create(n, 2)
+    try:
+        qs.qs_set_amplitudes(h, psi)
+        idx, amp = qs.qs_top_amplitudes(h, k)
+    finally:
+        qs.qs_destroy(h)
+    widx, wamp = oracle.top_k(psi, n, k)
+    assert np.array_equal(idx, widx)
+    assert np.array_equal(amp, wamp)
 
 
 def test_invalid_records(qs):

@@ -96,3 +96,56 @@ def test_window_search_cuts_passes():
     g = inputs.tfim(33, 50)
     pog, lm = check_plan(33, qs.QS_C64, g)
     assert len(lm) <= 90
+
+
+def _deps_in_order(gates, pog):
+    last = {}
+    for i, g in enumerate(gates):
+        for q in g[1]:
+            if q in last:
+                assert pog[last[q]] <= pog[i]
+            last[q] = i
+
+
+def test_diag_merge_cuts_passes_for_complete_qaoa():
+    """Fully connected QAOA: each layer's equal-angle RZZ run becomes one phase-function
+    pass (merged plan), far fewer passes than packing all-pairs RZZ into chunk passes."""
+    n = 22
+    gates = inputs.qaoa_complete(n, p=2, seed=1)
+    pog_m, lm_m = qs.qs_plan(n, qs.QS_C128, gates)
+    pog_n, lm_n = qs.qs_plan(n, qs.QS_C128, gates, qs.options(flags=qs.QS_OPT_NO_DIAG_MERGE))
+    assert len(lm_m) < len(lm_n)
+    _deps_in_order(gates, pog_m)
+    # the RZZ gates of one layer share one streamed pass (no local mask)
+    npairs = n * (n - 1) // 2
+    start = n
+    for _ in range(2):
+        layer = pog_m[start:start + npairs]
+        assert (layer == layer[0]).all()
+        assert int(lm_m[layer[0]]) == 0
+        start += npairs + n
+
+
+def test_diag_merge_not_taken_for_tfim_chain():
+    """TFIM: chunk passes follow the chain's light cone; merging each RZZ layer into a
+    full-state pass would need more passes, so the plain plan is kept."""
+    n = 24
+    gates = inputs.tfim(n, steps=10)
+    _, lm_m = qs.qs_plan(n, qs.QS_C64, gates)
+    _, lm_n = qs.qs_plan(n, qs.QS_C64, gates, qs.options(flags=qs.QS_OPT_NO_DIAG_MERGE))
+    assert len(lm_m) == len(lm_n)
+
+
+def test_diag_merge_respects_non_diagonal_barriers():
+    """A merged run never crosses a non-diagonal gate: gates before and after it on the
+    same qubits keep their order."""
+    n = 20
+    r = np.random.default_rng(3)
+    gates = []
+    for layer in range(6):
+        gates += [("h", (q,), ()) for q in range(n)]
+        for _ in range(30):
+            a, b = (int(x) for x in r.choice(n, 2, replace=False))
+            gates.append(("rzz", (a, b), (0.7,)))
+    pog, lm = qs.qs_plan(n, qs.QS_C64, gates, qs.options(chunk_m=8))
+    _deps_in_order(gates, pog)
