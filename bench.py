@@ -261,6 +261,7 @@ def run_ours(args, rank, world, local):
         extra["planned"] = time_planned(qs, h, stream, recs, n, B)
         if B == 16:
             extra["df32"] = time_df32(qs, h, stream, recs, n, sweeps, peak)
+            extra["c64"] = time_c64(qs, stream, n, sweeps, peak)
     qs.qs_destroy(h)
     del host_in
 
@@ -304,6 +305,38 @@ def time_df32(qs, h, stream, recs, n, sweeps, peak):
         ms = evs[i].elapsed_time(evs[i + 1])
         tot += ms
         byts = float(np.mean([alg_bytes_per_gate(name, g[1], n, 16) for g in sweeps[name]]))
+        per[name] = {"ms": round(ms / len(sweeps[name]), 4),
+                     "GBps": round(byts / (ms / len(sweeps[name]) * 1e-3) / 1e9, 1)}
+        per[name]["frac_of_measured_hbm"] = round(per[name]["GBps"] / peak, 3)
+    n_g = sum(len(g) for g in sweeps.values())
+    return {"value": round(n_g / (tot * 1e-3), 2), "unit": "gates/s", "ms_per_step": round(tot, 3),
+            "per_gate": per}
+
+
+def time_c64(qs, stream, n, sweeps, peak):
+    """Context row: the same gate-by-gate sweep on a complex64 state of the same qubit count
+    (8 GiB at 30 qubits): every one-qubit gate is an HBM-bound pass there."""
+    import torch
+    h = qs.qs_create(n, qs.QS_C64)
+    try:
+        qs.qs_set_stream(h, stream.cuda_stream)
+        recs = {name: qs.gate_records(g) for name, g in sweeps.items()}
+        opts = qs.options(mode=qs.QS_MODE_GATE)
+        for name in GATE_TYPES:
+            qs.qs_apply_circuit(h, recs[name], opts)
+        evs = [torch.cuda.Event(enable_timing=True) for _ in range(len(GATE_TYPES) + 1)]
+        for i, name in enumerate(GATE_TYPES):
+            evs[i].record(stream)
+            qs.qs_apply_circuit(h, recs[name], opts)
+        evs[-1].record(stream)
+        torch.cuda.synchronize()
+    finally:
+        qs.qs_destroy(h)
+    per, tot = {}, 0.0
+    for i, name in enumerate(GATE_TYPES):
+        ms = evs[i].elapsed_time(evs[i + 1])
+        tot += ms
+        byts = float(np.mean([alg_bytes_per_gate(name, g[1], n, 8) for g in sweeps[name]]))
         per[name] = {"ms": round(ms / len(sweeps[name]), 4),
                      "GBps": round(byts / (ms / len(sweeps[name]) * 1e-3) / 1e9, 1)}
         per[name]["frac_of_measured_hbm"] = round(per[name]["GBps"] / peak, 3)

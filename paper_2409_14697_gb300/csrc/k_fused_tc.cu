@@ -64,22 +64,25 @@ __device__ __forceinline__ void rot8(float2 (&v)[8], int sh) {
 // chunk starting at (l & 7), so the 32 lanes of a warp touch 8 different offsets at a time
 // instead of 32 times the same bank when groups sit 2^k amplitudes apart; a 3-stage select
 // network puts the values back in column order for tcgen05.st (and the reverse for D).
-__device__ void tc_apply(float2 *tile, const KOp &op, const float *bh, const float *bl, const uint32_t *aoff,
-                         uint32_t tmem, uint64_t *bar, uint32_t &mma_phase, int m, int *abort_flag) {
+// Row tiles [tb, te) of the op (tc_apply below picks the ranges).
+__device__ void tc_apply_tiles(float2 *tile, const KOp &op, const float *bh, const float *bl, const uint32_t *aoff,
+                               uint32_t tmem, uint64_t *bar, uint32_t &mma_phase, int *abort_flag, int tb,
+                               int te) {
     const int k = op.k;
     const int D = 1 << k;             // amplitudes per group
     const int K2 = 2 * D;             // reals per group (GEMM K and N)
-    const int G = 1 << (m - k);       // groups in the tile
-    const int RT = G >> 7;            // 128-group row tiles
+    const int RT = te;                // tiles run from tb to te
+    const int NT = te - tb;           // row tiles held in TMEM at once
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int wg = warp >> 2, wq = warp & 3;
     const uint32_t lane_off = (uint32_t)(32 * wq) << 16;
     const int rsh = lane & 7;
-    // TMEM column layout
-    const uint32_t col_ah = 0, col_al = (uint32_t)(RT * K2), col_d = (uint32_t)(2 * RT * K2);
+    // TMEM column layout (tile t at column offset (t - tb) * K2 inside each part)
+    const uint32_t col_ah = 0u - (uint32_t)(tb * K2), col_al = (uint32_t)((NT - tb) * K2),
+                   col_d = (uint32_t)((2 * NT - tb) * K2);
     // work split: with one row tile both warpgroups share it (even / odd column chunks)
-    const int t0 = RT >= 2 ? wg : 0, tstep = RT >= 2 ? 2 : 1;
-    const int c0 = RT >= 2 ? 0 : wg, cstep = RT >= 2 ? 1 : 2;
+    const int t0 = NT >= 2 ? tb + wg : tb, tstep = NT >= 2 ? 2 : 1;
+    const int c0 = NT >= 2 ? 0 : wg, cstep = NT >= 2 ? 1 : 2;
     int sorted[8];
     for (int j = 0; j < k; j++) sorted[j] = op.pos[j];
     for (int a = 1; a < k; a++)
@@ -119,7 +122,7 @@ __device__ void tc_apply(float2 *tile, const KOp &op, const float *bh, const flo
     if (threadIdx.x == 0) {
         const uint32_t idesc = tc::idesc_tf32(128, K2);
         const uint32_t lbo = 128, sbo = (uint32_t)(K2 / 4) * 128;
-        for (int t = 0; t < RT; t++) {
+        for (int t = tb; t < RT; t++) {
             const uint32_t d = tmem + col_d + (uint32_t)(t * K2);
             for (int s = 0; s < K2 / 8; s++) {
                 const uint32_t ah = tmem + col_ah + (uint32_t)(t * K2 + 8 * s);
@@ -164,9 +167,28 @@ __device__ void tc_apply(float2 *tile, const KOp &op, const float *bh, const flo
     tc::fence_after();
 }
 
-__global__ void __launch_bounds__(kTcThreads, 1)
+// Applies one F_TC op: all row tiles of the tile at once (TMEM holds 3 x RT x 2^(k+1)
+// columns), or one row tile after the other when seq (3 x 2^(k+1) columns: k <= 5 fits in
+// 256 columns, so two CTAs share an SM and one's MMAs overlap the other's gathers).
+__device__ void tc_apply(float2 *tile, const KOp &op, const float *bh, const float *bl, const uint32_t *aoff,
+                         uint32_t tmem, uint64_t *bar, uint32_t &mma_phase, int m, int *abort_flag, int seq) {
+    const int RT = (1 << (m - op.k)) >> 7;  // 128-group row tiles
+    if (!seq) {
+        tc_apply_tiles(tile, op, bh, bl, aoff, tmem, bar, mma_phase, abort_flag, 0, RT);
+        return;
+    }
+    for (int t = 0; t < RT; t++) {
+        tc_apply_tiles(tile, op, bh, bl, aoff, tmem, bar, mma_phase, abort_flag, t, t + 1);
+        if (*(volatile int *)abort_flag) return;
+    }
+}
+
+__global__ void __launch_bounds__(kTcThreads, 2)
 k_chunk_tc(float2 *__restrict__ psi, const ChunkArgs a, const KOp *__restrict__ ops, const float *__restrict__ mats,
-           const float *__restrict__ bmats, uint32_t b_floats, int b_resident, int *__restrict__ err) {
+           const float *__restrict__ bmats, uint32_t b_floats, int b_resident, int seq, int *__restrict__ err) {
+    // TMEM columns: seq (blocks of at most 5 qubits, one row tile at a time) fits in 256, so
+    // two CTAs share an SM's 512 columns
+    const uint32_t tmem_cols = seq ? 256u : kTmemCols;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     float2 *tile = (float2 *)smem_raw;
     float *bh = (float *)(smem_raw + ((size_t)8 << a.m));
@@ -189,7 +211,7 @@ k_chunk_tc(float2 *__restrict__ psi, const ChunkArgs a, const KOp *__restrict__ 
         s_loaded = -1;
     }
     if (threadIdx.x < 32) {
-        tc::alloc(&s_tmem, kTmemCols);
+        tc::alloc(&s_tmem, tmem_cols);
         tc::relinquish();
     }
     if (b_resident) {
@@ -249,12 +271,12 @@ k_chunk_tc(float2 *__restrict__ psi, const ChunkArgs a, const KOp *__restrict__ 
                 __syncthreads();
                 const float *obh = b_resident ? bh + s_op.mat : bh;
                 const float *obl = b_resident ? obh + s_op.nmat / 2 : bl;
-                tc_apply(tile, s_op, obh, obl, s_aoff, tmem, &bar_mma, mma_phase, a.m, &abort_flag);
+                tc_apply(tile, s_op, obh, obl, s_aoff, tmem, &bar_mma, mma_phase, a.m, &abort_flag, seq);
                 if (abort_flag) break;
             } else {
                 for (int j = threadIdx.x; j < s_op.nmat; j += blockDim.x) s_m[j] = mats[s_op.mat + j];
                 __syncthreads();
-                apply_op_smem<float>(tile, s_op, s_m, a.m);
+                apply_op_smem<float, false>(tile, s_op, s_m, a.m);
                 __syncthreads();
             }
         }
@@ -276,7 +298,7 @@ k_chunk_tc(float2 *__restrict__ psi, const ChunkArgs a, const KOp *__restrict__ 
     tc::fence_before();
     __syncthreads();
     tc::fence_after();
-    if (threadIdx.x < 32) tc::dealloc(tmem, kTmemCols);
+    if (threadIdx.x < 32) tc::dealloc(tmem, tmem_cols);
 }
 
 }  // namespace
@@ -302,14 +324,22 @@ void launch_chunk_pass_tc(DeviceState &st, uint64_t lmask, const std::vector<KOp
     const KOp *d_ops = (const KOp *)upload_params(st, kops.data(), kops.size() * sizeof(KOp));
     const float *d_m = (const float *)upload_params(st, tm.data(), tm.size() * sizeof(float));
     const float *d_b = (const float *)upload_params(st, bmats.data(), bmats.size() * sizeof(float));
+    // blocks of at most 5 qubits: one row tile at a time in 256 TMEM columns, two CTAs per SM
+    int kmax = 0;
+    for (const KOp &k : kops)
+        if (k.fkind == F_TC) kmax = std::max(kmax, (int)k.k);
+    const int seq = kmax <= 5 ? 1 : 0;
     // B operands: all resident if they fit next to the tile, else one op's at a time
     const size_t tile_bytes = (size_t)8 << a.m;
     const size_t all_b = bmats.size() * sizeof(float);
-    const int resident = tile_bytes + all_b <= 200 * 1024 ? 1 : 0;
+    const size_t per_cta = seq ? 104 * 1024 : 200 * 1024;
+    const int resident = tile_bytes + all_b <= per_cta ? 1 : 0;
     const uint32_t bf = resident ? (uint32_t)bmats.size() : b_floats;
-    // tile + B; at least 120 KB so that one CTA (and one TMEM owner) runs per SM
+    // tile + B.  512 TMEM columns: at least 120 KB, so that one CTA (one TMEM owner) runs per
+    // SM; 256 columns: at least 80 KB, so that at most two do
     size_t smem = tile_bytes + (resident ? all_b : 2 * (size_t)b_floats * sizeof(float));
-    smem = std::max<size_t>(smem, 120 * 1024);
+    smem = std::max<size_t>(smem, seq ? 80 * 1024 : 120 * 1024);
+    if (seq && smem > 104 * 1024) fail(QS_ERR_INVALID, "tensor-core chunk pass exceeds shared memory");
     if (smem > 220 * 1024) fail(QS_ERR_INVALID, "tensor-core chunk pass exceeds shared memory");
     static bool attr = false;
     if (!attr) {
@@ -317,7 +347,7 @@ void launch_chunk_pass_tc(DeviceState &st, uint64_t lmask, const std::vector<KOp
         attr = true;
     }
     const int grid = persistent_grid((const void *)k_chunk_tc, kTcThreads, smem, a.n_tiles);
-    k_chunk_tc<<<grid, kTcThreads, smem, st.stream>>>((float2 *)st.psi, a, d_ops, d_m, d_b, bf, resident,
+    k_chunk_tc<<<grid, kTcThreads, smem, st.stream>>>((float2 *)st.psi, a, d_ops, d_m, d_b, bf, resident, seq,
                                                        st.dev_err);
     QS_CUDA(cudaGetLastError());
     count_launch();

@@ -195,6 +195,7 @@ struct RpMember {
     int type = 0;
     int tgt = -1;       // register-slot operand (a position the phase must hold in registers)
     int a = -1, b = -1; // position operands (-1: bit 1 for every amplitude, -2: bit 0)
+    int form = RP_GENERAL;  // RP_M1: RP_GENERAL / RP_REAL / RP_RX
     double pay[8] = {0, 0, 0, 0, 0, 0, 0, 0};
 };
 
@@ -206,6 +207,20 @@ bool rp_member(const Op &op, const int *pos, RpMember &mb) {
     };
     auto mat = [&](cd m00, cd m01, cd m10, cd m11) {
         put(0, m00); put(1, m01); put(2, m10); put(3, m11);
+    };
+    // a one-qubit M1 in its cheapest form
+    auto m1 = [&](cd m00, cd m01, cd m10, cd m11) {
+        mb.type = RP_M1;
+        if (m00.imag() == 0.0 && m01.imag() == 0.0 && m10.imag() == 0.0 && m11.imag() == 0.0) {
+            mb.form = RP_REAL;
+            mb.pay[0] = m00.real(); mb.pay[1] = m01.real(); mb.pay[2] = m10.real(); mb.pay[3] = m11.real();
+        } else if (m00.imag() == 0.0 && m11.imag() == 0.0 && m01.real() == 0.0 && m10.real() == 0.0) {
+            mb.form = RP_RX;
+            mb.pay[0] = m00.real(); mb.pay[1] = m01.imag(); mb.pay[2] = m10.imag(); mb.pay[3] = m11.real();
+        } else {
+            mb.form = RP_GENERAL;
+            mat(m00, m01, m10, m11);
+        }
     };
     // diagonal on positions (a, b), entry index 2 x_a + x_b
     auto diag = [&](int a, int b, cd d0, cd d1, cd d2, cd d3) {
@@ -244,9 +259,8 @@ bool rp_member(const Op &op, const int *pos, RpMember &mb) {
     switch (op.kind) {
     case K_H: {
         const double r = 1.0 / std::sqrt(2.0);
-        mb.type = RP_M1;
         mb.tgt = P(0);
-        mat(r, r, r, -r);
+        m1(r, r, r, -r);
         return true;
     }
     case K_PERM1:
@@ -254,9 +268,8 @@ bool rp_member(const Op &op, const int *pos, RpMember &mb) {
         mb.tgt = P(0);
         return true;
     case K_DENSE1:
-        mb.type = RP_M1;
         mb.tgt = P(0);
-        mat(op.m[0], op.m[1], op.m[2], op.m[3]);
+        m1(op.m[0], op.m[1], op.m[2], op.m[3]);
         return true;
     case K_DIAG1:
         diag1(P(0), op.m[0], op.m[1]);
@@ -408,8 +421,10 @@ std::vector<KOp> build_register_phases(const std::vector<Op> &ops, const int *po
                 else pend.push_back({RP_PARITY, 0, 0, 0, {}, {pair}, ev, fv});
                 continue;
             }
-            Pending p{e.type, e.tgt >= 0 ? slot_of[e.tgt] : 0, ea, eb, {}, {}, 0.0, 0.0};
-            const int npay = e.type == RP_X ? 0 : e.type == RP_PH ? 2 : 8;
+            // a 2x2 member carries its form in operand b
+            Pending p{e.type, e.tgt >= 0 ? slot_of[e.tgt] : 0, ea, e.type == RP_M1 ? e.form : eb, {}, {}, 0.0, 0.0};
+            const int npay = e.type == RP_X ? 0 : e.type == RP_PH ? 2
+                             : (e.type == RP_M1 && e.form != RP_GENERAL) ? 4 : 8;
             p.pay.assign(e.pay, e.pay + npay);
             pend.push_back(std::move(p));
         }

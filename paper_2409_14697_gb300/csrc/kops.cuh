@@ -50,7 +50,9 @@ constexpr int kRpAlways = 31;     // position operand whose bit is 1 for every a
 constexpr int kRpNever = 30;      // position operand whose bit is 0 for every amplitude
 constexpr int kRpMaxMembers = 56; // ops per phase: 1 + 9 * 56 reals <= kMaxOpReals
 enum RpType : int {
-    RP_M1 = 0,  // 2x2 matrix (row-major re, im) on register slot `slot`
+    RP_M1 = 0,  // 2x2 matrix on register slot `slot`; operand b holds its form: RP_GENERAL
+                // (8 reals, row-major re, im), RP_REAL (4 reals: m00 m01 m10 m11; H, RY) or
+                // RP_RX (4 reals: m00, Im m01, Im m10, m11; real diagonal, imaginary off-diagonal)
     RP_C1,      // the same, only where the bit at position a is 1
     RP_X,       // exchange on `slot` where the bit at position a is 1
     RP_DIAG,    // multiply by d[2 x_a + x_b] (one position: a = b, d1 = d2 unused)
@@ -62,6 +64,7 @@ enum RpType : int {
                 // number of patterns with x_a != x_b (equal-angle RZZ / RZ layers), np <= 15
 };
 constexpr int kRpMaxParity = 15;
+enum RpForm : int { RP_GENERAL = 0, RP_REAL = 1, RP_RX = 2 };
 
 // Host+device description of one op in a given index space (HBM amplitude/element
 // indices for K1, tile-local indices for K2).

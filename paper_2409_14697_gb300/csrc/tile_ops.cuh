@@ -216,6 +216,36 @@ __device__ __forceinline__ void rp_m1(float2 (&v)[kRpRegs], const float (&M)[8])
     }
 }
 
+// real 2x2 (a b; c d): 4 multiply-adds per amplitude
+template <int J>
+__device__ __forceinline__ void rp_mr(float2 (&v)[kRpRegs], float a, float b, float c, float d) {
+#pragma unroll
+    for (int r = 0; r < kRpRegs; r++) {
+        if (r & (1 << J)) continue;
+        float2 &x = v[r], &y = v[r | (1 << J)];
+        const float pxr = b * y.x, pxi = b * y.y, pyr = c * x.x, pyi = c * x.y;
+        x.x = fmaf(a, x.x, pxr);
+        x.y = fmaf(a, x.y, pxi);
+        y.x = fmaf(d, y.x, pyr);
+        y.y = fmaf(d, y.y, pyi);
+    }
+}
+
+// (c0, i s01; i s10, c1) with real c0, s01, s10, c1 (RX): 4 multiply-adds per amplitude
+template <int J>
+__device__ __forceinline__ void rp_mx(float2 (&v)[kRpRegs], float c0, float s01, float s10, float c1) {
+#pragma unroll
+    for (int r = 0; r < kRpRegs; r++) {
+        if (r & (1 << J)) continue;
+        float2 &x = v[r], &y = v[r | (1 << J)];
+        const float p1 = -s01 * y.y, p2 = s01 * y.x, p3 = -s10 * x.y, p4 = s10 * x.x;
+        x.x = fmaf(c0, x.x, p1);
+        x.y = fmaf(c0, x.y, p2);
+        y.x = fmaf(c1, y.x, p3);
+        y.y = fmaf(c1, y.y, p4);
+    }
+}
+
 template <int J>
 __device__ __forceinline__ void rp_c1(float2 (&v)[kRpRegs], const float (&M)[8], uint32_t K) {
 #pragma unroll
@@ -386,6 +416,30 @@ __device__ __forceinline__ void rphase_run(float2 *tile, const KOp &ph, const fl
         mm += 1 + len;
         switch (type) {
         case RP_M1:
+            if (eb != RP_GENERAL) {
+                // the 4-real forms: X M X reverses the payload order
+                const int f = (int)((sigma >> J) & 1u);
+                const float q0 = P[3 * f], q1 = P[1 + f], q2 = P[2 - f], q3 = P[3 - 3 * f];
+                if (eb == RP_REAL) {
+                    switch (J) {
+                    case 0: rp_mr<0>(v, q0, q1, q2, q3); break;
+                    case 1: rp_mr<1>(v, q0, q1, q2, q3); break;
+                    case 2: rp_mr<2>(v, q0, q1, q2, q3); break;
+                    case 3: rp_mr<3>(v, q0, q1, q2, q3); break;
+                    default: rp_mr<4>(v, q0, q1, q2, q3); break;
+                    }
+                } else {
+                    switch (J) {
+                    case 0: rp_mx<0>(v, q0, q1, q2, q3); break;
+                    case 1: rp_mx<1>(v, q0, q1, q2, q3); break;
+                    case 2: rp_mx<2>(v, q0, q1, q2, q3); break;
+                    case 3: rp_mx<3>(v, q0, q1, q2, q3); break;
+                    default: rp_mx<4>(v, q0, q1, q2, q3); break;
+                    }
+                }
+                break;
+            }
+            [[fallthrough]];
         case RP_C1: {
             // X M X in this lane's register order where bit J of sigma is set: the rows and
             // columns of the payload are read swapped
@@ -485,8 +539,10 @@ __device__ __forceinline__ void rphase_run(float2 *tile, const KOp &ph, const fl
     }
 }
 
-// Applies one op to the tile; op and its matrix entries are in shared memory.
-template <typename T>
+// Applies one op to the tile; op and its matrix entries are in shared memory.  RP = false
+// leaves the register-phase code out (kernels that never receive F_RPHASE ops keep their
+// registers for themselves).
+template <typename T, bool RP = true>
 __device__ __forceinline__ void apply_op_smem(typename C2T<T>::type *tile, const KOp &op, const T *sm, int m) {
     switch (op.fkind) {
     case F_H: groups_apply<T, 2>(tile, op, m, SH<T>{(T)0.70710678118654752440}); break;
@@ -543,7 +599,7 @@ __device__ __forceinline__ void apply_op_smem(typename C2T<T>::type *tile, const
         else if (op.k == 4) dense_k_smem<T, 4>(tile, op, sm, m);
         break;
     case F_RPHASE:
-        if constexpr (std::is_same<T, float>::value) rphase_run(tile, op, sm);
+        if constexpr (std::is_same<T, float>::value && RP) rphase_run(tile, op, sm);
         break;
     default:
         break;
