@@ -182,6 +182,9 @@ void launch_batch_kernel(Batch &b) {
     static bool attr_set[2] = {false, false};
     if (!attr_set[sizeof(T) == 8]) {
         QS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+        // the whole unified L1 as shared memory: two CTAs of up to ~104 KB per SM
+        QS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                     (int)cudaSharedmemCarveoutMaxShared));
         attr_set[sizeof(T) == 8] = true;
     }
     const size_t smem = sizeof(V) << b.max_m;

@@ -157,6 +157,9 @@ void launch_t(DeviceState &st, const ChunkArgs &a, const std::vector<KOp> &kops,
     static bool attr_set = false;
     if (!attr_set) {
         QS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+        // the whole unified L1 as shared memory: two CTAs of up to ~104 KB per SM
+        QS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                     (int)cudaSharedmemCarveoutMaxShared));
         attr_set = true;
     }
     const int grid = persistent_grid((const void *)kern, kChunkThreads, smem, a.n_tiles);

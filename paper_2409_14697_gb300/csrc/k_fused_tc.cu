@@ -344,9 +344,15 @@ void launch_chunk_pass_tc(DeviceState &st, uint64_t lmask, const std::vector<KOp
     static bool attr = false;
     if (!attr) {
         QS_CUDA(cudaFuncSetAttribute(k_chunk_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024));
+        // the whole unified L1 as shared memory, so that two CTAs of ~100 KB fit on an SM
+        QS_CUDA(cudaFuncSetAttribute(k_chunk_tc, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                     (int)cudaSharedmemCarveoutMaxShared));
         attr = true;
     }
-    const int grid = persistent_grid((const void *)k_chunk_tc, kTcThreads, smem, a.n_tiles);
+    // seq: two CTAs per SM (each holds 256 of the SM's 512 TMEM columns); CTAs share
+    // nothing, so a grid larger than what is resident only queues
+    const int grid = seq ? (int)std::min<uint64_t>(a.n_tiles, (uint64_t)device_sm_count() * 2)
+                         : persistent_grid((const void *)k_chunk_tc, kTcThreads, smem, a.n_tiles);
     k_chunk_tc<<<grid, kTcThreads, smem, st.stream>>>((float2 *)st.psi, a, d_ops, d_m, d_b, bf, resident, seq,
                                                        st.dev_err);
     QS_CUDA(cudaGetLastError());
