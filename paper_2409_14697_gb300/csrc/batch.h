@@ -21,6 +21,8 @@ struct BatchPass {
     uint64_t tile_start; // global work index of this pass's tile 0
     uint64_t ops_off;    // first KOp of the pass
     uint64_t mats_off;   // first matrix real of the pass
+    uint32_t n_reals;    // matrix reals of the pass
+    int32_t staged;      // 1: ops and reals are copied into shared memory once per work item
 };
 
 struct Batch {
@@ -31,6 +33,7 @@ struct Batch {
     std::vector<BatchPass> passes;
     uint64_t state_elems = 0, total_items = 0;
     int max_m = 0, grid = 0;
+    size_t prog_bytes = 0;  // largest staged pass program (ops + reals), in bytes
     long long wait_limit_ns = 2000000000ll;
     cudaStream_t stream = nullptr;
     bool owns_stream = true;

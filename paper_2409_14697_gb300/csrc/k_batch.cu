@@ -24,6 +24,9 @@ namespace qs {
 namespace {
 
 constexpr int kBatchThreads = kTileThreads;
+// Largest pass program (ops + reals) staged in shared memory per work item; two CTAs per SM
+// must still fit next to their 64 KiB tiles.
+constexpr size_t kBatchProgMax = 36 * 1024;
 
 __device__ __forceinline__ unsigned int ld_acquire(const unsigned int *p) {
     unsigned int v;
@@ -43,7 +46,7 @@ __global__ void __launch_bounds__(kBatchThreads, 2)
 k_batch(typename C2T<T>::type *__restrict__ states, const BatchPass *__restrict__ passes, int n_passes,
         uint64_t total_items, const KOp *__restrict__ ops, const T *__restrict__ mats,
         unsigned long long *__restrict__ counter, unsigned int *__restrict__ done, int *__restrict__ err,
-        int *__restrict__ abort_all, long long wait_limit_ns) {
+        int *__restrict__ abort_all, long long wait_limit_ns, uint32_t prog_off) {
     using V = typename C2T<T>::type;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     V *tile = (V *)smem_raw;
@@ -144,7 +147,35 @@ k_batch(typename C2T<T>::type *__restrict__ states, const BatchPass *__restrict_
             __syncthreads();
             if (*(volatile int *)abort_all) break;
         }
-        apply_ops_tile<T>(tile, ops + bp.ops_off, bp.n_ops, mats + bp.mats_off, bp.m, s_op, s_m);
+        // one call site of the op code (register phases are large); a staged pass has its ops
+        // and reals copied once per work item, then needs one barrier per op
+        KOp *st_ops = (KOp *)(smem_raw + prog_off);
+        T *st_m = (T *)(smem_raw + prog_off + (size_t)bp.n_ops * sizeof(KOp));
+        if (bp.staged) {
+            const uint32_t *src = (const uint32_t *)(ops + bp.ops_off);
+            uint32_t *dst = (uint32_t *)st_ops;
+            const uint32_t nw = (uint32_t)bp.n_ops * (uint32_t)(sizeof(KOp) / 4);
+            for (uint32_t j = threadIdx.x; j < nw; j += blockDim.x) dst[j] = src[j];
+            for (uint32_t j = threadIdx.x; j < bp.n_reals; j += blockDim.x) st_m[j] = mats[bp.mats_off + j];
+            __syncthreads();
+        }
+        for (int i = 0; i < bp.n_ops; i++) {
+            const KOp *op;
+            const T *om;
+            if (bp.staged) {
+                op = st_ops + i;
+                om = st_m + op->mat;
+            } else {
+                if (threadIdx.x == 0) s_op = ops[bp.ops_off + i];
+                __syncthreads();
+                for (int j = threadIdx.x; j < s_op.nmat; j += blockDim.x) s_m[j] = mats[bp.mats_off + s_op.mat + j];
+                __syncthreads();
+                op = &s_op;
+                om = s_m;
+            }
+            apply_op_smem<T>(tile, *op, om, bp.m);
+            __syncthreads();
+        }
         ptx::fence_proxy_async_smem();
         __syncthreads();
         // the write-back addresses are rebuilt from shared memory instead of being kept live
@@ -187,13 +218,15 @@ void launch_batch_kernel(Batch &b) {
                                      (int)cudaSharedmemCarveoutMaxShared));
         attr_set[sizeof(T) == 8] = true;
     }
-    const size_t smem = sizeof(V) << b.max_m;
+    const size_t tile_bytes = sizeof(V) << b.max_m;
+    const size_t smem = tile_bytes + b.prog_bytes;
     b.grid = persistent_grid((const void *)kern, kBatchThreads, smem, b.total_items);
     QS_CUDA(cudaMemsetAsync(b.d_counter, 0, sizeof(unsigned long long), b.stream));
     QS_CUDA(cudaMemsetAsync(b.d_done, 0, sizeof(unsigned int) * b.passes.size(), b.stream));
     kern<<<b.grid, kBatchThreads, smem, b.stream>>>((V *)b.d_states, b.d_passes, (int)b.passes.size(),
                                                    b.total_items, b.d_ops, (const T *)b.d_mats, b.d_counter,
-                                                   b.d_done, b.d_err, b.d_abort, b.wait_limit_ns);
+                                                   b.d_done, b.d_err, b.d_abort, b.wait_limit_ns,
+                                                   (uint32_t)tile_bytes);
     QS_CUDA(cudaGetLastError());
     count_launch();
 }
@@ -204,6 +237,7 @@ void batch_build(Batch &b, const std::vector<std::vector<Op>> &circ_ops, const s
     const size_t B = c128 ? 16 : 8;
     const int m_max = o.chunk_m > 0 ? o.chunk_m : (c128 ? 12 : 13);
     b.max_m = 0;
+    b.prog_bytes = 0;
     // per-circuit planning
     struct CP { std::vector<Pass> plan; std::vector<std::vector<KOp>> kops; std::vector<std::vector<double>> mats; std::vector<uint64_t> lm; };
     std::vector<CP> cps(circ_ops.size());
@@ -293,6 +327,12 @@ void batch_build(Batch &b, const std::vector<std::vector<Op>> &circ_ops, const s
             bp.tile_start = items;
             bp.ops_off = all_ops.size();
             bp.mats_off = all_mats.size();
+            bp.n_reals = (uint32_t)cps[c].mats[lvl].size();
+            {
+                const size_t prog = (size_t)bp.n_ops * sizeof(KOp) + (size_t)bp.n_reals * B / 2;
+                bp.staged = prog <= kBatchProgMax ? 1 : 0;
+                if (bp.staged) b.prog_bytes = std::max(b.prog_bytes, (prog + 15) / 16 * 16);
+            }
             if ((B << bp.c0) % 16 != 0) fail(QS_ERR_UNSUPPORTED, "batched tile runs below 16 bytes");
             items += bp.n_tiles;
             all_ops.insert(all_ops.end(), cps[c].kops[lvl].begin(), cps[c].kops[lvl].end());

@@ -83,6 +83,10 @@ k_chunk(typename C2T<T>::type *__restrict__ psi, const ChunkArgs a, const KOp *_
             if (threadIdx.x == 0) atomicExch(err, QS_ERR_TIMEOUT);
             break;
         }
+        if constexpr (DF) {  // amplitudes as float pairs for the whole pass
+            df_tile_split((double2 *)tile, a.m);
+            __syncthreads();
+        }
         // one call site of the op code (it is large: register phases)
         for (int i = 0; i < a.n_ops; i++) {
             const KOp *op;
@@ -98,8 +102,12 @@ k_chunk(typename C2T<T>::type *__restrict__ psi, const ChunkArgs a, const KOp *_
                 op = &s_op;
                 om = s_m;
             }
-            if constexpr (DF) apply_op_smem_df((double2 *)tile, *op, (const df::F2 *)om, s_fb, a.m);
+            if constexpr (DF) apply_op_dftile((double2 *)tile, *op, (const df::F2 *)om, s_fb, a.m);
             else apply_op_smem<T>(tile, *op, om, a.m);
+            __syncthreads();
+        }
+        if constexpr (DF) {
+            df_tile_join((double2 *)tile, a.m);
             __syncthreads();
         }
         ptx::fence_proxy_async_smem();

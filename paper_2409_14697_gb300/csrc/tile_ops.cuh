@@ -687,6 +687,168 @@ __device__ __forceinline__ void apply_op_smem_df(double2 *tile, const KOp &op, c
     }
 }
 
+// ---- complex128 double-float tiles ------------------------------------------------------
+// For a whole pass the tile holds every amplitude as four floats (re hi, re lo, im hi,
+// im lo) in its own 16-byte slot: split once after the load and joined once before the
+// store, so that the ops in between run on FP32 units only (the per-op join to double is
+// an FP64 add per value, which bound the earlier double-float sweeps by the FP64 pipe).
+// Values stay normalised pairs (|lo| <= ulp(hi) / 2) between ops.
+struct DfAmp {
+    df::F2 r, i;
+};
+
+__device__ __forceinline__ df::F2 df_norm(df::Acc a) {  // Fast2Sum of (s, c)
+    const float h = __fadd_rn(a.s, a.c);
+    return df::F2{h, __fsub_rn(a.c, __fsub_rn(h, a.s))};
+}
+
+__device__ __forceinline__ void df_tile_split(double2 *tile, int m) {
+    for (uint32_t x = threadIdx.x; x < (1u << m); x += blockDim.x) {
+        const double2 a = tile[x];
+        const df::F2 r = df::split(a.x), i = df::split(a.y);
+        reinterpret_cast<float4 *>(tile)[x] = make_float4(r.h, r.l, i.h, i.l);
+    }
+}
+__device__ __forceinline__ void df_tile_join(double2 *tile, int m) {
+    for (uint32_t x = threadIdx.x; x < (1u << m); x += blockDim.x) {
+        const float4 f = reinterpret_cast<const float4 *>(tile)[x];
+        tile[x] = make_double2(df::join(f.x, f.y), df::join(f.z, f.w));
+    }
+}
+
+__device__ __forceinline__ DfAmp df_ld(const float4 *p) {
+    const float4 f = *p;
+    return DfAmp{df::F2{f.x, f.y}, df::F2{f.z, f.w}};
+}
+__device__ __forceinline__ void df_st(float4 *p, const DfAmp &a) { *p = make_float4(a.r.h, a.r.l, a.i.h, a.i.l); }
+
+// a * d (complex, both as pairs), normalised
+__device__ __forceinline__ DfAmp df_cmul(const DfAmp &a, df::F2 dr, df::F2 di) {
+    df::Acc re = df::mul(dr, a.r);
+    df::mac(re, dfneg(di), a.i);
+    df::Acc im = df::mul(dr, a.i);
+    df::mac(im, di, a.r);
+    return DfAmp{df_norm(re), df_norm(im)};
+}
+
+template <int NT, typename Fn>
+__device__ __forceinline__ void df_groups_apply(float4 *tile, const KOp &op, int m, const Fn &fn) {
+    const uint32_t ng = 1u << (m - op.nf);
+    const uint32_t set = (uint32_t)op.set_mask;
+    for (uint32_t g = threadIdx.x; g < ng; g += blockDim.x) {
+        const uint32_t base = (uint32_t)insert_zero_bits(g, op.nf, op.fb) | set;
+        DfAmp v[NT];
+#pragma unroll
+        for (int t = 0; t < NT; t++) v[t] = df_ld(tile + (base + (uint32_t)op.off[t]));
+        fn(v);
+#pragma unroll
+        for (int t = 0; t < NT; t++) df_st(tile + (base + (uint32_t)op.off[t]), v[t]);
+    }
+}
+
+struct DtH {
+    df::F2 r;
+    __device__ void operator()(DfAmp *v) const {
+        const DfAmp a = v[0], b = v[1];
+        v[0].r = df_norm(df::scale(df::add(a.r, b.r), r));
+        v[0].i = df_norm(df::scale(df::add(a.i, b.i), r));
+        v[1].r = df_norm(df::scale(df::sub(a.r, b.r), r));
+        v[1].i = df_norm(df::scale(df::sub(a.i, b.i), r));
+    }
+};
+struct DtSwap {
+    __device__ void operator()(DfAmp *v) const {
+        const DfAmp t = v[0];
+        v[0] = v[1];
+        v[1] = t;
+    }
+};
+struct DtNeg {
+    __device__ void operator()(DfAmp *v) const {
+        v[0].r = dfneg(v[0].r);
+        v[0].i = dfneg(v[0].i);
+    }
+};
+// y_r = sum_c m[r][c] x_c over NT touched elements (matrix as pairs, row-major re/im)
+template <int NT> struct DtDense {
+    const df::F2 *m;
+    __device__ void operator()(DfAmp *v) const {
+        DfAmp x[NT];
+#pragma unroll
+        for (int t = 0; t < NT; t++) x[t] = v[t];
+#pragma unroll
+        for (int r = 0; r < NT; r++) {
+            const df::F2 *row = m + 2 * NT * r;
+            df::Acc a = df::mul(row[0], x[0].r);
+            df::Acc b = df::mul(row[0], x[0].i);
+            df::mac(a, dfneg(row[1]), x[0].i);
+            df::mac(b, row[1], x[0].r);
+#pragma unroll
+            for (int c = 1; c < NT; c++) {
+                df::mac(a, row[2 * c], x[c].r);
+                df::mac(a, dfneg(row[2 * c + 1]), x[c].i);
+                df::mac(b, row[2 * c], x[c].i);
+                df::mac(b, row[2 * c + 1], x[c].r);
+            }
+            v[r] = DfAmp{df_norm(a), df_norm(b)};
+        }
+    }
+};
+template <int NT> struct DtDiag {
+    const df::F2 *d;
+    __device__ void operator()(DfAmp *v) const {
+#pragma unroll
+        for (int t = 0; t < NT; t++) v[t] = df_cmul(v[t], d[2 * t], d[2 * t + 1]);
+    }
+};
+
+// Applies one op to a double-float tile (df_tile_split done); sm holds the op's reals as
+// (hi, lo) pairs.  Dense blocks of 3 or more qubits are applied in FP64 (the tile is
+// joined, the op applied, and the tile split again); every thread of the block must call
+// this.
+__device__ __forceinline__ void apply_op_dftile(double2 *tile_raw, const KOp &op, const df::F2 *sm, double *sd,
+                                                int m) {
+    float4 *tile = reinterpret_cast<float4 *>(tile_raw);
+    switch (op.fkind) {
+    case F_H: df_groups_apply<2>(tile, op, m, DtH{df::F2{0.70710677f, 1.21016175e-08f}}); break;
+    case F_SWAP: df_groups_apply<2>(tile, op, m, DtSwap{}); break;
+    case F_NEG: df_groups_apply<1>(tile, op, m, DtNeg{}); break;
+    case F_DENSE1: df_groups_apply<2>(tile, op, m, DtDense<2>{sm}); break;
+    case F_DIAG1: df_groups_apply<2>(tile, op, m, DtDiag<2>{sm}); break;
+    case F_PHASE: df_groups_apply<1>(tile, op, m, DtDiag<1>{sm}); break;
+    case F_DIAG2: df_groups_apply<4>(tile, op, m, DtDiag<4>{sm}); break;
+    case F_DENSE2: df_groups_apply<4>(tile, op, m, DtDense<4>{sm}); break;
+    case F_DIAGK:
+    case F_CDIAGK: {
+        // table over the k positions pos[0..k-1]; F_CDIAGK visits only the elements with
+        // its nf control positions pos[k..] (ascending) set
+        const int kt = op.k, kc = op.fkind == F_CDIAGK ? op.nf : 0;
+        const uint32_t ng = 1u << (m - kc);
+        for (uint32_t g = threadIdx.x; g < ng; g += blockDim.x) {
+            uint32_t x = g;
+            for (int j = 0; j < kc; j++) {
+                const int b = op.pos[kt + j];
+                x = ((x >> b) << (b + 1)) | (x & ((1u << b) - 1u));
+            }
+            if (kc) x |= (uint32_t)op.set_mask;
+            uint32_t s = 0;
+            for (int j = 0; j < kt; j++) s |= ((x >> op.pos[j]) & 1u) << (kt - 1 - j);
+            df_st(tile + x, df_cmul(df_ld(tile + x), sm[2 * s], sm[2 * s + 1]));
+        }
+        break;
+    }
+    default: {
+        df_tile_join(tile_raw, m);
+        for (int j = threadIdx.x; j < op.nmat; j += blockDim.x) sd[j] = (double)sm[j].h + (double)sm[j].l;
+        __syncthreads();
+        apply_op_smem<double>(tile_raw, op, sd, m);
+        __syncthreads();
+        df_tile_split(tile_raw, m);
+        break;
+    }
+    }
+}
+
 // Stages op i and its matrix entries into shared memory, then applies it; every thread
 // of the block must call this (it synchronises).
 template <typename T>

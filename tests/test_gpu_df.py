@@ -130,3 +130,26 @@ def test_planned_dense_blocks_df(qs):
     finally:
         qs.qs_destroy(h)
     assert np.max(np.abs(got - want)) <= TOL_C128
+
+
+@pytest.mark.parametrize("n", [14, 18])
+def test_planned_qft_df_tiles(qs, n):
+    """QFT with double-float tiles: merged controlled-phase blocks (F_CDIAGK) and H on
+    float pairs held for the whole pass."""
+    gates = inputs.qft(n)
+    psi0 = inputs.gaussian_state(n, seed=n + 5)
+    want = oracle.run(psi0.copy(), n, gates)
+    got = run(qs, n, psi0, gates, qs.QS_MODE_AUTO, qs.QS_PREC_DF32)
+    assert np.max(np.abs(got - want)) <= TOL_C128
+
+
+def test_planned_long_circuit_df_tiles(qs):
+    """Hundreds of ops inside each pass on float pairs (errors add over the ops of a pass,
+    each op within ~2^-46 of sum |m x|)."""
+    n = 16
+    gates = inputs.brickwork(n, 40, seed=3) + inputs.qaoa_3regular(n, p=3, seed=3) + \
+        inputs.tfim(n, steps=20, dt=0.05) + inputs.random_circuit(n, 400, seed=9)
+    psi0 = inputs.gaussian_state(n, seed=11)
+    want = oracle.run(psi0.copy(), n, gates)
+    got = run(qs, n, psi0, gates, qs.QS_MODE_AUTO, qs.QS_PREC_DF32)
+    assert np.max(np.abs(got - want)) <= TOL_C128
