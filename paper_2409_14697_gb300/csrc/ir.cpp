@@ -186,6 +186,14 @@ bool is_diagonal(const Op &op) { return op.kind == K_DIAG1 || op.kind == K_DIAG;
 
 }  // namespace
 
+bool op_is_diagonal(const Op &op) {
+    switch (op.kind) {
+    case K_DIAG1: case K_DIAG: case K_PHASEFN: return true;
+    case K_CTRL1: return op.m[1] == cd(0.0) && op.m[2] == cd(0.0);
+    default: return false;
+    }
+}
+
 double op_flops(const Op &op) {
     switch (op.kind) {
     case K_H: return 4.0;

@@ -330,19 +330,24 @@ std::vector<KOp> build_register_phases(const std::vector<Op> &ops, const int *po
     // One greedy phase from `first`: an op joins if none of its positions is blocked by an
     // earlier op left out, its register operand fits in R (at most kRpBits positions,
     // within `allowed`) and the program has room; otherwise its positions become blocked.
+    // diagonal ops commute with one another: one left out only blocks later non-diagonal ops
+    std::vector<char> diag(N);
+    for (size_t i = 0; i < N; i++) diag[i] = op_is_diagonal(ops[i]);
     auto trial = [&](size_t first, uint32_t allowed, std::vector<int> &taken) {
-        uint32_t R = 0, blocked = 0;
+        uint32_t R = 0, blocked = 0, blocked_diag = 0;
         taken.clear();
         for (size_t i = first; i < N; i++) {
             if (done[i]) continue;
             const uint32_t tm = touch[i];
-            bool take = ok[i] && !(tm & blocked) && (int)taken.size() < kRpMaxMembers;
+            const uint32_t blk = diag[i] ? blocked : (blocked | blocked_diag);
+            bool take = ok[i] && !(tm & blk) && (int)taken.size() < kRpMaxMembers;
             if (take && mb[i].tgt >= 0) {
                 const uint32_t need = 1u << mb[i].tgt;
                 take = (need & ~allowed) == 0 && __builtin_popcount(R | need) <= kRpBits;
                 if (take) R |= need;
             }
             if (take) taken.push_back((int)i);
+            else if (diag[i]) blocked_diag |= tm;
             else blocked |= tm;
             if ((blocked & all) == all) break;
         }

@@ -122,25 +122,32 @@ Trial greedy_pass(const std::vector<Op> &ops, const std::vector<char> &done, siz
     const uint64_t all = (n >= 64) ? ~0ull : ((1ull << n) - 1ull);
     const uint64_t low = (1ull << pp.c) - 1ull;
     Trial tr;
-    uint64_t L = low, blocked = 0;
+    // qubits of ops left for a later pass: a non-diagonal op left behind blocks every later
+    // op on its qubits; a diagonal one only blocks later non-diagonal ops (diagonal gates
+    // commute with one another, so they may pass it)
+    uint64_t L = low, blocked = 0, blocked_diag = 0;
     for (size_t i = first; i < ops.size(); i++) {
         if (done[i]) continue;
         const Op &op = ops[i];
         const uint64_t qm = op.qmask();
+        const bool diag = op_is_diagonal(op);
+        const uint64_t blk = diag ? blocked : (blocked | blocked_diag);
         if (!chunkable(op, pp)) {
-            if (tr.ops.empty() && !(qm & blocked)) {
+            if (tr.ops.empty() && !(qm & (blocked | blocked_diag))) {
                 tr.stream = true;
                 tr.ops.push_back((int)i);
             }
             break;  // a non-chunkable op is a barrier for this pass
         }
-        if (qm & blocked) {
-            blocked |= qm;
-        } else if ((qm & ~(low | allowed)) == 0 && __builtin_popcountll(L | qm) <= pp.m) {
+        bool take = false;
+        if (!(qm & blk) && (qm & ~(low | allowed)) == 0 && __builtin_popcountll(L | qm) <= pp.m) {
             L |= qm;
             tr.ops.push_back((int)i);
-        } else {
-            blocked |= qm;
+            take = true;
+        }
+        if (!take) {
+            if (diag) blocked_diag |= qm;
+            else blocked |= qm;
         }
         if ((blocked & all) == all) break;
     }

@@ -83,6 +83,8 @@ std::vector<Op> fuse_ops(const std::vector<Op> &ops, int fuse_k, double sweep_fl
 // is 1, are set; sweep_cost is added per separate sweep).  FP64 host products; blocks
 // that come out as the identity are dropped.
 std::vector<Op> merge_tile_diagonals(const std::vector<Op> &ops, int max_k, double sweep_cost);
+// True for ops that are diagonal in the computational basis (they commute with each other).
+bool op_is_diagonal(const Op &op);
 // Real flops per amplitude of applying op alone (structure-aware).
 double op_flops(const Op &op);
 

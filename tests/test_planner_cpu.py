@@ -11,6 +11,9 @@ def built():
     build.build()
 
 
+DIAGONAL = {"z", "s", "t", "rz", "p", "cz", "cp", "rzz"}
+
+
 def qmask(g):
     m = 0
     for q in g[1]:
@@ -32,13 +35,7 @@ def check_plan(n, dtype, gates, chunk_m=0):
             assert qmask(g) & ~L == 0
             assert bin(L).count("1") == m
             assert L & ((1 << c) - 1) == (1 << c) - 1
-    # dependencies: gates sharing a qubit keep their order across passes
-    last = {}
-    for i, g in enumerate(gates):
-        for q in g[1]:
-            if q in last:
-                assert pog[last[q]] <= pog[i]
-            last[q] = i
+    _deps_in_order(gates, pog)
     return pog, lm
 
 
@@ -99,12 +96,23 @@ def test_window_search_cuts_passes():
 
 
 def _deps_in_order(gates, pog):
-    last = {}
+    """Gates sharing a qubit keep their pass order unless both are diagonal (diagonal gates
+    commute with each other, so the planner may run a later one in an earlier pass)."""
+    last_any, last_nondiag = {}, {}
     for i, g in enumerate(gates):
+        d = g[0] in DIAGONAL
         for q in g[1]:
-            if q in last:
-                assert pog[last[q]] <= pog[i]
-            last[q] = i
+            # this gate must not run before any earlier non-diagonal gate on q, and a
+            # non-diagonal gate not before any earlier gate on q
+            ref = last_nondiag.get(q) if d else last_any.get(q)
+            if ref is not None:
+                assert pog[ref] <= pog[i], (i, g, ref, gates[ref])
+        for q in g[1]:
+            if not d:
+                last_nondiag[q] = i
+            # the latest gate on q that a later non-diagonal gate must follow
+            if not d or q not in last_any or pog[i] >= pog[last_any[q]]:
+                last_any[q] = i
 
 
 def test_diag_merge_cuts_passes_for_complete_qaoa():
