@@ -153,12 +153,17 @@ def sweep_gates(n):
     return {name: inputs.gate_sweep(n, name, seed=2, count=30) for name in GATE_TYPES}
 
 
-def alg_bytes_per_gate(name, q_list, n, B):
+def alg_bytes_per_gate(name, q_list, n, B, last=True):
     """Algorithmic HBM bytes of one application (read + write of the amplitudes it
-    changes; selecting bits inside a 32-byte sector count as full passes)."""
+    changes; selecting bits inside a 32-byte sector count as full passes).  Gate-by-gate
+    runs apply every RZ of a call but the last as diag(1, e^{i theta}), which changes only
+    the half with the target bit set; the last carries the collected global phase and
+    changes every amplitude (last=True)."""
     full = 2.0 * B * (1 << n)
     sector_bits = 1 if B == 16 else 2
-    if name in ("h", "x", "rz", "u3"):
+    if name == "rz":
+        return full if (last or q_list[0] < sector_bits) else full / 2
+    if name in ("h", "x", "u3"):
         return full
     a, b = q_list
     if name == "cz":
@@ -169,6 +174,12 @@ def alg_bytes_per_gate(name, q_list, n, B):
     if name in ("cnot", "cu3"):
         return full / 2 if a >= sector_bits else full
     return full
+
+
+def sweep_bytes(name, gates, n, B):
+    """Mean algorithmic bytes per gate of one sweep applied as one call."""
+    return float(np.mean([alg_bytes_per_gate(name, g[1], n, B, last=(i == len(gates) - 1))
+                          for i, g in enumerate(gates)]))
 
 
 def run_ours(args, rank, world, local):
@@ -231,7 +242,7 @@ def run_ours(args, rank, world, local):
     per_gate = {}
     for name in GATE_TYPES:
         launch_ms = per_type_ms[name] / (args.steps * len(sweeps[name]))
-        byts = float(np.mean([alg_bytes_per_gate(name, g[1], n, B) for g in sweeps[name]]))
+        byts = sweep_bytes(name, sweeps[name], n, B)
         per_gate[name] = {"ms": round(launch_ms, 4), "alg_bytes": byts,
                           "GBps": round(byts / (launch_ms * 1e-3) / 1e9, 1),
                           "frac_of_measured_hbm": round(byts / (launch_ms * 1e-3) / 1e9 / peak, 3),
@@ -304,7 +315,7 @@ def time_df32(qs, h, stream, recs, n, sweeps, peak):
     for i, name in enumerate(GATE_TYPES):
         ms = evs[i].elapsed_time(evs[i + 1])
         tot += ms
-        byts = float(np.mean([alg_bytes_per_gate(name, g[1], n, 16) for g in sweeps[name]]))
+        byts = sweep_bytes(name, sweeps[name], n, 16)
         per[name] = {"ms": round(ms / len(sweeps[name]), 4),
                      "GBps": round(byts / (ms / len(sweeps[name]) * 1e-3) / 1e9, 1)}
         per[name]["frac_of_measured_hbm"] = round(per[name]["GBps"] / peak, 3)
@@ -336,7 +347,7 @@ def time_c64(qs, stream, n, sweeps, peak):
     for i, name in enumerate(GATE_TYPES):
         ms = evs[i].elapsed_time(evs[i + 1])
         tot += ms
-        byts = float(np.mean([alg_bytes_per_gate(name, g[1], n, 8) for g in sweeps[name]]))
+        byts = sweep_bytes(name, sweeps[name], n, 8)
         per[name] = {"ms": round(ms / len(sweeps[name]), 4),
                      "GBps": round(byts / (ms / len(sweeps[name]) * 1e-3) / 1e9, 1)}
         per[name]["frac_of_measured_hbm"] = round(per[name]["GBps"] / peak, 3)
@@ -390,8 +401,9 @@ def run_e2e(qs, h, host_in, recs, opts, n, B, n_gates, world):
 
 
 # FP64 instructions per amplitude (FMA-class issues, one FP64 pipe slot each) of the
-# complex128 streaming updates; the other gate types issue none on the FP64 pipe.
-FP64_INSTR_PER_AMP = {"h": 3, "rz": 4, "u3": 7, "cu3": 3.5}
+# complex128 streaming updates; the other gate types issue none on the FP64 pipe.  RZ: 29
+# of a call's 30 change half the amplitudes (4 per changed amplitude), the last all.
+FP64_INSTR_PER_AMP = {"h": 3, "rz": (29 * 2 + 4) / 30, "u3": 7, "cu3": 3.5}
 # FP64 pipe peak: 2 FP64 instructions per clock per SM (ncu: the U3 kernel at 0.526e12/s
 # keeps the FP64 pipe 83.8 % busy) x 152 SMs x 2.07 GHz max SM clock = 1.26 TFLOP/s.
 FP64_PEAK_TINSTR = 2 * 152 * 2.07e9 / 1e12
@@ -646,6 +658,13 @@ def wl_reductions(args):
              "expectation_z_all": (lambda: qs.qs_expectation_z(h), state),
              "renormalize": (lambda: qs.qs_renormalize(h), 3 * state),
              "top_1024": (lambda: qs.qs_top_amplitudes(h, 1024), state)}
+    # spot checks against host sums of the same state (FP64), before any renormalisation
+    ez, nrm = qs.qs_expectation_z(h)
+    p = np.abs(hv.astype(np.complex128)) ** 2
+    out["norm_vs_host"] = abs(nrm - float(p.sum()))
+    half = 1 << (n - 1)  # the top qubit is 0 on the first half of the indices
+    out["expz_top_qubit_vs_host"] = abs(ez[n - 1] - float(p[:half].sum() - p[half:].sum()))
+    del p
     for name, (fn, nbytes) in cases.items():
         for _ in range(max(args.warmup, 3)):
             fn()
@@ -653,12 +672,6 @@ def wl_reductions(args):
         gbps = nbytes / (ms * 1e-3) / 1e9
         out["ops"][name] = {"ms": round(ms, 4), "alg_bytes": nbytes, "GBps": round(gbps, 1),
                             "frac_of_measured_hbm": round(gbps / peak, 3)}
-    # spot checks against host sums of the same state (FP64)
-    ez, nrm = qs.qs_expectation_z(h)
-    p = np.abs(hv.astype(np.complex128)) ** 2
-    out["norm_vs_host"] = abs(nrm - float(p.sum()))
-    half = 1 << (n - 1)  # the top qubit is 0 on the first half of the indices
-    out["expz_top_qubit_vs_host"] = abs(ez[n - 1] - float(p[:half].sum() - p[half:].sum()))
     out["alg_bytes_note"] = "norm, <Z>, top-K: one read of the state; renormalize: norm read + scale read/write"
     qs.qs_destroy(h)
     return out

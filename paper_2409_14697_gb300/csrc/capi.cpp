@@ -140,7 +140,7 @@ void run_circuit(DeviceState &d, const std::vector<Op> &ops, const qs_options &o
     const int mode = o.mode;
     try {
         if (mode == QS_MODE_GATE) {
-            for (const Op &op : ops) {
+            for (const Op &op : fold_global_phases(ops)) {
                 launch_stream_op(d, op);
                 st.passes++;
                 st.bytes += stream_bytes(op, d.n, d.dtype);

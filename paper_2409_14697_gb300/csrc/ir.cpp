@@ -194,6 +194,22 @@ bool op_is_diagonal(const Op &op) {
     }
 }
 
+std::vector<Op> fold_global_phases(const std::vector<Op> &ops) {
+    std::vector<Op> out = ops;
+    int last = -1;
+    for (size_t i = 0; i < out.size(); i++)
+        if (out[i].kind == K_DIAG1 && out[i].m[0] != cd(1.0)) last = (int)i;
+    cd phase = 1.0;
+    for (int i = 0; i < last; i++) {
+        Op &op = out[i];
+        if (op.kind != K_DIAG1 || op.m[0] == cd(1.0) || op.m[0] == cd(0.0)) continue;
+        phase *= op.m[0];
+        op.m = {cd(1.0), op.m[1] / op.m[0]};
+    }
+    if (last >= 0) out[last].m = {out[last].m[0] * phase, out[last].m[1] * phase};
+    return out;
+}
+
 double op_flops(const Op &op) {
     switch (op.kind) {
     case K_H: return 4.0;

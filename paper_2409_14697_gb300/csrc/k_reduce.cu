@@ -6,15 +6,18 @@
 //    is constant over it and only its total is needed for that qubit (qubits < cb are
 //    split into thread bits and loop bits); the second level combines groups of 256 such
 //    records, adding the 8 qubits spelled by the record index within the group; the last
-//    level combines the few second-level records.  Everything is accumulated in FP64 in a
-//    fixed order (per-thread loop, fixed butterfly trees, fixed upper levels), so results
-//    are bitwise reproducible whatever else runs on the GPU.
+//    level combines the few second-level records.  Everything is summed in a fixed order
+//    (per-thread pairwise trees, fixed butterfly trees, fixed upper levels), so results
+//    are bitwise reproducible whatever else runs on the GPU.  complex128 sums in FP64;
+//    complex64 sums each thread's groups of 16 exact squares in double-float FP32 and
+//    everything above in FP64 (FP64 throughput is the limit of these passes on GB300).
 //  * top-K |a|^2: exact radix select of the K-th largest key (the bit pattern of the
 //    non-negative probability, monotone in its value), then a deterministic gather of
 //    the elements above it and of the lowest-index ties, then one-block bitonic sort.
 //  * |0...0> and scaling.
 #include <algorithm>
 #include <mutex>
+#include <type_traits>
 
 #include "capi_util.h"
 #include "qs_internal.h"
@@ -38,12 +41,57 @@ __device__ __forceinline__ double f2d_exact(float x) {
     const uint32_t hi = (b & 0x80000000u) | ((e + 896u) << 20) | ((b & 0x7FFFFFu) >> 3);
     return __hiloint2double((int)hi, (int)((b & 7u) << 29));
 }
-// |a|^2 for sums (not keys): one FP64 multiply and one fused multiply-add
-__device__ __forceinline__ double prob_sum(double2 a) { return __fma_rn(a.x, a.x, __dmul_rn(a.y, a.y)); }
-__device__ __forceinline__ double prob_sum(float2 a) {
-    const double x = f2d_exact(a.x), y = f2d_exact(a.y);
-    return __fma_rn(x, x, __dmul_rn(y, y));
-}
+// Sums of |a|^2 inside one thread of the first level, over a group of 16 or 32 amplitudes.
+// complex128: FP64, with a pair of amplitudes summed as one chain of fused multiply-adds.
+// complex64: the squares of the stored floats are exact as FP32 pairs (x*x and
+// fma(x, x, -x*x)) and are added as double-float values (hi, lo: an FP32 two-sum per
+// addition, then a renormalisation), so a group's sums run on the FP32 pipe and the FP64
+// pipe sees one exact conversion and one addition per group sum.  Each double-float
+// addition of non-negative terms errs by at most 3 * 2^-48 of its result and a leaf (one
+// |a|^2) by the same, so a pairwise tree of depth <= 5 is within 18 * 2^-48 (6.4e-14) of
+// its exact sum.
+struct SumF64 {
+    using T = double;
+    static __device__ __forceinline__ T add(T a, T b) { return __dadd_rn(a, b); }
+    static __device__ __forceinline__ T leaf(double2 a) { return __fma_rn(a.x, a.x, __dmul_rn(a.y, a.y)); }
+    // |a|^2 + |b|^2 with pb = |b|^2: four FP64 instructions for two amplitudes
+    static __device__ __forceinline__ T pair(double2 a, double2 b, T &pb) {
+        pb = leaf(b);
+        return __fma_rn(a.x, a.x, __fma_rn(a.y, a.y, pb));
+    }
+    static __device__ __forceinline__ double to_double(T a) { return a; }
+};
+struct SumDF32 {
+    using T = float2;  // (hi, lo), |lo| <= ulp(hi) / 2
+    // hi + lo of s + l rounded to nearest, exactly (Fast2Sum: |s| >= |l| here)
+    static __device__ __forceinline__ T renorm(float s, float l) {
+        const float h = __fadd_rn(s, l);
+        return make_float2(h, __fsub_rn(l, __fsub_rn(h, s)));
+    }
+    static __device__ __forceinline__ T add(T a, T b) {
+        const float s = __fadd_rn(a.x, b.x);
+        const float bb = __fsub_rn(s, a.x);
+        const float e = __fadd_rn(__fsub_rn(a.x, __fsub_rn(s, bb)), __fsub_rn(b.x, bb));  // TwoSum
+        return renorm(s, __fadd_rn(__fadd_rn(a.y, b.y), e));
+    }
+    static __device__ __forceinline__ T leaf(float2 a) {
+        const float hx = __fmul_rn(a.x, a.x), hy = __fmul_rn(a.y, a.y);
+        const float lx = __fmaf_rn(a.x, a.x, -hx), ly = __fmaf_rn(a.y, a.y, -hy);
+        const float s = __fadd_rn(hx, hy);
+        const float bb = __fsub_rn(s, hx);
+        const float e = __fadd_rn(__fsub_rn(hx, __fsub_rn(s, bb)), __fsub_rn(hy, bb));
+        return renorm(s, __fadd_rn(__fadd_rn(lx, ly), e));
+    }
+    static __device__ __forceinline__ T pair(float2 a, float2 b, T &pb) {
+        pb = leaf(b);
+        return add(leaf(a), pb);
+    }
+    // hi + lo spans at most 48 significant bits: the FP64 sum is exact
+    static __device__ __forceinline__ double to_double(T a) { return __dadd_rn(f2d_exact(a.x), f2d_exact(a.y)); }
+};
+template <typename V> struct SumOf;
+template <> struct SumOf<double2> { using S = SumF64; };
+template <> struct SumOf<float2> { using S = SumDF32; };
 
 
 // Butterfly sum over a warp: fixed order, identical result in every lane.
@@ -53,26 +101,82 @@ __device__ __forceinline__ double warp_sum(double v) {
     return v;
 }
 
+// Pairwise sum of x[0..N-1] (N a power of two) in a fixed order.
+template <typename S, int N, typename A>
+__device__ __forceinline__ A tree_sum(const A *x) {
+    if constexpr (N == 1) return x[0];
+    else return S::add(tree_sum<S, N / 2>(x), tree_sum<S, N / 2>(x + N / 2));
+}
+
+// Levels L.. of a group's tree, M nodes at level L in cur[]: mass[L] = sum of the odd
+// nodes (bit L of the loop index set), then the pair sums move up; returns the group total.
+template <typename S, int L, int M, int BITS>
+struct TreeLevels {
+    using A = typename S::T;
+    static __device__ __forceinline__ A run(A *cur, A *mass) {
+        if constexpr (M == 1) {
+            return cur[0];
+        } else {
+            if (BITS) {
+                A odd[M / 2];
+#pragma unroll
+                for (int i = 0; i < M / 2; i++) odd[i] = cur[2 * i + 1];
+                mass[L] = tree_sum<S, M / 2>(odd);
+            }
+#pragma unroll
+            for (int i = 0; i < M / 2; i++) cur[i] = S::add(cur[2 * i], cur[2 * i + 1]);
+            return TreeLevels<S, L + 1, M / 2, BITS>::run(cur, mass);
+        }
+    }
+};
+
 // Level 1: part[blk*(cb+1) + 0] = block total; part[blk*(cb+1) + 1 + q] = mass with bit q
-// set, q < cb.  JB = loop bits per thread (cb = tb + JB); BITS = 0: totals only.
+// set, q < cb.  JB = loop bits per thread (cb = tb + JB); BITS = 0: totals only (the same
+// operations in the same order, so a norm equals the total of a <Z_q> call bit for bit).
+// A thread loads its amplitudes in groups of 2^U (the low U loop bits; U = 4 for
+// complex128, 5 for complex64) and sums each group by a fixed pairwise tree; the mass of
+// low loop bit l is a pairwise sum of the odd nodes of the tree's level l; the high loop
+// bits take the group totals.  Group results go to FP64 accumulators, so no double-float
+// sum spans more than one tree of depth <= 5.
 template <typename V, int JB, int BITS>
 __global__ void __launch_bounds__(256)
 k_expz_part(const V *__restrict__ psi, int cb, int tb, double *__restrict__ part) {
+    using S = typename SumOf<V>::S;
+    using A = typename S::T;
+    constexpr int UMAX = std::is_same<V, float2>::value ? 5 : 4;
+    constexpr int U = JB < UMAX ? JB : UMAX;
+    constexpr int NJ = JB > 0 ? JB : 1;
+    constexpr int H = U > 0 ? (1 << (U - 1)) : 1;  // pairs per group
     __shared__ double s_tot[256];
-    __shared__ double s_j[JB > 0 ? JB : 1][256];
+    __shared__ double s_j[NJ][256];
     const int T = 1 << tb, t = threadIdx.x;
     const uint64_t start = (uint64_t)blockIdx.x << cb;
-    double tot = 0.0, jacc[JB > 0 ? JB : 1];
+    double tot = 0.0, jacc[NJ];
 #pragma unroll
-    for (int b = 0; b < JB; b++) jacc[b] = 0.0;
-#pragma unroll 4
-    for (int j = 0; j < (1 << JB); j++) {
-        const double p = prob_sum(psi[start + ((uint64_t)j << tb) + t]);
-        tot += p;
+    for (int b = 0; b < NJ; b++) jacc[b] = 0.0;
+#pragma unroll 1
+    for (int g = 0; g < (1 << (JB - U)); g++) {
+        V v[1 << U];
+#pragma unroll
+        for (int j = 0; j < (1 << U); j++) v[j] = psi[start + ((uint64_t)((g << U) + j) << tb) + t];
+        A gt, mass[U > 0 ? U : 1];
+        if constexpr (U == 0) {
+            gt = S::leaf(v[0]);
+        } else {
+            A cur[H], odd[H];
+#pragma unroll
+            for (int i = 0; i < H; i++) cur[i] = S::pair(v[2 * i], v[2 * i + 1], odd[i]);
+            if (BITS) mass[0] = tree_sum<S, H>(odd);
+            gt = TreeLevels<S, 1, H, BITS>::run(cur, mass);
+        }
+        const double gd = S::to_double(gt);
+        tot = __dadd_rn(tot, gd);
         if (BITS) {
 #pragma unroll
-            for (int b = 0; b < JB; b++)
-                if ((j >> b) & 1) jacc[b] += p;
+            for (int l = 0; l < U; l++) jacc[l] = __dadd_rn(jacc[l], S::to_double(mass[l]));
+#pragma unroll
+            for (int b = U; b < JB; b++)
+                if ((g >> (b - U)) & 1) jacc[b] = __dadd_rn(jacc[b], gd);
         }
     }
     s_tot[t] = tot;
@@ -521,7 +625,10 @@ k_tk_collect(const V *__restrict__ psi, uint64_t n, TkState *__restrict__ ts,
     }
 }
 
-int chunk_bits(int n) { return std::min(n, std::max(12, n - 18)); }
+// First-level block = 2^cb amplitudes: large enough that the block's combine step (cb + 1
+// sums over 256 thread values) stays small beside the per-amplitude work, small enough to
+// leave 2^12 blocks or more (several waves of resident blocks) from 24 qubits on.
+int chunk_bits(int n) { return std::min(n, std::max(12, std::min(16, n - 12))); }
 
 }  // namespace
 

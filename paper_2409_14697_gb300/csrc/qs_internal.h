@@ -85,6 +85,12 @@ std::vector<Op> fuse_ops(const std::vector<Op> &ops, int fuse_k, double sweep_fl
 std::vector<Op> merge_tile_diagonals(const std::vector<Op> &ops, int max_k, double sweep_cost);
 // True for ops that are diagonal in the computational basis (they commute with each other).
 bool op_is_diagonal(const Op &op);
+// Gate-by-gate form of a circuit: every one-qubit diagonal diag(d0, d1) with d0 != 1 (RZ)
+// but the last becomes diag(1, d1 / d0), which changes only the amplitudes with the
+// target bit set; the product of the factored d0 (a global phase) is multiplied into the
+// last one, applied in full.  The product of the ops is unchanged (FP64 host arithmetic),
+// so the state is exact again when the last op has run.
+std::vector<Op> fold_global_phases(const std::vector<Op> &ops);
 // Real flops per amplitude of applying op alone (structure-aware).
 double op_flops(const Op &op);
 

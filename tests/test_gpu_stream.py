@@ -76,6 +76,56 @@ def test_every_gate_every_target(qs, n, dtype):
 
 
 @pytest.mark.parametrize("dtype", [2, 1])
+@pytest.mark.parametrize("n", [3, 12])
+def test_gate_mode_folded_rz_phases(qs, n, dtype):
+    """Many RZ in one gate-by-gate call, mixed with H, CNOT and P: every RZ but the last
+    runs as diag(1, e^{i theta}) on the half of the state with the target bit set and the
+    collected global phase rides on the last one, so the state after the call equals the
+    oracle's element by element, and the call's byte count shows the half passes."""
+    psi0 = inputs.gaussian_state(n, seed=40 + n)
+    if dtype == 1:
+        psi0 = psi0.astype(np.complex64)
+    r = np.random.default_rng(41 + n)
+    gates = []
+    for i in range(3 * n):
+        q = i % n
+        gates.append(("rz", (q,), (float(r.uniform(0, 2 * math.pi)),)))
+        if i % 4 == 1:
+            gates.append(("h", ((q + 1) % n,), ()))
+        if i % 5 == 2:
+            gates.append(("cnot", (q, (q + 2) % n), ()))
+        if i % 7 == 3:
+            gates.append(("p", (q,), (float(r.uniform(0, 2 * math.pi)),)))
+    gates.append(("u3", (0,), tuple(float(a) for a in r.uniform(0, 2 * math.pi, 3))))
+    h = qs.qs_create(n, dtype)
+    try:
+        qs.qs_set_amplitudes(h, psi0)
+        qs.qs_apply_circuit(h, gates, qs.options(mode=qs.QS_MODE_GATE))
+        st = qs.qs_last_stats(h)
+        got = qs.qs_amplitudes(h).astype(np.complex128)
+    finally:
+        qs.qs_destroy(h)
+    want = psi0.astype(np.complex128)
+    oracle.run(want, n, gates)
+    check(got, want, dtype)
+    # bytes: read + write of the changed amplitudes, whole 32-byte sectors
+    B = 16 if dtype == 2 else 8
+    sb = 1 if dtype == 2 else 2
+    full = 2.0 * B * (1 << n)
+    last_rz = max(i for i, g in enumerate(gates) if g[0] == "rz")
+    want_bytes = 0.0
+    for i, (name, qb, _) in enumerate(gates):
+        if name in ("rz", "p"):
+            half = qb[0] >= sb and (name == "p" or i != last_rz)
+            want_bytes += full / 2 if half else full
+        elif name == "cnot":
+            want_bytes += full / 2 if qb[0] >= sb else full
+        else:
+            want_bytes += full
+    assert st["bytes"] == pytest.approx(want_bytes, rel=1e-12)
+
+
+@pytest.mark.parametrize("dtype", [2, 1])
 def test_brickwork_12q(qs, dtype):
     """20 layers of U3 on every qubit + CZ brickwork from |0...0>, all 4096 amplitudes."""
     n = 12
