@@ -266,7 +266,7 @@ def run_ours(args, rank, world, local):
 
     e2e = None
     if not args.no_e2e:
-        e2e = run_e2e(qs, h, host_in, recs, opts, n, B, n_gates, world)
+        e2e = run_e2e(qs, h, host_in, recs, opts, n, B, n_gates, world, dt)
     extra = {}
     if not args.no_extra:
         extra["planned"] = time_planned(qs, h, stream, recs, n, B)
@@ -379,31 +379,49 @@ def time_planned(qs, h, stream, recs, n, B):
     return out
 
 
-def run_e2e(qs, h, host_in, recs, opts, n, B, n_gates, world):
-    """Same metric through the C ABI with host buffers: each step copies the initial
-    state from pinned host memory (H2D), applies the 240 gates, and copies the final
-    state back to pinned host memory (D2H)."""
+def run_e2e(qs, h, host_in, recs, opts, n, B, n_gates, world, dt):
+    """Same metric through the C ABI with host buffers.  Each step copies the initial state
+    from pinned host memory into a state (H2D), applies the 240 gates and copies the final
+    state back into pinned host memory (D2H); the host waits for a step's result before
+    it reuses that step's buffers.  Two states on two streams keep two steps in flight (as
+    the serving loop does with its slots), so one step's copies overlap the other's gates:
+    step s runs on state s % 2 with the stream-ordered copy entry points."""
     import torch
-    host_out = torch.empty_like(host_in, pin_memory=True)
-    reps = 2
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for _ in range(reps):
-        qs.qs_set_amplitudes_from(h, 0, 1 << n, host_in.data_ptr())
-        for name in GATE_TYPES:
-            qs.qs_apply_circuit(h, recs[name], opts)
-        qs.qs_amplitudes_into(h, 0, 1 << n, host_out.data_ptr())
-    dt = (time.perf_counter() - t0) / reps
+    h2 = qs.qs_create(n, dt)
+    states = [h, h2]
+    outs = [torch.empty_like(host_in, pin_memory=True) for _ in range(2)]
+    steps = 6
+    N = 1 << n
+    try:
+        for st in states:
+            qs.qs_synchronize(st)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for s in range(steps):
+            st = states[s % 2]
+            if s >= 2:
+                qs.qs_synchronize(st)             # step s - 2's final state is on the host
+                float(outs[s % 2][0])
+            qs.qs_set_amplitudes_async(st, 0, N, host_in.data_ptr())
+            for name in GATE_TYPES:
+                qs.qs_apply_circuit(st, recs[name], opts)
+            qs.qs_amplitudes_async(st, 0, N, outs[s % 2].data_ptr())
+        for st in states:
+            qs.qs_synchronize(st)
+        wall = (time.perf_counter() - t0) / steps
+    finally:
+        qs.qs_destroy(h2)
     rec_bytes = 72 * n_gates
-    return {"value": round(world * n_gates / dt, 2), "unit": "gates/s",
+    return {"value": round(world * n_gates / wall, 2), "unit": "gates/s",
             "h2d_bytes_per_step": (B << n) + rec_bytes, "d2h_bytes_per_step": B << n,
-            "ms_per_step": round(dt * 1e3, 2), "steps": reps}
+            "ms_per_step": round(wall * 1e3, 2), "steps": steps, "states_in_flight": 2}
 
 
 # FP64 instructions per amplitude (FMA-class issues, one FP64 pipe slot each) of the
-# complex128 streaming updates; the other gate types issue none on the FP64 pipe.  RZ: 29
-# of a call's 30 change half the amplitudes (4 per changed amplitude), the last all.
-FP64_INSTR_PER_AMP = {"h": 3, "rz": (29 * 2 + 4) / 30, "u3": 7, "cu3": 3.5}
+# complex128 streaming updates; the other gate types issue none on the FP64 pipe.  In a
+# gate-by-gate call of 30: RZ, 29 change half the amplitudes (4 per changed amplitude) and
+# the last all; H, 29 are the unscaled butterfly (2) and the last carries the scale (3).
+FP64_INSTR_PER_AMP = {"h": (29 * 2 + 3) / 30, "rz": (29 * 2 + 4) / 30, "u3": 7, "cu3": 3.5}
 # FP64 pipe peak: 2 FP64 instructions per clock per SM (ncu: the U3 kernel at 0.526e12/s
 # keeps the FP64 pipe 83.8 % busy) x 152 SMs x 2.07 GHz max SM clock = 1.26 TFLOP/s.
 FP64_PEAK_TINSTR = 2 * 152 * 2.07e9 / 1e12

@@ -199,11 +199,23 @@ int qs_plan(int n_qubits, qs_dtype dt, const qs_gate *gates, size_t n_gates, con
 /* ---- amplitudes and reductions -------------------------------------------------- */
 
 /* Copies cnt amplitudes [off, off+cnt) from host memory (the state's dtype, interleaved)
- * into the state; synchronous.  QS_ERR_INVALID if the range exceeds 2^n. */
+ * into the state; synchronous.  QS_ERR_INVALID if the range exceeds 2^n.  Page-locked
+ * host buffers (cudaHostAlloc / cudaHostRegister) of 4 MiB or more, 8-byte aligned, are
+ * read by a copy kernel over the CPU-GPU link; other memory by cudaMemcpyAsync.  The
+ * caller keeps ownership of host_src, which must hold cnt amplitudes. */
 int qs_set_amplitudes(qs_state *s, uint64_t off, uint64_t cnt, const void *host_src);
 /* Copies cnt amplitudes [off, off+cnt) of the state to host memory (state's dtype);
- * synchronous (waits for queued gates). */
+ * synchronous (waits for queued gates).  Same copy paths as qs_set_amplitudes. */
 int qs_amplitudes(qs_state *s, uint64_t off, uint64_t cnt, void *host_dst);
+/* Stream-ordered forms of the two copies above: enqueued on the state's stream after the
+ * work queued so far, they return at once.  The caller keeps host_src (unchanged) and
+ * host_dst (unread) alive until qs_synchronize(s) returns; a timeout of earlier queued
+ * work is reported there.  Both use cudaMemcpyAsync (the copy engines, so they take no
+ * SMs from kernels of other streams): asynchronous for page-locked buffers; for pageable
+ * ones the call waits as cudaMemcpyAsync does.  With two states on two streams, the
+ * copies of one overlap the gates of the other. */
+int qs_set_amplitudes_async(qs_state *s, uint64_t off, uint64_t cnt, const void *host_src);
+int qs_amplitudes_async(qs_state *s, uint64_t off, uint64_t cnt, void *host_dst);
 /* Squared norm sum_i |a_i|^2, accumulated in FP64 in a fixed order (deterministic). */
 int qs_norm(qs_state *s, double *out);
 /* <Z_q> = sum_i |a_i|^2 (1 - 2 bit_q(i)) for q = 0..n-1 into out[0..n-1] (FP64, fixed

@@ -140,7 +140,9 @@ void run_circuit(DeviceState &d, const std::vector<Op> &ops, const qs_options &o
     const int mode = o.mode;
     try {
         if (mode == QS_MODE_GATE) {
-            for (const Op &op : fold_global_phases(ops)) {
+            std::vector<Op> gops = fold_global_phases(ops);
+            if (d.dtype == QS_C128 && d.prec == QS_PREC_FP64) defer_hadamard_scale(gops);
+            for (const Op &op : gops) {
                 launch_stream_op(d, op);
                 st.passes++;
                 st.bytes += stream_bytes(op, d.n, d.dtype);
@@ -397,7 +399,7 @@ int qs_set_amplitudes(qs_state *s, uint64_t off, uint64_t cnt, const void *host_
     const uint64_t N = 1ull << s->d.n;
     if (off > N || cnt > N - off) fail(QS_ERR_INVALID, "amplitude range out of bounds");
     const size_t B = amp_bytes(s->d.dtype);
-    QS_CUDA(cudaMemcpyAsync((char *)s->d.psi + off * B, host_src, cnt * B, cudaMemcpyHostToDevice, s->d.stream));
+    copy_host(s->d, (char *)s->d.psi + off * B, host_src, cnt * B, true, true);
     QS_CUDA(cudaStreamSynchronize(s->d.stream));
     QS_API_END
 }
@@ -409,8 +411,28 @@ int qs_amplitudes(qs_state *s, uint64_t off, uint64_t cnt, void *host_dst) {
     if (off > N || cnt > N - off) fail(QS_ERR_INVALID, "amplitude range out of bounds");
     const size_t B = amp_bytes(s->d.dtype);
     sync_and_check(s->d);
-    QS_CUDA(cudaMemcpyAsync(host_dst, (const char *)s->d.psi + off * B, cnt * B, cudaMemcpyDeviceToHost, s->d.stream));
+    copy_host(s->d, host_dst, (const char *)s->d.psi + off * B, cnt * B, false, true);
     QS_CUDA(cudaStreamSynchronize(s->d.stream));
+    QS_API_END
+}
+
+int qs_set_amplitudes_async(qs_state *s, uint64_t off, uint64_t cnt, const void *host_src) {
+    QS_API_BEGIN
+    if (!s || (cnt && !host_src)) fail(QS_ERR_INVALID, "NULL argument");
+    const uint64_t N = 1ull << s->d.n;
+    if (off > N || cnt > N - off) fail(QS_ERR_INVALID, "amplitude range out of bounds");
+    const size_t B = amp_bytes(s->d.dtype);
+    copy_host(s->d, (char *)s->d.psi + off * B, host_src, cnt * B, true, false);
+    QS_API_END
+}
+
+int qs_amplitudes_async(qs_state *s, uint64_t off, uint64_t cnt, void *host_dst) {
+    QS_API_BEGIN
+    if (!s || (cnt && !host_dst)) fail(QS_ERR_INVALID, "NULL argument");
+    const uint64_t N = 1ull << s->d.n;
+    if (off > N || cnt > N - off) fail(QS_ERR_INVALID, "amplitude range out of bounds");
+    const size_t B = amp_bytes(s->d.dtype);
+    copy_host(s->d, host_dst, (const char *)s->d.psi + off * B, cnt * B, false, false);
     QS_API_END
 }
 

@@ -127,7 +127,7 @@ std::vector<cd> Op::full() const {
     std::vector<cd> f(d * d, 0.0);
     switch (kind) {
     case K_H: {
-        const double r = 1.0 / std::sqrt(2.0);
+        const double r = m.empty() ? 1.0 / std::sqrt(2.0) : m[0].real();
         f = {r, r, r, -r};
         break;
     }
@@ -210,6 +210,25 @@ std::vector<Op> fold_global_phases(const std::vector<Op> &ops) {
     return out;
 }
 
+void defer_hadamard_scale(std::vector<Op> &ops) {
+    int last = -1;
+    for (size_t i = 0; i < ops.size(); i++)
+        if (ops[i].kind == K_H) last = (int)i;
+    int c = 0;  // unscaled Hadamards since the last scaled one
+    for (int i = 0; i <= last; i++) {
+        if (ops[i].kind != K_H) continue;
+        if (i == last || c == kMaxUnscaledH) {
+            const int k = c + 1;  // factor 2^(-k/2)
+            const double r = (k % 2 == 0) ? std::ldexp(1.0, -k / 2) : std::ldexp(std::sqrt(0.5), -(k - 1) / 2);
+            ops[i].m = {cd(r)};
+            c = 0;
+        } else {
+            ops[i].m = {cd(1.0)};
+            c++;
+        }
+    }
+}
+
 double op_flops(const Op &op) {
     switch (op.kind) {
     case K_H: return 4.0;
@@ -262,16 +281,31 @@ double diag_cost(const std::vector<cd> &d) {
 
 }  // namespace
 
-std::vector<Op> merge_tile_diagonals(const std::vector<Op> &ops, int max_k, double sweep_cost) {
+uint64_t hi_local_choices(const Op &op) {
+    std::vector<cd> d;
+    if (!(op.kind == K_CTRL1 || (op.kind == K_DIAG && op.k == 2)) || !diag_of(op, d)) return 0;
+    for (const cd &z : d)
+        if (z == cd(0.0)) return 0;
+    // d over (q0, q1), q0 most significant: q0 may stay local if d(0, x) = 1, q1 if d(x, 0) = 1
+    uint64_t r = 0;
+    if (d[0] == cd(1.0) && d[1] == cd(1.0)) r |= 1ull << op.q[0];
+    if (d[0] == cd(1.0) && d[2] == cd(1.0)) r |= 1ull << op.q[1];
+    return r;
+}
+
+std::vector<Op> merge_tile_diagonals(const std::vector<Op> &ops, int max_k, double sweep_cost, uint64_t lmask) {
     std::vector<Op> out;
-    std::vector<int> Q;                  // block qubits, Q[0] most significant
+    std::vector<int> Q;                  // block qubits (local), Q[0] most significant
     std::vector<cd> D;                   // block diagonal over Q
+    std::vector<HiTerm> terms;           // factors from non-local qubits
     std::vector<const Op *> members;
+    bool forced = false;                 // a member has a non-local qubit: emit the block
     double member_cost = 0.0;
+    auto is_local = [&](int q) { return lmask == 0 || ((lmask >> q) & 1ull) != 0; };
     auto flush = [&]() {
         if (members.empty()) return;
-        // controls: qubits on whose 0-half every entry is 1; the block then costs a complex
-        // multiply on the elements with all controls set
+        // controls: qubits on whose 0-half every entry is 1 and to which every HiTerm is
+        // tied; the block then costs a complex multiply on the elements with all controls set
         const int K = (int)Q.size();
         int nctl = 0;
         for (int j = 0; j < K; j++) {
@@ -279,18 +313,20 @@ std::vector<Op> merge_tile_diagonals(const std::vector<Op> &ops, int max_k, doub
             bool ctl = true;
             for (size_t x = 0; x < D.size() && ctl; x++)
                 if (!((x >> bit) & 1) && D[x] != cd(1.0)) ctl = false;
+            for (const HiTerm &t : terms) ctl = ctl && t.t == Q[j];
             nctl += ctl;
         }
-        bool identity = true;
+        bool identity = terms.empty();
         for (const cd &z : D) identity = identity && z == cd(1.0);
         const double merged = identity ? 0.0 : 4.0 / (double)(1u << nctl) + sweep_cost;
-        if (members.size() >= 2 && merged < member_cost) {
+        if (forced || (members.size() >= 2 && merged < member_cost)) {
             if (!identity) {
                 Op b;
                 b.kind = K_DIAG;
                 b.k = K;
                 for (int j = 0; j < K; j++) b.q[j] = Q[j];
                 b.m = D;
+                b.hi = terms;
                 out.push_back(std::move(b));
             }
         } else {
@@ -299,6 +335,8 @@ std::vector<Op> merge_tile_diagonals(const std::vector<Op> &ops, int max_k, doub
         members.clear();
         Q.clear();
         D.clear();
+        terms.clear();
+        forced = false;
         member_cost = 0.0;
     };
     for (const Op &op : ops) {
@@ -308,15 +346,42 @@ std::vector<Op> merge_tile_diagonals(const std::vector<Op> &ops, int max_k, doub
             out.push_back(op);
             continue;
         }
-        std::vector<int> nQ = Q;
+        // the op's local part: its diagonal on its local qubits, with the x_h = 0 slice
+        // and HiTerms for a non-local qubit h (two-qubit diagonals only)
+        int jh = -1;
         for (int j = 0; j < op.k; j++)
-            if (std::find(nQ.begin(), nQ.end(), op.q[j]) == nQ.end()) nQ.push_back(op.q[j]);
-        if ((int)nQ.size() > max_k) {
+            if (!is_local(op.q[j])) jh = j;
+        std::vector<int> lq;
+        std::vector<cd> dl;
+        std::vector<HiTerm> nt;
+        if (jh < 0) {
+            lq.assign(op.q, op.q + op.k);
+            dl = d;
+        } else {
+            if (op.k != 2 || !((hi_local_choices(op) >> op.q[1 - jh]) & 1ull))
+                fail(QS_ERR_INVALID, "internal: diagonal with a non-local qubit");
+            const int ja = 1 - jh, qa = op.q[ja], qh = op.q[jh];
+            auto dd = [&](int xa, int xh) {
+                return d[(size_t)(((ja == 0 ? xa : xh) << 1) | (ja == 0 ? xh : xa))];
+            };
+            lq = {qa};
+            dl = {dd(0, 0), dd(1, 0)};
+            const cd g0 = dd(0, 1) / dd(0, 0), g1 = dd(1, 1) / dd(1, 0);
+            if (g0 != cd(1.0)) nt.push_back({-1, qh, g0});
+            const cd r = g1 / g0;
+            if (r != cd(1.0)) nt.push_back({qa, qh, r});
+        }
+        std::vector<int> nQ = Q;
+        for (int q : lq)
+            if (std::find(nQ.begin(), nQ.end(), q) == nQ.end()) nQ.push_back(q);
+        const bool with_terms = !terms.empty() || !nt.empty();
+        if ((int)nQ.size() > (with_terms ? max_k - 1 : max_k) || terms.size() + nt.size() > (size_t)kMaxHiTerms) {
             flush();
-            nQ.assign(op.q, op.q + op.k);
+            nQ = lq;
         }
         std::sort(nQ.begin(), nQ.end(), [](int a, int b) { return a > b; });
         const int K = (int)nQ.size();
+        const int kl = (int)lq.size();
         std::vector<cd> nD((size_t)1 << K, 1.0);
         for (size_t x = 0; x < nD.size(); x++) {
             auto bit_of = [&](int q) {
@@ -326,20 +391,22 @@ std::vector<Op> merge_tile_diagonals(const std::vector<Op> &ops, int max_k, doub
             };
             size_t xo = 0;  // index into the old block
             for (size_t t = 0; t < Q.size(); t++) xo |= (size_t)bit_of(Q[t]) << (Q.size() - 1 - t);
-            size_t xm = 0;  // index into the op's own diagonal
-            for (int j = 0; j < op.k; j++) xm |= (size_t)bit_of(op.q[j]) << (op.k - 1 - j);
-            nD[x] = (members.empty() ? cd(1.0) : D[xo]) * d[xm];
+            size_t xm = 0;  // index into the op's local diagonal
+            for (int j = 0; j < kl; j++) xm |= (size_t)bit_of(lq[j]) << (kl - 1 - j);
+            nD[x] = (members.empty() ? cd(1.0) : D[xo]) * dl[xm];
         }
         Q = nQ;
         D = std::move(nD);
+        terms.insert(terms.end(), nt.begin(), nt.end());
         members.push_back(&op);
+        forced = forced || jh >= 0;
         member_cost += diag_cost(d) + sweep_cost;
     }
     flush();
     return out;
 }
 
-std::vector<Op> fuse_ops(const std::vector<Op> &ops, int fuse_k, double sweep_flops) {
+std::vector<Op> fuse_ops(const std::vector<Op> &ops, int fuse_k, double sweep_flops, uint64_t lmask) {
     if (fuse_k <= 1) return ops;
     std::vector<Op> out;
     std::vector<int> Q;                  // qubits of the current block, Q[0] most significant
@@ -375,6 +442,12 @@ std::vector<Op> fuse_ops(const std::vector<Op> &ops, int fuse_k, double sweep_fl
     };
 
     for (const Op &op : ops) {
+        if (lmask && (op.qmask() & ~lmask)) {
+            // a gate with a qubit outside the pass's local set is applied on its own
+            flush();
+            out.push_back(op);
+            continue;
+        }
         std::vector<int> nQ = Q;
         for (int j = 0; j < op.k; j++) {
             bool have = false;

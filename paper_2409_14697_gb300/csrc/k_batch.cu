@@ -253,6 +253,7 @@ void batch_build(Batch &b, const std::vector<std::vector<Op>> &circ_ops, const s
         qs_options oc = o;
         oc.chunk_m = std::min(m_max, n);
         PlanParams pp = plan_params(d, oc);
+        pp.hi_diag = false;  // the batched kernel applies ops on local qubits only
         pp.c = std::min(pp.c, std::max(1, pp.m - 2));
         if ((B << pp.c) < 16) pp.c = c128 ? 1 : 1;
         CP &cp = cps[c];

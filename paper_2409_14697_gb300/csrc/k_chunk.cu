@@ -11,6 +11,7 @@
 // and the tile is written back once by TMA bulk stores.  One full HBM read + write per
 // pass, however many ops it holds.
 #include <algorithm>
+#include <type_traits>
 
 #include "chunk.h"
 #include "kops.cuh"
@@ -23,6 +24,82 @@ namespace {
 constexpr int kChunkThreads = kTileThreads;
 // Dynamic shared memory of a staged pass (tile + program): two CTAs per SM must fit.
 constexpr size_t kStagedSmemLimit = 104 * 1024;
+
+// Global amplitude index of tile t with its local bits zero.
+__device__ __forceinline__ uint64_t tile_base(uint64_t t, const ChunkArgs &a) {
+    uint64_t base = t << a.c0;
+    for (int j = 0; j < a.nlh; j++) {
+        const int b = a.lhigh[j];
+        base = ((base >> b) << (b + 1)) | (base & ((1ull << b) - 1ull));
+    }
+    return base;
+}
+
+// Reals of the table as FP64 (plain, or (hi, lo) float pairs with double-float passes).
+template <bool DF> struct TabReal;
+template <> struct TabReal<false> {
+    template <typename T> static __device__ __forceinline__ double get(const T *p, int i) { return (double)p[i]; }
+    template <typename T> static __device__ __forceinline__ void put(T *p, int i, double v) { p[i] = (T)v; }
+};
+template <> struct TabReal<true> {
+    template <typename T> static __device__ __forceinline__ double get(const T *p, int i) {
+        const df::F2 x = ((const df::F2 *)p)[i];
+        return df::join(x.h, x.l);
+    }
+    template <typename T> static __device__ __forceinline__ void put(T *p, int i, double v) {
+        ((df::F2 *)p)[i] = df::split(v);
+    }
+};
+
+// Per-tile table of an F_CDIAGK block with non-local terms (op.nt > 0): the table with,
+// for every term whose global qubit is 1 in this tile, its factor on the entries it covers.
+// Warp w + 1 multiplies up the terms of table bit w (warp 0: the terms on every entry), in
+// a fixed butterfly; then each entry takes the factors of its set bits.  FP64 throughout.
+// src: the op's reals; dst: scratch for the 2 * 2^k table reals (may equal src).
+template <bool DF, typename T>
+__device__ void fold_hi_terms(const KOp &op, const T *src, T *dst, uint64_t base) {
+    __shared__ double s_f[2 * 8];  // [0]: every entry, [1 + b]: entries with table bit b
+    using R = TabReal<DF>;
+    const int kt = op.k, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t ne = 1u << kt;
+    if (warp <= kt && warp < 8) {
+        const int tb = warp - 1;
+        double fr = 1.0, fi = 0.0;
+        for (int i = lane; i < op.nt; i += 32) {
+            const int o = (int)(2 * ne) + 4 * i;
+            if ((int)R::get(src, o) != tb || !((base >> (int)R::get(src, o + 1)) & 1ull)) continue;
+            const double gr = R::get(src, o + 2), gi = R::get(src, o + 3);
+            const double r = fr * gr - fi * gi;
+            fi = fr * gi + fi * gr;
+            fr = r;
+        }
+#pragma unroll
+        for (int d = 16; d > 0; d >>= 1) {
+            const double gr = __shfl_xor_sync(0xffffffffu, fr, d), gi = __shfl_xor_sync(0xffffffffu, fi, d);
+            const double r = fr * gr - fi * gi;
+            fi = fr * gi + fi * gr;
+            fr = r;
+        }
+        if (lane == 0) {
+            s_f[2 * warp] = fr;
+            s_f[2 * warp + 1] = fi;
+        }
+    }
+    __syncthreads();
+    for (uint32_t s = threadIdx.x; s < ne; s += blockDim.x) {
+        double vr = R::get(src, 2 * s), vi = R::get(src, 2 * s + 1);
+        for (int w = 0; w <= kt; w++) {
+            if (w > 0 && !((s >> (w - 1)) & 1u)) continue;
+            const double gr = s_f[2 * w], gi = s_f[2 * w + 1];
+            const double r = vr * gr - vi * gi;
+            vi = vr * gi + vi * gr;
+            vr = r;
+        }
+        R::put(dst, 2 * s, vr);
+        R::put(dst, 2 * s + 1, vi);
+    }
+    __syncthreads();
+}
 
 // DF: complex128 with double-float arithmetic; mats then holds (hi, lo) float pairs.
 template <typename T, bool DF>
@@ -101,6 +178,12 @@ k_chunk(typename C2T<T>::type *__restrict__ psi, const ChunkArgs a, const KOp *_
                 __syncthreads();
                 op = &s_op;
                 om = s_m;
+            }
+            if constexpr (std::is_same<T, double>::value) {  // complex128 passes only
+                if (op->fkind == F_CDIAGK && op->nt > 0) {
+                    fold_hi_terms<DF>(*op, om, s_m, tile_base(t, a));
+                    om = s_m;
+                }
             }
             if constexpr (DF) apply_op_dftile((double2 *)tile, *op, (const df::F2 *)om, s_fb, a.m);
             else apply_op_smem<T>(tile, *op, om, a.m);

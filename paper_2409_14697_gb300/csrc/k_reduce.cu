@@ -649,6 +649,54 @@ void launch_scale(DeviceState &st, double f) {
     count_launch();
 }
 
+namespace {
+
+// Word-wise copy by a grid-stride loop (one of the two sides is mapped host memory).
+template <typename W>
+__global__ void __launch_bounds__(256) k_copy_words(const W *__restrict__ src, W *__restrict__ dst, uint64_t n) {
+    for (uint64_t i = (uint64_t)blockIdx.x * 256 + threadIdx.x; i < n; i += (uint64_t)gridDim.x * 256)
+        dst[i] = src[i];
+}
+
+// Device address of [p, p + bytes) if the whole range is page-locked host memory mapped
+// into this device's address space (first and last byte checked), else null.
+const void *mapped_range(const void *p, size_t bytes) {
+    cudaPointerAttributes a0{}, a1{};
+    const char *last = (const char *)p + bytes - 1;
+    if (cudaPointerGetAttributes(&a0, p) != cudaSuccess || cudaPointerGetAttributes(&a1, last) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return nullptr;
+    }
+    if (a0.type != cudaMemoryTypeHost || a1.type != cudaMemoryTypeHost || !a0.devicePointer || !a1.devicePointer)
+        return nullptr;
+    if ((const char *)a1.devicePointer != (const char *)a0.devicePointer + (bytes - 1)) return nullptr;
+    return a0.devicePointer;
+}
+
+}  // namespace
+
+void copy_host(DeviceState &st, void *dst, const void *src, size_t bytes, bool to_device, bool use_sms) {
+    if (bytes == 0) return;
+    constexpr size_t kMinKernelBytes = 4u << 20;
+    const void *host = to_device ? src : dst;
+    const void *mh = (use_sms && bytes >= kMinKernelBytes) ? mapped_range(host, bytes) : nullptr;
+    const char *s = to_device ? (const char *)mh : (const char *)src;
+    char *d = to_device ? (char *)dst : (char *)mh;
+    const uintptr_t align = (uintptr_t)s | (uintptr_t)d | (uintptr_t)bytes;
+    if (mh && (align & 7u) == 0) {
+        const int grid = device_sm_count() * 8;
+        if ((align & 15u) == 0)
+            k_copy_words<int4><<<grid, 256, 0, st.stream>>>((const int4 *)s, (int4 *)d, bytes / 16);
+        else
+            k_copy_words<uint2><<<grid, 256, 0, st.stream>>>((const uint2 *)s, (uint2 *)d, bytes / 8);
+        QS_CUDA(cudaGetLastError());
+        count_launch();
+        return;
+    }
+    QS_CUDA(cudaMemcpyAsync(dst, src, bytes, to_device ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToHost,
+                            st.stream));
+}
+
 size_t scratch_expz_bytes(int n) { return expz_pipeline_doubles(n, chunk_bits(n)) * sizeof(double); }
 
 // Norm and <Z_q> into out_dev (n + 1 doubles); the partials use st.scratch.

@@ -54,6 +54,18 @@ template <typename T> struct FH {
     T r;
     template <int L> __device__ void operator()(Amp<T, L> *v) const { f_h<T, L>(v, r); }
 };
+// The Hadamard butterfly without its scale (a + b, a - b): 2 additions per amplitude.
+template <typename T> struct FHSum {
+    static constexpr int NT = 2;
+    template <int L> __device__ void operator()(Amp<T, L> *v) const {
+#pragma unroll
+        for (int l = 0; l < L; l++) {
+            const T ar = v[0].r[l], ai = v[0].i[l], br = v[1].r[l], bi = v[1].i[l];
+            v[0].r[l] = ar + br; v[0].i[l] = ai + bi;
+            v[1].r[l] = ar - br; v[1].i[l] = ai - bi;
+        }
+    }
+};
 template <typename T> struct FSwap {
     static constexpr int NT = 2;
     template <int L> __device__ void operator()(Amp<T, L> *v) const { f_swap<T, L>(v); }
@@ -388,7 +400,7 @@ bool launch_df(DeviceState &st, const KOp &k, const std::vector<double> &mats) {
     switch (k.fkind) {
     case F_H: {
         FHDF f;
-        split_host(1.0 / std::sqrt(2.0), f.r);
+        split_host(k.nmat ? mats[k.mat] : 1.0 / std::sqrt(2.0), f.r);
         dispatch_elem<double>(st, k, f);
         return true;
     }
@@ -413,8 +425,13 @@ void launch_typed(DeviceState &st, const Op &op) {
     }
     switch (k.fkind) {
     case F_H: {
+        const double r = k.nmat ? mats[k.mat] : 1.0 / std::sqrt(2.0);
+        if (r == 1.0) {
+            dispatch_elem<T>(st, k, FHSum<T>{});
+            return;
+        }
         FH<T> f;
-        f.r = (T)(1.0 / std::sqrt(2.0));
+        f.r = (T)r;
         dispatch_elem<T>(st, k, f);
         return;
     }

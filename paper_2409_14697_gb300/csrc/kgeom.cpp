@@ -68,7 +68,9 @@ KOp make_kop(const Op &op, const int *pos, std::vector<double> &mats) {
     switch (op.kind) {
     case K_H: {
         const int p = P(0);
-        return base(F_H, {p}, 0, {0, 1ull << p});
+        KOp k = base(F_H, {p}, 0, {0, 1ull << p});
+        if (!op.m.empty()) push_c(mats, k, {op.m[0]});  // scale (re, 0) instead of 1/sqrt2
+        return k;
     }
     case K_PERM1: {
         const int p = P(0);
@@ -151,7 +153,63 @@ KOp make_kop(const Op &op, const int *pos, std::vector<double> &mats) {
     fail(QS_ERR_INVALID, "unknown op kind");
 }
 
+namespace {
+
+// A diagonal block with factors from non-local qubits: F_CDIAGK whose reals hold the table
+// over its non-control positions, then nt terms (table bit or -1, global qubit, re, im).
+// Controls: qubits on whose 0-half the table is 1 and to which every term is tied (every
+// visited element has them set, so such a term applies to the whole table).
+KOp make_hi_block_kop(const Op &op, const int *pos, std::vector<double> &mats) {
+    const int K = op.k;
+    std::vector<int> ctl, tab;  // operand indices
+    for (int j = 0; j < K; j++) {
+        const int bit = K - 1 - j;
+        bool c = true;
+        for (size_t x = 0; x < op.m.size() && c; x++)
+            if (!((x >> bit) & 1) && op.m[x] != cd(1.0)) c = false;
+        for (const HiTerm &t : op.hi) c = c && t.t == op.q[j];
+        (c ? ctl : tab).push_back(j);
+    }
+    KOp k{};
+    k.fkind = F_CDIAGK;
+    k.k = (int)tab.size();
+    for (int i = 0; i < k.k; i++) k.pos[i] = pos[op.q[tab[i]]];
+    std::vector<int> cp;
+    for (int j : ctl) cp.push_back(pos[op.q[j]]);
+    std::sort(cp.begin(), cp.end());
+    k.nf = (int)cp.size();
+    for (int i = 0; i < k.nf; i++) {
+        k.pos[k.k + i] = cp[i];
+        k.set_mask |= 1ull << cp[i];
+    }
+    k.mat = (int32_t)mats.size();
+    for (size_t s = 0; s < (1ull << k.k); s++) {
+        size_t x = 0;
+        for (int j : ctl) x |= (size_t)1 << (K - 1 - j);
+        for (int i = 0; i < k.k; i++)
+            if ((s >> (k.k - 1 - i)) & 1) x |= (size_t)1 << (K - 1 - tab[i]);
+        mats.push_back(op.m[x].real());
+        mats.push_back(op.m[x].imag());
+    }
+    for (const HiTerm &t : op.hi) {
+        int tb = -1;
+        for (int i = 0; i < k.k; i++)
+            if (op.q[tab[i]] == t.t) tb = k.k - 1 - i;
+        mats.push_back((double)tb);
+        mats.push_back((double)t.h);
+        mats.push_back(t.f.real());
+        mats.push_back(t.f.imag());
+    }
+    k.nt = (int32_t)op.hi.size();
+    k.nmat = (int32_t)mats.size() - k.mat;
+    if (k.nmat > kMaxOpReals) fail(QS_ERR_INVALID, "internal: diagonal block too large");
+    return k;
+}
+
+}  // namespace
+
 KOp make_tile_kop(const Op &op, const int *pos, std::vector<double> &mats) {
+    if (op.kind == K_DIAG && !op.hi.empty()) return make_hi_block_kop(op, pos, mats);
     if (op.kind != K_DIAG || op.k < 3) return make_kop(op, pos, mats);
     const int K = op.k;
     std::vector<int> ctl, tab;  // operand indices

@@ -29,7 +29,10 @@ enum FKind : int32_t {
     F_TC,        // dense block on the tensor cores (k = 4..6; mat/nmat index the B operand)
     F_RPHASE,    // complex64 register phase: a run of ops on 2^5 amplitudes per thread in registers
     F_CDIAGK,    // tile passes: diagonal over k table positions pos[0..k-1] on the elements whose
-                 // nf control positions pos[k..k+nf-1] (ascending, set_mask) are all set
+                 // nf control positions pos[k..k+nf-1] (ascending, set_mask) are all set; nt
+                 // terms after the table, (table bit or -1, global qubit h, re, im): where
+                 // bit h of the tile is 1, entries with that table bit set (all for -1) take
+                 // the factor (the kernel folds them into a per-tile copy of the table)
 };
 
 // Structure of an F_DENSE1 matrix (FP64 operations per amplitude for complex128 work):
@@ -72,7 +75,7 @@ struct KOp {
     int32_t fkind;
     int32_t nf;         // fixed bits (F_H..F_DENSE2)
     int32_t fb[3];      // fixed bits ascending
-    int32_t nt;         // touched elements per group
+    int32_t nt;         // touched elements per group; F_CDIAGK: number of non-local terms
     uint64_t set_mask;  // forced-one bits
     uint64_t off[4];    // touched element offsets
     int32_t k;          // operand count (F_DIAGK / F_DENSEK); F_DENSE1: a D1_* structure class

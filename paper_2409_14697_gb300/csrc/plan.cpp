@@ -61,6 +61,9 @@ int launch_pass_ops(DeviceState &st, uint64_t lmask, const std::vector<Op> &fuse
     std::vector<float> bmats;
     uint32_t b_floats = 0;
     bool any_tc = false;
+    for (const Op &op : fused)
+        if ((op.qmask() & ~lmask) != 0)  // non-local qubits only as terms of diagonal blocks
+            fail(QS_ERR_INVALID, "internal: op with a qubit outside the pass's local set");
     for (const Op &op : fused) {
         if (use_tc && op.kind == K_DENSE && tc_available(m, op.k)) {
             KOp k{};
@@ -100,6 +103,9 @@ PlanParams plan_params(const DeviceState &st, const qs_options &o) {
     // complex64 with fusion width 4..6: dense blocks go to the tensor cores (K3)
     p.tc = !c128 && o.fuse_k >= 4 && tc_available(p.m, std::min(o.fuse_k, 6));
     p.force_chunk = o.mode == QS_MODE_CHUNK;
+    // complex128 single-state passes: a two-qubit diagonal with one qubit outside the local
+    // set is a per-tile factor on the other (non-local terms folded into the block's table)
+    p.hi_diag = c128;
     if (p.tc) {
         p.fuse_k = std::min(o.fuse_k, 6);
         p.sweep_flops = 1e30;  // fuse whenever the block fits: its cost is on the tensor pipe
@@ -144,6 +150,20 @@ Trial greedy_pass(const std::vector<Op> &ops, const std::vector<char> &done, siz
             L |= qm;
             tr.ops.push_back((int)i);
             take = true;
+        } else if (!(qm & blk) && pp.hi_diag) {
+            // a controlled phase with its control local (already, or added if it fits) and
+            // the other qubit a tile constant
+            const uint64_t ch = hi_local_choices(op);
+            uint64_t q1 = ch & L;
+            if (!q1) {
+                const uint64_t cand = ch & (low | allowed);
+                if (cand && __builtin_popcountll(L) < pp.m) q1 = cand;
+            }
+            if (q1) {
+                L |= q1 & (~q1 + 1ull);
+                tr.ops.push_back((int)i);
+                take = true;
+            }
         }
         if (!take) {
             if (diag) blocked_diag |= qm;
@@ -212,7 +232,9 @@ std::vector<Pass> choose_plan(const std::vector<Op> &ops, int n, const PlanParam
     std::vector<Op> m = merge_diagonal_runs(ops, kMinMergedRun, &org);
     if (m.size() >= ops.size()) return plan;
     std::vector<Pass> alt = make_plan(m, n, pp);
-    if (alt.size() >= plan.size()) return plan;
+    // equal pass counts: the merged runs (one table lookup per amplitude) cost less FP64
+    // work than the same gates as diagonal blocks inside chunk passes
+    if (alt.size() > plan.size()) return plan;
     merged = std::move(m);
     origin = std::move(org);
     return alt;
@@ -258,13 +280,17 @@ void run_planned(DeviceState &st, const std::vector<Op> &ops, const qs_options &
         std::vector<Op> pops;
         pops.reserve(p.ops.size());
         for (int i : p.ops) pops.push_back(ops_r[i]);
-        std::vector<Op> fused = fuse_ops(pops, pp.fuse_k, pp.sweep_flops);
+        // FP64 complex128: the pass's Hadamards but its last run unscaled (exact at pass end)
+        if (st.dtype == QS_C128 && st.prec == QS_PREC_FP64) defer_hadamard_scale(pops);
+        std::vector<Op> fused = fuse_ops(pops, pp.fuse_k, pp.sweep_flops, p.lmask);
         // runs of diagonal gates (e.g. a QFT target's controlled phases) as one diagonal
         // block per up to 8 qubits, where that is cheaper; register phases already hold
         // one- and two-qubit diagonals without a sweep
         const bool phases = st.dtype == QS_C64 && st.reg_phases && !pp.tc &&
                             rphase_applicable(__builtin_popcountll(p.lmask), kTileThreadBits);
-        if (!phases) fused = merge_tile_diagonals(fused, kTileDiagQubits, st.dtype == QS_C128 ? 0.5 : 4.0);
+        if (!phases)
+            fused = merge_tile_diagonals(fused, kTileDiagQubits, st.dtype == QS_C128 ? 0.5 : 4.0,
+                                         pp.hi_diag ? p.lmask : 0);
         stats.tile_sweeps += launch_pass_ops(st, p.lmask, fused, pp.tc);
         stats.passes++;
         stats.bytes += 2.0 * B * (double)(1ull << n);

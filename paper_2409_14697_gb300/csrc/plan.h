@@ -13,6 +13,7 @@ struct PlanParams {
     double sweep_flops;  // fusion cost gate (see fuse_ops)
     bool tc;             // complex64 blocks of 4..6 qubits run on the tensor cores
     bool force_chunk;    // QS_MODE_CHUNK: single-op passes also run as chunk passes
+    bool hi_diag = false;  // two-qubit diagonals may join with one qubit outside the local set
 };
 
 struct Pass {

@@ -49,13 +49,25 @@ enum OpKind : int32_t {
 
 struct PhaseFn;
 
+// A factor of a diagonal block that depends on a qubit outside the pass's local set (whose
+// bit is fixed within a tile): when bit h of the tile is 1, the entries of the block with
+// local qubit t set (every entry for t = -1) are multiplied by f.
+struct HiTerm {
+    int t;
+    int h;
+    cd f;
+};
+constexpr int kMaxHiTerms = 64;
+
 struct Op {
     OpKind kind;
     int k = 0;          // operand count
     int q[8] = {0};     // operands
-    std::vector<cd> m;  // K_DIAG1: 2 entries; K_DENSE1/K_CTRL1: 4; K_DIAG: 2^k; K_DENSE: 4^k
+    std::vector<cd> m;  // K_DIAG1: 2 entries; K_DENSE1/K_CTRL1: 4; K_DIAG: 2^k; K_DENSE: 4^k;
+                        // K_H: empty (1/sqrt2) or {scale} (gate-by-gate deferred scale)
     std::shared_ptr<const PhaseFn> pf;  // K_PHASEFN
     uint64_t wide_mask = 0;             // K_PHASEFN: every qubit the function reads
+    std::vector<HiTerm> hi;             // K_DIAG blocks of a chunk pass: non-local factors
     // The full 2^k x 2^k matrix of the op on q[0..k-1] (row-major).
     std::vector<cd> full() const;
     uint64_t qmask() const {
@@ -76,13 +88,25 @@ Op lower_gate(const qs_gate &g);
 // function; here, with sweep_flops >= 0, a merge is taken only if the fused block costs at
 // most the flops per amplitude of its members applied one by one plus sweep_flops (the
 // value of one saved pass over the tile).  sweep_flops < 0 merges whenever the width fits.
-std::vector<Op> fuse_ops(const std::vector<Op> &ops, int fuse_k, double sweep_flops = -1.0);
+// lmask != 0: ops with a qubit outside lmask (a chunk pass's local set) are not fused.
+std::vector<Op> fuse_ops(const std::vector<Op> &ops, int fuse_k, double sweep_flops = -1.0, uint64_t lmask = 0);
 // Merges runs of consecutive diagonal gates into diagonal blocks of at most max_k qubits
 // where that costs fewer FP64 operations per amplitude in a shared-memory pass (a block
 // multiplies only the elements whose "control" qubits, those on whose 0-half every entry
 // is 1, are set; sweep_cost is added per separate sweep).  FP64 host products; blocks
 // that come out as the identity are dropped.
-std::vector<Op> merge_tile_diagonals(const std::vector<Op> &ops, int max_k, double sweep_cost);
+//
+// With lmask != 0 (the pass's local qubits), two-qubit diagonals with one qubit outside
+// lmask are taken too: d(x_a, x_h) = d(x_a, 0) * [x_h ? d(x_a, 1) / d(x_a, 0) : 1], so the
+// block's table gets the x_h = 0 slice on its local qubit a and the rest becomes HiTerms
+// (g0 = d(0,1)/d(0,0) on every entry, g1/g0 with g1 = d(1,1)/d(1,0) on the entries with a
+// set).  A block with HiTerms has at most max_k - 1 local qubits and 64 terms.
+std::vector<Op> merge_tile_diagonals(const std::vector<Op> &ops, int max_k, double sweep_cost,
+                                     uint64_t lmask = 0);
+// Qubits of a two-qubit diagonal (no zero entry) that may be its only local qubit in a
+// chunk pass: a with d(0, x) = 1 for both x (the gate is then a phase on a's 1-half chosen
+// by the other bit, which keeps a a control of the block: CP, CZ, controlled RZ).  0 if none.
+uint64_t hi_local_choices(const Op &op);
 // True for ops that are diagonal in the computational basis (they commute with each other).
 bool op_is_diagonal(const Op &op);
 // Gate-by-gate form of a circuit: every one-qubit diagonal diag(d0, d1) with d0 != 1 (RZ)
@@ -91,6 +115,13 @@ bool op_is_diagonal(const Op &op);
 // last one, applied in full.  The product of the ops is unchanged (FP64 host arithmetic),
 // so the state is exact again when the last op has run.
 std::vector<Op> fold_global_phases(const std::vector<Op> &ops);
+// Gate-by-gate complex128 FP64 form of the Hadamards of a circuit: all but the last (and
+// every (kMaxUnscaledH + 1)-th) become the unscaled butterfly (a + b, a - b), 2 FP64
+// additions per amplitude instead of 3 FP64 instructions; the collected factor 2^(-k/2) is
+// carried by the next scaled one (K_H with m = {scale}), so the state is exact again when
+// the last Hadamard has run.  Between, amplitudes grow by at most 2^(kMaxUnscaledH / 2).
+constexpr int kMaxUnscaledH = 63;
+void defer_hadamard_scale(std::vector<Op> &ops);
 // Real flops per amplitude of applying op alone (structure-aware).
 double op_flops(const Op &op);
 
@@ -158,6 +189,15 @@ void launch_scale_ratio(DeviceState &st, const double *norms_dev);
 void top_k_async(DeviceState &st, uint32_t k, uint64_t *idx_dev, double *amp_dev);
 size_t scratch_expz_bytes(int n);
 size_t scratch_topk_bytes(int n, uint32_t k);
+
+// Host <-> device copy of `bytes` on st.stream (asynchronous).  With use_sms, ranges of
+// page-locked host memory mapped into the device (cudaHostAlloc, registered memory) of
+// 4 MiB or more are copied by a kernel that reads or writes them over the CPU-GPU link: on
+// GB300 copy-engine transfers were measured to run at 20-46 GB/s for their first gigabytes
+// now and then before reaching the link rate (211 GB/s in, 194 GB/s out), while SM copies
+// hold that rate from the start.  Without use_sms (copies meant to overlap kernels of
+// other streams) and for other host memory: cudaMemcpyAsync on the copy engines.
+void copy_host(DeviceState &st, void *dst, const void *src, size_t bytes, bool to_device, bool use_sms);
 
 // Algorithmic bytes of one streaming application of op on an n-qubit state.
 double stream_bytes(const Op &op, int n, int dtype);

@@ -42,6 +42,14 @@ template <typename T> struct SH {
     T r;
     __device__ void operator()(Amp<T, 1> *v) const { f_h<T, 1>(v, r); }
 };
+// Unscaled Hadamard butterfly (a + b, a - b): 2 additions per amplitude.
+template <typename T> struct SHSum {
+    __device__ void operator()(Amp<T, 1> *v) const {
+        const T ar = v[0].r[0], ai = v[0].i[0], br = v[1].r[0], bi = v[1].i[0];
+        v[0].r[0] = ar + br; v[0].i[0] = ai + bi;
+        v[1].r[0] = ar - br; v[1].i[0] = ai - bi;
+    }
+};
 template <typename T> struct SSwap {
     __device__ void operator()(Amp<T, 1> *v) const { f_swap<T, 1>(v); }
 };
@@ -545,7 +553,10 @@ __device__ __forceinline__ void rphase_run(float2 *tile, const KOp &ph, const fl
 template <typename T, bool RP = true>
 __device__ __forceinline__ void apply_op_smem(typename C2T<T>::type *tile, const KOp &op, const T *sm, int m) {
     switch (op.fkind) {
-    case F_H: groups_apply<T, 2>(tile, op, m, SH<T>{(T)0.70710678118654752440}); break;
+    case F_H:  // scale in the reals when a pass defers it (1: the unscaled butterfly)
+        if (op.nmat >= 1 && sm[0] == (T)1) groups_apply<T, 2>(tile, op, m, SHSum<T>{});
+        else groups_apply<T, 2>(tile, op, m, SH<T>{op.nmat >= 1 ? sm[0] : (T)0.70710678118654752440});
+        break;
     case F_SWAP: groups_apply<T, 2>(tile, op, m, SSwap<T>{}); break;
     case F_DENSE1:
         if constexpr (std::is_same<T, double>::value) {

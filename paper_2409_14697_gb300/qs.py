@@ -105,6 +105,8 @@ _SIGS = {
                                ctypes.POINTER(ctypes.c_int64)]),
     "qs_set_amplitudes": (ctypes.c_int, [_VP, ctypes.c_uint64, ctypes.c_uint64, _VP]),
     "qs_amplitudes": (ctypes.c_int, [_VP, ctypes.c_uint64, ctypes.c_uint64, _VP]),
+    "qs_set_amplitudes_async": (ctypes.c_int, [_VP, ctypes.c_uint64, ctypes.c_uint64, _VP]),
+    "qs_amplitudes_async": (ctypes.c_int, [_VP, ctypes.c_uint64, ctypes.c_uint64, _VP]),
     "qs_norm": (ctypes.c_int, [_VP, _DP]),
     "qs_expectation_z": (ctypes.c_int, [_VP, _DP, _DP]),
     "qs_top_amplitudes": (ctypes.c_int, [_VP, ctypes.c_uint32, _U64P, _DP]),
@@ -277,6 +279,16 @@ def qs_amplitudes_into(h, off: int, cnt: int, host_ptr: int):
 
 def qs_set_amplitudes_from(h, off: int, cnt: int, host_ptr: int):
     _check(load().qs_set_amplitudes(h, off, cnt, host_ptr))
+
+
+def qs_set_amplitudes_async(h, off: int, cnt: int, host_ptr: int):
+    """Stream-ordered host -> state copy; keep the buffer alive until qs_synchronize(h)."""
+    _check(load().qs_set_amplitudes_async(h, off, cnt, host_ptr))
+
+
+def qs_amplitudes_async(h, off: int, cnt: int, host_ptr: int):
+    """Stream-ordered state -> host copy; read the buffer after qs_synchronize(h)."""
+    _check(load().qs_amplitudes_async(h, off, cnt, host_ptr))
 
 
 def qs_norm(h) -> float:

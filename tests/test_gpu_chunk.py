@@ -185,6 +185,54 @@ def test_register_phases_brickwork_sweeps(qs):
     assert st["tile_sweeps"] * 4 <= st["ops_after_fuse"]
 
 
+def _nonlocal_phase_circuit(n, seed):
+    """QFT, then a seeded mix of H, U3, CNOT, RZ and controlled phases (CP, CZ and CU3 with
+    theta = 0, a phase on the target chosen by the control)."""
+    r = np.random.default_rng(seed)
+    gates = list(inputs.qft(n))
+    for _ in range(300):
+        a, b = (int(x) for x in r.choice(n, 2, replace=False))
+        kind = int(r.integers(7))
+        if kind == 0:
+            gates.append(("h", (a,), ()))
+        elif kind == 1:
+            gates.append(("u3", (a,), tuple(float(x) for x in r.uniform(0, 2 * np.pi, 3))))
+        elif kind == 2:
+            gates.append(("cnot", (a, b), ()))
+        elif kind == 3:
+            gates.append(("rz", (a,), (float(r.uniform(0, 2 * np.pi)),)))
+        elif kind == 4:
+            gates.append(("cp", (a, b), (float(r.uniform(0, 2 * np.pi)),)))
+        elif kind == 5:
+            gates.append(("cz", (a, b), ()))
+        else:
+            gates.append(("cu3", (a, b), (0.0, float(r.uniform(0, 2 * np.pi)), float(r.uniform(0, 2 * np.pi)))))
+    return gates
+
+
+@pytest.mark.parametrize("prec", [1, 2])
+@pytest.mark.parametrize("n,m", [(14, 6), (18, 8), (20, 12)])
+def test_nonlocal_controlled_phases(qs, n, m, prec):
+    """complex128 passes take controlled phases whose other qubit is outside the local set
+    (a per-tile factor folded into the block's table).  The plan must use that (some
+    controlled phase in a pass with one of its qubits non-local), and the state must equal
+    the oracle's with FP64 and with double-float arithmetic."""
+    gates = _nonlocal_phase_circuit(n, seed=n + m)
+    pog, lm = qs.qs_plan(n, 2, gates, qs.options(chunk_m=m))
+    hi = 0
+    for (name, qb, _), p in zip(gates, pog):
+        L = int(lm[p])
+        if L and name in ("cp", "cz", "cu3") and len(qb) == 2:
+            if sum((L >> q) & 1 for q in qb) == 1:
+                hi += 1
+    assert hi > 0
+    psi0 = inputs.gaussian_state(n, seed=n + 1)
+    want = oracle.run(psi0.copy(), n, gates)
+    got, st = run_gpu(qs, n, 2, psi0, gates, qs.QS_MODE_AUTO, chunk_m=m, precision=prec)
+    assert np.max(np.abs(got - want)) <= TOL_C128
+    assert st["passes"] == len(lm)
+
+
 @pytest.mark.parametrize("dtype,flags", [(2, 0), (1, 1)])
 @pytest.mark.parametrize("n", [14, 20])
 def test_qft_merged_diagonal_blocks(qs, n, dtype, flags):

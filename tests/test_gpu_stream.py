@@ -126,6 +126,100 @@ def test_gate_mode_folded_rz_phases(qs, n, dtype):
 
 
 @pytest.mark.parametrize("dtype", [2, 1])
+@pytest.mark.parametrize("n", [4, 12])
+def test_gate_mode_deferred_hadamard_scale(qs, n, dtype):
+    """Over 200 Hadamards in one gate-by-gate call, mixed with U3, CNOT and RZ: complex128
+    runs all but every 64th and the last as the unscaled butterfly and lets the next scaled
+    one carry 2^(-k/2); the state after the call equals the oracle's element by element."""
+    psi0 = inputs.gaussian_state(n, seed=50 + n)
+    if dtype == 1:
+        psi0 = psi0.astype(np.complex64)
+    r = np.random.default_rng(51 + n)
+    gates = []
+    for i in range(210):
+        q = int(r.integers(n))
+        gates.append(("h", (q,), ()))
+        if i % 9 == 4:
+            gates.append(("u3", ((q + 1) % n,), tuple(float(a) for a in r.uniform(0, 2 * math.pi, 3))))
+        if i % 11 == 5:
+            gates.append(("cnot", (q, (q + 1) % n), ()))
+        if i % 13 == 6:
+            gates.append(("rz", (q,), (float(r.uniform(0, 2 * math.pi)),)))
+    gates.append(("x", (0,), ()))
+    got = run_gpu(qs, n, dtype, psi0, gates, qs.QS_MODE_GATE)
+    want = psi0.astype(np.complex128)
+    oracle.run(want, n, gates)
+    check(got, want, dtype)
+
+
+@pytest.mark.parametrize("dtype", [2, 1])
+def test_pinned_host_copies(qs, dtype):
+    """Page-locked host buffers of 4 MiB or more take the copy-kernel path in both
+    directions (whole state and an odd sub-range); every byte must round-trip, and the
+    pageable path must give the same bytes."""
+    torch = pytest.importorskip("torch")
+    n = 20 if dtype == 2 else 21
+    npdt = np.complex128 if dtype == 2 else np.complex64
+    psi = inputs.gaussian_state(n, seed=77).astype(npdt)
+    pin_in = torch.empty(psi.view(np.uint8).size, dtype=torch.uint8, pin_memory=True)
+    assert pin_in.is_pinned()
+    pin_in.numpy()[:] = psi.view(np.uint8)
+    pin_out = torch.zeros_like(pin_in).pin_memory()
+    h = qs.qs_create(n, dtype)
+    try:
+        qs.qs_set_amplitudes_from(h, 0, 1 << n, pin_in.data_ptr())
+        assert np.array_equal(qs.qs_amplitudes(h), psi)           # pageable read-back
+        qs.qs_amplitudes_into(h, 0, 1 << n, pin_out.data_ptr())
+        assert np.array_equal(pin_out.numpy().view(npdt), psi)
+        # odd offset and count (8-byte aligned for complex64): 3/4 of the state
+        off, cnt = 3, (3 << (n - 2)) + 1
+        B = psi.itemsize
+        scaled = (psi * npdt(0.5)).astype(npdt)
+        src = torch.empty(scaled.view(np.uint8).size, dtype=torch.uint8, pin_memory=True)
+        src.numpy()[:] = scaled.view(np.uint8)
+        qs.qs_set_amplitudes_from(h, off, cnt, src.data_ptr() + off * B)
+        want = psi.copy()
+        want[off:off + cnt] = scaled[off:off + cnt]
+        assert np.array_equal(qs.qs_amplitudes(h), want)
+        pin_out.zero_()
+        qs.qs_amplitudes_into(h, off, cnt, pin_out.data_ptr() + off * B)
+        got = pin_out.numpy().view(npdt)
+        assert np.array_equal(got[off:off + cnt], want[off:off + cnt])
+        assert not got[:off].any() and not got[off + cnt:].any()
+    finally:
+        qs.qs_destroy(h)
+
+
+def test_async_copies_two_states(qs):
+    """Stream-ordered copies on two states in flight (as the end-to-end benchmark runs them):
+    pinned input shared by both, a circuit per state, each state's result into its own
+    pinned buffer; after qs_synchronize both equal the oracle."""
+    torch = pytest.importorskip("torch")
+    n = 19
+    psi = inputs.gaussian_state(n, seed=91)
+    pin_in = torch.empty(psi.view(np.float64).size, dtype=torch.float64, pin_memory=True)
+    pin_in.numpy()[:] = psi.view(np.float64)
+    outs = [torch.zeros_like(pin_in).pin_memory() for _ in range(2)]
+    circuits = [inputs.gate_sweep(n, "u3", seed=5, count=n) + inputs.gate_sweep(n, "cnot", seed=5, count=n),
+                inputs.gate_sweep(n, "h", seed=6, count=n) + inputs.gate_sweep(n, "rz", seed=6, count=n)]
+    hs = [qs.qs_create(n, 2) for _ in range(2)]
+    try:
+        for h, circ, out in zip(hs, circuits, outs):
+            qs.qs_set_amplitudes_async(h, 0, 1 << n, pin_in.data_ptr())
+            qs.qs_apply_circuit(h, circ, qs.options(mode=qs.QS_MODE_GATE))
+            qs.qs_amplitudes_async(h, 0, 1 << n, out.data_ptr())
+        for h in hs:
+            qs.qs_synchronize(h)
+    finally:
+        for h in hs:
+            qs.qs_destroy(h)
+    for circ, out in zip(circuits, outs):
+        want = psi.copy()
+        oracle.run(want, n, circ)
+        check(out.numpy().view(np.complex128), want, 2)
+
+
+@pytest.mark.parametrize("dtype", [2, 1])
 def test_brickwork_12q(qs, dtype):
     """20 layers of U3 on every qubit + CZ brickwork from |0...0>, all 4096 amplitudes."""
     n = 12

@@ -28,11 +28,15 @@ def check_plan(n, dtype, gates, chunk_m=0):
     c = min(4 if dtype == qs.QS_C128 else 5, m)
     assert len(pog) == len(gates)
     assert (pog >= 0).all() and (pog < len(lm)).all()
-    # every gate of a chunk pass lies inside the pass's local qubits
+    # every gate of a chunk pass lies inside the pass's local qubits, except that complex128
+    # passes take two-qubit diagonals with one qubit outside (a per-tile factor on the other)
     for i, g in enumerate(gates):
         L = int(lm[pog[i]])
         if L:
-            assert qmask(g) & ~L == 0
+            if dtype == qs.QS_C128 and g[0] in DIAGONAL and len(g[1]) == 2:
+                assert qmask(g) & L, (i, g)
+            else:
+                assert qmask(g) & ~L == 0, (i, g)
             assert bin(L).count("1") == m
             assert L & ((1 << c) - 1) == (1 << c) - 1
     _deps_in_order(gates, pog)
@@ -95,6 +99,35 @@ def test_window_search_cuts_passes():
     assert len(lm) <= 90
 
 
+@pytest.mark.parametrize("n", [23, 30])
+def test_qft_controlled_phases_with_nonlocal_qubit(n):
+    """complex128 passes take a target's controlled phases whatever its partner's position
+    (a per-tile factor when the partner is outside the local set), so each pass takes the
+    next 8 Hadamard targets: 30 qubits need 6 passes instead of 35; complex64 keeps the old
+    rule (register phases hold local gates only)."""
+    gates = inputs.qft(n)
+    pog, lm = check_plan(n, qs.QS_C128, gates)
+    assert len(lm) <= (4 if n == 23 else 6)
+    pog64, lm64 = check_plan(n, qs.QS_C64, gates)
+    assert len(lm64) > 2 * len(lm)
+
+
+def test_nonlocal_diagonals_only_controlled_phases():
+    """RZZ (no control) stays a local-only gate; CP, CZ and CU3(0, ..) may leave one qubit
+    outside the pass."""
+    n = 20
+    r = np.random.default_rng(4)
+    gates = [("h", (q,), ()) for q in range(n)]
+    for _ in range(200):
+        a, b = (int(x) for x in r.choice(n, 2, replace=False))
+        gates.append(("rzz", (a, b), (0.3,)))
+    pog, lm = qs.qs_plan(n, qs.QS_C128, gates, qs.options(chunk_m=8, flags=qs.QS_OPT_NO_DIAG_MERGE))
+    for (name, qb, _), p in zip(gates, pog):
+        L = int(lm[p])
+        if L:
+            assert qmask((name, qb, ())) & ~L == 0
+
+
 def _deps_in_order(gates, pog):
     """Gates sharing a qubit keep their pass order unless both are diagonal (diagonal gates
     commute with each other, so the planner may run a later one in an earlier pass)."""
@@ -120,9 +153,16 @@ def test_diag_merge_cuts_passes_for_complete_qaoa():
     pass (merged plan), far fewer passes than packing all-pairs RZZ into chunk passes."""
     n = 22
     gates = inputs.qaoa_complete(n, p=2, seed=1)
+    # complex64 passes hold only local gates: merging saves passes
+    pog_m, lm_m = qs.qs_plan(n, qs.QS_C64, gates)
+    pog_n, lm_n = qs.qs_plan(n, qs.QS_C64, gates, qs.options(flags=qs.QS_OPT_NO_DIAG_MERGE))
+    assert len(lm_m) < len(lm_n)
+    _deps_in_order(gates, pog_m)
+    # complex128 passes also take RZZ with a non-local qubit; at equal pass counts the merged
+    # runs (one table lookup per amplitude) are kept
     pog_m, lm_m = qs.qs_plan(n, qs.QS_C128, gates)
     pog_n, lm_n = qs.qs_plan(n, qs.QS_C128, gates, qs.options(flags=qs.QS_OPT_NO_DIAG_MERGE))
-    assert len(lm_m) < len(lm_n)
+    assert len(lm_m) <= len(lm_n)
     _deps_in_order(gates, pog_m)
     # the RZZ gates of one layer share one streamed pass (no local mask)
     npairs = n * (n - 1) // 2
