@@ -191,8 +191,11 @@ int qs_last_stats(const qs_state *s, qs_stats *out);
  * and "In-cache Operations"; Sec. III-A tier 4): no GPU is touched.  For an n-qubit state
  * of dtype dt, writes for each gate the index of the pass that executes it into
  * pass_of_gate[n_gates]; for each pass p < *n_passes (at most n_gates passes), its local
- * qubit mask into pass_lmask[p] (0 for a pass run by the streaming kernel).  The caller
- * allocates both arrays with n_gates entries.  Errors as qs_apply_circuit. */
+ * qubit mask into pass_lmask[p] (0 for a pass run by the streaming kernel).  Every qubit
+ * of a gate is in its pass's mask, except that complex128 passes take a controlled phase
+ * (CP, CZ, CU3 with theta = 0) with one of its qubits in the mask and the other outside
+ * (a per-tile factor).  The caller allocates both arrays with n_gates entries.  Errors as
+ * qs_apply_circuit. */
 int qs_plan(int n_qubits, qs_dtype dt, const qs_gate *gates, size_t n_gates, const qs_options *opt,
             int32_t *pass_of_gate, uint64_t *pass_lmask, int64_t *n_passes);
 
