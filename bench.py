@@ -379,18 +379,17 @@ def time_planned(qs, h, stream, recs, n, B):
     return out
 
 
-def run_e2e(qs, h, host_in, recs, opts, n, B, n_gates, world, dt):
+def run_e2e(qs, h, host_in, recs, opts, n, B, n_gates, world, dt, in_flight=2, steps=6):
     """Same metric through the C ABI with host buffers.  Each step copies the initial state
     from pinned host memory into a state (H2D), applies the 240 gates and copies the final
     state back into pinned host memory (D2H); the host waits for a step's result before
-    it reuses that step's buffers.  Two states on two streams keep two steps in flight (as
-    the serving loop does with its slots), so one step's copies overlap the other's gates:
-    step s runs on state s % 2 with the stream-ordered copy entry points."""
+    it reuses that step's buffers.  `in_flight` states on their own streams keep that many
+    steps in flight (as the serving loop does with its slots), so one step's copies
+    overlap the others' gates: step s runs on state s % in_flight with the stream-ordered
+    copy entry points."""
     import torch
-    h2 = qs.qs_create(n, dt)
-    states = [h, h2]
-    outs = [torch.empty_like(host_in, pin_memory=True) for _ in range(2)]
-    steps = 6
+    states = [h] + [qs.qs_create(n, dt) for _ in range(in_flight - 1)]
+    outs = [torch.empty_like(host_in, pin_memory=True) for _ in range(in_flight)]
     N = 1 << n
     try:
         for st in states:
@@ -398,23 +397,25 @@ def run_e2e(qs, h, host_in, recs, opts, n, B, n_gates, world, dt):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         for s in range(steps):
-            st = states[s % 2]
-            if s >= 2:
-                qs.qs_synchronize(st)             # step s - 2's final state is on the host
-                float(outs[s % 2][0])
+            k = s % in_flight
+            st = states[k]
+            if s >= in_flight:
+                qs.qs_synchronize(st)             # step s - in_flight's final state is on the host
+                float(outs[k][0])
             qs.qs_set_amplitudes_async(st, 0, N, host_in.data_ptr())
             for name in GATE_TYPES:
                 qs.qs_apply_circuit(st, recs[name], opts)
-            qs.qs_amplitudes_async(st, 0, N, outs[s % 2].data_ptr())
+            qs.qs_amplitudes_async(st, 0, N, outs[k].data_ptr())
         for st in states:
             qs.qs_synchronize(st)
         wall = (time.perf_counter() - t0) / steps
     finally:
-        qs.qs_destroy(h2)
+        for st in states[1:]:
+            qs.qs_destroy(st)
     rec_bytes = 72 * n_gates
     return {"value": round(world * n_gates / wall, 2), "unit": "gates/s",
             "h2d_bytes_per_step": (B << n) + rec_bytes, "d2h_bytes_per_step": B << n,
-            "ms_per_step": round(wall * 1e3, 2), "steps": steps, "states_in_flight": 2}
+            "ms_per_step": round(wall * 1e3, 2), "steps": steps, "states_in_flight": in_flight}
 
 
 # FP64 instructions per amplitude (FMA-class issues, one FP64 pipe slot each) of the

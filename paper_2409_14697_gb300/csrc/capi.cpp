@@ -399,7 +399,7 @@ int qs_set_amplitudes(qs_state *s, uint64_t off, uint64_t cnt, const void *host_
     const uint64_t N = 1ull << s->d.n;
     if (off > N || cnt > N - off) fail(QS_ERR_INVALID, "amplitude range out of bounds");
     const size_t B = amp_bytes(s->d.dtype);
-    copy_host(s->d, (char *)s->d.psi + off * B, host_src, cnt * B, true, true);
+    copy_host(s->d, (char *)s->d.psi + off * B, host_src, cnt * B, true, 0);
     QS_CUDA(cudaStreamSynchronize(s->d.stream));
     QS_API_END
 }
@@ -411,7 +411,7 @@ int qs_amplitudes(qs_state *s, uint64_t off, uint64_t cnt, void *host_dst) {
     if (off > N || cnt > N - off) fail(QS_ERR_INVALID, "amplitude range out of bounds");
     const size_t B = amp_bytes(s->d.dtype);
     sync_and_check(s->d);
-    copy_host(s->d, host_dst, (const char *)s->d.psi + off * B, cnt * B, false, true);
+    copy_host(s->d, host_dst, (const char *)s->d.psi + off * B, cnt * B, false, 0);
     QS_CUDA(cudaStreamSynchronize(s->d.stream));
     QS_API_END
 }
@@ -422,7 +422,7 @@ int qs_set_amplitudes_async(qs_state *s, uint64_t off, uint64_t cnt, const void 
     const uint64_t N = 1ull << s->d.n;
     if (off > N || cnt > N - off) fail(QS_ERR_INVALID, "amplitude range out of bounds");
     const size_t B = amp_bytes(s->d.dtype);
-    copy_host(s->d, (char *)s->d.psi + off * B, host_src, cnt * B, true, false);
+    copy_host(s->d, (char *)s->d.psi + off * B, host_src, cnt * B, true, kAsyncCopyCtas);
     QS_API_END
 }
 
@@ -432,7 +432,7 @@ int qs_amplitudes_async(qs_state *s, uint64_t off, uint64_t cnt, void *host_dst)
     const uint64_t N = 1ull << s->d.n;
     if (off > N || cnt > N - off) fail(QS_ERR_INVALID, "amplitude range out of bounds");
     const size_t B = amp_bytes(s->d.dtype);
-    copy_host(s->d, host_dst, (const char *)s->d.psi + off * B, cnt * B, false, false);
+    copy_host(s->d, host_dst, (const char *)s->d.psi + off * B, cnt * B, false, kAsyncCopyCtas);
     QS_API_END
 }
 

@@ -10,6 +10,7 @@
 #include <cstring>
 #include <stdexcept>
 
+#include "kops.cuh"
 #include "qs_internal.h"
 
 namespace qs {
@@ -230,12 +231,21 @@ void defer_hadamard_scale(std::vector<Op> &ops) {
 }
 
 double op_flops(const Op &op) {
+    // FP64 operations per amplitude of the one-qubit forms (general 8, real first entry 7,
+    // real 4, RX-like 4)
+    auto dense1 = [](const std::vector<cd> &u) {
+        switch (d1_class(u)) {
+        case D1_REAL: case D1_RX: return 4.0;
+        case D1_R0: return 7.0;
+        default: return 8.0;
+        }
+    };
     switch (op.kind) {
-    case K_H: return 4.0;
+    case K_H: return (!op.m.empty() && op.m[0] == cd(1.0)) ? 2.0 : 3.0;
     case K_PERM1: case K_SWAP: return 0.0;
     case K_DIAG1: return op.m[0] == cd(1.0) ? 2.0 : 4.0;
-    case K_DENSE1: return 8.0;
-    case K_CTRL1: return 4.0;
+    case K_DENSE1: return dense1(op.m);
+    case K_CTRL1: return 0.5 * dense1(op.m);
     case K_DIAG: return 4.0;
     case K_DENSE: return 4.0 * (double)(1 << op.k);
     case K_PHASEFN: return 6.0;

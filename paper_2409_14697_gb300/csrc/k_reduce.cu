@@ -651,11 +651,21 @@ void launch_scale(DeviceState &st, double f) {
 
 namespace {
 
-// Word-wise copy by a grid-stride loop (one of the two sides is mapped host memory).
+// Word-wise copy by a grid-stride loop (one of the two sides is mapped host memory); four
+// loads in flight per thread, so a small grid still covers the link's latency.
 template <typename W>
 __global__ void __launch_bounds__(256) k_copy_words(const W *__restrict__ src, W *__restrict__ dst, uint64_t n) {
-    for (uint64_t i = (uint64_t)blockIdx.x * 256 + threadIdx.x; i < n; i += (uint64_t)gridDim.x * 256)
-        dst[i] = src[i];
+    constexpr int kUn = 4;
+    const uint64_t stride = (uint64_t)gridDim.x * 256;
+    uint64_t i = (uint64_t)blockIdx.x * 256 + threadIdx.x;
+    for (; i + (kUn - 1) * stride < n; i += kUn * stride) {
+        W v[kUn];
+#pragma unroll
+        for (int u = 0; u < kUn; u++) v[u] = src[i + u * stride];
+#pragma unroll
+        for (int u = 0; u < kUn; u++) dst[i + u * stride] = v[u];
+    }
+    for (; i < n; i += stride) dst[i] = src[i];
 }
 
 // Device address of [p, p + bytes) if the whole range is page-locked host memory mapped
@@ -675,16 +685,16 @@ const void *mapped_range(const void *p, size_t bytes) {
 
 }  // namespace
 
-void copy_host(DeviceState &st, void *dst, const void *src, size_t bytes, bool to_device, bool use_sms) {
+void copy_host(DeviceState &st, void *dst, const void *src, size_t bytes, bool to_device, int ctas) {
     if (bytes == 0) return;
     constexpr size_t kMinKernelBytes = 4u << 20;
     const void *host = to_device ? src : dst;
-    const void *mh = (use_sms && bytes >= kMinKernelBytes) ? mapped_range(host, bytes) : nullptr;
+    const void *mh = bytes >= kMinKernelBytes ? mapped_range(host, bytes) : nullptr;
     const char *s = to_device ? (const char *)mh : (const char *)src;
     char *d = to_device ? (char *)dst : (char *)mh;
     const uintptr_t align = (uintptr_t)s | (uintptr_t)d | (uintptr_t)bytes;
     if (mh && (align & 7u) == 0) {
-        const int grid = device_sm_count() * 8;
+        const int grid = ctas > 0 ? ctas : device_sm_count() * 8;
         if ((align & 15u) == 0)
             k_copy_words<int4><<<grid, 256, 0, st.stream>>>((const int4 *)s, (int4 *)d, bytes / 16);
         else

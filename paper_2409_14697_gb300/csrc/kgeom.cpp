@@ -6,11 +6,6 @@
 
 namespace qs {
 
-namespace {
-
-bool is_one(cd z) { return z == cd(1.0, 0.0); }
-
-// D1_* class of a 2x2 matrix (row-major)
 int32_t d1_class(const std::vector<cd> &u) {
     const bool real = u[0].imag() == 0.0 && u[1].imag() == 0.0 && u[2].imag() == 0.0 && u[3].imag() == 0.0;
     if (real) return D1_REAL;
@@ -18,6 +13,11 @@ int32_t d1_class(const std::vector<cd> &u) {
     if (u[0].imag() == 0.0) return D1_R0;
     return D1_GENERAL;
 }
+
+namespace {
+
+bool is_one(cd z) { return z == cd(1.0, 0.0); }
+
 bool is_minus_one(cd z) { return z == cd(-1.0, 0.0); }
 
 void push_c(std::vector<double> &mats, KOp &k, std::initializer_list<cd> vals) {

@@ -122,7 +122,11 @@ std::vector<Op> fold_global_phases(const std::vector<Op> &ops);
 // the last Hadamard has run.  Between, amplitudes grow by at most 2^(kMaxUnscaledH / 2).
 constexpr int kMaxUnscaledH = 63;
 void defer_hadamard_scale(std::vector<Op> &ops);
-// Real flops per amplitude of applying op alone (structure-aware).
+// Structure class (D1_GENERAL, D1_R0, D1_REAL, D1_RX of kops.cuh) of a 2x2 matrix,
+// row-major: the cheapest form the complex128 kernels apply it with.
+int32_t d1_class(const std::vector<cd> &u);
+// Real flops per amplitude of applying op alone (structure-aware: the complex128 forms of
+// one-qubit matrices, the unscaled Hadamard, the elements a controlled op touches).
 double op_flops(const Op &op);
 
 // ---------------------------------------------------------------------------------
@@ -190,14 +194,18 @@ void top_k_async(DeviceState &st, uint32_t k, uint64_t *idx_dev, double *amp_dev
 size_t scratch_expz_bytes(int n);
 size_t scratch_topk_bytes(int n, uint32_t k);
 
-// Host <-> device copy of `bytes` on st.stream (asynchronous).  With use_sms, ranges of
-// page-locked host memory mapped into the device (cudaHostAlloc, registered memory) of
-// 4 MiB or more are copied by a kernel that reads or writes them over the CPU-GPU link: on
-// GB300 copy-engine transfers were measured to run at 20-46 GB/s for their first gigabytes
-// now and then before reaching the link rate (211 GB/s in, 194 GB/s out), while SM copies
-// hold that rate from the start.  Without use_sms (copies meant to overlap kernels of
-// other streams) and for other host memory: cudaMemcpyAsync on the copy engines.
-void copy_host(DeviceState &st, void *dst, const void *src, size_t bytes, bool to_device, bool use_sms);
+// Host <-> device copy of `bytes` on st.stream (asynchronous).  Ranges of page-locked host
+// memory mapped into the device (cudaHostAlloc, registered memory) of 4 MiB or more are
+// copied by a kernel that reads or writes them over the CPU-GPU link: on GB300 copy-engine
+// transfers were measured to run at 20-46 GB/s for their first gigabytes now and then
+// before reaching the link rate (211 GB/s in, 194 GB/s out), while SM copies hold that
+// rate from the start.  ctas: the copy kernel's grid (0: 8 per SM, for copies the caller
+// waits for; a few dozen for copies meant to overlap kernels of other streams, which keep
+// the other SMs).  Other host memory: cudaMemcpyAsync.
+void copy_host(DeviceState &st, void *dst, const void *src, size_t bytes, bool to_device, int ctas);
+// Grid of the copy kernel for stream-ordered copies (4 loads in flight per thread cover the
+// link's latency; the rest of the GPU stays with the gates of other streams).
+constexpr int kAsyncCopyCtas = 32;
 
 // Algorithmic bytes of one streaming application of op on an n-qubit state.
 double stream_bytes(const Op &op, int n, int dtype);
