@@ -185,6 +185,29 @@ def test_register_phases_brickwork_sweeps(qs):
     assert st["tile_sweeps"] * 4 <= st["ops_after_fuse"]
 
 
+def test_fusion_cost_counts_one_qubit_forms(qs):
+    """complex128 fusion counts each one-qubit matrix at the FP64 cost of its form: RX, RY
+    (4 per amplitude) and U3 (7) on different qubits stay apart, because a 4x4 block costs
+    16; H then U3 on one qubit merge (8 against 3 + 7).  Parity with the oracle either way."""
+    n = 14
+    r = np.random.default_rng(3)
+    layer = [("rx", (q,), (float(r.uniform(0, 6.28)),)) for q in range(n)]
+    layer += [("ry", (q,), (float(r.uniform(0, 6.28)),)) for q in range(n)]
+    layer += [("u3", (q,), tuple(float(x) for x in r.uniform(0, 6.28, 3))) for q in range(n)]
+    psi0 = inputs.gaussian_state(n, seed=3)
+    want = oracle.run(psi0.copy(), n, layer)
+    got, st = run_gpu(qs, n, 2, psi0, layer, qs.QS_MODE_AUTO, chunk_m=8, fuse_k=2)
+    assert np.max(np.abs(got - want)) <= TOL_C128
+    assert st["ops_after_fuse"] == len(layer)
+    pairs = []
+    for q in range(n):
+        pairs += [("h", (q,), ()), ("u3", (q,), tuple(float(x) for x in r.uniform(0, 6.28, 3)))]
+    want = oracle.run(psi0.copy(), n, pairs)
+    got, st = run_gpu(qs, n, 2, psi0, pairs, qs.QS_MODE_AUTO, chunk_m=8, fuse_k=2)
+    assert np.max(np.abs(got - want)) <= TOL_C128
+    assert st["ops_after_fuse"] == n
+
+
 def _nonlocal_phase_circuit(n, seed):
     """QFT, then a seeded mix of H, U3, CNOT, RZ and controlled phases (CP, CZ and CU3 with
     theta = 0, a phase on the target chosen by the control)."""
