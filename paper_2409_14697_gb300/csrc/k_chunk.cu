@@ -137,11 +137,7 @@ k_chunk(typename C2T<T>::type *__restrict__ psi, const ChunkArgs a, const KOp *_
     __syncthreads();
     uint32_t phase = 0;
     for (uint64_t t = blockIdx.x; t < a.n_tiles; t += gridDim.x) {
-        uint64_t base = t << a.c0;
-        for (int j = 0; j < a.nlh; j++) {
-            const int b = a.lhigh[j];
-            base = ((base >> b) << (b + 1)) | (base & ((1ull << b) - 1ull));
-        }
+        uint64_t base = tile_base(t, a);
         if (threadIdx.x == 0) ptx::mbar_arrive_expect_tx(&bar, tile_bytes);
         __syncthreads();
         for (uint32_t r = threadIdx.x; r < nruns; r += blockDim.x) {
@@ -198,11 +194,7 @@ k_chunk(typename C2T<T>::type *__restrict__ psi, const ChunkArgs a, const KOp *_
         // the write-back addresses are rebuilt rather than kept live through the ops
         // (register pressure of the complex64 register phases)
         asm volatile("" ::: "memory");
-        base = t << a.c0;
-        for (int j = 0; j < a.nlh; j++) {
-            const int b = a.lhigh[j];
-            base = ((base >> b) << (b + 1)) | (base & ((1ull << b) - 1ull));
-        }
+        base = tile_base(t, a);
         for (uint32_t r = threadIdx.x; r < nruns; r += blockDim.x) {
             uint64_t off = 0;
             for (int j = 0; j < a.nlh; j++) off |= (uint64_t)((r >> j) & 1u) << a.lhigh[j];

@@ -90,6 +90,10 @@ PlanParams plan_params(const DeviceState &st, const qs_options &o) {
     PlanParams p;
     const bool c128 = st.dtype == QS_C128;
     p.m = o.chunk_m > 0 ? o.chunk_m : (c128 ? 12 : 13);
+    // complex128 passes are bound by the FP64 pipe of the SMs that hold tiles: a small
+    // state (18 qubits and less) gets about 64 tiles, so that many SMs share its work (the
+    // extra passes are cheap: such a state stays in L2)
+    if (c128 && o.chunk_m <= 0) p.m = std::max(7, std::min(p.m, st.n - 6));
     p.c = c128 ? 4 : 5;                  // runs of 256 bytes
     p.m = std::min(p.m, st.n);
     p.c = std::min(p.c, p.m);

@@ -99,14 +99,22 @@ def test_circuit_families(qs, dtype, family):
 
 @pytest.mark.parametrize("dtype", [2, 1])
 def test_config1_brickwork_12q_auto(qs, dtype):
-    """The 12-qubit workload: one tile holds the whole state, one pass for 350 gates."""
+    """The 12-qubit workload.  complex64: one tile holds the whole state, one pass for 350
+    gates.  complex128 (FP64-bound): tiles of 2^7 amplitudes, so 32 SMs share the work in
+    several passes; the same result either way, and with the one-tile plan."""
     n = 12
     gates = inputs.brickwork(n, 20, seed=1)
     want = oracle.run(oracle.zero_state(n), n, gates)
     psi0 = oracle.zero_state(n).astype(np.complex64 if dtype == 1 else np.complex128)
     got, st = run_gpu(qs, n, dtype, psi0, gates, qs.QS_MODE_AUTO)
     assert np.max(np.abs(got - want)) <= tol(dtype)
-    assert st["passes"] == 1
+    if dtype == 1:
+        assert st["passes"] == 1
+    else:
+        assert 1 < st["passes"] < len(gates) / 4
+        got1, st1 = run_gpu(qs, n, dtype, psi0, gates, qs.QS_MODE_AUTO, chunk_m=12)
+        assert np.max(np.abs(got1 - want)) <= tol(dtype)
+        assert st1["passes"] == 1
 
 
 @pytest.mark.parametrize("dtype", [2, 1])

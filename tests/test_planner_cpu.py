@@ -24,6 +24,8 @@ def qmask(g):
 def check_plan(n, dtype, gates, chunk_m=0):
     pog, lm = qs.qs_plan(n, dtype, gates, qs.options(chunk_m=chunk_m))
     m = chunk_m or (12 if dtype == qs.QS_C128 else 13)
+    if dtype == qs.QS_C128 and not chunk_m:   # small complex128 states: about 64 tiles
+        m = max(7, min(m, n - 6))
     m = min(m, n)
     c = min(4 if dtype == qs.QS_C128 else 5, m)
     assert len(pog) == len(gates)
@@ -48,7 +50,8 @@ def check_plan(n, dtype, gates, chunk_m=0):
 def test_brickwork_plan_valid(n, dtype):
     gates = inputs.brickwork(n, 10, seed=1)
     pog, lm = check_plan(n, dtype, gates)
-    if n <= 12:
+    m = 13 if dtype == qs.QS_C64 else max(7, min(12, n - 6))
+    if n <= m:
         assert len(lm) == 1           # the whole state is one tile: one pass
     else:
         assert len(lm) < len(gates) / 4
