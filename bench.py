@@ -52,7 +52,8 @@ def parse():
                     choices=["gates30", "circuit12", "circuits33", "batched", "served", "reductions", "paper"],
                     help="gates30: the headline benchmark; the others print their own JSON line")
     ap.add_argument("--count", type=int, default=0, help="circuits/requests for batched/served")
-    ap.add_argument("--fuse-k", type=int, default=5)
+    ap.add_argument("--fuse-k", type=int, default=0,
+                    help="circuits33: fusion width (default: register phases k=1, then tensor-core blocks k=5)")
     ap.add_argument("--rate", type=float, default=2000.0)
     ap.add_argument("--no-rphases", action="store_true",
                     help="complex64 passes: one shared-memory sweep per op (no register phases)")
@@ -539,8 +540,9 @@ def wl_circuit12(args):
 
 
 def wl_circuits33(args):
-    """33-qubit complex64 circuits (64 GiB state) with fused blocks of fuse_k qubits on the
-    tensor cores: brickwork 40 layers, QAOA p=4 on a 3-regular graph, TFIM 50 steps.
+    """33-qubit complex64 circuits (64 GiB state): brickwork 40 layers, QAOA p=4 on a
+    3-regular graph, TFIM 50 steps; by default with unfused gates in register phases (the
+    fastest path) and with fused 5-qubit blocks on the tensor cores, or with --fuse-k only.
     Checks at full size: norm, and 1 - |<0|C^-1 C|0>|^2 (circuit then inverse)."""
     import torch
     from paper_2409_14697_gb300 import inputs, qs
@@ -548,35 +550,45 @@ def wl_circuits33(args):
     stream = torch.cuda.Stream()
     h = qs.qs_create(n, qs.QS_C64)
     qs.qs_set_stream(h, stream.cuda_stream)
-    tc = "tensor cores" if args.fuse_k >= 4 else ("SIMT" if args.no_rphases else "SIMT, register phases")
-    out = {"workload": f"{n}-qubit circuits, complex64, fused k={args.fuse_k} ({tc})", "qubits": n,
-           "state_bytes": 8 << n, "circuits": {}}
-    opts = qs.options(fuse_k=args.fuse_k)
-    if args.no_rphases:
-        opts.flags |= qs.QS_OPT_NO_REG_PHASES
     fams = {"brickwork40": inputs.brickwork(n, 40, seed=3), "qaoa_p4": inputs.qaoa_3regular(n, p=4, seed=3),
             "tfim50": inputs.tfim(n, steps=50, dt=0.05)}
-    for name, gates in fams.items():
-        recs = qs.gate_records(gates)
-        inv = qs.gate_records(inputs.inverse(gates))
-        qs.qs_reset(h)
-        qs.qs_apply_circuit(h, recs, opts)      # warm-up (also plans)
-        qs.qs_synchronize(h)
-        qs.qs_reset(h)
-        ms = _event_ms(stream, lambda: qs.qs_apply_circuit(h, recs, opts))
-        st = qs.qs_last_stats(h)
-        nrm = qs.qs_norm(h)
-        qs.qs_apply_circuit(h, inv, opts)
-        a0 = qs.qs_amplitudes(h, 0, 1)[0]
-        nrm2 = qs.qs_norm(h)
-        out["circuits"][name] = {"gates": len(gates), "ms": round(ms, 2), "passes": st["passes"],
-                                 "ops_after_fuse": st["ops_after_fuse"],
-                                 "tile_sweeps": st["tile_sweeps"],
-                                 "gates_per_s": round(len(gates) * 1e3 / ms, 1),
-                                 "pass_GBps": round(st["bytes"] / (ms * 1e-3) / 1e9, 1),
-                                 "norm_minus_1": nrm - 1.0, "inverse_infidelity": 1.0 - abs(complex(a0)) ** 2,
-                                 "inverse_infidelity_normalised": 1.0 - abs(complex(a0)) ** 2 / nrm2}
+    widths = [args.fuse_k] if args.fuse_k > 0 else [1, 5]
+    variants = {}
+    for k in widths:
+        tc = "tensor cores" if k >= 4 else ("SIMT" if args.no_rphases else "SIMT, register phases")
+        opts = qs.options(fuse_k=k)
+        if args.no_rphases:
+            opts.flags |= qs.QS_OPT_NO_REG_PHASES
+        rows = {}
+        for name, gates in fams.items():
+            recs = qs.gate_records(gates)
+            inv = qs.gate_records(inputs.inverse(gates))
+            qs.qs_reset(h)
+            qs.qs_apply_circuit(h, recs, opts)      # warm-up (also plans)
+            qs.qs_synchronize(h)
+            qs.qs_reset(h)
+            ms = _event_ms(stream, lambda: qs.qs_apply_circuit(h, recs, opts))
+            st = qs.qs_last_stats(h)
+            nrm = qs.qs_norm(h)
+            qs.qs_apply_circuit(h, inv, opts)
+            a0 = qs.qs_amplitudes(h, 0, 1)[0]
+            nrm2 = qs.qs_norm(h)
+            rows[name] = {"gates": len(gates), "ms": round(ms, 2), "passes": st["passes"],
+                          "ops_after_fuse": st["ops_after_fuse"],
+                          "tile_sweeps": st["tile_sweeps"],
+                          "gates_per_s": round(len(gates) * 1e3 / ms, 1),
+                          "pass_GBps": round(st["bytes"] / (ms * 1e-3) / 1e9, 1),
+                          "norm_minus_1": nrm - 1.0, "inverse_infidelity": 1.0 - abs(complex(a0)) ** 2,
+                          "inverse_infidelity_normalised": 1.0 - abs(complex(a0)) ** 2 / nrm2}
+        variants[f"k{k}"] = {"path": f"fused k={k} ({tc})", "circuits": rows}
     qs.qs_destroy(h)
+    out = {"workload": f"{n}-qubit circuits, complex64", "qubits": n, "state_bytes": 8 << n}
+    if len(variants) == 1:
+        only = next(iter(variants.values()))
+        out["workload"] += f", {only['path']}"
+        out["circuits"] = only["circuits"]
+    else:
+        out["variants"] = variants
     return out
 
 
