@@ -230,6 +230,87 @@ void defer_hadamard_scale(std::vector<Op> &ops) {
     }
 }
 
+std::vector<Op> split_one_qubit_phases(const std::vector<Op> &ops) {
+    // [[a, b], [c, d]] with real a: R = [[a, -s], [s, a]], s = |c|, e^{i phi} = c / s,
+    // e^{i lambda} = -b / s; taken only where P(phi) R P(lambda) reproduces the matrix
+    struct Parts {
+        cd pl, pf;
+        double a, s;
+        bool diag;
+    };
+    auto split = [](const Op &op, Parts &r) {
+        if (op.kind != K_DENSE1 || op.m[0].imag() != 0.0) return false;
+        const cd a = op.m[0], b = op.m[1], c = op.m[2], d = op.m[3];
+        const double s = std::abs(c);
+        if (s == 0.0) {  // already diagonal
+            if (b != cd(0.0)) return false;
+            r.diag = true;
+            return true;
+        }
+        r.diag = false;
+        r.a = a.real();
+        r.s = s;
+        r.pf = c / s;
+        r.pl = -b / s;
+        const double tol = 1e-14;
+        if (std::abs(r.pl * (-s) - b) > tol || std::abs(r.pf * s - c) > tol ||
+            std::abs(r.pf * r.pl * r.a - d) > tol)
+            return false;
+        return true;
+    };
+    std::vector<Op> out;
+    size_t i = 0;
+    while (i < ops.size()) {
+        // a run of splittable one-qubit ops on distinct qubits
+        size_t j = i;
+        uint64_t seen = 0;
+        std::vector<Parts> parts;
+        while (j < ops.size()) {
+            Parts pr;
+            const uint64_t qm = ops[j].qmask();
+            if ((qm & seen) || !split(ops[j], pr)) break;
+            seen |= qm;
+            parts.push_back(pr);
+            j++;
+        }
+        if (j == i) {
+            out.push_back(ops[i++]);
+            continue;
+        }
+        for (size_t t = i; t < j; t++) {  // P(lambda) of every member, then R, then P(phi)
+            const Parts &pr = parts[t - i];
+            Op p;
+            p.kind = K_DIAG1;
+            p.k = 1;
+            p.q[0] = ops[t].q[0];
+            p.m = pr.diag ? std::vector<cd>{ops[t].m[0], ops[t].m[3]} : std::vector<cd>{cd(1.0), pr.pl};
+            out.push_back(std::move(p));
+        }
+        for (size_t t = i; t < j; t++) {
+            const Parts &pr = parts[t - i];
+            if (pr.diag) continue;
+            Op r;
+            r.kind = K_DENSE1;
+            r.k = 1;
+            r.q[0] = ops[t].q[0];
+            r.m = {cd(pr.a), cd(-pr.s), cd(pr.s), cd(pr.a)};
+            out.push_back(std::move(r));
+        }
+        for (size_t t = i; t < j; t++) {
+            const Parts &pr = parts[t - i];
+            if (pr.diag) continue;
+            Op p;
+            p.kind = K_DIAG1;
+            p.k = 1;
+            p.q[0] = ops[t].q[0];
+            p.m = {cd(1.0), pr.pf};
+            out.push_back(std::move(p));
+        }
+        i = j;
+    }
+    return out;
+}
+
 double op_flops(const Op &op) {
     // FP64 operations per amplitude of the one-qubit forms (general 8, real first entry 7,
     // real 4, RX-like 4)

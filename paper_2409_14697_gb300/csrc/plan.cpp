@@ -287,6 +287,10 @@ void run_planned(DeviceState &st, const std::vector<Op> &ops, const qs_options &
         // FP64 complex128: the pass's Hadamards but its last run unscaled (exact at pass end)
         if (st.dtype == QS_C128 && st.prec == QS_PREC_FP64) defer_hadamard_scale(pops);
         std::vector<Op> fused = fuse_ops(pops, pp.fuse_k, pp.sweep_flops, p.lmask);
+        // throughput-bound passes (256 tiles or more): U3 as a real rotation between phases
+        // that join the diagonal runs; small states are latency-bound, extra ops cost more
+        if (st.dtype == QS_C128 && st.prec == QS_PREC_FP64 && n - __builtin_popcountll(p.lmask) >= 8)
+            fused = split_one_qubit_phases(fused);
         // runs of diagonal gates (e.g. a QFT target's controlled phases) as one diagonal
         // block per up to 8 qubits, where that is cheaper; register phases already hold
         // one- and two-qubit diagonals without a sweep

@@ -196,7 +196,8 @@ def test_register_phases_brickwork_sweeps(qs):
 def test_fusion_cost_counts_one_qubit_forms(qs):
     """complex128 fusion counts each one-qubit matrix at the FP64 cost of its form: RX, RY
     (4 per amplitude) and U3 (7) on different qubits stay apart, because a 4x4 block costs
-    16; H then U3 on one qubit merge (8 against 3 + 7).  Parity with the oracle either way."""
+    16 (U3 then split into a real rotation and phases: at least as many ops as gates); H
+    then U3 on one qubit merge (8 against 3 + 7).  Parity with the oracle either way."""
     n = 14
     r = np.random.default_rng(3)
     layer = [("rx", (q,), (float(r.uniform(0, 6.28)),)) for q in range(n)]
@@ -206,7 +207,7 @@ def test_fusion_cost_counts_one_qubit_forms(qs):
     want = oracle.run(psi0.copy(), n, layer)
     got, st = run_gpu(qs, n, 2, psi0, layer, qs.QS_MODE_AUTO, chunk_m=8, fuse_k=2)
     assert np.max(np.abs(got - want)) <= TOL_C128
-    assert st["ops_after_fuse"] == len(layer)
+    assert st["ops_after_fuse"] >= len(layer)
     pairs = []
     for q in range(n):
         pairs += [("h", (q,), ()), ("u3", (q,), tuple(float(x) for x in r.uniform(0, 6.28, 3)))]
