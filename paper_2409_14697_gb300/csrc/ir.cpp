@@ -231,15 +231,17 @@ void defer_hadamard_scale(std::vector<Op> &ops) {
 }
 
 std::vector<Op> split_one_qubit_phases(const std::vector<Op> &ops) {
-    // [[a, b], [c, d]] with real a: R = [[a, -s], [s, a]], s = |c|, e^{i phi} = c / s,
-    // e^{i lambda} = -b / s; taken only where P(phi) R P(lambda) reproduces the matrix
+    // u = [[a, b], [c, d]] with real a: R = [[a, -s], [s, a]], s = |c|, e^{i phi} = c / s,
+    // e^{i lambda} = -b / s; taken only where P(phi) R P(lambda) reproduces u, and only for
+    // one-qubit matrices of the U3 class (real first entry, complex elsewhere: real and
+    // RX-like matrices already cost 4; a controlled split costs two controlled phases).
     struct Parts {
         cd pl, pf;
         double a, s;
         bool diag;
     };
     auto split = [](const Op &op, Parts &r) {
-        if (op.kind != K_DENSE1 || op.m[0].imag() != 0.0) return false;
+        if (op.kind != K_DENSE1 || d1_class(op.m) != D1_R0) return false;
         const cd a = op.m[0], b = op.m[1], c = op.m[2], d = op.m[3];
         const double s = std::abs(c);
         if (s == 0.0) {  // already diagonal
@@ -258,10 +260,22 @@ std::vector<Op> split_one_qubit_phases(const std::vector<Op> &ops) {
             return false;
         return true;
     };
+    auto part = [](const Op &src, std::vector<cd> u) {
+        Op p;
+        p.kind = src.kind;
+        p.k = src.k;
+        for (int j = 0; j < src.k; j++) p.q[j] = src.q[j];
+        if (src.kind == K_DENSE1 && u[1] == cd(0.0) && u[2] == cd(0.0)) {
+            p.kind = K_DIAG1;
+            u = {u[0], u[3]};
+        }
+        p.m = std::move(u);
+        return p;
+    };
     std::vector<Op> out;
     size_t i = 0;
     while (i < ops.size()) {
-        // a run of splittable one-qubit ops on distinct qubits
+        // a run of splittable ops on disjoint qubit sets
         size_t j = i;
         uint64_t seen = 0;
         std::vector<Parts> parts;
@@ -279,32 +293,15 @@ std::vector<Op> split_one_qubit_phases(const std::vector<Op> &ops) {
         }
         for (size_t t = i; t < j; t++) {  // P(lambda) of every member, then R, then P(phi)
             const Parts &pr = parts[t - i];
-            Op p;
-            p.kind = K_DIAG1;
-            p.k = 1;
-            p.q[0] = ops[t].q[0];
-            p.m = pr.diag ? std::vector<cd>{ops[t].m[0], ops[t].m[3]} : std::vector<cd>{cd(1.0), pr.pl};
-            out.push_back(std::move(p));
+            out.push_back(part(ops[t], pr.diag ? ops[t].m : std::vector<cd>{cd(1.0), cd(0.0), cd(0.0), pr.pl}));
         }
         for (size_t t = i; t < j; t++) {
             const Parts &pr = parts[t - i];
-            if (pr.diag) continue;
-            Op r;
-            r.kind = K_DENSE1;
-            r.k = 1;
-            r.q[0] = ops[t].q[0];
-            r.m = {cd(pr.a), cd(-pr.s), cd(pr.s), cd(pr.a)};
-            out.push_back(std::move(r));
+            if (!pr.diag) out.push_back(part(ops[t], {cd(pr.a), cd(-pr.s), cd(pr.s), cd(pr.a)}));
         }
         for (size_t t = i; t < j; t++) {
             const Parts &pr = parts[t - i];
-            if (pr.diag) continue;
-            Op p;
-            p.kind = K_DIAG1;
-            p.k = 1;
-            p.q[0] = ops[t].q[0];
-            p.m = {cd(1.0), pr.pf};
-            out.push_back(std::move(p));
+            if (!pr.diag) out.push_back(part(ops[t], {cd(1.0), cd(0.0), cd(0.0), pr.pf}));
         }
         i = j;
     }

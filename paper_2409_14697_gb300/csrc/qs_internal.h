@@ -122,13 +122,13 @@ std::vector<Op> fold_global_phases(const std::vector<Op> &ops);
 // the last Hadamard has run.  Between, amplitudes grow by at most 2^(kMaxUnscaledH / 2).
 constexpr int kMaxUnscaledH = 63;
 void defer_hadamard_scale(std::vector<Op> &ops);
-// complex128 FP64 chunk passes of 256 tiles or more: a one-qubit matrix with a real first entry (U3) is
-// P(phi) R P(lambda) with R = [[a, -s], [s, a]] real (4 FP64 instructions per amplitude
-// instead of 7) and P(x) = diag(1, e^{ix}).  For each run of such ops on distinct qubits
-// the P(lambda) of all come first, then the R, then the P(phi) (ops on distinct qubits
-// commute), so the phases join the neighbouring diagonal gates (a CZ layer) in one run that
-// merge_tile_diagonals applies as a few table multiplies.  Ops whose matrix the split does
-// not reproduce to 1e-14 are kept.
+// complex128 FP64 chunk passes of 256 tiles or more: a one-qubit matrix with a real first
+// entry and complex others (U3) is P(phi) R P(lambda) with R = [[a, -s], [s, a]] real (4
+// FP64 instructions per amplitude instead of 7) and P(x) = diag(1, e^{ix}).  For each run
+// of such ops on distinct qubits the P(lambda) of all come first, then the R, then the
+// P(phi) (ops on distinct qubits commute), so the phases join the neighbouring diagonal
+// gates (a CZ layer) in one run that merge_tile_diagonals applies as a few table
+// multiplies.  Ops whose matrix the split does not reproduce to 1e-14 are kept.
 std::vector<Op> split_one_qubit_phases(const std::vector<Op> &ops);
 // Structure class (D1_GENERAL, D1_R0, D1_REAL, D1_RX of kops.cuh) of a 2x2 matrix,
 // row-major: the cheapest form the complex128 kernels apply it with.
