@@ -101,9 +101,11 @@ PlanParams plan_params(const DeviceState &st, const qs_options &o) {
     // phases apply gates unfused (a fused block costs more flops than its members there)
     const bool phases = !c128 && st.reg_phases && rphase_applicable(p.m, kTileThreadBits);
     p.fuse_k = std::min(o.fuse_k > 0 ? o.fuse_k : (phases ? 1 : 2), 4);
-    // FP64 is 1/72 of FP32 on GB300: for complex128 a fused block must not add flops;
-    // complex64 arithmetic is cheap next to a shared-memory sweep of the tile
-    p.sweep_flops = c128 ? 1.0 : 24.0;
+    // FP64 is 1/72 of FP32 on GB300: for complex128 FP64 a fused block must not add flops;
+    // double-float and complex64 arithmetic run on the FP32 pipe and are cheap next to a
+    // shared-memory sweep of the tile (double-float applies every one-qubit matrix in its
+    // general form, so two fused gates cost what they cost apart, plus the saved sweep)
+    p.sweep_flops = !c128 ? 24.0 : (st.prec == QS_PREC_DF32 ? 8.0 : 1.0);
     // complex64 with fusion width 4..6: dense blocks go to the tensor cores (K3)
     p.tc = !c128 && o.fuse_k >= 4 && tc_available(p.m, std::min(o.fuse_k, 6));
     p.force_chunk = o.mode == QS_MODE_CHUNK;
