@@ -267,7 +267,12 @@ def run_ours(args, rank, world, local):
 
     e2e = None
     if not args.no_e2e:
-        e2e = run_e2e(qs, h, host_in, recs, opts, n, B, n_gates, world, dt)
+        qs.qs_destroy(h)    # the e2e states are its own
+        h = None
+        e2e = run_e2e(qs, host_in, recs, opts, n, B, n_gates, world, dt)
+        h = qs.qs_create(n, dt)
+        qs.qs_set_stream(h, stream.cuda_stream)
+        qs.qs_set_amplitudes_from(h, 0, 1 << n, host_in.data_ptr())
     extra = {}
     if not args.no_extra:
         extra["planned"] = time_planned(qs, h, stream, recs, n, B)
@@ -380,16 +385,23 @@ def time_planned(qs, h, stream, recs, n, B):
     return out
 
 
-def run_e2e(qs, h, host_in, recs, opts, n, B, n_gates, world, dt, in_flight=2, steps=8):
+def run_e2e(qs, host_in, recs, opts, n, B, n_gates, world, dt, in_flight=2, steps=8):
     """Same metric through the C ABI with host buffers.  Each step copies the initial state
     from pinned host memory into a state (H2D), applies the 240 gates and copies the final
     state back into pinned host memory (D2H); the host waits for a step's result before
     it reuses that step's buffers.  `in_flight` states on their own streams keep that many
-    steps in flight (as the serving loop does with its slots), so one step's copies
-    overlap the others' gates: step s runs on state s % in_flight with the stream-ordered
-    copy entry points."""
+    steps in flight (as the serving loop does with its slots): step s runs on state
+    s % in_flight with the stream-ordered copy entry points, and its gates wait (CUDA event)
+    for the gates of step s - 1, so one step's copies run under another's gates instead of
+    the states computing in lockstep."""
     import torch
-    states = [h] + [qs.qs_create(n, dt) for _ in range(in_flight - 1)]
+    states, streams = [], []
+    for _ in range(in_flight):
+        st = qs.qs_create(n, dt)
+        sm = torch.cuda.Stream()
+        qs.qs_set_stream(st, sm.cuda_stream)
+        states.append(st)
+        streams.append(sm)
     outs = [torch.empty_like(host_in, pin_memory=True) for _ in range(in_flight)]
     N = 1 << n
     try:
@@ -397,21 +409,26 @@ def run_e2e(qs, h, host_in, recs, opts, n, B, n_gates, world, dt, in_flight=2, s
             qs.qs_synchronize(st)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
+        prev = None
         for s in range(steps):
             k = s % in_flight
-            st = states[k]
+            st, sm = states[k], streams[k]
             if s >= in_flight:
                 qs.qs_synchronize(st)             # step s - in_flight's final state is on the host
                 float(outs[k][0])
             qs.qs_set_amplitudes_async(st, 0, N, host_in.data_ptr())
+            if prev is not None:
+                sm.wait_event(prev)
             for name in GATE_TYPES:
                 qs.qs_apply_circuit(st, recs[name], opts)
+            prev = torch.cuda.Event()
+            prev.record(sm)
             qs.qs_amplitudes_async(st, 0, N, outs[k].data_ptr())
         for st in states:
             qs.qs_synchronize(st)
         wall = (time.perf_counter() - t0) / steps
     finally:
-        for st in states[1:]:
+        for st in states:
             qs.qs_destroy(st)
     rec_bytes = 72 * n_gates
     return {"value": round(world * n_gates / wall, 2), "unit": "gates/s",

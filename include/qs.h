@@ -213,11 +213,10 @@ int qs_amplitudes(qs_state *s, uint64_t off, uint64_t cnt, void *host_dst);
 /* Stream-ordered forms of the two copies above: enqueued on the state's stream after the
  * work queued so far, they return at once.  The caller keeps host_src (unchanged) and
  * host_dst (unread) alive until qs_synchronize(s) returns; a timeout of earlier queued
- * work is reported there.  Page-locked buffers of 4 MiB or more are copied by a copy
- * kernel of 32 CTAs (the rest of the GPU stays with kernels of other streams), smaller or
- * unaligned ones by cudaMemcpyAsync; for pageable memory the call waits as
- * cudaMemcpyAsync does.  With two states on two streams, the copies of one overlap the
- * gates of the other. */
+ * work is reported there.  Both use cudaMemcpyAsync on the copy engines, which need no
+ * SMs, so they run under kernels of other streams: asynchronous for page-locked buffers;
+ * for pageable memory the call waits as cudaMemcpyAsync does.  With two states on two
+ * streams, the copies of one run under the gates of the other. */
 int qs_set_amplitudes_async(qs_state *s, uint64_t off, uint64_t cnt, const void *host_src);
 int qs_amplitudes_async(qs_state *s, uint64_t off, uint64_t cnt, void *host_dst);
 /* Squared norm sum_i |a_i|^2, accumulated in FP64 in a fixed order (deterministic). */

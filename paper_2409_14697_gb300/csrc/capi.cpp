@@ -60,15 +60,15 @@ void ensure_scratch(DeviceState &st, size_t bytes) {
     st.scratch_bytes = cap;
 }
 
-// Parameter arena: two halves used alternately by successive qs_apply_circuit calls.
-// Before a half is reused, the event recorded after its last copy is waited on, so the
+// Parameter arenas: a ring of kArenas used in turn by successive qs_apply_circuit calls.
+// Before an arena is reused, the event recorded after its last copy is waited on, so the
 // pinned staging memory is never rewritten while a copy from it may still be pending.
 void arena_begin(DeviceState &st) {
-    st.arena_cur ^= 1;
+    st.arena_cur = (st.arena_cur + 1) % kArenas;
     st.arena_used = 0;
     const int c = st.arena_cur;
     if (st.arena_ev[c]) QS_CUDA(cudaEventSynchronize(st.arena_ev[c]));
-    // buffers this half outgrew during its last use are idle now
+    // buffers this arena outgrew during its last use are idle now
     for (auto &r : st.arena_retired[c]) {
         if (r.first) cudaFree(r.first);
         if (r.second) cudaFreeHost(r.second);
@@ -88,7 +88,7 @@ void *upload_params(DeviceState &st, const void *host, size_t bytes) {
     if (need > st.arena_cap[c]) {
         // grow: earlier uploads of this call (and queued copies from the pinned staging)
         // still refer to the old buffers, so they are retired, not freed; arena_begin frees
-        // them once this half's event shows that nothing uses them
+        // them once this arena's event shows that nothing uses them
         st.arena_retired[c].push_back({st.arena_dev[c], st.arena_host[c]});
         st.arena_dev[c] = st.arena_host[c] = nullptr;
         const size_t cap = std::max<size_t>(need * 2, 1 << 16);
@@ -182,7 +182,7 @@ void run_circuit(DeviceState &d, const std::vector<Op> &ops, const qs_options &o
 
 void free_device_state(DeviceState &d) {
     if (d.stream) cudaStreamSynchronize(d.stream);
-    for (int c = 0; c < 2; c++) {
+    for (int c = 0; c < kArenas; c++) {
         if (d.arena_dev[c]) cudaFree(d.arena_dev[c]);
         if (d.arena_host[c]) cudaFreeHost(d.arena_host[c]);
         for (auto &r : d.arena_retired[c]) {
@@ -422,7 +422,7 @@ int qs_set_amplitudes_async(qs_state *s, uint64_t off, uint64_t cnt, const void 
     const uint64_t N = 1ull << s->d.n;
     if (off > N || cnt > N - off) fail(QS_ERR_INVALID, "amplitude range out of bounds");
     const size_t B = amp_bytes(s->d.dtype);
-    copy_host(s->d, (char *)s->d.psi + off * B, host_src, cnt * B, true, kAsyncCopyCtas);
+    copy_host(s->d, (char *)s->d.psi + off * B, host_src, cnt * B, true, kCopyEngines);
     QS_API_END
 }
 
@@ -432,7 +432,7 @@ int qs_amplitudes_async(qs_state *s, uint64_t off, uint64_t cnt, void *host_dst)
     const uint64_t N = 1ull << s->d.n;
     if (off > N || cnt > N - off) fail(QS_ERR_INVALID, "amplitude range out of bounds");
     const size_t B = amp_bytes(s->d.dtype);
-    copy_host(s->d, host_dst, (const char *)s->d.psi + off * B, cnt * B, false, kAsyncCopyCtas);
+    copy_host(s->d, host_dst, (const char *)s->d.psi + off * B, cnt * B, false, kCopyEngines);
     QS_API_END
 }
 

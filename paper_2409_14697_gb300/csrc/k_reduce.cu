@@ -689,7 +689,7 @@ void copy_host(DeviceState &st, void *dst, const void *src, size_t bytes, bool t
     if (bytes == 0) return;
     constexpr size_t kMinKernelBytes = 4u << 20;
     const void *host = to_device ? src : dst;
-    const void *mh = bytes >= kMinKernelBytes ? mapped_range(host, bytes) : nullptr;
+    const void *mh = (ctas != kCopyEngines && bytes >= kMinKernelBytes) ? mapped_range(host, bytes) : nullptr;
     const char *s = to_device ? (const char *)mh : (const char *)src;
     char *d = to_device ? (char *)dst : (char *)mh;
     const uintptr_t align = (uintptr_t)s | (uintptr_t)d | (uintptr_t)bytes;

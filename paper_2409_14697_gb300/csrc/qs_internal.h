@@ -150,6 +150,11 @@ struct StreamGeom {
     uint64_t n_groups;  // 2^(n_elem_bits - nf)
 };
 
+// Parameter arenas per state, used in turn by successive qs_apply_circuit calls: a call
+// waits (on the host) only for the call kArenas - 1 before it, so a caller can queue that
+// many calls on a state whose stream waits for other work without stalling.
+constexpr int kArenas = 16;
+
 struct DeviceState {
     void *psi = nullptr;  // amplitudes
     int n = 0;            // qubits
@@ -161,14 +166,14 @@ struct DeviceState {
     void *scratch = nullptr;
     size_t scratch_bytes = 0;
     int num_sms = 0;
-    // parameter arenas (double-buffered per qs_apply_circuit call)
-    void *arena_dev[2] = {nullptr, nullptr};
-    void *arena_host[2] = {nullptr, nullptr};
-    size_t arena_cap[2] = {0, 0};
+    // parameter arenas (a ring, one per qs_apply_circuit call)
+    void *arena_dev[kArenas] = {};
+    void *arena_host[kArenas] = {};
+    size_t arena_cap[kArenas] = {};
     size_t arena_used = 0;
     int arena_cur = 0;
-    cudaEvent_t arena_ev[2] = {nullptr, nullptr};
-    std::vector<std::pair<void *, void *>> arena_retired[2];  // outgrown (device, pinned) buffers
+    cudaEvent_t arena_ev[kArenas] = {};
+    std::vector<std::pair<void *, void *>> arena_retired[kArenas];  // outgrown (device, pinned) buffers
     // device error word written by bounded waits (QS_ERR_TIMEOUT), checked on sync
     int *dev_err = nullptr;
     // two FP64 squared norms (before / after) for the norm-preserving correction
@@ -208,12 +213,12 @@ size_t scratch_topk_bytes(int n, uint32_t k);
 // transfers were measured to run at 20-46 GB/s for their first gigabytes now and then
 // before reaching the link rate (211 GB/s in, 194 GB/s out), while SM copies hold that
 // rate from the start.  ctas: the copy kernel's grid (0: 8 per SM, for copies the caller
-// waits for; a few dozen for copies meant to overlap kernels of other streams, which keep
-// the other SMs).  Other host memory: cudaMemcpyAsync.
+// waits for), or kCopyEngines: cudaMemcpyAsync on the copy engines, for copies meant to run
+// under kernels of other streams (a copy kernel there waits for SM slots that persistent
+// kernels hold, and a slow start of a copy-engine transfer is hidden).  Other host memory:
+// cudaMemcpyAsync.
 void copy_host(DeviceState &st, void *dst, const void *src, size_t bytes, bool to_device, int ctas);
-// Grid of the copy kernel for stream-ordered copies (4 loads in flight per thread cover the
-// link's latency; the rest of the GPU stays with the gates of other streams).
-constexpr int kAsyncCopyCtas = 32;
+constexpr int kCopyEngines = -1;
 
 // Algorithmic bytes of one streaming application of op on an n-qubit state.
 double stream_bytes(const Op &op, int n, int dtype);
