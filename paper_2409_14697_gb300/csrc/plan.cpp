@@ -286,8 +286,8 @@ void run_planned(DeviceState &st, const std::vector<Op> &ops, const qs_options &
         std::vector<Op> pops;
         pops.reserve(p.ops.size());
         for (int i : p.ops) pops.push_back(ops_r[i]);
-        // FP64 complex128: the pass's Hadamards but its last run unscaled (exact at pass end)
-        if (st.dtype == QS_C128 && st.prec == QS_PREC_FP64) defer_hadamard_scale(pops);
+        // complex128: the pass's Hadamards but its last run unscaled (exact at pass end)
+        if (st.dtype == QS_C128) defer_hadamard_scale(pops);
         std::vector<Op> fused = fuse_ops(pops, pp.fuse_k, pp.sweep_flops, p.lmask);
         // throughput-bound passes (256 tiles or more): U3 as a real rotation between phases
         // that join the diagonal runs; small states are latency-bound, extra ops cost more

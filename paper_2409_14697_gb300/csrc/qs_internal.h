@@ -115,7 +115,8 @@ bool op_is_diagonal(const Op &op);
 // last one, applied in full.  The product of the ops is unchanged (FP64 host arithmetic),
 // so the state is exact again when the last op has run.
 std::vector<Op> fold_global_phases(const std::vector<Op> &ops);
-// Gate-by-gate complex128 FP64 form of the Hadamards of a circuit: all but the last (and
+// complex128 form of the Hadamards of a circuit (gate-by-gate FP64 calls, and the ops of a
+// chunk pass): all but the last (and
 // every (kMaxUnscaledH + 1)-th) become the unscaled butterfly (a + b, a - b), 2 FP64
 // additions per amplitude instead of 3 FP64 instructions; the collected factor 2^(-k/2) is
 // carried by the next scaled one (K_H with m = {scale}), so the state is exact again when

@@ -620,84 +620,6 @@ __device__ __forceinline__ void apply_op_smem(typename C2T<T>::type *tile, const
 // ---- complex128 ops with double-float arithmetic (matrix reals as (hi, lo) pairs) --------
 __device__ __forceinline__ df::F2 dfneg(df::F2 a) { return df::F2{-a.h, -a.l}; }
 
-struct SDfH {
-    df::F2 r;
-    __device__ void operator()(Amp<double, 1> *v) const {
-        const df::F2 ar = df::split(v[0].r[0]), ai = df::split(v[0].i[0]);
-        const df::F2 br = df::split(v[1].r[0]), bi = df::split(v[1].i[0]);
-        v[0].r[0] = df::result(df::scale(df::add(ar, br), r));
-        v[0].i[0] = df::result(df::scale(df::add(ai, bi), r));
-        v[1].r[0] = df::result(df::scale(df::sub(ar, br), r));
-        v[1].i[0] = df::result(df::scale(df::sub(ai, bi), r));
-    }
-};
-// y_r = sum_c m[r][c] x_c over NT touched elements, matrix as pairs (row-major, re/im)
-template <int NT> struct SDfDense {
-    const df::F2 *m;
-    __device__ void operator()(Amp<double, 1> *v) const {
-        df::F2 xr[NT], xi[NT];
-#pragma unroll
-        for (int t = 0; t < NT; t++) {
-            xr[t] = df::split(v[t].r[0]);
-            xi[t] = df::split(v[t].i[0]);
-        }
-#pragma unroll
-        for (int r = 0; r < NT; r++) {
-            const df::F2 *row = m + 2 * NT * r;
-            df::Acc a = df::mul(row[0], xr[0]);
-            df::Acc b = df::mul(row[0], xi[0]);
-            df::mac(a, dfneg(row[1]), xi[0]);
-            df::mac(b, row[1], xr[0]);
-#pragma unroll
-            for (int c = 1; c < NT; c++) {
-                df::mac(a, row[2 * c], xr[c]);
-                df::mac(a, dfneg(row[2 * c + 1]), xi[c]);
-                df::mac(b, row[2 * c], xi[c]);
-                df::mac(b, row[2 * c + 1], xr[c]);
-            }
-            v[r].r[0] = df::result(a);
-            v[r].i[0] = df::result(b);
-        }
-    }
-};
-template <int NT> struct SDfDiag {
-    const df::F2 *d;
-    __device__ void operator()(Amp<double, 1> *v) const {
-#pragma unroll
-        for (int t = 0; t < NT; t++) {
-            const df::F2 xr = df::split(v[t].r[0]), xi = df::split(v[t].i[0]);
-            df::Acc a = df::mul(d[2 * t], xr);
-            df::mac(a, dfneg(d[2 * t + 1]), xi);
-            df::Acc b = df::mul(d[2 * t], xi);
-            df::mac(b, d[2 * t + 1], xr);
-            v[t].r[0] = df::result(a);
-            v[t].i[0] = df::result(b);
-        }
-    }
-};
-
-// Applies one op with double-float arithmetic; sm holds the op's reals as (hi, lo) pairs.
-// Wider diagonal and dense blocks rebuild FP64 entries (hi + lo) and use FP64 arithmetic.
-__device__ __forceinline__ void apply_op_smem_df(double2 *tile, const KOp &op, const df::F2 *sm, double *sd,
-                                                 int m) {
-    switch (op.fkind) {
-    case F_H: groups_apply<double, 2>(tile, op, m, SDfH{df::F2{0.70710677f, 1.21016175e-08f}}); break;
-    case F_SWAP: groups_apply<double, 2>(tile, op, m, SSwap<double>{}); break;
-    case F_NEG: groups_apply<double, 1>(tile, op, m, SNeg<double>{}); break;
-    case F_DENSE1: groups_apply<double, 2>(tile, op, m, SDfDense<2>{sm}); break;
-    case F_DIAG1: groups_apply<double, 2>(tile, op, m, SDfDiag<2>{sm}); break;
-    case F_PHASE: groups_apply<double, 1>(tile, op, m, SDfDiag<1>{sm}); break;
-    case F_DIAG2: groups_apply<double, 4>(tile, op, m, SDfDiag<4>{sm}); break;
-    case F_DENSE2: groups_apply<double, 4>(tile, op, m, SDfDense<4>{sm}); break;
-    default: {
-        for (int j = threadIdx.x; j < op.nmat; j += blockDim.x) sd[j] = (double)sm[j].h + (double)sm[j].l;
-        __syncthreads();
-        apply_op_smem<double>(tile, op, sd, m);
-        break;
-    }
-    }
-}
-
 // ---- complex128 double-float tiles ------------------------------------------------------
 // For a whole pass the tile holds every amplitude as four floats (re hi, re lo, im hi,
 // im lo) in its own 16-byte slot: split once after the load and joined once before the
@@ -767,6 +689,16 @@ struct DtH {
         v[1].i = df_norm(df::scale(df::sub(a.i, b.i), r));
     }
 };
+// Unscaled Hadamard butterfly (a + b, a - b) on double-float amplitudes.
+struct DtHSum {
+    __device__ void operator()(DfAmp *v) const {
+        const DfAmp a = v[0], b = v[1];
+        v[0].r = df_norm(df::add(a.r, b.r));
+        v[0].i = df_norm(df::add(a.i, b.i));
+        v[1].r = df_norm(df::sub(a.r, b.r));
+        v[1].i = df_norm(df::sub(a.i, b.i));
+    }
+};
 struct DtSwap {
     __device__ void operator()(DfAmp *v) const {
         const DfAmp t = v[0];
@@ -821,7 +753,10 @@ __device__ __forceinline__ void apply_op_dftile(double2 *tile_raw, const KOp &op
                                                 int m) {
     float4 *tile = reinterpret_cast<float4 *>(tile_raw);
     switch (op.fkind) {
-    case F_H: df_groups_apply<2>(tile, op, m, DtH{df::F2{0.70710677f, 1.21016175e-08f}}); break;
+    case F_H:  // scale in the reals when a pass defers it (1: the unscaled butterfly)
+        if (op.nmat >= 1 && sm[0].h == 1.0f && sm[0].l == 0.0f) df_groups_apply<2>(tile, op, m, DtHSum{});
+        else df_groups_apply<2>(tile, op, m, DtH{op.nmat >= 1 ? sm[0] : df::F2{0.70710677f, 1.21016175e-08f}});
+        break;
     case F_SWAP: df_groups_apply<2>(tile, op, m, DtSwap{}); break;
     case F_NEG: df_groups_apply<1>(tile, op, m, DtNeg{}); break;
     case F_DENSE1: df_groups_apply<2>(tile, op, m, DtDense<2>{sm}); break;
