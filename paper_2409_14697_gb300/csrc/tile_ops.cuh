@@ -795,19 +795,4 @@ __device__ __forceinline__ void apply_op_dftile(double2 *tile_raw, const KOp &op
     }
 }
 
-// Stages op i and its matrix entries into shared memory, then applies it; every thread
-// of the block must call this (it synchronises).
-template <typename T>
-__device__ __forceinline__ void apply_ops_tile(typename C2T<T>::type *tile, const KOp *ops, int n_ops,
-                                               const T *mats, int m, KOp &s_op, T *s_m) {
-    for (int i = 0; i < n_ops; i++) {
-        if (threadIdx.x == 0) s_op = ops[i];
-        __syncthreads();
-        for (int j = threadIdx.x; j < s_op.nmat; j += blockDim.x) s_m[j] = mats[s_op.mat + j];
-        __syncthreads();
-        apply_op_smem<T>(tile, s_op, s_m, m);
-        __syncthreads();
-    }
-}
-
 }  // namespace qs
