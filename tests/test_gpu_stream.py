@@ -220,6 +220,27 @@ def test_async_copies_two_states(qs):
 
 
 @pytest.mark.parametrize("dtype", [2, 1])
+def test_async_copies_pageable_and_small(qs, dtype):
+    """Stream-ordered copies from and to pageable numpy memory, and below the 4 MiB kernel
+    threshold: the same bytes as the synchronous copies."""
+    n = 12
+    npdt = np.complex128 if dtype == 2 else np.complex64
+    psi = inputs.gaussian_state(n, seed=93).astype(npdt)
+    out = np.zeros_like(psi)
+    h = qs.qs_create(n, dtype)
+    try:
+        qs.qs_set_amplitudes_async(h, 0, 1 << n, psi.ctypes.data)
+        qs.qs_synchronize(h)
+        assert np.array_equal(qs.qs_amplitudes(h), psi)
+        qs.qs_amplitudes_async(h, 5, 100, out.ctypes.data + 5 * psi.itemsize)
+        qs.qs_synchronize(h)
+        assert np.array_equal(out[5:105], psi[5:105])
+        assert not out[:5].any() and not out[105:].any()
+    finally:
+        qs.qs_destroy(h)
+
+
+@pytest.mark.parametrize("dtype", [2, 1])
 def test_brickwork_12q(qs, dtype):
     """20 layers of U3 on every qubit + CZ brickwork from |0...0>, all 4096 amplitudes."""
     n = 12
