@@ -244,7 +244,8 @@ def _nonlocal_phase_circuit(n, seed):
 
 @pytest.mark.parametrize("prec", [1, 2])
 @pytest.mark.parametrize("n,m", [(14, 6), (18, 8), (20, 12)])
-def test_nonlocal_controlled_phases(qs, n, m, prec):
+@pytest.mark.parametrize("mode", ["auto", "chunk"])
+def test_nonlocal_controlled_phases(qs, n, m, prec, mode):
     """complex128 passes take controlled phases whose other qubit is outside the local set
     (a per-tile factor folded into the block's table).  The plan must use that (some
     controlled phase in a pass with one of its qubits non-local), and the state must equal
@@ -260,9 +261,11 @@ def test_nonlocal_controlled_phases(qs, n, m, prec):
     assert hi > 0
     psi0 = inputs.gaussian_state(n, seed=n + 1)
     want = oracle.run(psi0.copy(), n, gates)
-    got, st = run_gpu(qs, n, 2, psi0, gates, qs.QS_MODE_AUTO, chunk_m=m, precision=prec)
+    md = qs.QS_MODE_AUTO if mode == "auto" else qs.QS_MODE_CHUNK   # chunk: single-op passes too
+    got, st = run_gpu(qs, n, 2, psi0, gates, md, chunk_m=m, precision=prec)
     assert np.max(np.abs(got - want)) <= TOL_C128
-    assert st["passes"] == len(lm)
+    if mode == "auto":
+        assert st["passes"] == len(lm)
 
 
 @pytest.mark.parametrize("dtype,flags", [(2, 0), (1, 1)])
