@@ -385,7 +385,7 @@ def time_planned(qs, h, stream, recs, n, B):
     return out
 
 
-def run_e2e(qs, host_in, recs, opts, n, B, n_gates, world, dt, in_flight=2, steps=8):
+def run_e2e(qs, host_in, recs, opts, n, B, n_gates, world, dt, in_flight=3, steps=9):
     """Same metric through the C ABI with host buffers.  Each step copies the initial state
     from pinned host memory into a state (H2D), applies the 240 gates and copies the final
     state back into pinned host memory (D2H); the host waits for a step's result before
