@@ -54,7 +54,9 @@ template <> struct TabReal<true> {
 // Per-tile table of an F_CDIAGK block with non-local terms (op.nt > 0): the table with,
 // for every term whose global qubit is 1 in this tile, its factor on the entries it covers.
 // Warp w + 1 multiplies up the terms of table bit w (warp 0: the terms on every entry), in
-// a fixed butterfly; then each entry takes the factors of its set bits.  FP64 throughout.
+// a fixed butterfly; then each entry takes the factors of its set bits.  Factors without
+// terms (op.off[0]) are skipped: a QFT target's terms all sit on its control, so one warp
+// works.  FP64 throughout.
 // src: the op's reals; dst: scratch for the 2 * 2^k table reals (may equal src).
 template <bool DF, typename T>
 __device__ void fold_hi_terms(const KOp &op, const T *src, T *dst, uint64_t base) {
@@ -62,7 +64,13 @@ __device__ void fold_hi_terms(const KOp &op, const T *src, T *dst, uint64_t base
     using R = TabReal<DF>;
     const int kt = op.k, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint32_t ne = 1u << kt;
-    if (warp <= kt && warp < 8) {
+    const uint64_t with_terms = op.off[0];  // bit w: factor w has terms
+    if (warp <= kt && warp < 8 && !((with_terms >> warp) & 1ull)) {
+        if (lane == 0) {
+            s_f[2 * warp] = 1.0;
+            s_f[2 * warp + 1] = 0.0;
+        }
+    } else if (warp <= kt && warp < 8) {
         const int tb = warp - 1;
         double fr = 1.0, fi = 0.0;
         for (int i = lane; i < op.nt; i += 32) {
@@ -89,7 +97,7 @@ __device__ void fold_hi_terms(const KOp &op, const T *src, T *dst, uint64_t base
     for (uint32_t s = threadIdx.x; s < ne; s += blockDim.x) {
         double vr = R::get(src, 2 * s), vi = R::get(src, 2 * s + 1);
         for (int w = 0; w <= kt; w++) {
-            if (w > 0 && !((s >> (w - 1)) & 1u)) continue;
+            if (!((with_terms >> w) & 1ull) || (w > 0 && !((s >> (w - 1)) & 1u))) continue;
             const double gr = s_f[2 * w], gi = s_f[2 * w + 1];
             const double r = vr * gr - vi * gi;
             vi = vr * gi + vi * gr;

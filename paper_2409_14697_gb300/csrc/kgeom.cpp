@@ -195,6 +195,7 @@ KOp make_hi_block_kop(const Op &op, const int *pos, std::vector<double> &mats) {
         int tb = -1;
         for (int i = 0; i < k.k; i++)
             if (op.q[tab[i]] == t.t) tb = k.k - 1 - i;
+        k.off[0] |= 1ull << (tb + 1);  // which factors the kernel has to build
         mats.push_back((double)tb);
         mats.push_back((double)t.h);
         mats.push_back(t.f.real());

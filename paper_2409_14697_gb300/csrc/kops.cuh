@@ -32,7 +32,8 @@ enum FKind : int32_t {
                  // nf control positions pos[k..k+nf-1] (ascending, set_mask) are all set; nt
                  // terms after the table, (table bit or -1, global qubit h, re, im): where
                  // bit h of the tile is 1, entries with that table bit set (all for -1) take
-                 // the factor (the kernel folds them into a per-tile copy of the table)
+                 // the factor (the kernel folds them into a per-tile copy of the table);
+                 // off[0] bit tb + 1 marks the table bits that have terms
 };
 
 // Structure of an F_DENSE1 matrix (FP64 operations per amplitude for complex128 work):
