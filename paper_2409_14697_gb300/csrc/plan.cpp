@@ -246,6 +246,34 @@ std::vector<Pass> choose_plan(const std::vector<Op> &ops, int n, const PlanParam
     return alt;
 }
 
+namespace {
+
+// The ops one chunk pass applies, in order: the pass's gates, then
+//  1. complex128: its Hadamards but the last run unscaled (exact at the pass's end);
+//  2. fusion into dense blocks where that does not add arithmetic (gates with a qubit
+//     outside the tile stay apart);
+//  3. complex128 FP64 passes of 256 tiles or more: U3 as a real rotation between phases
+//     that join the diagonal runs (smaller states are latency-bound: extra ops cost more);
+//  4. runs of diagonal gates (a QFT target's controlled phases, the phases of step 3) as
+//     diagonal blocks of up to 8 tile qubits, with factors for qubits outside the tile
+//     (complex64 register phases hold one- and two-qubit diagonals without a sweep).
+std::vector<Op> pass_program(const DeviceState &st, const PlanParams &pp, const Pass &p, const std::vector<Op> &ops) {
+    const int local = __builtin_popcountll(p.lmask);
+    std::vector<Op> pops;
+    pops.reserve(p.ops.size());
+    for (int i : p.ops) pops.push_back(ops[i]);
+    if (st.dtype == QS_C128) defer_hadamard_scale(pops);
+    std::vector<Op> fused = fuse_ops(pops, pp.fuse_k, pp.sweep_flops, p.lmask);
+    if (st.dtype == QS_C128 && st.prec == QS_PREC_FP64 && st.n - local >= 8) fused = split_one_qubit_phases(fused);
+    const bool phases = st.dtype == QS_C64 && st.reg_phases && !pp.tc && rphase_applicable(local, kTileThreadBits);
+    if (!phases)
+        fused = merge_tile_diagonals(fused, kTileDiagQubits, st.dtype == QS_C128 ? 0.5 : 4.0,
+                                     pp.hi_diag ? p.lmask : 0);
+    return fused;
+}
+
+}  // namespace
+
 void run_planned(DeviceState &st, const std::vector<Op> &ops, const qs_options &o, qs_stats &stats) {
     const int n = st.n;
     const PlanParams pp = plan_params(st, o);
@@ -283,24 +311,7 @@ void run_planned(DeviceState &st, const std::vector<Op> &ops, const qs_options &
             stats.passes++;
             continue;
         }
-        std::vector<Op> pops;
-        pops.reserve(p.ops.size());
-        for (int i : p.ops) pops.push_back(ops_r[i]);
-        // complex128: the pass's Hadamards but its last run unscaled (exact at pass end)
-        if (st.dtype == QS_C128) defer_hadamard_scale(pops);
-        std::vector<Op> fused = fuse_ops(pops, pp.fuse_k, pp.sweep_flops, p.lmask);
-        // throughput-bound passes (256 tiles or more): U3 as a real rotation between phases
-        // that join the diagonal runs; small states are latency-bound, extra ops cost more
-        if (st.dtype == QS_C128 && st.prec == QS_PREC_FP64 && n - __builtin_popcountll(p.lmask) >= 8)
-            fused = split_one_qubit_phases(fused);
-        // runs of diagonal gates (e.g. a QFT target's controlled phases) as one diagonal
-        // block per up to 8 qubits, where that is cheaper; register phases already hold
-        // one- and two-qubit diagonals without a sweep
-        const bool phases = st.dtype == QS_C64 && st.reg_phases && !pp.tc &&
-                            rphase_applicable(__builtin_popcountll(p.lmask), kTileThreadBits);
-        if (!phases)
-            fused = merge_tile_diagonals(fused, kTileDiagQubits, st.dtype == QS_C128 ? 0.5 : 4.0,
-                                         pp.hi_diag ? p.lmask : 0);
+        const std::vector<Op> fused = pass_program(st, pp, p, ops_r);
         stats.tile_sweeps += launch_pass_ops(st, p.lmask, fused, pp.tc);
         stats.passes++;
         stats.bytes += 2.0 * B * (double)(1ull << n);
