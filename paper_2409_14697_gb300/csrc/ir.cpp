@@ -390,20 +390,26 @@ std::vector<Op> merge_tile_diagonals(const std::vector<Op> &ops, int max_k, doub
     bool forced = false;                 // a member has a non-local qubit: emit the block
     double member_cost = 0.0;
     auto is_local = [&](int q) { return lmask == 0 || ((lmask >> q) & 1ull) != 0; };
-    auto flush = [&]() {
-        if (members.empty()) return;
-        // controls: qubits on whose 0-half every entry is 1 and to which every HiTerm is
-        // tied; the block then costs a complex multiply on the elements with all controls set
-        const int K = (int)Q.size();
+    // controls: qubits on whose 0-half every entry is 1 and to which every HiTerm is tied;
+    // a block costs a complex multiply on the elements with all controls set, and its
+    // table covers the other qubits only
+    auto controls = [](const std::vector<int> &q, const std::vector<cd> &d, const std::vector<HiTerm> &tt) {
+        const int K = (int)q.size();
         int nctl = 0;
         for (int j = 0; j < K; j++) {
             const int bit = K - 1 - j;
             bool ctl = true;
-            for (size_t x = 0; x < D.size() && ctl; x++)
-                if (!((x >> bit) & 1) && D[x] != cd(1.0)) ctl = false;
-            for (const HiTerm &t : terms) ctl = ctl && t.t == Q[j];
+            for (size_t x = 0; x < d.size() && ctl; x++)
+                if (!((x >> bit) & 1) && d[x] != cd(1.0)) ctl = false;
+            for (const HiTerm &t : tt) ctl = ctl && t.t == q[j];
             nctl += ctl;
         }
+        return nctl;
+    };
+    auto flush = [&]() {
+        if (members.empty()) return;
+        const int K = (int)Q.size();
+        const int nctl = controls(Q, D, terms);
         bool identity = terms.empty();
         for (const cd &z : D) identity = identity && z == cd(1.0);
         const double merged = identity ? 0.0 : 4.0 / (double)(1u << nctl) + sweep_cost;
@@ -459,33 +465,51 @@ std::vector<Op> merge_tile_diagonals(const std::vector<Op> &ops, int max_k, doub
             const cd r = g1 / g0;
             if (r != cd(1.0)) nt.push_back({qa, qh, r});
         }
-        std::vector<int> nQ = Q;
-        for (int q : lq)
-            if (std::find(nQ.begin(), nQ.end(), q) == nQ.end()) nQ.push_back(q);
-        const bool with_terms = !terms.empty() || !nt.empty();
-        if ((int)nQ.size() > (with_terms ? max_k - 1 : max_k) || terms.size() + nt.size() > (size_t)kMaxHiTerms) {
+        // the block with this op: qubits high-to-low, entries, terms
+        auto extend = [&](std::vector<int> &nQ, std::vector<cd> &nD, std::vector<HiTerm> &nterms) {
+            const bool fresh = members.empty();
+            nQ = fresh ? lq : Q;
+            if (!fresh)
+                for (int q : lq)
+                    if (std::find(nQ.begin(), nQ.end(), q) == nQ.end()) nQ.push_back(q);
+            std::sort(nQ.begin(), nQ.end(), [](int a, int b) { return a > b; });
+            const int K = (int)nQ.size();
+            const int kl = (int)lq.size();
+            nD.assign((size_t)1 << K, 1.0);
+            for (size_t x = 0; x < nD.size(); x++) {
+                auto bit_of = [&](int q) {
+                    for (int t = 0; t < K; t++)
+                        if (nQ[t] == q) return (int)((x >> (K - 1 - t)) & 1);
+                    return 0;
+                };
+                size_t xo = 0;  // index into the old block
+                for (size_t t = 0; t < Q.size(); t++) xo |= (size_t)bit_of(Q[t]) << (Q.size() - 1 - t);
+                size_t xm = 0;  // index into the op's local diagonal
+                for (int j = 0; j < kl; j++) xm |= (size_t)bit_of(lq[j]) << (kl - 1 - j);
+                nD[x] = (fresh ? cd(1.0) : D[xo]) * dl[xm];
+            }
+            nterms = fresh ? nt : terms;
+            if (!fresh) nterms.insert(nterms.end(), nt.begin(), nt.end());
+        };
+        // limits: at most max_k qubits; a table of at most 2^max_k entries, 2^(max_k - 1)
+        // with terms (so that table and terms fit one op's reals, and every table bit
+        // with terms has a factor slot)
+        auto fits = [&](const std::vector<int> &q, const std::vector<cd> &d, const std::vector<HiTerm> &tt) {
+            const int table_bits = (int)q.size() - controls(q, d, tt);
+            return (int)q.size() <= max_k && table_bits <= (tt.empty() ? max_k : max_k - 1) &&
+                   tt.size() <= (size_t)kMaxHiTerms;
+        };
+        std::vector<int> nQ;
+        std::vector<cd> nD;
+        std::vector<HiTerm> nterms;
+        extend(nQ, nD, nterms);
+        if (!members.empty() && !fits(nQ, nD, nterms)) {
             flush();
-            nQ = lq;
+            extend(nQ, nD, nterms);
         }
-        std::sort(nQ.begin(), nQ.end(), [](int a, int b) { return a > b; });
-        const int K = (int)nQ.size();
-        const int kl = (int)lq.size();
-        std::vector<cd> nD((size_t)1 << K, 1.0);
-        for (size_t x = 0; x < nD.size(); x++) {
-            auto bit_of = [&](int q) {
-                for (int t = 0; t < K; t++)
-                    if (nQ[t] == q) return (int)((x >> (K - 1 - t)) & 1);
-                return 0;
-            };
-            size_t xo = 0;  // index into the old block
-            for (size_t t = 0; t < Q.size(); t++) xo |= (size_t)bit_of(Q[t]) << (Q.size() - 1 - t);
-            size_t xm = 0;  // index into the op's local diagonal
-            for (int j = 0; j < kl; j++) xm |= (size_t)bit_of(lq[j]) << (kl - 1 - j);
-            nD[x] = (members.empty() ? cd(1.0) : D[xo]) * dl[xm];
-        }
-        Q = nQ;
+        Q = std::move(nQ);
         D = std::move(nD);
-        terms.insert(terms.end(), nt.begin(), nt.end());
+        terms = std::move(nterms);
         members.push_back(&op);
         forced = forced || jh >= 0;
         member_cost += diag_cost(d) + sweep_cost;

@@ -100,7 +100,8 @@ std::vector<Op> fuse_ops(const std::vector<Op> &ops, int fuse_k, double sweep_fl
 // lmask are taken too: d(x_a, x_h) = d(x_a, 0) * [x_h ? d(x_a, 1) / d(x_a, 0) : 1], so the
 // block's table gets the x_h = 0 slice on its local qubit a and the rest becomes HiTerms
 // (g0 = d(0,1)/d(0,0) on every entry, g1/g0 with g1 = d(1,1)/d(1,0) on the entries with a
-// set).  A block with HiTerms has at most max_k - 1 local qubits and 64 terms.
+// set).  A block's table covers its non-control qubits: at most 2^max_k entries, and
+// 2^(max_k - 1) with HiTerms (at most 64), so that table and terms fit one op's reals.
 std::vector<Op> merge_tile_diagonals(const std::vector<Op> &ops, int max_k, double sweep_cost,
                                      uint64_t lmask = 0);
 // Qubits of a two-qubit diagonal (no zero entry) that may be its only local qubit in a
