@@ -1,0 +1,48 @@
+"""CPU test of the host rewrites the executor applies before its kernels run (global-phase
+fold, deferred Hadamard scale, gate fusion, U3 split, diagonal merge with non-local
+controlled phases, and their chunk-pass order): builds ``host_transforms_check.cpp``
+against the package's host sources with g++ and runs it on seeded random circuits.  Each
+rewrite must leave a 10-qubit state unchanged to 1e-12 and keep the limits the kernels
+rely on.  No GPU: the CUDA headers are needed only for declarations."""
+import os
+import shutil
+import subprocess
+from pathlib import Path
+
+import pytest
+
+ROOT = Path(__file__).resolve().parents[1]
+CSRC = ROOT / "paper_2409_14697_gb300" / "csrc"
+
+
+def _cuda_include():
+    for base in (os.environ.get("CUDA_HOME"), os.environ.get("CUDA_PATH"), "/usr/local/cuda"):
+        if base and (Path(base) / "include" / "cuda_runtime.h").exists():
+            return str(Path(base) / "include")
+    nvcc = shutil.which("nvcc")
+    if nvcc:
+        inc = Path(nvcc).resolve().parents[1] / "include"
+        if (inc / "cuda_runtime.h").exists():
+            return str(inc)
+    return None
+
+
+@pytest.fixture(scope="module")
+def checker(tmp_path_factory):
+    gxx = shutil.which("g++")
+    inc = _cuda_include()
+    if gxx is None or inc is None:
+        pytest.skip("g++ or the CUDA headers are not available")
+    exe = tmp_path_factory.mktemp("host_transforms") / "host_transforms_check"
+    cmd = [gxx, "-O1", "-std=c++17", f"-I{CSRC}", f"-I{ROOT / 'include'}", f"-I{inc}",
+           str(ROOT / "tests" / "host_transforms_check.cpp"), str(CSRC / "ir.cpp"),
+           str(CSRC / "kgeom.cpp"), "-o", str(exe)]
+    r = subprocess.run(cmd, capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0, r.stderr[-4000:]
+    return exe
+
+
+@pytest.mark.parametrize("seed", [1, 2, 3])
+def test_host_rewrites_keep_the_circuit(checker, seed):
+    r = subprocess.run([str(checker), str(seed), "24"], capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0 and "OK" in r.stdout, r.stdout[-4000:]
