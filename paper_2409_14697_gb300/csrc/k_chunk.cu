@@ -51,7 +51,7 @@ template <> struct TabReal<true> {
     }
 };
 
-// Per-tile table of an F_CDIAGK block with non-local terms (op.nt > 0): the table with,
+// Per-tile table of an F_CDIAGK / F_HCDIAGK block with non-local terms (op.nt > 0): the table with,
 // for every term whose global qubit is 1 in this tile, its factor on the entries it covers.
 // Warp w + 1 multiplies up the terms of table bit w (warp 0: the terms on every entry), in
 // a fixed butterfly; then each entry takes the factors of its set bits.  Factors without
@@ -184,7 +184,7 @@ k_chunk(typename C2T<T>::type *__restrict__ psi, const ChunkArgs a, const KOp *_
                 om = s_m;
             }
             if constexpr (std::is_same<T, double>::value) {  // complex128 passes only
-                if (op->fkind == F_CDIAGK && op->nt > 0) {
+                if ((op->fkind == F_CDIAGK || op->fkind == F_HCDIAGK) && op->nt > 0) {
                     fold_hi_terms<DF>(*op, om, s_m, tile_base(t, a));
                     om = s_m;
                 }

@@ -34,6 +34,9 @@ enum FKind : int32_t {
                  // bit h of the tile is 1, entries with that table bit set (all for -1) take
                  // the factor (the kernel folds them into a per-tile copy of the table);
                  // off[0] bit tb + 1 marks the table bits that have terms
+    F_HCDIAGK,   // tile passes, complex128 FP64: the unscaled Hadamard butterfly (a + b, a - b)
+                 // on the single control pos[k] of an F_CDIAGK, then that F_CDIAGK (fields
+                 // as there, nf = 1): one sweep instead of two
 };
 
 // Structure of an F_DENSE1 matrix (FP64 operations per amplitude for complex128 work):

@@ -586,9 +586,12 @@ __device__ __forceinline__ void apply_op_smem(typename C2T<T>::type *tile, const
         }
         break;
     }
-    case F_CDIAGK: {
+    case F_CDIAGK:
+    case F_HCDIAGK: {
         const int kt = op.k, kc = op.nf;
         const uint32_t ng = 1u << (m - kc);
+        // F_HCDIAGK (nf = 1): first the butterfly with the partner across the control bit
+        const uint32_t hb = op.fkind == F_HCDIAGK ? 1u << op.pos[kt] : 0u;
         for (uint32_t g = threadIdx.x; g < ng; g += blockDim.x) {
             uint32_t x = g;
             for (int j = 0; j < kc; j++) {
@@ -600,6 +603,14 @@ __device__ __forceinline__ void apply_op_smem(typename C2T<T>::type *tile, const
             for (int j = 0; j < kt; j++) s |= ((x >> op.pos[j]) & 1u) << (kt - 1 - j);
             Amp<T, 1> v;
             ld_amp<T>(tile + x, v);
+            if (hb) {
+                Amp<T, 1> u[2];
+                ld_amp<T>(tile + (x ^ hb), u[0]);
+                u[1] = v;
+                SHSum<T>{}(u);
+                st_amp<T>(tile + (x ^ hb), u[0]);
+                v = u[1];
+            }
             f_diag<T, 1, 1>(&v, sm + 2 * s);
             st_amp<T>(tile + x, v);
         }

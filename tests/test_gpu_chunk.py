@@ -282,3 +282,22 @@ def test_qft_merged_diagonal_blocks(qs, n, dtype, flags):
     assert np.max(np.abs(got - want)) <= tol(dtype)
     # fewer tile sweeps than ops: the controlled phases of a target share blocks
     assert st["tile_sweeps"] < len(gates)
+
+
+@pytest.mark.parametrize("prec", [1, 2])
+@pytest.mark.parametrize("n,m", [(14, 0), (18, 8), (20, 12)])
+def test_qft_hadamard_joined_with_controlled_block(qs, n, m, prec):
+    """complex128 FP64 passes apply an unscaled Hadamard and the next diagonal block
+    controlled by its qubit (a QFT target's controlled phases, with factors from
+    non-local partners where the tile is narrower than the state) in one sweep: fewer
+    sweeps than ops after the merge (chunk mode: every pass a tile pass).  Double-float
+    keeps them apart.  Oracle parity for both."""
+    gates = inputs.qft(n)
+    psi0 = inputs.gaussian_state(n, seed=3 * n + m)
+    want = oracle.run(psi0.copy(), n, gates)
+    got, st = run_gpu(qs, n, 2, psi0, gates, qs.QS_MODE_CHUNK, chunk_m=m, precision=prec)
+    assert np.max(np.abs(got - want)) <= TOL_C128
+    if prec == 1:
+        assert st["tile_sweeps"] < st["ops_after_fuse"]
+    else:
+        assert st["tile_sweeps"] == st["ops_after_fuse"]
