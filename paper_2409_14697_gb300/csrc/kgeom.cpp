@@ -247,6 +247,28 @@ KOp make_tile_kop(const Op &op, const int *pos, std::vector<double> &mats) {
     return k;
 }
 
+std::vector<KOp> join_h_cdiag(const std::vector<KOp> &kops, const std::vector<double> &mats) {
+    std::vector<KOp> out;
+    out.reserve(kops.size());
+    for (size_t i = 0; i < kops.size(); i++) {
+        const KOp &h = kops[i];
+        const bool unscaled_h = h.fkind == F_H && h.nmat == 2 && mats[(size_t)h.mat] == 1.0 &&
+                                mats[(size_t)h.mat + 1] == 0.0;
+        if (unscaled_h && i + 1 < kops.size()) {
+            const KOp &d = kops[i + 1];
+            if (d.fkind == F_CDIAGK && d.nf == 1 && d.pos[d.k] == h.fb[0]) {
+                KOp j = d;
+                j.fkind = F_HCDIAGK;
+                out.push_back(j);
+                i++;
+                continue;
+            }
+        }
+        out.push_back(h);
+    }
+    return out;
+}
+
 namespace {
 
 // One op as a register-phase member (tile positions); false if a phase cannot hold it.

@@ -16,6 +16,12 @@ KOp make_kop(const Op &op, const int *pos, std::vector<double> &mats);
 // elements with every control set.
 KOp make_tile_kop(const Op &op, const int *pos, std::vector<double> &mats);
 
+// complex128 FP64 tile programs: an unscaled Hadamard (F_H with scale 1) directly followed
+// by an F_CDIAGK whose only control is the Hadamard's position becomes one F_HCDIAGK (the
+// block multiplies only the elements the butterfly's difference lands on, so both fit
+// one sweep of the tile; a QFT target and its controlled phases).
+std::vector<KOp> join_h_cdiag(const std::vector<KOp> &kops, const std::vector<double> &mats);
+
 // complex64 tiles of 2^m amplitudes with 2^thread_bits threads: true if register phases
 // apply (m = thread_bits + kRpBits).
 bool rphase_applicable(int m, int thread_bits);

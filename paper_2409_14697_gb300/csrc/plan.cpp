@@ -42,36 +42,6 @@ bool chunkable(const Op &op, const PlanParams &pp) {
 
 }  // namespace
 
-namespace {
-
-// An unscaled Hadamard directly followed by a diagonal block whose only control is the
-// Hadamard's qubit (a QFT target and its controlled phases) becomes one F_HCDIAGK: the
-// block multiplies only the elements the butterfly's difference lands on, so both fit one
-// sweep of the tile.
-std::vector<KOp> join_h_cdiag(const std::vector<KOp> &kops, const std::vector<double> &mats) {
-    std::vector<KOp> out;
-    out.reserve(kops.size());
-    for (size_t i = 0; i < kops.size(); i++) {
-        const KOp &h = kops[i];
-        const bool unscaled_h = h.fkind == F_H && h.nmat == 2 && mats[(size_t)h.mat] == 1.0 &&
-                                mats[(size_t)h.mat + 1] == 0.0;
-        if (unscaled_h && i + 1 < kops.size()) {
-            const KOp &d = kops[i + 1];
-            if (d.fkind == F_CDIAGK && d.nf == 1 && d.pos[d.k] == h.fb[0]) {
-                KOp j = d;
-                j.fkind = F_HCDIAGK;
-                out.push_back(j);
-                i++;
-                continue;
-            }
-        }
-        out.push_back(h);
-    }
-    return out;
-}
-
-}  // namespace
-
 // Launches one chunk pass over lmask applying `fused` (tensor cores where allowed);
 // returns the number of tile sweeps.
 int launch_pass_ops(DeviceState &st, uint64_t lmask, const std::vector<Op> &fused, bool use_tc) {

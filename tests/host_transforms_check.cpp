@@ -9,7 +9,9 @@
 //   split_one_qubit_phases, merge_tile_diagonals (with non-local controlled phases),
 //   and the chunk-pass order: deferred scale, fusion, split, diagonal merge.
 // Also checks the structural limits the kernels rely on (operand counts, table sizes,
-// term counts, unscaled Hadamard runs, nothing fused across the local set).
+// term counts, unscaled Hadamard runs, nothing fused across the local set), and runs the
+// chunk-pass program as launched: its tile KOps (make_tile_kop, then join_h_cdiag)
+// interpreted tile by tile on the CPU from the semantics kops.cuh documents.
 // Usage: host_transforms_check <seed> <trials>; prints OK and exits 0 on success.
 #include <cmath>
 #include <cstdio>
@@ -18,6 +20,7 @@
 #include <string>
 #include <vector>
 
+#include "kgeom.h"
 #include "qs_internal.h"
 
 namespace qs {
@@ -196,6 +199,162 @@ void check_h_runs(const std::vector<Op> &ops, int trial) {
     check(last < 0 || (!ops[last].m.empty() && ops[last].m[0] != cd(1.0)), "last Hadamard unscaled", trial);
 }
 
+// ---- tile programs: the KOps a chunk pass launches, interpreted on the CPU --------------
+// Each tile holds the 2^m amplitudes whose non-local qubits equal the tile's bits; tile
+// position r is the r-th qubit of the local set.  Semantics per KOp kind as the kernels
+// document them (kops.cuh): groups of elements base + off[t] over the bases with the fixed
+// bits fb clear and set_mask set; F_DIAGK / F_DENSEK on positions pos[]; F_CDIAGK on the
+// elements with its control positions set, with the factors of its terms whose global
+// qubit is 1 in the tile; F_HCDIAGK the unscaled butterfly across its control first.
+int g_joins = 0;
+
+void apply_kop(State &tile, int m, const KOp &k, const std::vector<double> &mats, uint64_t base) {
+    auto C = [&](int i) { return cd(mats[(size_t)k.mat + 2 * i], mats[(size_t)k.mat + 2 * i + 1]); };
+    const uint32_t N = 1u << m;
+    auto table_index = [&](uint32_t x, int kt) {
+        uint32_t s = 0;
+        for (int j = 0; j < kt; j++) s |= ((x >> k.pos[j]) & 1u) << (kt - 1 - j);
+        return s;
+    };
+    switch (k.fkind) {
+    case F_DIAGK:
+        for (uint32_t x = 0; x < N; x++) tile[x] *= C((int)table_index(x, k.k));
+        return;
+    case F_CDIAGK:
+    case F_HCDIAGK: {
+        uint32_t cm = 0;
+        for (int j = 0; j < k.nf; j++) cm |= 1u << k.pos[k.k + j];
+        if (cm != (uint32_t)k.set_mask) fail(QS_ERR_INVALID, "controls and set_mask disagree");
+        if (k.fkind == F_HCDIAGK && k.nf != 1) fail(QS_ERR_INVALID, "joined block with several controls");
+        const int ne = 1 << k.k;
+        for (uint32_t x = 0; x < N; x++) {
+            if ((x & cm) != cm) continue;
+            const uint32_t s = table_index(x, k.k);
+            cd f = C((int)s);
+            for (int i = 0; i < k.nt; i++) {
+                const double *t = &mats[(size_t)k.mat + 2 * ne + 4 * i];
+                const int tb = (int)t[0], h = (int)t[1];
+                if (((base >> h) & 1ull) && (tb < 0 || ((s >> tb) & 1u))) f *= cd(t[2], t[3]);
+            }
+            if (k.fkind == F_HCDIAGK) {
+                const uint32_t x0 = x ^ (1u << k.pos[k.k]);
+                const cd a0 = tile[x0], a1 = tile[x];
+                tile[x0] = a0 + a1;
+                tile[x] = (a0 - a1) * f;
+            } else {
+                tile[x] *= f;
+            }
+        }
+        return;
+    }
+    case F_DENSEK: {
+        const uint32_t D = 1u << k.k;
+        uint32_t pm = 0;
+        for (int j = 0; j < k.k; j++) pm |= 1u << k.pos[j];
+        std::vector<cd> in(D);
+        std::vector<uint32_t> idx(D);
+        for (uint32_t b = 0; b < N; b++) {
+            if (b & pm) continue;
+            for (uint32_t v = 0; v < D; v++) {
+                uint32_t e = b;
+                for (int j = 0; j < k.k; j++)
+                    if ((v >> (k.k - 1 - j)) & 1u) e |= 1u << k.pos[j];
+                idx[v] = e;
+                in[v] = tile[e];
+            }
+            for (uint32_t r = 0; r < D; r++) {
+                cd acc = 0.0;
+                for (uint32_t c = 0; c < D; c++) acc += C((int)(r * D + c)) * in[c];
+                tile[idx[r]] = acc;
+            }
+        }
+        return;
+    }
+    default:
+        break;
+    }
+    int nt;
+    switch (k.fkind) {
+    case F_PHASE: case F_NEG: nt = 1; break;
+    case F_H: case F_SWAP: case F_DIAG1: case F_DENSE1: nt = 2; break;
+    case F_DIAG2: case F_DENSE2: nt = 4; break;
+    default: fail(QS_ERR_INVALID, "tile op kind outside this check");
+    }
+    uint32_t fm = 0;
+    for (int j = 0; j < k.nf; j++) fm |= 1u << k.fb[j];
+    for (uint32_t x = 0; x < N; x++) {
+        if (x & fm) continue;
+        const uint32_t b = x | (uint32_t)k.set_mask;
+        uint32_t e[4];
+        cd a[4];
+        for (int t = 0; t < nt; t++) {
+            e[t] = b + (uint32_t)k.off[t];
+            a[t] = tile[e[t]];
+        }
+        cd o[4];
+        switch (k.fkind) {
+        case F_PHASE: o[0] = a[0] * C(0); break;
+        case F_NEG: o[0] = -a[0]; break;
+        case F_H: {
+            const double r = k.nmat >= 1 ? mats[(size_t)k.mat] : 1.0 / std::sqrt(2.0);
+            o[0] = r * (a[0] + a[1]);
+            o[1] = r * (a[0] - a[1]);
+            break;
+        }
+        case F_SWAP: o[0] = a[1]; o[1] = a[0]; break;
+        case F_DIAG1: o[0] = a[0] * C(0); o[1] = a[1] * C(1); break;
+        case F_DIAG2:
+            for (int t = 0; t < 4; t++) o[t] = a[t] * C(t);
+            break;
+        default:  // F_DENSE1, F_DENSE2: the full matrix, row-major
+            for (int r = 0; r < nt; r++) {
+                o[r] = 0.0;
+                for (int c = 0; c < nt; c++) o[r] += C(r * nt + c) * a[c];
+            }
+        }
+        for (int t = 0; t < nt; t++) tile[e[t]] = o[t];
+    }
+}
+
+State run_tiles(const State &psi0, int n, uint64_t L, const std::vector<KOp> &kops, const std::vector<double> &mats) {
+    std::vector<int> lq, hq;
+    for (int b = 0; b < n; b++) ((L >> b) & 1ull ? lq : hq).push_back(b);
+    const int m = (int)lq.size();
+    State psi = psi0, tile((size_t)1 << m);
+    for (uint64_t t = 0; t < (1ull << hq.size()); t++) {
+        uint64_t base = 0;
+        for (size_t j = 0; j < hq.size(); j++)
+            if ((t >> j) & 1ull) base |= 1ull << hq[j];
+        auto gidx = [&](uint32_t x) {
+            uint64_t a = base;
+            for (int r = 0; r < m; r++)
+                if ((x >> r) & 1u) a |= 1ull << lq[r];
+            return a;
+        };
+        for (uint32_t x = 0; x < tile.size(); x++) tile[x] = psi[gidx(x)];
+        for (const KOp &k : kops) apply_kop(tile, m, k, mats, base);
+        for (uint32_t x = 0; x < tile.size(); x++) psi[gidx(x)] = tile[x];
+    }
+    return psi;
+}
+
+// The pass program as launched: tile KOps on tile-local positions, then the Hadamard join.
+void check_tile_program(const State &psi0, const State &ref, int n, uint64_t lmask, const std::vector<Op> &prog,
+                        double tol, int trial) {
+    const uint64_t L = lmask ? lmask : (1ull << n) - 1;
+    int pos[64] = {0};
+    int r = 0;
+    for (int b = 0; b < n; b++)
+        if ((L >> b) & 1ull) pos[b] = r++;
+    std::vector<double> mats;
+    std::vector<KOp> kops;
+    for (const Op &op : prog) kops.push_back(make_tile_kop(op, pos, mats));
+    check(rel_err(ref, run_tiles(psi0, n, L, kops, mats)) < tol, "tile program", trial);
+    const std::vector<KOp> joined = join_h_cdiag(kops, mats);
+    for (const KOp &k : joined) g_joins += k.fkind == F_HCDIAGK;
+    check(rel_err(ref, run_tiles(psi0, n, L, joined, mats)) < tol, "tile program with joined Hadamards", trial);
+}
+
 }  // namespace
 
 int main(int argc, char **argv) {
@@ -246,11 +405,14 @@ int main(int argc, char **argv) {
             p = merge_tile_diagonals(p, 8, 0.5, lmask);
             check_merged(p, 8, lmask, trial);
             check(rel_err(ref, run(psi0, p)) < tol, "chunk-pass pipeline", trial);
+            check_tile_program(psi0, ref, n, lmask, p, tol, trial);
         } catch (const Error &e) {
             std::printf("FAIL trial %d: error %d %s\n", trial, e.code, e.msg.c_str());
             g_bad++;
         }
     }
-    std::printf("%s (%d trials)\n", g_bad ? "FAIL" : "OK", trials);
+    // QFT-like circuits must have exercised the join
+    if (trials >= 2) check(g_joins > 0, "no Hadamard joined with its controlled block", -1);
+    std::printf("%s (%d trials, %d joined Hadamards)\n", g_bad ? "FAIL" : "OK", trials, g_joins);
     return g_bad ? 1 : 0;
 }

@@ -3,7 +3,9 @@ fold, deferred Hadamard scale, gate fusion, U3 split, diagonal merge with non-lo
 controlled phases, and their chunk-pass order): builds ``host_transforms_check.cpp``
 against the package's host sources with g++ and runs it on seeded random circuits.  Each
 rewrite must leave a 10-qubit state unchanged to 1e-12 and keep the limits the kernels
-rely on.  No GPU: the CUDA headers are needed only for declarations."""
+rely on; the resulting tile programs (kernel ops on tile positions, with non-local terms
+and Hadamards joined with their controlled blocks) are interpreted tile by tile and must
+give the same state.  No GPU: the CUDA headers are needed only for declarations."""
 import os
 import shutil
 import subprocess
