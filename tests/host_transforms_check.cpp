@@ -92,7 +92,33 @@ double rel_err(const State &a, const State &b) {
     return e / s;
 }
 
-// Random gate records of every fixed type (no QS_DENSE), angles uniform in [0, 2 pi);
+// Random unitary of dimension D (Gram-Schmidt on Gaussian columns), row-major (re, im).
+std::vector<double> random_unitary(std::mt19937_64 &g, int D) {
+    std::normal_distribution<double> N;
+    std::vector<cd> u((size_t)D * D);
+    for (int c = 0; c < D; c++) {
+        std::vector<cd> v(D);
+        for (cd &z : v) z = cd(N(g), N(g));
+        for (int p = 0; p < c; p++) {
+            cd dot = 0.0;
+            for (int r = 0; r < D; r++) dot += std::conj(u[(size_t)r * D + p]) * v[r];
+            for (int r = 0; r < D; r++) v[r] -= dot * u[(size_t)r * D + p];
+        }
+        double nrm = 0.0;
+        for (const cd &z : v) nrm += std::norm(z);
+        nrm = std::sqrt(nrm);
+        for (int r = 0; r < D; r++) u[(size_t)r * D + c] = v[r] / nrm;
+    }
+    std::vector<double> out;
+    for (const cd &z : u) {
+        out.push_back(z.real());
+        out.push_back(z.imag());
+    }
+    return out;
+}
+
+// Random gate records of every type (QS_DENSE: a random unitary on 1 to 3 qubits), angles
+// uniform in [0, 2 pi);
 // with lmask != 0 only gates a chunk pass over that local set may hold: all qubits local,
 // or a two-qubit diagonal whose one local qubit may carry it (hi_local_choices).
 // Mixes: 0 every type alike, 1 QFT-like (Hadamard targets with controlled phases),
@@ -125,19 +151,27 @@ std::vector<Op> random_ops(std::mt19937_64 &g, int n, int count, uint64_t lmask,
             }
             continue;
         }
-        r.type = (mix == 2 && g() % 5 != 0) ? QS_H : (int)(g() % 17);
-        const bool two = r.type >= QS_CNOT;
-        r.nq = two ? 2 : 1;
-        r.q[0] = (int)(g() % n);
-        if (two) {
-            do r.q[1] = (int)(g() % n);
-            while (r.q[1] == r.q[0]);
+        r.type = (mix == 2 && g() % 5 != 0) ? QS_H : (int)(g() % 18);
+        r.nq = r.type == QS_DENSE ? 1 + (int)(g() % 3) : (r.type >= QS_CNOT ? 2 : 1);
+        for (int j = 0; j < r.nq; j++) {
+            bool again;
+            do {
+                r.q[j] = (int)(g() % n);
+                again = false;
+                for (int i = 0; i < j; i++) again = again || r.q[i] == r.q[j];
+            } while (again);
         }
         for (double &p : r.p) p = ang(g);
+        std::vector<double> dense;
+        if (r.type == QS_DENSE) {
+            dense = random_unitary(g, 1 << r.nq);
+            r.m = dense.data();
+        }
+        validate_gate(r, n);
         Op op = lower_gate(r);
         bool ok = true;
         for (int j = 0; j < op.k; j++) ok = ok && local(op.q[j]);
-        if (!ok && op.k == 2)
+        if (!ok && op.k == 2 && r.type != QS_DENSE)
             for (int j = 0; j < 2; j++)
                 if (local(op.q[j]) && !local(op.q[1 - j]) && ((hi_local_choices(op) >> op.q[j]) & 1ull)) ok = true;
         if (ok) ops.push_back(op);
@@ -173,10 +207,11 @@ void check_merged(const std::vector<Op> &ops, int max_k, uint64_t lmask, int tri
     }
 }
 
-void check_fused(const std::vector<Op> &ops, int fuse_k, uint64_t lmask, int trial) {
+// fused blocks: at most fuse_k qubits (a wider gate passes through as it is)
+void check_fused(const std::vector<Op> &ops, int fuse_k, int widest_gate, uint64_t lmask, int trial) {
     for (const Op &b : ops) {
         if (b.kind == K_DENSE || (b.kind == K_DIAG && b.k > 2))
-            check(b.k <= fuse_k, "fused block wider than fuse_k", trial);
+            check(b.k <= std::max(fuse_k, widest_gate), "fused block wider than fuse_k", trial);
         if (lmask && b.k > 2) check((b.qmask() & ~lmask) == 0, "fused across the local set", trial);
     }
 }
@@ -376,6 +411,8 @@ int main(int argc, char **argv) {
         const int mix = trial % 3;
         const std::vector<Op> ops = random_ops(g, n, mix == 2 ? 200 : 120, lmask, mix);
         const State ref = run(psi0, ops);
+        int widest = 0;
+        for (const Op &op : ops) widest = std::max(widest, op.k);
         try {
             if (!lmask) {
                 check(rel_err(ref, run(psi0, fold_global_phases(ops))) < tol, "fold_global_phases", trial);
@@ -387,7 +424,7 @@ int main(int argc, char **argv) {
             for (int k : {2, 3, 4}) {
                 for (double cost : {-1.0, 1.0, 24.0}) {
                     const std::vector<Op> f = fuse_ops(ops, k, cost, lmask);
-                    check_fused(f, k, lmask, trial);
+                    check_fused(f, k, widest, lmask, trial);
                     check(rel_err(ref, run(psi0, f)) < tol, "fuse_ops", trial);
                 }
             }
