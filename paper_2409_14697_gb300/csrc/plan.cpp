@@ -247,17 +247,6 @@ std::vector<Pass> choose_plan(const std::vector<Op> &ops, int n, const PlanParam
     return alt;
 }
 
-namespace {
-
-// The ops one chunk pass applies, in order: the pass's gates, then
-//  1. complex128: its Hadamards but the last run unscaled (exact at the pass's end);
-//  2. fusion into dense blocks where that does not add arithmetic (gates with a qubit
-//     outside the tile stay apart);
-//  3. complex128 FP64 passes of 256 tiles or more: U3 as a real rotation between phases
-//     that join the diagonal runs (smaller states are latency-bound: extra ops cost more);
-//  4. runs of diagonal gates (a QFT target's controlled phases, the phases of step 3) as
-//     diagonal blocks of up to 8 tile qubits, with factors for qubits outside the tile
-//     (complex64 register phases hold one- and two-qubit diagonals without a sweep).
 std::vector<Op> pass_program(const DeviceState &st, const PlanParams &pp, const Pass &p, const std::vector<Op> &ops) {
     const int local = __builtin_popcountll(p.lmask);
     std::vector<Op> pops;
@@ -272,8 +261,6 @@ std::vector<Op> pass_program(const DeviceState &st, const PlanParams &pp, const 
                                      pp.hi_diag ? p.lmask : 0);
     return fused;
 }
-
-}  // namespace
 
 void run_planned(DeviceState &st, const std::vector<Op> &ops, const qs_options &o, qs_stats &stats) {
     const int n = st.n;

@@ -31,6 +31,17 @@ std::vector<Pass> make_plan(const std::vector<Op> &ops, int n, const PlanParams 
 // left empty).
 std::vector<Pass> choose_plan(const std::vector<Op> &ops, int n, const PlanParams &pp, const qs_options &o,
                               std::vector<Op> &merged, std::vector<std::pair<size_t, size_t>> &origin);
+// The ops one chunk pass applies, in order: the pass's gates, then
+//  1. complex128: its Hadamards but the last run unscaled (exact at the pass's end);
+//  2. fusion into dense blocks where that does not add arithmetic (gates with a qubit
+//     outside the tile stay apart);
+//  3. complex128 FP64 passes of 256 tiles or more: U3 as a real rotation between phases
+//     that join the diagonal runs (smaller states are latency-bound: extra ops cost more);
+//  4. runs of diagonal gates (a QFT target's controlled phases, the phases of step 3) as
+//     diagonal blocks of up to 8 tile qubits, with factors for qubits outside the tile
+//     (complex64 register phases hold one- and two-qubit diagonals without a sweep).
+// ops: the list the pass's indices refer to (choose_plan's merged list where it made one).
+std::vector<Op> pass_program(const DeviceState &st, const PlanParams &pp, const Pass &p, const std::vector<Op> &ops);
 // One chunk pass over lmask applying ops already fused (tensor cores if use_tc).
 int launch_pass_ops(DeviceState &st, uint64_t lmask, const std::vector<Op> &fused, bool use_tc);
 // Plans `ops` into passes and launches them on st.stream, filling stats.

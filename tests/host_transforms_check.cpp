@@ -11,8 +11,11 @@
 // Also checks the structural limits the kernels rely on (operand counts, table sizes,
 // term counts, unscaled Hadamard runs, nothing fused across the local set), and runs the
 // chunk-pass program as launched: its tile KOps (make_tile_kop, then join_h_cdiag)
-// interpreted tile by tile on the CPU from the semantics kops.cuh documents.
+// interpreted tile by tile on the CPU from the semantics kops.cuh documents.  Finally the
+// whole planned complex128 path (plan_params, choose_plan, pass_program) is emulated on
+// 10- and 14-qubit states with several chunk widths, FP64 and double-float.
 // Usage: host_transforms_check <seed> <trials>; prints OK and exits 0 on success.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -20,11 +23,32 @@
 #include <string>
 #include <vector>
 
+#include "chunk.h"
 #include "kgeom.h"
+#include "phasefn.h"
+#include "plan.h"
 #include "qs_internal.h"
 
 namespace qs {
 void fail(int code, const std::string &msg) { throw Error{code, msg}; }
+void cuda_check(cudaError_t, const char *what) { fail(QS_ERR_CUDA, what); }
+// The planner's host code is linked as it is; everything that would touch a GPU fails.
+void launch_chunk_pass(DeviceState &, uint64_t, const std::vector<KOp> &, const std::vector<double> &) {
+    fail(QS_ERR_INVALID, "no GPU in this check");
+}
+void launch_chunk_pass_tc(DeviceState &, uint64_t, const std::vector<KOp> &, const std::vector<double> &,
+                          const std::vector<float> &, uint32_t) {
+    fail(QS_ERR_INVALID, "no GPU in this check");
+}
+void launch_stream_op(DeviceState &, const Op &) { fail(QS_ERR_INVALID, "no GPU in this check"); }
+void reduce_norm_async(DeviceState &, double *) { fail(QS_ERR_INVALID, "no GPU in this check"); }
+void launch_scale_ratio(DeviceState &, const double *) { fail(QS_ERR_INVALID, "no GPU in this check"); }
+bool tc_available(int, int) { return false; }
+void build_tc_operand(const std::vector<cd> &, int, std::vector<float> &, int &, int &) {
+    fail(QS_ERR_INVALID, "no GPU in this check");
+}
+// states of at least 9 qubits (the phase-function pass works in units of 2^9 amplitudes)
+bool phasefn_supported(int n) { return n >= 9; }
 }  // namespace qs
 
 using namespace qs;
@@ -122,13 +146,57 @@ std::vector<double> random_unitary(std::mt19937_64 &g, int D) {
 // with lmask != 0 only gates a chunk pass over that local set may hold: all qubits local,
 // or a two-qubit diagonal whose one local qubit may carry it (hi_local_choices).
 // Mixes: 0 every type alike, 1 QFT-like (Hadamard targets with controlled phases),
-// 2 Hadamard-heavy (four in five gates, runs past the unscaled limit).
+// 2 Hadamard-heavy (four in five gates, runs past the unscaled limit), 3 QAOA-like
+// (layers of equal-angle RZZ on random pairs or on every pair of a random qubit set,
+// then RX on every qubit).
 std::vector<Op> random_ops(std::mt19937_64 &g, int n, int count, uint64_t lmask, int mix) {
     std::uniform_real_distribution<double> ang(0.0, 2.0 * M_PI);
     std::vector<Op> ops;
     auto local = [&](int q) { return lmask == 0 || ((lmask >> q) & 1ull); };
     while ((int)ops.size() < count) {
         qs_gate r{};
+        if (mix == 3) {  // a cost layer of RZZ (one angle per layer), then the RX mixer
+            const double gamma = ang(g), beta = ang(g);
+            std::vector<std::pair<int, int>> edges;
+            if (g() & 1) {  // every pair of a random set of 4 to 7 qubits (fully connected)
+                std::vector<int> set;
+                const int w = 4 + (int)(g() % 4);
+                while ((int)set.size() < w) {
+                    const int q = (int)(g() % n);
+                    if (std::find(set.begin(), set.end(), q) == set.end()) set.push_back(q);
+                }
+                for (int i = 0; i < w; i++)
+                    for (int j = i + 1; j < w; j++) edges.push_back({set[i], set[j]});
+            } else {  // 2n random pairs
+                for (int e = 0; e < 2 * n; e++) {
+                    const int a = (int)(g() % n);
+                    int b;
+                    do b = (int)(g() % n);
+                    while (b == a);
+                    edges.push_back({a, b});
+                }
+            }
+            for (const auto &e : edges) {
+                if ((int)ops.size() >= count) break;
+                qs_gate z{};
+                z.type = QS_RZZ;
+                z.nq = 2;
+                z.q[0] = e.first;
+                z.q[1] = e.second;
+                z.p[0] = gamma;
+                if (local(z.q[0]) && local(z.q[1])) ops.push_back(lower_gate(z));
+            }
+            for (int q = 0; q < n && (int)ops.size() < count; q++) {
+                if (!local(q)) continue;
+                qs_gate x{};
+                x.type = QS_RX;
+                x.nq = 1;
+                x.q[0] = q;
+                x.p[0] = beta;
+                ops.push_back(lower_gate(x));
+            }
+            continue;
+        }
         if (mix == 1) {  // Hadamard targets with controlled phases to every other qubit
             const int t = (int)(g() % n);
             if (!local(t)) continue;
@@ -390,6 +458,84 @@ void check_tile_program(const State &psi0, const State &ref, int n, uint64_t lma
     check(rel_err(ref, run_tiles(psi0, n, L, joined, mats)) < tol, "tile program with joined Hadamards", trial);
 }
 
+// A merged diagonal run (K_PHASEFN) as phasefn.h defines it: F(x) = table[sum over groups of
+// count_g(x) * stride_g], count = popcount(x & mask) (PF_WEIGHT) or the number of pairs with
+// both bits set (PF_PAIRS).
+void apply_phasefn(State &psi, const Op &op) {
+    const PhaseFn &f = *op.pf;
+    for (size_t x = 0; x < psi.size(); x++) {
+        size_t idx = 0;
+        for (const PfGroup &gr : f.groups) {
+            int count = 0;
+            if (gr.kind == PF_WEIGHT) {
+                count = __builtin_popcountll((uint64_t)x & gr.mask);
+            } else {
+                for (const auto &pr : gr.pairs) count += ((x >> pr.first) & 1) && ((x >> pr.second) & 1);
+            }
+            idx += (size_t)count * (size_t)gr.stride;
+        }
+        psi[x] *= f.table.at(idx);
+    }
+}
+
+// A complex128 call of the planned path, emulated: the real planner (choose_plan, merged
+// diagonal runs included) and per-pass program (pass_program); streaming passes apply
+// their ops directly, chunk passes run their tile programs as launched.  Every op must
+// run exactly once, every chunk pass must keep the low c qubits local, and the result
+// must equal the gates applied one by one.
+int g_planned_passes = 0, g_planned_terms = 0, g_phasefns = 0;
+
+void check_planned(const State &psi0, const State &ref, int n, const std::vector<Op> &ops, int chunk_m, int prec,
+                   int mode, double tol, int trial) {
+    DeviceState st;
+    st.n = n;
+    st.dtype = QS_C128;
+    st.prec = prec;
+    qs_options o{};
+    o.mode = mode;
+    o.chunk_m = chunk_m;
+    o.precision = prec;
+    const PlanParams pp = plan_params(st, o);
+    std::vector<Op> merged;
+    std::vector<std::pair<size_t, size_t>> origin;
+    const std::vector<Pass> plan = choose_plan(ops, n, pp, o, merged, origin);
+    const std::vector<Op> &ops_r = merged.empty() ? ops : merged;
+    std::vector<int> seen(ops_r.size(), 0);
+    State psi = psi0;
+    for (const Pass &p : plan) {
+        g_planned_passes++;
+        for (int i : p.ops) seen[(size_t)i]++;
+        if (p.stream) {
+            for (int i : p.ops) {
+                if (ops_r[(size_t)i].kind == K_PHASEFN) {
+                    apply_phasefn(psi, ops_r[(size_t)i]);
+                    g_phasefns++;
+                }
+                else apply(psi, ops_r[(size_t)i]);
+            }
+            continue;
+        }
+        const uint64_t low = (1ull << pp.c) - 1ull;
+        check((p.lmask & low) == low, "chunk pass without the low qubits", trial);
+        check(__builtin_popcountll(p.lmask) <= pp.m, "chunk pass wider than m", trial);
+        const std::vector<Op> prog = pass_program(st, pp, p, ops_r);
+        int pos[64] = {0};
+        int r = 0;
+        for (int b = 0; b < n; b++)
+            if ((p.lmask >> b) & 1ull) pos[b] = r++;
+        std::vector<double> mats;
+        std::vector<KOp> kops;
+        for (const Op &op : prog) {
+            kops.push_back(make_tile_kop(op, pos, mats));
+            g_planned_terms += (int)op.hi.size();
+        }
+        if (prec == QS_PREC_FP64) kops = join_h_cdiag(kops, mats);
+        psi = run_tiles(psi, n, p.lmask, kops, mats);
+    }
+    for (int c : seen) check(c == 1, "op not run exactly once", trial);
+    check(rel_err(ref, psi) < tol, "planned path", trial);
+}
+
 }  // namespace
 
 int main(int argc, char **argv) {
@@ -402,13 +548,13 @@ int main(int argc, char **argv) {
     for (int trial = 0; trial < trials; trial++) {
         State psi0(1ull << n);
         for (cd &z : psi0) z = cd(N(g), N(g));
-        // a local set of 7 of the 10 qubits (always the low 2), or none
+        // a local set of 7 of the 10 qubits (always the low 2), or none; every mix gets both
         uint64_t lmask = 0;
-        if (trial % 2) {
+        if ((trial >> 2) & 1) {
             lmask = 3;
             while (__builtin_popcountll(lmask) < 7) lmask |= 1ull << (2 + g() % (n - 2));
         }
-        const int mix = trial % 3;
+        const int mix = trial % 4;
         const std::vector<Op> ops = random_ops(g, n, mix == 2 ? 200 : 120, lmask, mix);
         const State ref = run(psi0, ops);
         int widest = 0;
@@ -443,6 +589,24 @@ int main(int argc, char **argv) {
             check_merged(p, 8, lmask, trial);
             check(rel_err(ref, run(psi0, p)) < tol, "chunk-pass pipeline", trial);
             check_tile_program(psi0, ref, n, lmask, p, tol, trial);
+            if (!lmask) {
+                // the whole planned path on this circuit: chunk widths that leave 2 to 6
+                // qubits outside the tile, FP64 and double-float, auto and chunk modes
+                for (int cm : {4, 6, 8})
+                    for (int prec : {QS_PREC_FP64, QS_PREC_DF32})
+                        check_planned(psi0, ref, n, ops, cm, prec, trial % 4 == 0 ? QS_MODE_CHUNK : QS_MODE_AUTO,
+                                      tol, trial);
+            }
+            if (trial % 4 == 0) {
+                // 14 qubits, 6-qubit tiles: passes of 256 tiles, where complex128 FP64 splits U3
+                const int n2 = 14;
+                State q0((size_t)1 << n2);
+                for (cd &z : q0) z = cd(N(g), N(g));
+                const std::vector<Op> ops2 = random_ops(g, n2, 100, 0, (trial / 4) % 4);
+                const State ref2 = run(q0, ops2);
+                for (int prec : {QS_PREC_FP64, QS_PREC_DF32})
+                    check_planned(q0, ref2, n2, ops2, 6, prec, QS_MODE_AUTO, tol, trial);
+            }
         } catch (const Error &e) {
             std::printf("FAIL trial %d: error %d %s\n", trial, e.code, e.msg.c_str());
             g_bad++;
@@ -450,6 +614,8 @@ int main(int argc, char **argv) {
     }
     // QFT-like circuits must have exercised the join
     if (trials >= 2) check(g_joins > 0, "no Hadamard joined with its controlled block", -1);
-    std::printf("%s (%d trials, %d joined Hadamards)\n", g_bad ? "FAIL" : "OK", trials, g_joins);
+        if (trials >= 4) check(g_planned_terms > 0 && g_phasefns > 0, "planned path not exercised", -1);
+    std::printf("%s (%d trials, %d joined Hadamards, %d planned passes, %d non-local terms, %d phase functions)\n",
+                g_bad ? "FAIL" : "OK", trials, g_joins, g_planned_passes, g_planned_terms, g_phasefns);
     return g_bad ? 1 : 0;
 }

@@ -5,7 +5,11 @@ against the package's host sources with g++ and runs it on seeded random circuit
 rewrite must leave a 10-qubit state unchanged to 1e-12 and keep the limits the kernels
 rely on; the resulting tile programs (kernel ops on tile positions, with non-local terms
 and Hadamards joined with their controlled blocks) are interpreted tile by tile and must
-give the same state.  No GPU: the CUDA headers are needed only for declarations."""
+give the same state.  The whole planned complex128 path is emulated too: the planner and
+per-pass programs as the library runs them (merged diagonal runs applied from their
+documented table semantics), every op exactly once, the same final state.  No GPU: the
+CUDA headers and runtime library are needed only to link; every launcher is a stub that
+fails."""
 import os
 import shutil
 import subprocess
@@ -35,10 +39,15 @@ def checker(tmp_path_factory):
     inc = _cuda_include()
     if gxx is None or inc is None:
         pytest.skip("g++ or the CUDA headers are not available")
+    # the planner's host code references the CUDA runtime (never called here)
+    lib = Path(inc).parent / "lib64"
+    if not any(lib.glob("libcudart.so*")):
+        pytest.skip("the CUDA runtime library is not available")
     exe = tmp_path_factory.mktemp("host_transforms") / "host_transforms_check"
+    srcs = [ROOT / "tests" / "host_transforms_check.cpp"] + \
+        [CSRC / f for f in ("ir.cpp", "kgeom.cpp", "plan.cpp", "phasefn.cpp")]
     cmd = [gxx, "-O1", "-std=c++17", f"-I{CSRC}", f"-I{ROOT / 'include'}", f"-I{inc}",
-           str(ROOT / "tests" / "host_transforms_check.cpp"), str(CSRC / "ir.cpp"),
-           str(CSRC / "kgeom.cpp"), "-o", str(exe)]
+           *map(str, srcs), f"-L{lib}", "-lcudart", f"-Wl,-rpath,{lib}", "-o", str(exe)]
     r = subprocess.run(cmd, capture_output=True, text=True, timeout=300)
     assert r.returncode == 0, r.stderr[-4000:]
     return exe
