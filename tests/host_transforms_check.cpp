@@ -11,7 +11,8 @@
 // Also checks the structural limits the kernels rely on (operand counts, table sizes,
 // term counts, unscaled Hadamard runs, nothing fused across the local set), and runs the
 // chunk-pass program as launched: its tile KOps (make_tile_kop, then join_h_cdiag)
-// interpreted tile by tile on the CPU from the semantics kops.cuh documents.  Finally the
+// interpreted tile by tile on the CPU from the semantics kops.cuh documents; likewise the
+// streaming ops of gate-by-gate and fused calls (make_kop on the whole state).  Finally the
 // whole planned complex128 path (plan_params, choose_plan, pass_program) is emulated on
 // 10- and 14-qubit states with several chunk widths, FP64 and double-float.
 // Usage: host_transforms_check <seed> <trials>; prints OK and exits 0 on success.
@@ -458,6 +459,18 @@ void check_tile_program(const State &psi0, const State &ref, int n, uint64_t lma
     check(rel_err(ref, run_tiles(psi0, n, L, joined, mats)) < tol, "tile program with joined Hadamards", trial);
 }
 
+// Streaming ops (one pass over the whole state each): make_kop on the state's own bit
+// positions, interpreted with the whole state as one tile.
+void check_stream_program(const State &psi0, const State &ref, int n, const std::vector<Op> &prog, const char *what,
+                          double tol, int trial) {
+    int ident[64];
+    for (int i = 0; i < 64; i++) ident[i] = i;
+    std::vector<double> mats;
+    std::vector<KOp> kops;
+    for (const Op &op : prog) kops.push_back(make_kop(op, ident, mats));
+    check(rel_err(ref, run_tiles(psi0, n, (1ull << n) - 1, kops, mats)) < tol, what, trial);
+}
+
 // A merged diagonal run (K_PHASEFN) as phasefn.h defines it: F(x) = table[sum over groups of
 // count_g(x) * stride_g], count = popcount(x & mask) (PF_WEIGHT) or the number of pairs with
 // both bits set (PF_PAIRS).
@@ -590,6 +603,15 @@ int main(int argc, char **argv) {
             check(rel_err(ref, run(psi0, p)) < tol, "chunk-pass pipeline", trial);
             check_tile_program(psi0, ref, n, lmask, p, tol, trial);
             if (!lmask) {
+                // gate-by-gate calls (QS_MODE_GATE): global phases folded, complex128 FP64
+                // Hadamards unscaled but for every 64th and the last, one streaming op each
+                std::vector<Op> gops = fold_global_phases(ops);
+                check_stream_program(psi0, ref, n, gops, "gate-by-gate ops", tol, trial);
+                defer_hadamard_scale(gops);
+                check_stream_program(psi0, ref, n, gops, "gate-by-gate ops, deferred scale", tol, trial);
+                // fused calls (QS_MODE_FUSED): dense blocks of up to 3 and 6 qubits
+                for (int k : {3, 6})
+                    check_stream_program(psi0, ref, n, fuse_ops(ops, k), "fused blocks", tol, trial);
                 // the whole planned path on this circuit: chunk widths that leave 2 to 6
                 // qubits outside the tile, FP64 and double-float, auto and chunk modes
                 for (int cm : {4, 6, 8})
