@@ -16,6 +16,7 @@
 // whole planned complex128 path (plan_params, choose_plan, pass_program) is emulated on
 // 10- and 14-qubit states with several chunk widths, FP64 and double-float.
 // Usage: host_transforms_check <seed> <trials>; prints OK and exits 0 on success.
+//        host_transforms_check --gates; prints the lowered gate matrices.
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
@@ -551,7 +552,31 @@ void check_planned(const State &psi0, const State &ref, int n, const std::vector
 
 }  // namespace
 
+// --gates: each fixed gate type lowered (lower_gate) at a few angle sets, as lines
+// "type p0 p1 p2 k re im re im ..." of its full 2^k x 2^k matrix (first operand most
+// significant), for a comparison with the oracle's own gate matrices.
+int print_lowered_gates() {
+    const double sets[][3] = {{0.0, 0.0, 0.0}, {M_PI, M_PI / 2, -M_PI / 4}, {0.3, 1.7, -2.9}, {5.1, -0.4, 2.2}};
+    for (int type = 0; type < QS_DENSE; type++) {
+        for (const auto &ps : sets) {
+            qs_gate r{};
+            r.type = type;
+            r.nq = type >= QS_CNOT ? 2 : 1;
+            r.q[0] = 0;
+            r.q[1] = 1;
+            for (int j = 0; j < 3; j++) r.p[j] = ps[j];
+            const Op op = lower_gate(r);
+            const std::vector<cd> f = op.full();
+            std::printf("%d %.17g %.17g %.17g %d", type, ps[0], ps[1], ps[2], op.k);
+            for (const cd &z : f) std::printf(" %.17g %.17g", z.real(), z.imag());
+            std::printf("\n");
+        }
+    }
+    return 0;
+}
+
 int main(int argc, char **argv) {
+    if (argc > 1 && std::string(argv[1]) == "--gates") return print_lowered_gates();
     const int seed = argc > 1 ? std::atoi(argv[1]) : 1;
     const int trials = argc > 2 ? std::atoi(argv[2]) : 20;
     std::mt19937_64 g((uint64_t)seed);

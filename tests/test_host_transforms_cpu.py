@@ -15,7 +15,11 @@ import shutil
 import subprocess
 from pathlib import Path
 
+import numpy as np
 import pytest
+
+import oracle
+from paper_2409_14697_gb300 import qs
 
 ROOT = Path(__file__).resolve().parents[1]
 CSRC = ROOT / "paper_2409_14697_gb300" / "csrc"
@@ -57,3 +61,21 @@ def checker(tmp_path_factory):
 def test_host_rewrites_keep_the_circuit(checker, seed):
     r = subprocess.run([str(checker), str(seed), "24"], capture_output=True, text=True, timeout=300)
     assert r.returncode == 0 and "OK" in r.stdout, r.stdout[-4000:]
+
+
+def test_lowered_gates_equal_the_oracle_matrices(checker):
+    """Every fixed gate type as the library lowers it (the matrices all of the checks above
+    start from) equals the oracle's matrix for that gate, at several angle sets."""
+    r = subprocess.run([str(checker), "--gates"], capture_output=True, text=True, timeout=60)
+    assert r.returncode == 0, r.stderr[-2000:]
+    names = {v: k for k, v in qs.GATE_TYPES.items()}
+    lines = r.stdout.strip().splitlines()
+    assert len(lines) == 17 * 4
+    for line in lines:
+        f = line.split()
+        name, params, k = names[int(f[0])], tuple(float(x) for x in f[1:4]), int(f[4])
+        vals = np.array([float(x) for x in f[5:]])
+        got = (vals[0::2] + 1j * vals[1::2]).reshape(1 << k, 1 << k)
+        want = oracle.gate_matrix(name, params)
+        assert got.shape == want.shape, name
+        assert np.max(np.abs(got - want)) <= 1e-15, (name, params)
