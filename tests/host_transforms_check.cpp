@@ -500,11 +500,12 @@ void apply_phasefn(State &psi, const Op &op) {
 int g_planned_passes = 0, g_planned_terms = 0, g_phasefns = 0;
 
 void check_planned(const State &psi0, const State &ref, int n, const std::vector<Op> &ops, int chunk_m, int prec,
-                   int mode, double tol, int trial) {
+                   int mode, double tol, int trial, int dtype = QS_C128) {
     DeviceState st;
     st.n = n;
-    st.dtype = QS_C128;
+    st.dtype = dtype;
     st.prec = prec;
+    st.reg_phases = false;  // complex64: the shared-memory ops, not register phases
     qs_options o{};
     o.mode = mode;
     o.chunk_m = chunk_m;
@@ -543,7 +544,7 @@ void check_planned(const State &psi0, const State &ref, int n, const std::vector
             kops.push_back(make_tile_kop(op, pos, mats));
             g_planned_terms += (int)op.hi.size();
         }
-        if (prec == QS_PREC_FP64) kops = join_h_cdiag(kops, mats);
+        if (dtype == QS_C128 && prec == QS_PREC_FP64) kops = join_h_cdiag(kops, mats);
         psi = run_tiles(psi, n, p.lmask, kops, mats);
     }
     for (int c : seen) check(c == 1, "op not run exactly once", trial);
@@ -643,6 +644,10 @@ int main(int argc, char **argv) {
                     for (int prec : {QS_PREC_FP64, QS_PREC_DF32})
                         check_planned(psi0, ref, n, ops, cm, prec, trial % 4 == 0 ? QS_MODE_CHUNK : QS_MODE_AUTO,
                                       tol, trial);
+                // complex64 host logic (its own fusion and merge thresholds, no non-local
+                // terms), applied here in double precision
+                for (int cm : {5, 8})
+                    check_planned(psi0, ref, n, ops, cm, QS_PREC_FP64, QS_MODE_AUTO, tol, trial, QS_C64);
             }
             if (trial % 4 == 0) {
                 // 14 qubits, 6-qubit tiles: passes of 256 tiles, where complex128 FP64 splits U3
