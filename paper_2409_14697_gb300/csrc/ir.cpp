@@ -381,12 +381,12 @@ uint64_t hi_local_choices(const Op &op) {
     return r;
 }
 
-std::vector<Op> merge_tile_diagonals(const std::vector<Op> &ops, int max_k, double sweep_cost, uint64_t lmask) {
+std::vector<Op> merge_tile_diagonals(std::vector<Op> ops, int max_k, double sweep_cost, uint64_t lmask) {
     std::vector<Op> out;
     std::vector<int> Q;                  // block qubits (local), Q[0] most significant
     std::vector<cd> D;                   // block diagonal over Q
     std::vector<HiTerm> terms;           // factors from non-local qubits
-    std::vector<const Op *> members;
+    std::vector<Op *> members;           // ops of the open block (moved out when it is split)
     bool forced = false;                 // a member has a non-local qubit: emit the block
     double member_cost = 0.0;
     auto is_local = [&](int q) { return lmask == 0 || ((lmask >> q) & 1ull) != 0; };
@@ -424,7 +424,7 @@ std::vector<Op> merge_tile_diagonals(const std::vector<Op> &ops, int max_k, doub
                 out.push_back(std::move(b));
             }
         } else {
-            for (const Op *m : members) out.push_back(*m);
+            for (Op *m : members) out.push_back(std::move(*m));
         }
         members.clear();
         Q.clear();
@@ -433,11 +433,11 @@ std::vector<Op> merge_tile_diagonals(const std::vector<Op> &ops, int max_k, doub
         forced = false;
         member_cost = 0.0;
     };
-    for (const Op &op : ops) {
+    for (Op &op : ops) {
         std::vector<cd> d;
         if (!diag_of(op, d)) {
             flush();
-            out.push_back(op);
+            out.push_back(std::move(op));
             continue;
         }
         // the op's local part: its diagonal on its local qubits, with the x_h = 0 slice
@@ -518,19 +518,19 @@ std::vector<Op> merge_tile_diagonals(const std::vector<Op> &ops, int max_k, doub
     return out;
 }
 
-std::vector<Op> fuse_ops(const std::vector<Op> &ops, int fuse_k, double sweep_flops, uint64_t lmask) {
+std::vector<Op> fuse_ops(std::vector<Op> ops, int fuse_k, double sweep_flops, uint64_t lmask) {
     if (fuse_k <= 1) return ops;
     std::vector<Op> out;
     std::vector<int> Q;                  // qubits of the current block, Q[0] most significant
     std::vector<cd> U;                   // its matrix
-    std::vector<const Op *> members;     // ops absorbed into the current block
+    std::vector<Op *> members;           // ops absorbed into the current block
     bool diag = true;
     double member_flops = 0.0;           // flops/amplitude of the members applied one by one
 
     auto flush = [&]() {
         if (members.empty()) return;
         if (members.size() == 1) {
-            out.push_back(*members[0]);
+            out.push_back(std::move(*members[0]));
         } else {
             Op b;
             b.k = (int)Q.size();
@@ -553,11 +553,11 @@ std::vector<Op> fuse_ops(const std::vector<Op> &ops, int fuse_k, double sweep_fl
         member_flops = 0.0;
     };
 
-    for (const Op &op : ops) {
+    for (Op &op : ops) {
         if (lmask && (op.qmask() & ~lmask)) {
             // a gate with a qubit outside the pass's local set is applied on its own
             flush();
-            out.push_back(op);
+            out.push_back(std::move(op));
             continue;
         }
         std::vector<int> nQ = Q;
@@ -581,17 +581,21 @@ std::vector<Op> fuse_ops(const std::vector<Op> &ops, int fuse_k, double sweep_fl
         // keep the block's qubits sorted high-to-low so that equal sets give equal orders
         std::sort(nQ.begin(), nQ.end(), [](int a, int b) { return a > b; });
         const size_t D = 1ull << nQ.size();
+        // a block of one op is emitted as that op: its matrix is formed when a second joins
         std::vector<cd> newU;
-        if (members.empty()) {
-            Op tmp = op;
-            newU = embed(tmp, nQ);
-        } else {
-            Op cur;
-            cur.kind = K_DENSE;
-            cur.k = (int)Q.size();
-            for (int j = 0; j < cur.k; j++) cur.q[j] = Q[j];
-            cur.m = U;
-            const std::vector<cd> A = embed(cur, nQ), B = embed(op, nQ);
+        if (!members.empty()) {
+            std::vector<cd> A;
+            if (members.size() == 1) {
+                A = embed(*members[0], nQ);
+            } else {
+                Op cur;
+                cur.kind = K_DENSE;
+                cur.k = (int)Q.size();
+                for (int j = 0; j < cur.k; j++) cur.q[j] = Q[j];
+                cur.m = U;
+                A = embed(cur, nQ);
+            }
+            const std::vector<cd> B = embed(op, nQ);
             newU.assign(D * D, 0.0);
             for (size_t r = 0; r < D; r++)
                 for (size_t t = 0; t < D; t++) {

@@ -272,7 +272,7 @@ void batch_build(Batch &b, const std::vector<std::vector<Op>> &circ_ops, const s
                     fail(QS_ERR_UNSUPPORTED, "batched circuits take dense blocks of at most 4 qubits");
             std::vector<Op> pops;
             for (int i : p.ops) pops.push_back(circ_ops[c][i]);
-            const std::vector<Op> fused = fuse_ops(pops, pp.fuse_k, pp.sweep_flops);
+            const std::vector<Op> fused = fuse_ops(std::move(pops), pp.fuse_k, pp.sweep_flops);
             int pos[64] = {0};
             int r = 0;
             for (int bit = 0; bit < n; bit++)

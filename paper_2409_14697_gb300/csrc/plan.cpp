@@ -238,6 +238,11 @@ std::vector<Pass> choose_plan(const std::vector<Op> &ops, int n, const PlanParam
     std::vector<std::pair<size_t, size_t>> org;
     std::vector<Op> m = merge_diagonal_runs(ops, kMinMergedRun, &org);
     if (m.size() >= ops.size()) return plan;
+    // each phase function is a streaming pass of its own (not chunkable): the merged plan
+    // has at least that many passes, plus one if any other op is left
+    size_t n_pf = 0;
+    for (const Op &op : m) n_pf += op.kind == K_PHASEFN;
+    if (n_pf + (m.size() > n_pf ? 1 : 0) > plan.size()) return plan;
     std::vector<Pass> alt = make_plan(m, n, pp);
     // equal pass counts: the merged runs (one table lookup per amplitude) cost less FP64
     // work than the same gates as diagonal blocks inside chunk passes
@@ -253,11 +258,11 @@ std::vector<Op> pass_program(const DeviceState &st, const PlanParams &pp, const 
     pops.reserve(p.ops.size());
     for (int i : p.ops) pops.push_back(ops[i]);
     if (st.dtype == QS_C128) defer_hadamard_scale(pops);
-    std::vector<Op> fused = fuse_ops(pops, pp.fuse_k, pp.sweep_flops, p.lmask);
+    std::vector<Op> fused = fuse_ops(std::move(pops), pp.fuse_k, pp.sweep_flops, p.lmask);
     if (st.dtype == QS_C128 && st.prec == QS_PREC_FP64 && st.n - local >= 8) fused = split_one_qubit_phases(fused);
     const bool phases = st.dtype == QS_C64 && st.reg_phases && !pp.tc && rphase_applicable(local, kTileThreadBits);
     if (!phases)
-        fused = merge_tile_diagonals(fused, kTileDiagQubits, st.dtype == QS_C128 ? 0.5 : 4.0,
+        fused = merge_tile_diagonals(std::move(fused), kTileDiagQubits, st.dtype == QS_C128 ? 0.5 : 4.0,
                                      pp.hi_diag ? p.lmask : 0);
     return fused;
 }

@@ -89,7 +89,7 @@ Op lower_gate(const qs_gate &g);
 // most the flops per amplitude of its members applied one by one plus sweep_flops (the
 // value of one saved pass over the tile).  sweep_flops < 0 merges whenever the width fits.
 // lmask != 0: ops with a qubit outside lmask (a chunk pass's local set) are not fused.
-std::vector<Op> fuse_ops(const std::vector<Op> &ops, int fuse_k, double sweep_flops = -1.0, uint64_t lmask = 0);
+std::vector<Op> fuse_ops(std::vector<Op> ops, int fuse_k, double sweep_flops = -1.0, uint64_t lmask = 0);
 // Merges runs of consecutive diagonal gates into diagonal blocks of at most max_k qubits
 // where that costs fewer FP64 operations per amplitude in a shared-memory pass (a block
 // multiplies only the elements whose "control" qubits, those on whose 0-half every entry
@@ -102,8 +102,7 @@ std::vector<Op> fuse_ops(const std::vector<Op> &ops, int fuse_k, double sweep_fl
 // (g0 = d(0,1)/d(0,0) on every entry, g1/g0 with g1 = d(1,1)/d(1,0) on the entries with a
 // set).  A block's table covers its non-control qubits: at most 2^max_k entries, and
 // 2^(max_k - 1) with HiTerms (at most 64), so that table and terms fit one op's reals.
-std::vector<Op> merge_tile_diagonals(const std::vector<Op> &ops, int max_k, double sweep_cost,
-                                     uint64_t lmask = 0);
+std::vector<Op> merge_tile_diagonals(std::vector<Op> ops, int max_k, double sweep_cost, uint64_t lmask = 0);
 // Qubits of a two-qubit diagonal (no zero entry) that may be its only local qubit in a
 // chunk pass: a with d(0, x) = 1 for both x (the gate is then a phase on a's 1-half chosen
 // by the other bit, which keeps a a control of the block: CP, CZ, controlled RZ).  0 if none.
