@@ -433,8 +433,11 @@ std::vector<Op> merge_tile_diagonals(std::vector<Op> ops, int max_k, double swee
         forced = false;
         member_cost = 0.0;
     };
+    // per-op scratch, reused across ops (the block's vectors trade buffers with it)
+    std::vector<cd> d, dl, nD;
+    std::vector<int> lq, nQ;
+    std::vector<HiTerm> nt, nterms;
     for (Op &op : ops) {
-        std::vector<cd> d;
         if (!diag_of(op, d)) {
             flush();
             out.push_back(std::move(op));
@@ -445,9 +448,7 @@ std::vector<Op> merge_tile_diagonals(std::vector<Op> ops, int max_k, double swee
         int jh = -1;
         for (int j = 0; j < op.k; j++)
             if (!is_local(op.q[j])) jh = j;
-        std::vector<int> lq;
-        std::vector<cd> dl;
-        std::vector<HiTerm> nt;
+        nt.clear();
         if (jh < 0) {
             lq.assign(op.q, op.q + op.k);
             dl = d;
@@ -499,17 +500,14 @@ std::vector<Op> merge_tile_diagonals(std::vector<Op> ops, int max_k, double swee
             return (int)q.size() <= max_k && table_bits <= (tt.empty() ? max_k : max_k - 1) &&
                    tt.size() <= (size_t)kMaxHiTerms;
         };
-        std::vector<int> nQ;
-        std::vector<cd> nD;
-        std::vector<HiTerm> nterms;
         extend(nQ, nD, nterms);
         if (!members.empty() && !fits(nQ, nD, nterms)) {
             flush();
             extend(nQ, nD, nterms);
         }
-        Q = std::move(nQ);
-        D = std::move(nD);
-        terms = std::move(nterms);
+        Q.swap(nQ);
+        D.swap(nD);
+        terms.swap(nterms);
         members.push_back(&op);
         forced = forced || jh >= 0;
         member_cost += diag_cost(d) + sweep_cost;
@@ -526,6 +524,7 @@ std::vector<Op> fuse_ops(std::vector<Op> ops, int fuse_k, double sweep_flops, ui
     std::vector<Op *> members;           // ops absorbed into the current block
     bool diag = true;
     double member_flops = 0.0;           // flops/amplitude of the members applied one by one
+    std::vector<int> nQ;                 // scratch: qubits of the block with the next op
 
     auto flush = [&]() {
         if (members.empty()) return;
@@ -560,7 +559,9 @@ std::vector<Op> fuse_ops(std::vector<Op> ops, int fuse_k, double sweep_flops, ui
             out.push_back(std::move(op));
             continue;
         }
-        std::vector<int> nQ = Q;
+        const double f_op = op_flops(op);
+        const bool op_diag = is_diagonal(op);
+        nQ.assign(Q.begin(), Q.end());
         for (int j = 0; j < op.k; j++) {
             bool have = false;
             for (int x : nQ) have |= x == op.q[j];
@@ -570,9 +571,9 @@ std::vector<Op> fuse_ops(std::vector<Op> ops, int fuse_k, double sweep_flops, ui
         if (fits && !members.empty() && sweep_flops >= 0.0) {
             // cost gate: the fused block may not cost more flops per amplitude than its
             // members one by one plus the saved shared-memory sweep
-            const bool ndiag = diag && is_diagonal(op);
+            const bool ndiag = diag && op_diag;
             const double fused = ndiag ? 4.0 : 4.0 * (double)(1 << nQ.size());
-            fits = fused <= member_flops + op_flops(op) + sweep_flops;
+            fits = fused <= member_flops + f_op + sweep_flops;
         }
         if (!fits) {
             flush();
@@ -604,11 +605,11 @@ std::vector<Op> fuse_ops(std::vector<Op> ops, int fuse_k, double sweep_flops, ui
                     for (size_t c = 0; c < D; c++) newU[r * D + c] += b * A[t * D + c];
                 }
         }
-        Q = nQ;
+        Q.assign(nQ.begin(), nQ.end());
         U = std::move(newU);
         members.push_back(&op);
-        member_flops += op_flops(op);
-        diag = diag && is_diagonal(op);
+        member_flops += f_op;
+        diag = diag && op_diag;
     }
     flush();
     return out;
