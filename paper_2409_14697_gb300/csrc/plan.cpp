@@ -130,7 +130,26 @@ struct Trial {
     bool stream = false;
 };
 
-Trial greedy_pass(const std::vector<Op> &ops, const std::vector<char> &done, size_t first, int n,
+// What the pass builder asks of each op, computed once per plan (a plan tries many passes).
+struct OpInfo {
+    uint64_t qm;   // qubits
+    uint64_t hi;   // qubits that may be its only local one (pp.hi_diag)
+    bool diag;
+    bool chunk;
+};
+
+std::vector<OpInfo> op_info(const std::vector<Op> &ops, const PlanParams &pp) {
+    std::vector<OpInfo> info(ops.size());
+    for (size_t i = 0; i < ops.size(); i++) {
+        info[i].qm = ops[i].qmask();
+        info[i].diag = op_is_diagonal(ops[i]);
+        info[i].chunk = chunkable(ops[i], pp);
+        info[i].hi = pp.hi_diag ? hi_local_choices(ops[i]) : 0;
+    }
+    return info;
+}
+
+Trial greedy_pass(const std::vector<OpInfo> &ops, const std::vector<char> &done, size_t first, int n,
                   const PlanParams &pp, uint64_t allowed) {
     const uint64_t all = (n >= 64) ? ~0ull : ((1ull << n) - 1ull);
     const uint64_t low = (1ull << pp.c) - 1ull;
@@ -141,11 +160,11 @@ Trial greedy_pass(const std::vector<Op> &ops, const std::vector<char> &done, siz
     uint64_t L = low, blocked = 0, blocked_diag = 0;
     for (size_t i = first; i < ops.size(); i++) {
         if (done[i]) continue;
-        const Op &op = ops[i];
-        const uint64_t qm = op.qmask();
-        const bool diag = op_is_diagonal(op);
+        const OpInfo &op = ops[i];
+        const uint64_t qm = op.qm;
+        const bool diag = op.diag;
         const uint64_t blk = diag ? blocked : (blocked | blocked_diag);
-        if (!chunkable(op, pp)) {
+        if (!op.chunk) {
             if (tr.ops.empty() && !(qm & (blocked | blocked_diag))) {
                 tr.stream = true;
                 tr.ops.push_back((int)i);
@@ -160,7 +179,7 @@ Trial greedy_pass(const std::vector<Op> &ops, const std::vector<char> &done, siz
         } else if (!(qm & blk) && pp.hi_diag) {
             // a controlled phase with its control local (already, or added if it fits) and
             // the other qubit a tile constant
-            const uint64_t ch = hi_local_choices(op);
+            const uint64_t ch = op.hi;
             uint64_t q1 = ch & L;
             if (!q1) {
                 const uint64_t cand = ch & (low | allowed);
@@ -189,6 +208,7 @@ std::vector<Pass> make_plan(const std::vector<Op> &ops, int n, const PlanParams 
     const uint64_t all = (n >= 64) ? ~0ull : ((1ull << n) - 1ull);
     const int free_slots = pp.m - pp.c;
     std::vector<char> done(ops.size(), 0);
+    const std::vector<OpInfo> info = op_info(ops, pp);
     size_t first = 0;
     while (first < ops.size()) {
         while (first < ops.size() && done[first]) first++;
@@ -196,11 +216,11 @@ std::vector<Pass> make_plan(const std::vector<Op> &ops, int n, const PlanParams 
         // candidates: unrestricted greedy, and greedy restricted to each window of
         // free_slots consecutive high qubits (chains and brickwork advance further when the
         // local window is chosen, not claimed by the first gates in circuit order)
-        Trial best = greedy_pass(ops, done, first, n, pp, all);
+        Trial best = greedy_pass(info, done, first, n, pp, all);
         if (!best.stream && free_slots > 0 && n > pp.m) {
             for (int s = pp.c; s + free_slots <= n; s++) {
                 const uint64_t win = ((1ull << free_slots) - 1ull) << s;
-                Trial t = greedy_pass(ops, done, first, n, pp, win);
+                Trial t = greedy_pass(info, done, first, n, pp, win);
                 if (!t.stream && t.ops.size() > best.ops.size()) best = std::move(t);
             }
         }
