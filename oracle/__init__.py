@@ -33,16 +33,45 @@ _lib = None
 
 
 def build(force: bool = False) -> str:
-    """Compile ``qs_oracle.c`` into ``libqs_oracle.so`` (plain -O2, one thread)."""
+    """Compile ``qs_oracle.c`` into ``libqs_oracle.so`` (plain -O2; OpenMP when the
+    compiler supports it, else one thread)."""
     if (not force and os.path.exists(_LIB)
             and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC)):
         return _LIB
     tmp = _LIB + f".tmp{os.getpid()}"
-    subprocess.check_call([
-        os.environ.get("CC", "gcc"), "-O2", "-std=c99", "-fPIC", "-shared",
-        "-fcx-limited-range", "-D_GNU_SOURCE", _SRC, "-o", tmp, "-lm"])
+    base = [os.environ.get("CC", "gcc"), "-O2", "-std=c99", "-fPIC", "-shared",
+            "-fcx-limited-range", "-D_GNU_SOURCE", _SRC, "-o", tmp, "-lm"]
+    r = subprocess.run(base[:1] + ["-fopenmp"] + base[1:], capture_output=True, text=True)
+    if r.returncode != 0:
+        subprocess.check_call(base)
     os.replace(tmp, _LIB)
     return _LIB
+
+
+def default_threads() -> int:
+    """Host threads the oracle uses unless told otherwise: QS_ORACLE_THREADS, else every
+    core this process may run on."""
+    env = os.environ.get("QS_ORACLE_THREADS")
+    if env:
+        return max(1, int(env))
+    try:
+        return max(1, len(os.sched_getaffinity(0)))
+    except AttributeError:
+        return max(1, os.cpu_count() or 1)
+
+
+def set_threads(t: int) -> int:
+    """Sets the oracle's thread count; returns the count in effect (1 without OpenMP).
+    Results do not depend on it (bitwise)."""
+    return int(_load().or_set_threads(int(t)))
+
+
+def threads() -> int:
+    return int(_load().or_get_threads())
+
+
+def has_openmp() -> bool:
+    return bool(_load().or_has_openmp())
 
 
 def _load():
@@ -65,6 +94,11 @@ def _load():
         lib.or_expz.argtypes = [dp, ctypes.c_int, dp]
         lib.or_top_k.argtypes = [dp, ctypes.c_int, ctypes.c_long, u64p, dp]
         lib.or_top_k.restype = ctypes.c_int
+        lib.or_set_threads.argtypes = [ctypes.c_int]
+        lib.or_set_threads.restype = ctypes.c_int
+        lib.or_get_threads.restype = ctypes.c_int
+        lib.or_has_openmp.restype = ctypes.c_int
+        lib.or_set_threads(default_threads())
         _lib = lib
     return _lib
 

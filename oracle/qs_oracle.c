@@ -24,12 +24,47 @@
  * Everything is applied gate by gate, in order: no fusion, no reordering, no
  * blocking.  Sums (norm, <Z_i>) use pairwise summation.  Arithmetic is C99
  * double complex.
+ *
+ * Threads (OpenMP, when the compiler has it): the groups of one gate are
+ * independent, so they are split over threads; each group's arithmetic is the
+ * same as with one thread.  The pairwise sums hand whole subtrees of the same
+ * tree to threads and add them in the same order.  Results are therefore bitwise
+ * equal for every thread count (a CPU test checks this).
  */
 #include <complex.h>
 #include <math.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+static int g_threads = 1;
+
+/* Threads used by or_apply_matrix, or_norm and or_expz (1 without OpenMP). */
+int or_set_threads(int t)
+{
+#ifdef _OPENMP
+    g_threads = t < 1 ? 1 : t;
+#else
+    (void)t;
+    g_threads = 1;
+#endif
+    return g_threads;
+}
+
+int or_get_threads(void) { return g_threads; }
+
+/* 1 if this build was compiled with OpenMP. */
+int or_has_openmp(void)
+{
+#ifdef _OPENMP
+    return 1;
+#else
+    return 0;
+#endif
+}
 
 typedef double complex cplx;
 
@@ -136,16 +171,19 @@ int or_gate_matrix(int type, const double *p, double *out_interleaved)
 /* Applies a k-qubit matrix U (row-major 2^k x 2^k, interleaved re/im) on
  * operands q[0..k-1] (q[0] most significant in the group index) to the
  * n-qubit state psi: for every base index x whose operand bits are all zero,
- * gather v_s = psi[x + sum_j bit_j(s) 2^q_j], form U v and scatter it back. */
+ * gather v_s = psi[x + sum_j bit_j(s) 2^q_j], form U v and scatter it back.
+ * The base indices are enumerated as b = 0 .. 2^(n-k)-1 with a zero bit
+ * inserted at each operand position (ascending), which lists each such x once. */
 int or_apply_matrix(double *psi_interleaved, int n, int k, const int *q,
                     const double *u_interleaved)
 {
     cplx *psi = (cplx *)psi_interleaved;
     const cplx *u = (const cplx *)u_interleaved;
-    uint64_t dim = (uint64_t)1 << n, opmask = 0;
-    int G = 1 << k;
+    uint64_t opmask = 0;
+    int G = 1 << k, nt = g_threads, sorted_q[12];
+    int64_t n_base;
     uint64_t *off;
-    cplx *v, *w;
+    cplx *vw;
     if (k < 1 || k > 12 || n < k || n > 40)
         return -1;
     for (int j = 0; j < k; j++) {
@@ -153,11 +191,14 @@ int or_apply_matrix(double *psi_interleaved, int n, int k, const int *q,
             return -1;
         opmask |= (uint64_t)1 << q[j];
     }
+    for (int j = 0, c = 0; j < n; j++)
+        if ((opmask >> j) & 1)
+            sorted_q[c++] = j;
+    n_base = (int64_t)1 << (n - k);
     off = malloc(sizeof(uint64_t) * G);
-    v = malloc(sizeof(cplx) * G);
-    w = malloc(sizeof(cplx) * G);
-    if (!off || !v || !w) {
-        free(off); free(v); free(w);
+    vw = malloc(sizeof(cplx) * 2 * G * (size_t)nt);   /* v and w per thread */
+    if (!off || !vw) {
+        free(off); free(vw);
         return -2;
     }
     for (int s = 0; s < G; s++) {
@@ -166,9 +207,22 @@ int or_apply_matrix(double *psi_interleaved, int n, int k, const int *q,
             if ((s >> (k - 1 - j)) & 1)
                 off[s] |= (uint64_t)1 << q[j];
     }
-    for (uint64_t x = 0; x < dim; x++) {
-        if (x & opmask)
-            continue;
+#ifdef _OPENMP
+#pragma omp parallel for num_threads(nt) schedule(static)
+#endif
+    for (int64_t b = 0; b < n_base; b++) {
+        int t = 0;
+        uint64_t x = (uint64_t)b;
+        cplx *v, *w;
+#ifdef _OPENMP
+        t = omp_get_thread_num();
+#endif
+        v = vw + (size_t)2 * G * t;
+        w = v + G;
+        for (int j = 0; j < k; j++) {   /* insert a zero bit at sorted_q[j] */
+            uint64_t lo = x & (((uint64_t)1 << sorted_q[j]) - 1);
+            x = ((x >> sorted_q[j]) << (sorted_q[j] + 1)) | lo;
+        }
         for (int s = 0; s < G; s++)
             v[s] = psi[x + off[s]];
         for (int r = 0; r < G; r++) {
@@ -180,7 +234,7 @@ int or_apply_matrix(double *psi_interleaved, int n, int k, const int *q,
         for (int s = 0; s < G; s++)
             psi[x + off[s]] = w[s];
     }
-    free(off); free(v); free(w);
+    free(off); free(vw);
     return 0;
 }
 
@@ -246,10 +300,44 @@ static double pw_sum(const cplx *psi, uint64_t lo, uint64_t hi, int bit)
     }
 }
 
+/* The same tree as pw_sum: ranges longer than `grain` are split at the same
+ * midpoint, the left half going to another thread; the two halves are added in
+ * the same order as pw_sum adds them. */
+static double pw_sum_tasks(const cplx *psi, uint64_t lo, uint64_t hi, int bit, int depth)
+{
+    uint64_t mid;
+    double a, b;
+    if (depth <= 0 || hi - lo <= ((uint64_t)1 << 16))
+        return pw_sum(psi, lo, hi, bit);
+    mid = lo + (hi - lo) / 2;
+#ifdef _OPENMP
+#pragma omp task shared(a)
+#endif
+    a = pw_sum_tasks(psi, lo, mid, bit, depth - 1);
+    b = pw_sum_tasks(psi, mid, hi, bit, depth - 1);
+#ifdef _OPENMP
+#pragma omp taskwait
+#endif
+    return a + b;
+}
+
+static double pw_sum_all(const cplx *psi, int n, int bit)
+{
+    double r = 0;
+    if (g_threads <= 1)
+        return pw_sum(psi, 0, (uint64_t)1 << n, bit);
+#ifdef _OPENMP
+#pragma omp parallel num_threads(g_threads)
+#pragma omp single
+#endif
+    r = pw_sum_tasks(psi, 0, (uint64_t)1 << n, bit, 12);
+    return r;
+}
+
 /* Squared norm sum_x |a_x|^2. */
 double or_norm(const double *psi, int n)
 {
-    return pw_sum((const cplx *)psi, 0, (uint64_t)1 << n, -1);
+    return pw_sum_all((const cplx *)psi, n, -1);
 }
 
 /* <psi| Z_i |psi> = sum_x |a_x|^2 (1 - 2 bit_i(x)) for i = 0..n-1 (not divided by
@@ -257,7 +345,7 @@ double or_norm(const double *psi, int n)
 void or_expz(const double *psi, int n, double *out)
 {
     for (int i = 0; i < n; i++)
-        out[i] = pw_sum((const cplx *)psi, 0, (uint64_t)1 << n, i);
+        out[i] = pw_sum_all((const cplx *)psi, n, i);
 }
 
 static const cplx *g_sort_psi;

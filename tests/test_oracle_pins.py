@@ -311,3 +311,30 @@ def test_oracle_rejects_bad_operands():
         oracle.run(psi, 3, [("cnot", (1, 1), ())])
     with pytest.raises(ValueError):
         oracle.run(psi, 3, [("h", (3,), ())])
+
+
+@pytest.mark.parametrize("n", [2, 6, 12, 16])
+def test_threads_are_bitwise_equal_to_one_thread(n):
+    """The threaded oracle (groups of a gate split over threads; whole subtrees of the
+    pairwise sums handed to threads) gives the same bits as one thread: states after a
+    mixed circuit with dense 3-qubit blocks, the norm and every <Z_q>."""
+    psi0 = inputs.gaussian_state(n, seed=40 + n)
+    gates = inputs.random_circuit(n, 60, seed=41)
+    if n >= 3:
+        gates += [("dense", (n - 1, 0, n // 2), inputs.random_unitary(3, seed=42))]
+    gates += inputs.sweep_all(n, count=2)
+    results = []
+    before = oracle.threads()
+    try:
+        for t in (1, 3, 8):
+            oracle.set_threads(t)
+            a = oracle.run(psi0.copy(), n, gates)
+            results.append((a, oracle.norm(a, n), oracle.expz(a, n)))
+    finally:
+        oracle.set_threads(before)
+    a1, n1, e1 = results[0]
+    assert abs(n1 - 1.0) < 1e-12
+    for a, nr, ez in results[1:]:
+        assert np.array_equal(a.view(np.uint64), a1.view(np.uint64))
+        assert np.float64(nr).tobytes() == np.float64(n1).tobytes()
+        assert np.array_equal(ez.view(np.uint64), e1.view(np.uint64))
