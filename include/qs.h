@@ -41,7 +41,7 @@
 extern "C" {
 #endif
 
-#define QS_ABI_VERSION 2
+#define QS_ABI_VERSION 3
 #define QS_MAX_QUBITS 36      /* index arithmetic limit; memory is the real limit */
 #define QS_MAX_GATE_QUBITS 8  /* operands per gate record */
 
@@ -142,6 +142,8 @@ typedef struct {
     double bytes;          /* algorithmic HBM bytes of those launches */
     int64_t tile_sweeps;   /* shared-memory sweeps of the tiles in chunk passes, summed over
                               passes (a register phase is one sweep for all its ops) */
+    int64_t tc_blocks;     /* dense blocks applied on the tensor cores (tcgen05), summed over
+                              passes */
 } qs_stats;
 
 /* ---- library ------------------------------------------------------------------ */
@@ -234,7 +236,8 @@ int qs_renormalize(qs_state *s, double *old_norm);
  * callers that cannot call cudaMalloc, e.g. a host program that has handed all device
  * memory to its own pool allocator, or a latency-critical loop that cannot afford
  * cudaMalloc's implicit device synchronisation.  Same results as qs_expectation_z (FP64,
- * fixed summation order; the block split differs, so the last bits may differ).
+ * fixed summation order): bit for bit up to 30 qubits; at 31 and 32 qubits the state is
+ * split into fewer, larger blocks, so the last bits may differ.
  *   dev_psi   device pointer to 2^n_qubits amplitudes of dtype dt (caller's memory,
  *             16-byte aligned), left unchanged;
  *   stream    cudaStream_t to run on (NULL: legacy default stream); the call waits for it;
@@ -242,7 +245,10 @@ int qs_renormalize(qs_state *s, double *old_norm);
  * Scratch: a file-scope device array of about 2.5 MB that every GPU loading this library
  * holds until process exit; nothing is allocated per call.  The first call on a device
  * looks up that array's device address (cudaGetSymbolAddress), so make it before any
- * stream capture.  All calls share the one array and it keeps the last call's contents;
+ * stream capture.  The address is kept for the life of the process: after a
+ * cudaDeviceReset of that device it is stale, so do not call this entry point again in a
+ * process that has reset the device.  All calls share the one array and it keeps the last
+ * call's contents;
  * every value a call reads it has written itself, so nothing needs clearing, but calls
  * that overlap on the GPU (on different streams or host threads) race.
  * Errors: QS_ERR_INVALID for NULL pointers, an unknown dtype or n_qubits outside 1..32

@@ -898,7 +898,8 @@ __device__ __align__(256) double g_noalloc_scratch[kNoAllocScratchDoubles];
 std::mutex g_noalloc_mu;
 double *g_noalloc_ptr[64] = {nullptr};
 
-// Device address of g_noalloc_scratch on the current device (looked up once per device).
+// Device address of g_noalloc_scratch on the current device (looked up once per device and
+// kept; a cudaDeviceReset of that device would leave the kept address stale).
 double *noalloc_scratch() {
     int dev = 0;
     QS_CUDA(cudaGetDevice(&dev));

@@ -43,8 +43,9 @@ bool chunkable(const Op &op, const PlanParams &pp) {
 }  // namespace
 
 // Launches one chunk pass over lmask applying `fused` (tensor cores where allowed);
-// returns the number of tile sweeps.
-int launch_pass_ops(DeviceState &st, uint64_t lmask, const std::vector<Op> &fused, bool use_tc) {
+// returns the number of tile sweeps and adds the tensor-core blocks to *tc_blocks.
+int launch_pass_ops(DeviceState &st, uint64_t lmask, const std::vector<Op> &fused, bool use_tc,
+                    int64_t *tc_blocks) {
     const int n = st.n;
     int pos[64] = {0};
     int r = 0;
@@ -77,6 +78,7 @@ int launch_pass_ops(DeviceState &st, uint64_t lmask, const std::vector<Op> &fuse
             b_floats = std::max<uint32_t>(b_floats, (uint32_t)(cnt / 2));
             kops.push_back(k);
             any_tc = true;
+            if (tc_blocks) (*tc_blocks)++;
         } else {
             kops.push_back(make_tile_kop(op, pos, mats));
         }
@@ -325,7 +327,7 @@ void run_planned(DeviceState &st, const std::vector<Op> &ops, const qs_options &
             continue;
         }
         const std::vector<Op> fused = pass_program(st, pp, p, ops_r);
-        stats.tile_sweeps += launch_pass_ops(st, p.lmask, fused, pp.tc);
+        stats.tile_sweeps += launch_pass_ops(st, p.lmask, fused, pp.tc, &stats.tc_blocks);
         stats.passes++;
         stats.bytes += 2.0 * B * (double)(1ull << n);
         n_ops += (int64_t)fused.size();

@@ -43,7 +43,8 @@ std::vector<Pass> choose_plan(const std::vector<Op> &ops, int n, const PlanParam
 // ops: the list the pass's indices refer to (choose_plan's merged list where it made one).
 std::vector<Op> pass_program(const DeviceState &st, const PlanParams &pp, const Pass &p, const std::vector<Op> &ops);
 // One chunk pass over lmask applying ops already fused (tensor cores if use_tc).
-int launch_pass_ops(DeviceState &st, uint64_t lmask, const std::vector<Op> &fused, bool use_tc);
+int launch_pass_ops(DeviceState &st, uint64_t lmask, const std::vector<Op> &fused, bool use_tc,
+                    int64_t *tc_blocks = nullptr);
 // Plans `ops` into passes and launches them on st.stream, filling stats.
 void run_planned(DeviceState &st, const std::vector<Op> &ops, const qs_options &o, qs_stats &stats);
 

@@ -21,3 +21,39 @@ def fidelity_gap(a, b):
     b = np.asarray(b, dtype=np.complex128)
     ov = abs(np.vdot(a, b)) ** 2
     return 1.0 - ov / (np.vdot(a, a).real * np.vdot(b, b).real)
+
+
+def _chunks(size, chunk=1 << 22):
+    return [(lo, min(size, lo + chunk)) for lo in range(0, size, chunk)]
+
+
+def _pool():
+    import concurrent.futures as cf
+    import os
+    try:
+        n = len(os.sched_getaffinity(0))
+    except AttributeError:
+        n = os.cpu_count() or 1
+    return cf.ThreadPoolExecutor(max_workers=max(1, n))
+
+
+def compare_large(got, want):
+    """(max-abs error, 1 - fidelity) of a GPU result (complex64 or complex128) against the
+    complex128 oracle state, computed in FP64 over chunks on every host core (numpy releases
+    the GIL), for states too large for one numpy temporary."""
+    assert got.size == want.size
+
+    def part(r):
+        lo, hi = r
+        g = got[lo:hi].astype(np.complex128, copy=False)
+        w = want[lo:hi]
+        return (float(np.max(np.abs(g - w))), complex(np.vdot(w, g)),
+                float(np.vdot(g, g).real), float(np.vdot(w, w).real))
+
+    with _pool() as ex:
+        parts = list(ex.map(part, _chunks(got.size)))
+    err = max(p[0] for p in parts)
+    ov = sum(p[1] for p in parts)
+    ng = sum(p[2] for p in parts)
+    nw = sum(p[3] for p in parts)
+    return err, 1.0 - abs(ov) ** 2 / (ng * nw)

@@ -39,6 +39,7 @@ def test_single_dense_block_fused_mode(qs, k):
     want = oracle.run(psi0.astype(np.complex64).astype(np.complex128), n, gates)
     got, st = run(qs, n, psi0, gates, mode=qs.QS_MODE_FUSED, fuse_k=k)
     assert st["passes"] == 1
+    assert st["tc_blocks"] == 1          # the block ran on the tensor cores
     assert np.max(np.abs(got - want)) <= TOL_C64
     assert fidelity_gap(got, want) <= 1e-6
 
@@ -53,6 +54,7 @@ def test_brickwork_auto_tensor_cores(qs, n, fk):
     assert np.max(np.abs(got - want)) <= TOL_C64
     assert fidelity_gap(got, want) <= 1e-6
     assert st["ops_after_fuse"] < len(gates)
+    assert st["tc_blocks"] > 0
 
 
 @pytest.mark.parametrize("family", ["qaoa", "tfim", "random"])
@@ -66,9 +68,10 @@ def test_families_tensor_cores(qs, family):
         gates = inputs.random_circuit(n, 300, seed=4)
     psi0 = inputs.gaussian_state(n, seed=6)
     want = oracle.run(psi0.astype(np.complex64).astype(np.complex128), n, gates)
-    got, _ = run(qs, n, psi0, gates, fuse_k=5)
+    got, st = run(qs, n, psi0, gates, fuse_k=5)
     assert np.max(np.abs(got - want)) <= TOL_C64
     assert fidelity_gap(got, want) <= 1e-6
+    assert st["tc_blocks"] > 0
 
 
 def test_tensor_core_path_matches_simt_path_24q(qs):
@@ -77,6 +80,7 @@ def test_tensor_core_path_matches_simt_path_24q(qs):
     gates = inputs.brickwork(n, 12, seed=9)
     psi0 = inputs.gaussian_state(n, seed=9)
     a, sa = run(qs, n, psi0, gates, fuse_k=6)
-    b, _ = run(qs, n, psi0, gates, fuse_k=2)
+    b, sb = run(qs, n, psi0, gates, fuse_k=2)
+    assert sa["tc_blocks"] > 0 and sb["tc_blocks"] == 0
     assert np.max(np.abs(a - b)) <= TOL_C64
     assert fidelity_gap(a, b) <= 1e-6
