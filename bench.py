@@ -59,6 +59,10 @@ def parse():
                     help="complex64 passes: one shared-memory sweep per op (no register phases)")
     ap.add_argument("--precision", default="fp64", choices=["fp64", "df32"],
                     help="complex128 arithmetic of the served workload")
+    ap.add_argument("--loads", default="",
+                    help="served: comma-separated offered loads in req/s for a load sweep")
+    ap.add_argument("--no-workloads", action="store_true",
+                    help="gates30: skip the compact summaries of the other workloads")
     return ap.parse_args()
 
 
@@ -229,6 +233,12 @@ def run_ours(args, rank, world, local):
         torch.cuda.synchronize()
         wall = time.perf_counter() - t0
     launches = qs.qs_launch_count() - l0
+    # correctness check of this run: the sweep is unitary, so the squared norm of the
+    # normalised initial state survives the warm-up and timed steps (FP64 rounding only)
+    norm_after = qs.qs_norm(h)
+    check = {"norm_after_timed_steps_minus_1": norm_after - 1.0,
+             "gates_applied": n_gates * (args.warmup + args.steps),
+             "ok": bool(abs(norm_after - 1.0) <= 1e-12)}
     per_type_ms = {name: 0.0 for name in GATE_TYPES}
     total_ms = 0.0
     for s in range(args.steps):
@@ -282,7 +292,6 @@ def run_ours(args, rank, world, local):
     qs.qs_destroy(h)
     del host_in
 
-    # correctness spot check of this run (norm preserved by the unitary sweep)
     out = {
         "metric": METRIC, "value": round(value, 2), "unit": "gates/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_per_step, 3),
@@ -297,6 +306,7 @@ def run_ours(args, rank, world, local):
         "clocks": clk.summary(),
         "gpu_launches": int(launches),
         "wall_s_timed": round(wall, 3),
+        "check": check,
     }
     if e2e:
         out["e2e"] = e2e
@@ -466,29 +476,61 @@ def load_traffic(kernel_gate, n, dtype):
         return None
 
 
+def host_cpu():
+    """CPU model and core count of this host (for the oracle rows)."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    return {"cpu_model": model, "nproc": os.cpu_count()}
+
+
 def cpu_baseline(args, n_gates_sample):
-    """The CPU oracle, as it stands, on the first gate of the first types of the sweep
-    at full size (same qubit count), timed on the host."""
+    """The CPU oracle, as it stands, timed on the host at full size (same qubit count):
+    one thread on the first gates of the first types of the sweep, and every host core
+    (OpenMP over the groups of a gate; bitwise the same result) on the first gate of every
+    type.  The all-cores row is the reported value."""
     import oracle
-    from paper_2409_14697_gb300 import inputs
     n = args.qubits
     sweeps = sweep_gates(n)
-    sample = [sweeps[name][0] for name in GATE_TYPES[:n_gates_sample]]
+    one = [sweeps[name][0] for name in GATE_TYPES[:n_gates_sample]]
+    every = [sweeps[name][0] for name in GATE_TYPES]
     psi = oracle.zero_state(n)
-    t0 = time.perf_counter()
-    oracle.run(psi, n, sample)
-    dt = time.perf_counter() - t0
-    return {"value": round(len(sample) / dt, 4), "unit": "gates/s", "cores": 1, "kind": "oracle",
-            "sample": f"{len(sample)} gates ({', '.join(g[0] for g in sample)}) of the sweep on a "
-                      f"{n}-qubit complex128 state, {dt:.1f} s"}
+    cores = oracle.default_threads()
+    before = oracle.threads()
+    try:
+        oracle.set_threads(1)
+        t0 = time.perf_counter()
+        oracle.run(psi, n, one)
+        dt1 = time.perf_counter() - t0
+        used = oracle.set_threads(cores)
+        t0 = time.perf_counter()
+        oracle.run(psi, n, every)
+        dtn = time.perf_counter() - t0
+    finally:
+        oracle.set_threads(before)
+    return {"value": round(len(every) / dtn, 4), "unit": "gates/s", "cores": used, "kind": "oracle",
+            "sample": f"one gate of each of the 8 types of the sweep on a {n}-qubit complex128 state, "
+                      f"{used} threads, {dtn:.1f} s",
+            **host_cpu(),
+            "single_thread": {"value": round(len(one) / dt1, 4), "unit": "gates/s", "cores": 1,
+                              "sample": f"{len(one)} gates ({', '.join(g[0] for g in one)}) of the sweep, "
+                                        f"{dt1:.1f} s"}}
 
 
 def run_reference(args, rank, world):
+    """The oracle as it stands on every host core, one gate of the sweep per step."""
     import oracle
     n = args.qubits
     sweeps = sweep_gates(n)
     seq = [g for name in GATE_TYPES for g in sweeps[name][:1]]
     psi = oracle.zero_state(n)
+    cores = oracle.threads()
     times = []
     for s in range(args.warmup + args.steps):
         g = seq[s % len(seq)]
@@ -503,8 +545,9 @@ def run_reference(args, rank, world):
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": f"{n}-qubit gate benchmark, c128, 8 gate types x 30 targets, gate-by-gate",
                        "qubits": n},
-            "cpu_baseline": {"value": round(v, 4), "unit": "gates/s", "cores": 1, "kind": "oracle",
-                             "sample": f"one gate per step, cycling {', '.join(GATE_TYPES)}, {n} qubits"},
+            "cpu_baseline": {"value": round(v, 4), "unit": "gates/s", "cores": cores, "kind": "oracle",
+                             "sample": f"one gate per step, cycling {', '.join(GATE_TYPES)}, {n} qubits, "
+                                       f"{cores} threads", **host_cpu()},
             "e2e": {"value": round(v, 4), "unit": "gates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
@@ -571,7 +614,9 @@ def wl_circuits33(args):
             "tfim50": inputs.tfim(n, steps=50, dt=0.05)}
     widths = [args.fuse_k] if args.fuse_k > 0 else [1, 5]
     variants = {}
+    inverse_widths = getattr(args, "inverse_widths", None)
     for k in widths:
+        with_inverse = inverse_widths is None or k in inverse_widths
         tc = "tensor cores" if k >= 4 else ("SIMT" if args.no_rphases else "SIMT, register phases")
         opts = qs.options(fuse_k=k)
         if args.no_rphases:
@@ -587,16 +632,18 @@ def wl_circuits33(args):
             ms = _event_ms(stream, lambda: qs.qs_apply_circuit(h, recs, opts))
             st = qs.qs_last_stats(h)
             nrm = qs.qs_norm(h)
-            qs.qs_apply_circuit(h, inv, opts)
-            a0 = qs.qs_amplitudes(h, 0, 1)[0]
-            nrm2 = qs.qs_norm(h)
             rows[name] = {"gates": len(gates), "ms": round(ms, 2), "passes": st["passes"],
                           "ops_after_fuse": st["ops_after_fuse"],
-                          "tile_sweeps": st["tile_sweeps"],
+                          "tile_sweeps": st["tile_sweeps"], "tc_blocks": st["tc_blocks"],
                           "gates_per_s": round(len(gates) * 1e3 / ms, 1),
                           "pass_GBps": round(st["bytes"] / (ms * 1e-3) / 1e9, 1),
-                          "norm_minus_1": nrm - 1.0, "inverse_infidelity": 1.0 - abs(complex(a0)) ** 2,
-                          "inverse_infidelity_normalised": 1.0 - abs(complex(a0)) ** 2 / nrm2}
+                          "norm_minus_1": nrm - 1.0}
+            if with_inverse:
+                qs.qs_apply_circuit(h, inv, opts)
+                a0 = qs.qs_amplitudes(h, 0, 1)[0]
+                nrm2 = qs.qs_norm(h)
+                rows[name]["inverse_infidelity"] = 1.0 - abs(complex(a0)) ** 2
+                rows[name]["inverse_infidelity_normalised"] = 1.0 - abs(complex(a0)) ** 2 / nrm2
         variants[f"k{k}"] = {"path": f"fused k={k} ({tc})", "circuits": rows}
     qs.qs_destroy(h)
     out = {"workload": f"{n}-qubit circuits, complex64", "qubits": n, "state_bytes": 8 << n}
@@ -778,82 +825,183 @@ def wl_paper(args):
     return out
 
 
-def wl_served(args):
-    """Poisson stream (mean rate --rate req/s) of circuits with n log-uniform in 10..30,
-    complex64 or complex128, each returning <Z_i> for all qubits and the top 1024
-    amplitudes; admission by an HBM budget of 150 GB; against the plain sequential path."""
-    import torch
-    from paper_2409_14697_gb300 import inputs, qs
-    count = args.count or 300
-    reqs = inputs.served_stream(count, rate_hz=args.rate, seed=11)
-    init_cache = {}
+class ServedInputs:
+    """Initial states of the served stream's sweep requests: for each (n, dtype) that occurs,
+    the first 2^n amplitudes of one seeded 30-qubit Gaussian vector (i.i.d. N(0,1) real and
+    imaginary parts), scaled to unit norm in FP64, held in page-locked host memory that the
+    requests borrow (QS_REQ_BORROW_INIT: nothing is copied at submission)."""
 
-    def init_for(r):
-        if not r["init_seed"]:
-            return None, r["gates"]
-        if r["n"] > 24:   # reading: large sweep requests start from H^n|0> built on the device
-            return None, [("h", (q,), ()) for q in range(r["n"])] + r["gates"]
-        key = (r["n"], r["dtype"])
-        if key not in init_cache:
-            init_cache[key] = inputs.gaussian_state(r["n"], seed=r["n"]).astype(
-                np.complex128 if r["dtype"] == "c128" else np.complex64)
-        return init_cache[key], r["gates"]
-    prepared = []
-    for r in reqs:
-        init, gates = init_for(r)
-        dt = qs.QS_C128 if r["dtype"] == "c128" else qs.QS_C64
-        prepared.append((r["t"], r["n"], dt, qs.gate_records(gates), len(gates), init, min(1024, 1 << r["n"])))
-    prec = qs.QS_PREC_DF32 if args.precision == "df32" else qs.QS_PREC_FP64
+    def __init__(self, reqs):
+        import torch
+        from paper_2409_14697_gb300 import inputs
+        need = sorted({(r["n"], r["dtype"]) for r in reqs if r["init_seed"]})
+        self.buf = {}
+        if not need:
+            return
+        top = max(n for n, _ in need)
+        base = inputs.gaussian_state(top, seed=700)   # unit norm over 2^top amplitudes
+        for n, dt in need:
+            part = base[:1 << n]
+            scale = 1.0 / math.sqrt(float(np.vdot(part, part).real))
+            npdt = np.complex128 if dt == "c128" else np.complex64
+            t = torch.empty(np.dtype(npdt).itemsize << n, dtype=torch.uint8, pin_memory=True)
+            v = t.numpy().view(npdt)
+            for lo in range(0, 1 << n, 1 << 24):
+                v[lo:lo + (1 << 24)] = part[lo:lo + (1 << 24)] * scale
+            self.buf[(n, dt)] = t
+        del base
+
+    def ptr(self, r):
+        return self.buf[(r["n"], r["dtype"])].data_ptr() if r["init_seed"] else 0
+
+
+def served_run(qs, prepared, rate, prec):
+    """Submits the prepared requests at their Poisson arrival times (scaled to `rate`) and
+    polls until all are done; returns (latencies, wall seconds, server stats)."""
     sv = qs.qs_server_create(150 * 10 ** 9, max_slots=8)
-    lat, tickets = [], []
-    t0 = time.perf_counter()
+    lat = []
     pending = {}
     i = 0
-    while i < len(prepared) or pending:
-        now = time.perf_counter() - t0
-        while i < len(prepared) and prepared[i][0] <= now:
-            t_arr, n, dt, recs, ng, init, k = prepared[i]
-            tk = qs.qs_submit(sv, n, dt, recs, top_k=k, init=init, precision=prec)
-            pending[tk] = (n, k)
-            i += 1
-        done = []
-        for tk, (n, k) in pending.items():
-            r = qs.qs_poll(sv, tk, n, k)
-            if r is not None:
-                lat.append(r["latency_s"])
-                done.append(tk)
-        for tk in done:
-            del pending[tk]
-        if not done:
-            time.sleep(0.0002)
-    wall = time.perf_counter() - t0
-    st = qs.qs_server_stats(sv)
-    qs.qs_server_destroy(sv)
-    # the plain sequential path: one request after the other through qs_apply_circuit
+    t0 = time.perf_counter()
+    try:
+        while i < len(prepared) or pending:
+            now = time.perf_counter() - t0
+            while i < len(prepared) and prepared[i]["t"] * (2000.0 / rate) <= now:
+                q = prepared[i]
+                tk = qs.qs_submit(sv, q["n"], q["dt"], q["recs"], top_k=q["k"], init_ptr=q["init"],
+                                  precision=prec)
+                pending[tk] = (q["n"], q["k"])
+                i += 1
+            done = []
+            for tk, (n, k) in pending.items():
+                r = qs.qs_poll(sv, tk, n, k)
+                if r is not None:
+                    lat.append(r["latency_s"])
+                    done.append(tk)
+            for tk in done:
+                del pending[tk]
+            if not done:
+                time.sleep(0.0002)
+        wall = time.perf_counter() - t0
+        st = qs.qs_server_stats(sv)
+    finally:
+        qs.qs_server_drain(sv)
+        qs.qs_server_destroy(sv)
+    return np.array(lat), wall, st
+
+
+def served_sequential(qs, prepared, prec):
+    """The plain path: one request after the other through qs_apply_circuit on one state per
+    (n, dtype), with the same initial states, <Z_q> and top-K reads."""
+    import torch
     hs = {}
     t1 = time.perf_counter()
-    for t_arr, n, dt, recs, ng, init, k in prepared:
-        key = (n, dt)
+    for q in prepared:
+        key = (q["n"], q["dt"])
         if key not in hs:
-            hs[key] = qs.qs_create(n, dt)
+            hs[key] = qs.qs_create(q["n"], q["dt"])
         h = hs[key]
-        if init is None:
-            qs.qs_reset(h)
+        if q["init"]:
+            qs.qs_set_amplitudes_from(h, 0, 1 << q["n"], q["init"])
         else:
-            qs.qs_set_amplitudes(h, init)
-        qs.qs_apply_circuit(h, recs, qs.options(precision=prec))
+            qs.qs_reset(h)
+        qs.qs_apply_circuit(h, q["recs"], qs.options(precision=prec))
         qs.qs_expectation_z(h)
-        qs.qs_top_amplitudes(h, k)
-    seq_wall = time.perf_counter() - t1
+        qs.qs_top_amplitudes(h, q["k"])
+    wall = time.perf_counter() - t1
     for h in hs.values():
         qs.qs_destroy(h)
-    lat = np.array(lat)
-    return {"workload": f"served: {count} Poisson requests at {args.rate:g} req/s, n 10-30 log-uniform, "
-                        f"c64/c128 ({args.precision} for c128), <Z_i> + top-1024, 150 GB budget, 8 slots",
-            "metric": "requests/s", "value": round(count / wall, 2), "p50_latency_s": round(float(np.percentile(lat, 50)), 4),
-            "p99_latency_s": round(float(np.percentile(lat, 99)), 4), "mean_latency_s": round(float(lat.mean()), 4),
-            "wall_s": round(wall, 2), "sequential_requests_per_s": round(count / seq_wall, 2),
-            "sequential_wall_s": round(seq_wall, 2), "peak_bytes": st["peak_bytes"], "failed": st["failed"]}
+    torch.cuda.synchronize()
+    return wall
+
+
+def wl_served(args, count=None, loads=None):
+    """Poisson stream of circuits with n log-uniform in 10..30, complex64 or complex128,
+    each returning <Z_i> for all qubits and the top 1024 amplitudes; admission by an HBM
+    budget of 150 GB, 8 slots; sweep requests start from seeded Gaussian states that they
+    borrow from page-locked host memory.  The same requests arrive at each offered load of
+    the sweep (arrival times scaled); the plain sequential path runs them once."""
+    from paper_2409_14697_gb300 import inputs, qs
+    count = count or args.count or 300
+    if loads is None:
+        loads = [float(x) for x in args.loads.split(",") if x] if args.loads else [args.rate]
+    reqs = inputs.served_stream(count, rate_hz=2000.0, seed=11)
+    si = ServedInputs(reqs)
+    prepared = []
+    for r in reqs:
+        prepared.append({"t": r["t"], "n": r["n"], "dt": qs.QS_C128 if r["dtype"] == "c128" else qs.QS_C64,
+                         "recs": qs.gate_records(r["gates"]), "k": min(1024, 1 << r["n"]), "init": si.ptr(r)})
+    prec = qs.QS_PREC_DF32 if args.precision == "df32" else qs.QS_PREC_FP64
+    seq_wall = served_sequential(qs, prepared, prec)
+    rows = {}
+    for rate in loads:
+        lat, wall, st = served_run(qs, prepared, rate, prec)
+        rows[f"{rate:g}"] = {"requests_per_s": round(count / wall, 2),
+                             "p50_latency_s": round(float(np.percentile(lat, 50)), 4),
+                             "p99_latency_s": round(float(np.percentile(lat, 99)), 4),
+                             "mean_latency_s": round(float(lat.mean()), 4), "wall_s": round(wall, 2),
+                             "peak_bytes": st["peak_bytes"], "failed": st["failed"]}
+    main = rows[f"{loads[0]:g}"]
+    return {"workload": f"served: {count} Poisson requests, n 10-30 log-uniform, c64/c128 "
+                        f"({args.precision} for c128), <Z_i> + top-1024, 150 GB budget, 8 slots; "
+                        f"sweep requests from borrowed page-locked Gaussian states",
+            "metric": "requests/s", "value": main["requests_per_s"], "offered_req_per_s": loads[0],
+            "p50_latency_s": main["p50_latency_s"], "p99_latency_s": main["p99_latency_s"],
+            "sequential_requests_per_s": round(count / seq_wall, 2), "sequential_wall_s": round(seq_wall, 2),
+            "loads": rows}
+
+
+def workload_summaries(args):
+    """Compact, bounded runs of the other configurations for the default bench line: the
+    12-qubit circuit, the 33-qubit circuits, the batched launch and the served stream."""
+    import copy
+    out = {}
+
+    def timed(name, fn):
+        t0 = time.perf_counter()
+        try:
+            out[name] = fn()
+        except Exception as e:  # a failing summary must not hide the headline
+            out[name] = {"error": f"{type(e).__name__}: {e}"}
+        out[name]["bench_s"] = round(time.perf_counter() - t0, 1)
+
+    def c12():
+        r = wl_circuit12(args)
+        return {"workload": r["workload"], "circuits_per_s": r["planned"]["circuits_per_s"],
+                "gate_by_gate_circuits_per_s": r["gate_by_gate"]["circuits_per_s"],
+                "max_abs_err_vs_oracle": max(r["planned"]["max_abs_err_vs_oracle"],
+                                             r["gate_by_gate"]["max_abs_err_vs_oracle"]),
+                "passes": r["planned"]["passes"]}
+
+    def c33():
+        a = copy.copy(args)
+        a.qubits, a.fuse_k, a.inverse_widths = 33, 0, (1,)
+        r = wl_circuits33(a)
+        res = {"workload": r["workload"]}
+        for key, v in r["variants"].items():
+            res[key] = {"path": v["path"]}
+            for fam, row in v["circuits"].items():
+                res[key][fam] = {x: row[x] for x in ("ms", "passes", "pass_GBps", "gates", "tc_blocks",
+                                                      "norm_minus_1", "inverse_infidelity_normalised")
+                                 if x in row}
+        return res
+
+    def batched():
+        a = copy.copy(args)
+        a.count = 4096
+        r = wl_batched(a)
+        return {x: r[x] for x in ("workload", "value", "one_at_a_time_circuits_per_s", "speedup_vs_one_at_a_time",
+                                  "max_abs_err", "max_infidelity", "autotuned")}
+
+    def served():
+        r = wl_served(args, count=120, loads=[2000.0, 8.0])
+        return r
+
+    timed("circuit12", c12)
+    timed("circuits33", c33)
+    timed("batched", batched)
+    timed("served", served)
+    return out
 
 
 def run_workload(args):
@@ -887,6 +1035,8 @@ def main():
     if rank == 0:
         if not args.no_cpu and world == 1:
             out["cpu_baseline"] = cpu_baseline(args, args.cpu_sample_gates)
+        if not args.no_workloads and world == 1 and args.qubits == N_QUBITS:
+            out["workloads"] = workload_summaries(args)
         print(json.dumps(out))
     if world > 1:
         import torch.distributed as dist

@@ -115,10 +115,20 @@ enum {
     QS_OPT_NO_DIAG_MERGE = 2,   /* QS_MODE_AUTO / QS_MODE_CHUNK: never merge runs of diagonal
                                    gates into one phase-function pass (by default both plans are
                                    built and the one with fewer passes over the state runs) */
-    QS_OPT_NO_TC_NORM_FIX = 4   /* no norm-preserving correction after complex64 circuits that
+    QS_OPT_NO_TC_NORM_FIX = 4,  /* no norm-preserving correction after complex64 circuits that
                                    used tensor-core blocks (by default the squared norm before
                                    the circuit is restored, removing the small systematic shrink
                                    of FP32 accumulation inside the MMA) */
+    QS_OPT_NO_TPB = 8           /* QS_MODE_AUTO / QS_MODE_CHUNK: no Tensor Product Booster.  By
+                                   default (states of 20 qubits or more) a call on a state that
+                                   holds |0...0> (after qs_create or qs_reset, before anything
+                                   else writes it) builds the longest prefix of the circuit whose
+                                   gates keep the qubits in independent groups as a tensor
+                                   product of the groups' small sub-states, in one write pass,
+                                   when that saves passes (Sec. III-A tier 1).  Amplitudes
+                                   written through the device pointer of qs_info are not seen:
+                                   call qs_set_amplitudes, or pass this flag, after such
+                                   writes. */
 };
 
 /* Options for qs_apply_circuit; pass NULL for defaults.  Zero fields mean "choose". */
@@ -144,6 +154,7 @@ typedef struct {
                               passes (a register phase is one sweep for all its ops) */
     int64_t tc_blocks;     /* dense blocks applied on the tensor cores (tcgen05), summed over
                               passes */
+    int64_t tpb_gates;     /* gates built by the Tensor Product Booster (QS_OPT_NO_TPB) */
 } qs_stats;
 
 /* ---- library ------------------------------------------------------------------ */
@@ -271,16 +282,28 @@ typedef struct {
     int32_t reserved[5];
 } qs_server_config;
 
+/* Bits of qs_request.flags. */
+enum {
+    QS_REQ_BORROW_INIT = 1  /* init_amplitudes is not copied at submission: the caller keeps
+                               the buffer alive and unchanged until qs_poll has returned QS_OK
+                               (or an error) for the ticket, and the request's stream copies
+                               straight from it when the request starts.  Several requests may
+                               borrow one buffer.  A page-locked buffer (cudaHostAlloc,
+                               cudaHostRegister) keeps that copy asynchronous on the copy
+                               engines; pageable memory makes the worker wait for it. */
+};
+
 typedef struct {
     int32_t n_qubits;
     int32_t dtype;                 /* QS_C64 or QS_C128 */
     const qs_gate *gates;          /* copied by qs_submit */
     uint64_t n_gates;
-    const void *init_amplitudes;   /* 2^n amplitudes of dtype (copied), or NULL for |0...0> */
+    const void *init_amplitudes;   /* 2^n amplitudes of dtype (copied unless borrowed, see
+                                      QS_REQ_BORROW_INIT), or NULL for |0...0> */
     uint32_t top_k;                /* amplitudes to return, <= min(2^n, 4096) */
     int32_t mode;                  /* QS_MODE_* for the circuit */
     int32_t precision;             /* QS_PREC_* for complex128 requests */
-    int32_t reserved;
+    uint32_t flags;                /* QS_REQ_* bits (0: copy init_amplitudes at submission) */
 } qs_request;
 
 typedef struct {

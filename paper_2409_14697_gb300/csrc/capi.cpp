@@ -174,14 +174,17 @@ void run_circuit(DeviceState &d, const std::vector<Op> &ops, const qs_options &o
         }
     } catch (...) {
         arena_end(d);
+        d.known_zero = false;
         throw;
     }
     arena_end(d);
+    if (!ops.empty()) d.known_zero = false;
     st.launches = (int64_t)(g_launches.load() - l0);
 }
 
 void free_device_state(DeviceState &d) {
     if (d.stream) cudaStreamSynchronize(d.stream);
+    tpb_free(d);
     for (int c = 0; c < kArenas; c++) {
         if (d.arena_dev[c]) cudaFree(d.arena_dev[c]);
         if (d.arena_host[c]) cudaFreeHost(d.arena_host[c]);

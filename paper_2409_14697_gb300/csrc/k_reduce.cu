@@ -638,9 +638,11 @@ void launch_set_zero_state(DeviceState &st) {
     k_set_one<<<1, 1, 0, st.stream>>>(st.psi, st.dtype == QS_C128);
     QS_CUDA(cudaGetLastError());
     count_launch();
+    st.known_zero = true;
 }
 
 void launch_scale(DeviceState &st, double f) {
+    st.known_zero = false;
     const uint64_t n = 1ull << st.n;
     const int grid = (int)std::min<uint64_t>((n + 255) / 256, (uint64_t)device_sm_count() * 8);
     if (st.dtype == QS_C128) k_scale<double2, double><<<grid, 256, 0, st.stream>>>((double2 *)st.psi, n, f);
@@ -686,6 +688,7 @@ const void *mapped_range(const void *p, size_t bytes) {
 }  // namespace
 
 void copy_host(DeviceState &st, void *dst, const void *src, size_t bytes, bool to_device, int ctas) {
+    if (to_device) st.known_zero = false;
     if (bytes == 0) return;
     constexpr size_t kMinKernelBytes = 4u << 20;
     const void *host = to_device ? src : dst;

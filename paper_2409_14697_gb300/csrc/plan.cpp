@@ -21,6 +21,7 @@
 #include "kgeom.h"
 #include "phasefn.h"
 #include "plan.h"
+#include "tpb.h"
 
 namespace qs {
 
@@ -305,8 +306,30 @@ void run_planned(DeviceState &st, const std::vector<Op> &ops, const qs_options &
     }
     std::vector<Op> merged;
     std::vector<std::pair<size_t, size_t>> origin;
-    const std::vector<Pass> plan = choose_plan(ops, n, pp, o, merged, origin);
-    const std::vector<Op> &ops_r = merged.empty() ? ops : merged;
+    std::vector<Pass> plan = choose_plan(ops, n, pp, o, merged, origin);
+    // Tensor Product Booster: on a |0...0> state, the prefix whose gates keep the qubits in
+    // independent groups is built in one write pass, if the rest then needs fewer passes
+    // (the booster's pass counted as one)
+    std::vector<Op> rest;
+    const std::vector<Op> *src = &ops;
+    if (st.known_zero && n >= kTpbMinQubits && (o.flags & QS_OPT_NO_TPB) == 0) {
+        const TpbPlan tp = tpb_find(ops, n);
+        if (!tp.taken.empty()) {
+            std::vector<Op> r = tpb_rest(ops, tp);
+            std::vector<Op> m2;
+            std::vector<std::pair<size_t, size_t>> o2;
+            std::vector<Pass> p2 = choose_plan(r, n, pp, o, m2, o2);
+            if (p2.size() + 1 <= plan.size()) {
+                tpb_execute(st, ops, tp, o, stats);
+                rest = std::move(r);
+                src = &rest;
+                plan = std::move(p2);
+                merged = std::move(m2);
+                origin = std::move(o2);
+            }
+        }
+    }
+    const std::vector<Op> &ops_r = merged.empty() ? *src : merged;
     // Tensor-core blocks accumulate in FP32 inside the MMA with truncation toward zero, a
     // small systematic shrink per block.  The circuit is unitary, so the FP64 squared norm
     // before it is restored afterwards (three extra read passes and one write pass).

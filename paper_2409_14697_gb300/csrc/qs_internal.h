@@ -156,6 +156,9 @@ struct StreamGeom {
 // many calls on a state whose stream waits for other work without stalling.
 constexpr int kArenas = 16;
 
+// Tensor Product Booster: most groups of one product pass (k_tpb.cu, tpb.cpp).
+constexpr int kTpbMaxGroups = 4;
+
 struct DeviceState {
     void *psi = nullptr;  // amplitudes
     int n = 0;            // qubits
@@ -179,12 +182,21 @@ struct DeviceState {
     int *dev_err = nullptr;
     // two FP64 squared norms (before / after) for the norm-preserving correction
     double *dev_norms = nullptr;
+    // the amplitudes are |0...0> (set by launch_set_zero_state; cleared by every other
+    // write): qs_apply_circuit may then build a prefix as a tensor product
+    bool known_zero = false;
+    // Tensor Product Booster: group sub-states (small states of their own) and their memory
+    DeviceState *tpb_sub[kTpbMaxGroups] = {};
+    void *tpb_buf = nullptr;
+    size_t tpb_buf_bytes = 0;
 };
 
 // Executor: runs one lowered circuit on d.stream (mode, fusion and planning from o).
 void run_circuit(DeviceState &d, const std::vector<Op> &ops, const qs_options &o, qs_stats &st);
 // Frees everything DeviceState owns except psi and the stream.
 void free_device_state(DeviceState &d);
+// Frees the booster's sub-states and memory (part of free_device_state).
+void tpb_free(DeviceState &d);
 void arena_begin(DeviceState &st);
 void arena_end(DeviceState &st);
 
@@ -192,6 +204,8 @@ void arena_end(DeviceState &st);
 void launch_stream_op(DeviceState &st, const Op &op);           // K1, one op, one pass
 void launch_phasefn(DeviceState &st, const Op &op);             // merged diagonal run, one pass
 void launch_set_zero_state(DeviceState &st);                    // |0..0>
+// psi[x] = prod_g tables[g][pext(x, masks[g])]: one write pass (masks partition the qubits)
+void launch_tpb_product(DeviceState &st, const void *const *tables, const uint64_t *masks, int groups);
 void launch_scale(DeviceState &st, double f);                   // psi *= f
 // Reductions (K4).  expz may be null (norm only).  Results are copied to host.
 void reduce_expz(DeviceState &st, double *norm, double *expz);

@@ -38,7 +38,8 @@ struct Request {
     int n;
     int dtype;
     std::vector<Op> ops;
-    std::vector<char> init;  // host amplitudes (empty: |0...0>)
+    std::vector<char> init;  // host amplitudes copied at submission (empty: none)
+    const void *init_borrowed = nullptr;  // caller's amplitudes (QS_REQ_BORROW_INIT)
     uint32_t top_k;
     qs_options opt;
     Clock::time_point t_submit;
@@ -126,7 +127,10 @@ void Server::start_request(Slot &s, Request &r) {
     d.dtype = r.dtype;
     const size_t state_bytes = r.bytes;
     QS_CUDA(cudaMallocFromPoolAsync(&d.psi, state_bytes, pool, d.stream));
-    if (r.init.empty()) {
+    d.known_zero = false;
+    if (r.init_borrowed) {
+        QS_CUDA(cudaMemcpyAsync(d.psi, r.init_borrowed, state_bytes, cudaMemcpyHostToDevice, d.stream));
+    } else if (r.init.empty()) {
         launch_set_zero_state(d);
     } else {
         if (s.h_init_cap < state_bytes) {
@@ -327,7 +331,10 @@ int qs_submit(qs_server *p, const qs_request *req, uint64_t *ticket) {
         }
         r.ops.push_back(lower_gate(req->gates[g]));
     }
-    if (req->init_amplitudes) {
+    if (req->flags & ~(uint32_t)QS_REQ_BORROW_INIT) fail(QS_ERR_INVALID, "unknown request flags");
+    if (req->init_amplitudes && (req->flags & QS_REQ_BORROW_INIT)) {
+        r.init_borrowed = req->init_amplitudes;
+    } else if (req->init_amplitudes) {
         r.init.resize(r.bytes);
         std::memcpy(r.init.data(), req->init_amplitudes, r.bytes);
     }

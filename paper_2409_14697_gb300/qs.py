@@ -21,7 +21,8 @@ QS_OK, QS_NOT_READY = 0, 1
 QS_ERR_INVALID, QS_ERR_NOMEM, QS_ERR_CUDA, QS_ERR_TIMEOUT, QS_ERR_BUSY, QS_ERR_UNSUPPORTED = -1, -2, -3, -4, -5, -6
 QS_MODE_AUTO, QS_MODE_GATE, QS_MODE_CHUNK, QS_MODE_FUSED = 0, 1, 2, 3
 QS_PREC_DEFAULT, QS_PREC_FP64, QS_PREC_DF32 = 0, 1, 2
-QS_OPT_NO_REG_PHASES, QS_OPT_NO_DIAG_MERGE, QS_OPT_NO_TC_NORM_FIX = 1, 2, 4
+QS_OPT_NO_REG_PHASES, QS_OPT_NO_DIAG_MERGE, QS_OPT_NO_TC_NORM_FIX, QS_OPT_NO_TPB = 1, 2, 4, 8
+QS_REQ_BORROW_INIT = 1
 
 GATE_TYPES = {
     "h": 0, "x": 1, "y": 2, "z": 3, "s": 4, "t": 5,
@@ -50,7 +51,7 @@ class qs_options(ctypes.Structure):
 class qs_stats(ctypes.Structure):
     _fields_ = [("gates_in", ctypes.c_int64), ("ops_after_fuse", ctypes.c_int64),
                 ("passes", ctypes.c_int64), ("launches", ctypes.c_int64), ("bytes", ctypes.c_double),
-                ("tile_sweeps", ctypes.c_int64), ("tc_blocks", ctypes.c_int64)]
+                ("tile_sweeps", ctypes.c_int64), ("tc_blocks", ctypes.c_int64), ("tpb_gates", ctypes.c_int64)]
 
 
 class qs_circuit(ctypes.Structure):
@@ -72,7 +73,7 @@ class qs_request(ctypes.Structure):
     _fields_ = [("n_qubits", ctypes.c_int32), ("dtype", ctypes.c_int32),
                 ("gates", ctypes.POINTER(qs_gate)), ("n_gates", ctypes.c_uint64),
                 ("init_amplitudes", ctypes.c_void_p), ("top_k", ctypes.c_uint32), ("mode", ctypes.c_int32),
-                ("precision", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("precision", ctypes.c_int32), ("flags", ctypes.c_uint32)]
 
 
 class qs_server_stats_t(ctypes.Structure):
@@ -339,8 +340,10 @@ def qs_server_create(hbm_budget_bytes: int, max_slots: int = 8):
 
 
 def qs_submit(sv, n_qubits: int, dtype: int, gates, top_k: int = 0, init=None, mode: int = QS_MODE_AUTO,
-              precision: int = QS_PREC_DEFAULT):
-    """Queues a request; returns its ticket (the library copies gates and init)."""
+              precision: int = QS_PREC_DEFAULT, init_ptr: int = 0):
+    """Queues a request; returns its ticket (the library copies gates and init).  init_ptr:
+    host address of 2^n amplitudes that the request borrows (QS_REQ_BORROW_INIT): keep that
+    buffer alive and unchanged until the ticket has been polled to completion."""
     recs = gates if isinstance(gates, ctypes.Array) else gate_records(gates)
     r = qs_request()
     r.n_qubits, r.dtype = n_qubits, dtype
@@ -349,6 +352,9 @@ def qs_submit(sv, n_qubits: int, dtype: int, gates, top_k: int = 0, init=None, m
     if init is not None:
         init = np.ascontiguousarray(init, dtype=np.complex64 if dtype == QS_C64 else np.complex128)
         r.init_amplitudes = init.ctypes.data
+    elif init_ptr:
+        r.init_amplitudes = init_ptr
+        r.flags = QS_REQ_BORROW_INIT
     r.top_k, r.mode, r.precision = top_k, mode, precision
     t = ctypes.c_uint64()
     _check(load().qs_submit(sv, ctypes.byref(r), ctypes.byref(t)))

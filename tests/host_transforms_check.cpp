@@ -30,6 +30,7 @@
 #include "phasefn.h"
 #include "plan.h"
 #include "qs_internal.h"
+#include "tpb.h"
 
 namespace qs {
 void fail(int code, const std::string &msg) { throw Error{code, msg}; }
@@ -51,6 +52,14 @@ void build_tc_operand(const std::vector<cd> &, int, std::vector<float> &, int &,
 }
 // states of at least 9 qubits (the phase-function pass works in units of 2^9 amplitudes)
 bool phasefn_supported(int n) { return n >= 9; }
+void launch_set_zero_state(DeviceState &) { fail(QS_ERR_INVALID, "no GPU in this check"); }
+void launch_tpb_product(DeviceState &, const void *const *, const uint64_t *, int) {
+    fail(QS_ERR_INVALID, "no GPU in this check");
+}
+void run_circuit(DeviceState &, const std::vector<Op> &, const qs_options &, qs_stats &) {
+    fail(QS_ERR_INVALID, "no GPU in this check");
+}
+void free_device_state(DeviceState &) {}
 }  // namespace qs
 
 using namespace qs;
@@ -576,6 +585,100 @@ int print_lowered_gates() {
     return 0;
 }
 
+// Tensor Product Booster host logic: on |0...0>, the prefix tpb_find takes, built as the
+// tensor product of the groups' sub-states (each from its relabelled ops, tpb_group_ops),
+// followed by the ops it leaves (tpb_rest), must give the circuit's state; the plan must
+// keep its limits (components, groups) and take no op that shares a qubit with an earlier
+// op left out.
+int g_tpb_taken = 0;
+
+void check_tpb(std::mt19937_64 &g, int n, int mix, double tol, int trial) {
+    std::uniform_real_distribution<double> ang(0.0, 2.0 * M_PI);
+    std::vector<Op> ops;
+    // a product-friendly start: one-qubit layer, then gates on neighbouring pairs
+    for (int q = 0; q < n; q++) {
+        qs_gate r{};
+        r.type = (trial & 1) ? QS_H : QS_U3;
+        r.nq = 1;
+        r.q[0] = q;
+        for (double &p : r.p) p = ang(g);
+        ops.push_back(lower_gate(r));
+    }
+    for (int e = 0; e < n; e++) {
+        qs_gate r{};
+        const int types[4] = {QS_CZ, QS_CNOT, QS_RZZ, QS_CU3};
+        r.type = types[g() % 4];
+        r.nq = 2;
+        r.q[0] = (int)(g() % n);
+        r.q[1] = (r.q[0] + 1 + (int)(g() % 2)) % n;
+        for (double &p : r.p) p = ang(g);
+        ops.push_back(lower_gate(r));
+    }
+    const std::vector<Op> tail = random_ops(g, n, 40, 0, mix);
+    ops.insert(ops.end(), tail.begin(), tail.end());
+    State zero((size_t)1 << n, 0.0);
+    zero[0] = 1.0;
+    const State ref = run(zero, ops);
+    const uint64_t all = (1ull << n) - 1ull;
+    for (const auto &lim : std::vector<std::pair<int, int>>{{1, 3}, {2, 4}, {3, 5}, {4, 6}, {14, 17}}) {
+        const TpbPlan tp = tpb_find(ops, n, lim.first, lim.second);
+        if (tp.taken.empty()) continue;
+        g_tpb_taken += (int)tp.taken.size();
+        uint64_t cover = 0;
+        bool ok = (int)tp.group_mask.size() <= kTpbMaxGroups && tp.group_ops.size() == tp.group_mask.size();
+        for (uint64_t gm : tp.group_mask) {
+            ok &= (cover & gm) == 0 && __builtin_popcountll(gm) <= lim.second;
+            cover |= gm;
+        }
+        check(ok && cover == all, "booster groups do not partition the qubits within their limit", trial);
+        std::vector<char> taken(ops.size(), 0);
+        for (int i : tp.taken) taken[i] = 1;
+        uint64_t left = 0;
+        int comp[64];
+        for (int q = 0; q < n; q++) comp[q] = q;
+        for (size_t i = 0; i < ops.size(); i++) {
+            const uint64_t qm = ops[i].qmask();
+            if (!taken[i]) {
+                left |= qm;
+                continue;
+            }
+            check((qm & left) == 0, "booster took an op past an earlier op it left out", trial);
+            int within = 0;
+            for (uint64_t gm : tp.group_mask) within += (qm & gm) == qm;
+            check(within == 1, "booster op spans groups", trial);
+            const int c0 = comp[ops[i].q[0]];
+            for (int j = 1; j < ops[i].k; j++) {
+                const int cj = comp[ops[i].q[j]];
+                for (int q = 0; q < n; q++)
+                    if (comp[q] == cj) comp[q] = c0;
+            }
+        }
+        for (int q = 0; q < n; q++) {
+            int sz = 0;
+            for (int p = 0; p < n; p++) sz += comp[p] == comp[q];
+            check(sz <= lim.first, "booster component above its limit", trial);
+        }
+        // the product state, then the rest
+        std::vector<State> subs;
+        for (size_t gi = 0; gi < tp.group_mask.size(); gi++) {
+            State s0((size_t)1 << __builtin_popcountll(tp.group_mask[gi]), 0.0);
+            s0[0] = 1.0;
+            subs.push_back(run(s0, tpb_group_ops(ops, tp, (int)gi, n)));
+        }
+        State psi((size_t)1 << n);
+        for (uint64_t x = 0; x <= all; x++) {
+            cd a = 1.0;
+            for (size_t gi = 0; gi < subs.size(); gi++) {
+                uint64_t idx = 0, m = tp.group_mask[gi];
+                for (int o = 0; m; o++, m &= m - 1) idx |= ((x >> __builtin_ctzll(m)) & 1ull) << o;
+                a *= subs[gi][idx];
+            }
+            psi[x] = a;
+        }
+        check(rel_err(ref, run(psi, tpb_rest(ops, tp))) < tol, "tensor-product prefix + rest", trial);
+    }
+}
+
 int main(int argc, char **argv) {
     if (argc > 1 && std::string(argv[1]) == "--gates") return print_lowered_gates();
     const int seed = argc > 1 ? std::atoi(argv[1]) : 1;
@@ -659,15 +762,18 @@ int main(int argc, char **argv) {
                 for (int prec : {QS_PREC_FP64, QS_PREC_DF32})
                     check_planned(q0, ref2, n2, ops2, 6, prec, QS_MODE_AUTO, tol, trial);
             }
+            check_tpb(g, n, mix, tol, trial);
         } catch (const Error &e) {
             std::printf("FAIL trial %d: error %d %s\n", trial, e.code, e.msg.c_str());
             g_bad++;
         }
     }
+    if (trials >= 2) check(g_tpb_taken > 0, "booster never took an op", -1);
     // QFT-like circuits must have exercised the join
     if (trials >= 2) check(g_joins > 0, "no Hadamard joined with its controlled block", -1);
         if (trials >= 4) check(g_planned_terms > 0 && g_phasefns > 0, "planned path not exercised", -1);
-    std::printf("%s (%d trials, %d joined Hadamards, %d planned passes, %d non-local terms, %d phase functions)\n",
-                g_bad ? "FAIL" : "OK", trials, g_joins, g_planned_passes, g_planned_terms, g_phasefns);
+    std::printf("%s (%d trials, %d joined Hadamards, %d planned passes, %d non-local terms, %d phase functions, "
+                "%d booster ops)\n",
+                g_bad ? "FAIL" : "OK", trials, g_joins, g_planned_passes, g_planned_terms, g_phasefns, g_tpb_taken);
     return g_bad ? 1 : 0;
 }

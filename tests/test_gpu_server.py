@@ -113,3 +113,39 @@ def test_error_paths(qs):
     finally:
         qs.qs_server_drain(sv)
         qs.qs_server_destroy(sv)
+
+
+def test_borrowed_initial_amplitudes(qs):
+    """Requests that borrow the caller's initial amplitudes (QS_REQ_BORROW_INIT, no copy at
+    submission): several requests share one page-locked buffer and one pageable buffer;
+    results are bitwise those of requests whose amplitudes were copied, and match the
+    oracle."""
+    torch = pytest.importorskip("torch")
+    n, k = 18, 16
+    psi = inputs.gaussian_state(n, seed=77)
+    pinned = torch.empty(psi.view(np.float64).size, dtype=torch.float64, pin_memory=True)
+    pinned.numpy()[:] = psi.view(np.float64)
+    pageable = psi.copy()
+    circuits = [inputs.gate_sweep(n, g, seed=9, count=30) for g in ("u3", "cnot", "h", "cu3")]
+    sv = qs.qs_server_create(4 << 30, max_slots=4)
+    try:
+        tickets = []
+        for i, g in enumerate(circuits):
+            ptr = pinned.data_ptr() if i % 2 == 0 else pageable.ctypes.data
+            tickets.append(qs.qs_submit(sv, n, 2, g, top_k=k, init_ptr=ptr))
+        borrowed = [wait(qs, sv, t, n, k) for t in tickets]
+        copied = [wait(qs, sv, qs.qs_submit(sv, n, 2, g, top_k=k, init=psi), n, k) for g in circuits]
+        with pytest.raises(qs.QsError) as e:          # unknown flag bits are rejected
+            r = qs.qs_request()
+            r.n_qubits, r.dtype, r.flags = n, 2, 8
+            t = qs.ctypes.c_uint64()
+            qs._check(qs.load().qs_submit(sv, qs.ctypes.byref(r), qs.ctypes.byref(t)))
+        assert e.value.code == qs.QS_ERR_INVALID
+    finally:
+        qs.qs_server_drain(sv)
+        qs.qs_server_destroy(sv)
+    for g, a, b in zip(circuits, borrowed, copied):
+        assert np.array_equal(a["expz"], b["expz"]) and a["norm"] == b["norm"]
+        assert np.array_equal(a["top_idx"], b["top_idx"]) and np.array_equal(a["top_amp"], b["top_amp"])
+        want = oracle.run(psi.copy(), n, g)
+        assert np.max(np.abs(a["expz"] - oracle.expz(want, n))) <= 1e-12

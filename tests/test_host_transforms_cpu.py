@@ -1,6 +1,7 @@
 """CPU test of the host rewrites the executor applies before its kernels run (global-phase
 fold, deferred Hadamard scale, gate fusion, U3 split, diagonal merge with non-local
-controlled phases, and their chunk-pass order): builds ``host_transforms_check.cpp``
+controlled phases, their chunk-pass order, and the Tensor Product Booster's prefix and
+groups): builds ``host_transforms_check.cpp``
 against the package's host sources with g++ and runs it on seeded random circuits.  Each
 rewrite must leave a 10-qubit state unchanged to 1e-12 and keep the limits the kernels
 rely on; the resulting tile programs (kernel ops on tile positions, with non-local terms
@@ -49,7 +50,7 @@ def checker(tmp_path_factory):
         pytest.skip("the CUDA runtime library is not available")
     exe = tmp_path_factory.mktemp("host_transforms") / "host_transforms_check"
     srcs = [ROOT / "tests" / "host_transforms_check.cpp"] + \
-        [CSRC / f for f in ("ir.cpp", "kgeom.cpp", "plan.cpp", "phasefn.cpp")]
+        [CSRC / f for f in ("ir.cpp", "kgeom.cpp", "plan.cpp", "phasefn.cpp", "tpb.cpp")]
     cmd = [gxx, "-O1", "-std=c++17", f"-I{CSRC}", f"-I{ROOT / 'include'}", f"-I{inc}",
            *map(str, srcs), f"-L{lib}", "-lcudart", f"-Wl,-rpath,{lib}", "-o", str(exe)]
     r = subprocess.run(cmd, capture_output=True, text=True, timeout=300)
