@@ -63,6 +63,8 @@ def parse():
                     help="served: comma-separated offered loads in req/s for a load sweep")
     ap.add_argument("--no-workloads", action="store_true",
                     help="gates30: skip the compact summaries of the other workloads")
+    ap.add_argument("--families", default="brickwork40,qaoa_p4,tfim50",
+                    help="circuits33: comma-separated circuit families to run")
     return ap.parse_args()
 
 
@@ -266,7 +268,8 @@ def run_ours(args, rank, world, local):
     if fp64 and fp64["frac"] > hbm["frac"]:
         roof = {"kernel": f"k_stream[{dom}]", "bound": "alu", "achieved": fp64["achieved"],
                 "peak": fp64["peak"], "unit": fp64["unit"], "frac": fp64["frac"],
-                "peak_source": fp64["peak_source"], "traffic": traffic, "hbm": hbm}
+                "peak_source": fp64["peak_source"], "dgemm_measured_peak": fp64["dgemm_measured_peak"],
+                "frac_of_dgemm": fp64["frac_of_dgemm"], "traffic": traffic, "hbm": hbm}
     else:
         roof = {"kernel": f"k_stream[{dom}]", "bound": "hbm", "achieved": hbm["achieved"], "peak": peak,
                 "peak_kind": peak_kind, "unit": "GB/s", "frac": hbm["frac"], "traffic": traffic}
@@ -645,6 +648,7 @@ def wl_circuits33(args):
     qs.qs_set_stream(h, stream.cuda_stream)
     fams = {"brickwork40": inputs.brickwork(n, 40, seed=3), "qaoa_p4": inputs.qaoa_3regular(n, p=4, seed=3),
             "tfim50": inputs.tfim(n, steps=50, dt=0.05)}
+    fams = {k: v for k, v in fams.items() if k in args.families.split(",")}
     widths = [args.fuse_k] if args.fuse_k > 0 else [1, 5]
     variants = {}
     inverse_widths = getattr(args, "inverse_widths", None)

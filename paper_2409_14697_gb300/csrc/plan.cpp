@@ -308,8 +308,9 @@ void run_planned(DeviceState &st, const std::vector<Op> &ops, const qs_options &
     std::vector<std::pair<size_t, size_t>> origin;
     std::vector<Pass> plan = choose_plan(ops, n, pp, o, merged, origin);
     // Tensor Product Booster: on a |0...0> state, the prefix whose gates keep the qubits in
-    // independent groups is built in one write pass, if the rest then needs fewer passes
-    // (the booster's pass counted as one)
+    // independent groups is built in one write pass, if that saves at least one pass (the
+    // booster's own pass counted as one: at equal counts the rest's passes can cost more,
+    // e.g. a QFT whose first target's controlled phases lose their diagonal block)
     std::vector<Op> rest;
     const std::vector<Op> *src = &ops;
     if (st.known_zero && n >= kTpbMinQubits && (o.flags & QS_OPT_NO_TPB) == 0) {
@@ -319,7 +320,7 @@ void run_planned(DeviceState &st, const std::vector<Op> &ops, const qs_options &
             std::vector<Op> m2;
             std::vector<std::pair<size_t, size_t>> o2;
             std::vector<Pass> p2 = choose_plan(r, n, pp, o, m2, o2);
-            if (p2.size() + 1 <= plan.size()) {
+            if (p2.size() + 1 < plan.size()) {
                 tpb_execute(st, ops, tp, o, stats);
                 rest = std::move(r);
                 src = &rest;
