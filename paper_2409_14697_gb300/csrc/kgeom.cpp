@@ -517,6 +517,8 @@ std::vector<KOp> build_register_phases(const std::vector<Op> &ops, const int *po
         k.mat = (int32_t)mats.size();
         mats.push_back((double)pend.size());
         auto emit = [&](int type, int slot, int ea, int eb, const std::vector<double> &pay) {
+            // the device reads codes below 2^23 without a conversion instruction
+            if (pay.size() >= 128) fail(QS_ERR_INVALID, "internal: register-phase member payload too long");
             mats.push_back((double)(type | slot << 3 | ea << 6 | eb << 11 | (int)pay.size() << 16));
             mats.insert(mats.end(), pay.begin(), pay.end());
         };

@@ -162,26 +162,26 @@ __device__ __forceinline__ void dense_k_smem(typename C2T<T>::type *tile, const 
 constexpr int kRpRegs = 1 << kRpBits;
 static_assert(kRpMaxMembers * 9 + 1 <= kMaxOpReals, "a phase program must fit the staged reals");
 
-__device__ __forceinline__ uint32_t rp_pattern(int j) {
-    switch (j) {  // bit r set iff bit j of r is set
-    case 0: return 0xAAAAAAAAu;
-    case 1: return 0xCCCCCCCCu;
-    case 2: return 0xF0F0F0F0u;
-    case 3: return 0xFF00FF00u;
-    default: return 0xFFFF0000u;
-    }
-}
+// Bit r set iff bit j of r is set (j < kRpBits; index 5..7 unused).
+static __constant__ uint32_t c_rp_pattern[8] = {0xAAAAAAAAu, 0xCCCCCCCCu, 0xF0F0F0F0u, 0xFF00FF00u, 0xFFFF0000u, 0u, 0u, 0u};
+
+__device__ __forceinline__ uint32_t rp_pattern(int j) { return c_rp_pattern[j & 7]; }
+
+// The integer value of a float that holds one in [0, 2^23) (program codes and operand
+// encodings): adding 2^23 puts it in the low mantissa bits, without a conversion
+// instruction.
+__device__ __forceinline__ uint32_t rp_int(float f) { return __float_as_uint(f + 8388608.0f) - 0x4B000000u; }
 
 // Bit r of the result = the bit at operand position `enc` of the amplitude in register r.
+// enc is the same for every thread of the block (it comes from the phase program).
 __device__ __forceinline__ uint32_t rp_mask(int enc, uint32_t sigma, uint32_t tid) {
     if (enc == kRpAlways) return 0xFFFFFFFFu;
     if (enc == kRpNever) return 0u;
     if (enc & 16) {
         const int j = enc & 15;
-        const uint32_t p = rp_pattern(j);
-        return ((sigma >> j) & 1u) ? ~p : p;
+        return rp_pattern(j) ^ (0u - ((sigma >> j) & 1u));
     }
-    return ((tid >> enc) & 1u) ? 0xFFFFFFFFu : 0u;
+    return 0u - ((tid >> enc) & 1u);
 }
 
 // A mask that is the same for every register (an operand spelled by the thread index).
@@ -324,7 +324,9 @@ __device__ __forceinline__ void rp_neg(float2 (&v)[kRpRegs], uint32_t K) {
 }
 
 // multiply register r by table[c(r)] (re, im pairs), c(r) = the 4-bit count whose bit j is
-// bit r of plane c_j
+// bit r of plane c_j.  The planes are first transposed into four words of nibbles (word i:
+// nibble m is the count of register 4m + i), so a register's count costs a shift and a mask
+// instead of four bit extracts.
 __device__ __forceinline__ void rp_table(float2 (&v)[kRpRegs], const float *table, uint32_t c0, uint32_t c1,
                                          uint32_t c2, uint32_t c3) {
     if (rp_uniform(c0) && rp_uniform(c1) && rp_uniform(c2) && rp_uniform(c3)) {
@@ -332,11 +334,15 @@ __device__ __forceinline__ void rp_table(float2 (&v)[kRpRegs], const float *tabl
         rp_scale(v, table[2 * k], table[2 * k + 1]);
         return;
     }
+    uint32_t w[4];
+#pragma unroll
+    for (int i = 0; i < 4; i++)
+        w[i] = ((c0 >> i) & 0x11111111u) | (((c1 >> i) & 0x11111111u) << 1) | (((c2 >> i) & 0x11111111u) << 2) |
+               (((c3 >> i) & 0x11111111u) << 3);
 #pragma unroll
     for (int r = 0; r < kRpRegs; r++) {
-        const int k = (int)(((c0 >> r) & 1u) | (((c1 >> r) & 1u) << 1) | (((c2 >> r) & 1u) << 2) |
-                            (((c3 >> r) & 1u) << 3));
-        v[r] = rp_cmul(v[r], table[2 * k], table[2 * k + 1]);
+        const uint32_t k2 = ((w[r & 3] >> (4 * (r >> 2))) & 15u) << 1;
+        v[r] = rp_cmul(v[r], table[k2], table[k2 + 1]);
     }
 }
 
@@ -414,10 +420,10 @@ __device__ __forceinline__ void rphase_run(float2 *tile, const KOp &ph, const fl
         rp_geometry(ph, tid, pb, base, sigma);
         rp_load<0>(v, tile, base, pb);
     }
-    const int nmem = (int)prog[0];
+    const int nmem = (int)rp_int(prog[0]);
     const float *mm = prog + 1;
     for (int i = 0; i < nmem; i++) {
-        const int code = (int)mm[0];
+        const int code = (int)rp_int(mm[0]);
         const int type = code & 7, J = (code >> 3) & 7, ea = (code >> 6) & 31, eb = (code >> 11) & 31;
         const int len = (code >> 16) & 255;
         const float *P = mm + 1;
@@ -503,7 +509,7 @@ __device__ __forceinline__ void rphase_run(float2 *tile, const KOp &ph, const fl
             // J + 1 sign patterns x_a x_b, one (a | b << 5) per payload real: signs multiply
             uint32_t K = 0;
             for (int q = 0; q <= J; q++) {
-                const int e = (int)P[q];
+                const int e = (int)rp_int(P[q]);
                 K ^= rp_mask(e & 31, sigma, tid) & rp_mask(e >> 5, sigma, tid);
             }
             rp_neg(v, K);
@@ -519,7 +525,7 @@ __device__ __forceinline__ void rphase_run(float2 *tile, const KOp &ph, const fl
             const int np = (len - 2) / 3;
             uint32_t c0 = 0, c1 = 0, c2 = 0, c3 = 0;
             for (int q = 0; q < np; q++) {
-                const int e = (int)P[q];
+                const int e = (int)rp_int(P[q]);
                 const uint32_t M = rp_mask(e & 31, sigma, tid) ^ rp_mask(e >> 5, sigma, tid);
                 uint32_t cy = c0 & M;
                 c0 ^= M;
