@@ -6,8 +6,9 @@ thread), so it finishes the benchmark sizes in minutes.
 * The 30-qubit gate benchmark: a seeded Gaussian state; H, X, RZ, U3, CNOT, CZ, SWAP and
   CU3 each applied 30 times across the targets (two-qubit gates on (q, q+1 mod 30)).
   After each type the GPU states are compared element by element with the oracle's:
-  complex128 gate by gate and as one planned call per type (max-abs <= 1e-12), complex64
-  gate by gate and planned (1 - F <= 1e-6 and the max-abs bound of the complex64 tests).
+  complex128 gate by gate (native FP64 and double-float arithmetic) and as one planned call
+  per type (max-abs <= 1e-12), complex64 gate by gate and planned (1 - F <= 1e-6 and the
+  max-abs bound of the complex64 tests).
 * The same sweep at 22 qubits, where every streaming kernel instance runs grids of several
   iterations per CTA.
 * The three circuit families of the 33-qubit benchmark at 28 qubits (brickwork of 40 U3+CZ
@@ -52,27 +53,29 @@ def _sweep_parity(qs, n, c64_planned=True):
     """Gate benchmark of every SWEEP_GATES type at n qubits; compares after each type.
     Returns a dict of per-type errors and timings (printed with -s)."""
     psi = inputs.gaussian_state(n, seed=2024)
-    variants = [("c128_gate", 2, qs.QS_MODE_GATE), ("c128_planned", 2, qs.QS_MODE_AUTO),
-                ("c64_gate", 1, qs.QS_MODE_GATE)]
+    variants = [("c128_gate", 2, qs.QS_MODE_GATE, qs.QS_PREC_FP64),
+                ("c128_planned", 2, qs.QS_MODE_AUTO, qs.QS_PREC_FP64),
+                ("c128_df32_gate", 2, qs.QS_MODE_GATE, qs.QS_PREC_DF32),
+                ("c64_gate", 1, qs.QS_MODE_GATE, 0)]
     if c64_planned:
-        variants.append(("c64_planned", 1, qs.QS_MODE_AUTO))
+        variants.append(("c64_planned", 1, qs.QS_MODE_AUTO, 0))
     hs = {}
     report = {"oracle_threads": oracle.threads(), "types": {}}
     try:
-        for name, dt, _ in variants:
+        for name, dt, _, _ in variants:
             hs[name] = qs.qs_create(n, dt)
             qs.qs_set_amplitudes(hs[name], psi if dt == 2 else psi.astype(np.complex64))
         buf = _pinned(16 << n)
         t_or = 0.0
         for gname in inputs.SWEEP_GATES:
             seg = inputs.gate_sweep(n, gname, seed=2, count=n)
-            for name, dt, mode in variants:
-                qs.qs_apply_circuit(hs[name], seg, qs.options(mode=mode))
+            for name, dt, mode, prec in variants:
+                qs.qs_apply_circuit(hs[name], seg, qs.options(mode=mode, precision=prec))
             t0 = time.time()
             oracle.run(psi, n, seg)
             t_or += time.time() - t0
             row = {}
-            for name, dt, mode in variants:
+            for name, dt, mode, prec in variants:
                 got = _download(qs, hs[name], n, buf, np.complex128 if dt == 2 else np.complex64)
                 err, gap = compare_large(got, psi)
                 row[name] = (err, gap)
