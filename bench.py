@@ -895,7 +895,7 @@ class ServedInputs:
 def served_run(qs, prepared, rate, prec):
     """Submits the prepared requests at their Poisson arrival times (scaled to `rate`) and
     polls until all are done; returns (latencies, wall seconds, server stats)."""
-    sv = qs.qs_server_create(150 * 10 ** 9, max_slots=8)
+    sv = qs.qs_server_create(150 * 10 ** 9, max_slots=8, small_slots=8, small_max_qubits=20)
     lat = []
     pending = {}
     i = 0
@@ -913,7 +913,7 @@ def served_run(qs, prepared, rate, prec):
             for tk, (n, k) in pending.items():
                 r = qs.qs_poll(sv, tk, n, k)
                 if r is not None:
-                    lat.append(r["latency_s"])
+                    lat.append((n, r["latency_s"]))
                     done.append(tk)
             for tk in done:
                 del pending[tk]
@@ -972,16 +972,26 @@ def wl_served(args, count=None, loads=None):
     seq_wall = served_sequential(qs, prepared, prec)
     rows = {}
     for rate in loads:
-        lat, wall, st = served_run(qs, prepared, rate, prec)
+        nl, wall, st = served_run(qs, prepared, rate, prec)
+        lat = nl[:, 1]
+        small = nl[nl[:, 0] <= 20, 1]
+        large = nl[nl[:, 0] > 20, 1]
         rows[f"{rate:g}"] = {"requests_per_s": round(count / wall, 2),
                              "p50_latency_s": round(float(np.percentile(lat, 50)), 4),
                              "p99_latency_s": round(float(np.percentile(lat, 99)), 4),
                              "mean_latency_s": round(float(lat.mean()), 4), "wall_s": round(wall, 2),
+                             "small_n_le_20": {"count": int(small.size),
+                                               "p50_latency_s": round(float(np.percentile(small, 50)), 4) if small.size else None,
+                                               "p99_latency_s": round(float(np.percentile(small, 99)), 4) if small.size else None},
+                             "large_n_gt_20": {"count": int(large.size),
+                                               "p50_latency_s": round(float(np.percentile(large, 50)), 4) if large.size else None,
+                                               "p99_latency_s": round(float(np.percentile(large, 99)), 4) if large.size else None},
                              "peak_bytes": st["peak_bytes"], "failed": st["failed"]}
     main = rows[f"{loads[0]:g}"]
     return {"workload": f"served: {count} Poisson requests, n 10-30 log-uniform, c64/c128 "
                         f"({args.precision} for c128), <Z_i> + top-1024, 150 GB budget, 8 slots; "
                         f"sweep requests from borrowed page-locked Gaussian states",
+            "lanes": "8 slots + 8 small-request slots (n <= 20 may overtake larger requests)",
             "metric": "requests/s", "value": main["requests_per_s"], "offered_req_per_s": loads[0],
             "p50_latency_s": main["p50_latency_s"], "p99_latency_s": main["p99_latency_s"],
             "sequential_requests_per_s": round(count / seq_wall, 2), "sequential_wall_s": round(seq_wall, 2),

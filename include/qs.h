@@ -274,12 +274,17 @@ int qs_expectation_z_noalloc(const void *dev_psi, int n_qubits, qs_dtype dt, voi
  * hbm_budget_bytes.  Every slot has its own CUDA stream, so admitted requests overlap on
  * the device.  A request runs its circuit (QS_MODE_* of `mode`, planned by default) from
  * |0...0> or from the caller's amplitudes, then returns <Z_q> for every qubit, the squared
- * norm and its top_k amplitudes.  Results are bitwise identical whatever else runs. */
+ * norm and its top_k amplitudes.  Results are bitwise identical whatever else runs.
+ * Large requests are admitted in submission order.  Small requests (small_max_qubits) may
+ * overtake them: they take a free small slot, else a free regular one, as soon as the
+ * budget allows, so a burst of large states does not hold them back. */
 
 typedef struct {
     uint64_t hbm_budget_bytes;  /* admission budget for the states in flight */
     int32_t max_slots;          /* requests in flight at once (1..256) */
-    int32_t reserved[5];
+    int32_t small_slots;        /* extra slots that only small requests use (0..256; 0: none) */
+    int32_t small_max_qubits;   /* a request of at most this many qubits is small */
+    int32_t reserved[3];
 } qs_server_config;
 
 /* Bits of qs_request.flags. */

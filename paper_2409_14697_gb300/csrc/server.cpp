@@ -205,46 +205,65 @@ void Server::run() {
         // 1. retire finished slots
         for (Slot *s : slots)
             if (s->busy && s->done.load(std::memory_order_acquire)) finish_slot(*s);
-        // 2. admit
+        // 2. admit: large requests in submission order (the first that cannot start holds
+        // back the later large ones); small requests whenever a slot and the budget allow,
+        // small-lane slots first
         std::unique_lock<std::mutex> lk(mu);
-        bool admitted = false;
-        while (!queue.empty()) {
-            Request &r = queue.front();
-            if (bytes_in_use + r.bytes > cfg.hbm_budget_bytes) break;
-            Slot *free_slot = nullptr;
-            for (Slot *s : slots)
-                if (!s->busy) { free_slot = s; break; }
-            if (!free_slot) break;
-            Request req = std::move(r);
-            queue.pop_front();
-            free_slot->busy = true;
-            free_slot->ticket = req.ticket;
-            free_slot->bytes = req.bytes;
-            free_slot->top_k = req.top_k;
-            free_slot->n = req.n;
-            free_slot->t_submit = req.t_submit;
-            free_slot->t_start = Clock::now();
-            bytes_in_use += req.bytes;
-            peak_bytes = std::max(peak_bytes, bytes_in_use);
-            lk.unlock();
-            try {
-                start_request(*free_slot, req);
-            } catch (const Error &e) {
-                lk.lock();
-                Result res;
-                res.status = e.code;
-                res.error = e.msg;
-                results[req.ticket] = std::move(res);
-                bytes_in_use -= req.bytes;
-                failed++;
-                completed++;
-                free_slot->busy = false;
-                cv.notify_all();
+        // starts one queued request (mu held; released while the request is queued on its
+        // slot's stream); false if none can start now
+        auto admit_one = [&]() -> bool {
+            bool large_blocked = false;
+            for (auto it = queue.begin(); it != queue.end(); ++it) {
+                const bool small = it->n <= cfg.small_max_qubits;
+                if ((!small && large_blocked) || bytes_in_use + it->bytes > cfg.hbm_budget_bytes) {
+                    large_blocked |= !small;
+                    continue;
+                }
+                Slot *free_slot = nullptr;
+                const int n_regular = cfg.max_slots;
+                if (small)
+                    for (size_t i = n_regular; i < slots.size() && !free_slot; i++)
+                        if (!slots[i]->busy) free_slot = slots[i];
+                for (int i = 0; i < n_regular && !free_slot; i++)
+                    if (!slots[i]->busy) free_slot = slots[i];
+                if (!free_slot) {
+                    large_blocked |= !small;
+                    continue;
+                }
+                Request req = std::move(*it);
+                queue.erase(it);  // iterators are not used again: the lock is released below
+                free_slot->busy = true;
+                free_slot->ticket = req.ticket;
+                free_slot->bytes = req.bytes;
+                free_slot->top_k = req.top_k;
+                free_slot->n = req.n;
+                free_slot->t_submit = req.t_submit;
+                free_slot->t_start = Clock::now();
+                bytes_in_use += req.bytes;
+                peak_bytes = std::max(peak_bytes, bytes_in_use);
                 lk.unlock();
+                try {
+                    start_request(*free_slot, req);
+                } catch (const Error &e) {
+                    lk.lock();
+                    Result res;
+                    res.status = e.code;
+                    res.error = e.msg;
+                    results[req.ticket] = std::move(res);
+                    bytes_in_use -= req.bytes;
+                    failed++;
+                    completed++;
+                    free_slot->busy = false;
+                    cv.notify_all();
+                    lk.unlock();
+                }
+                lk.lock();
+                return true;
             }
-            lk.lock();
-            admitted = true;
-        }
+            return false;
+        };
+        bool admitted = false;
+        while (admit_one()) admitted = true;
         if (stop && queue.empty()) {
             bool any = false;
             for (Slot *s : slots) any |= s->busy;
@@ -274,6 +293,7 @@ int qs_server_create(const qs_server_config *cfg, qs_server **out) {
     QS_API_BEGIN
     if (!cfg || !out) fail(QS_ERR_INVALID, "NULL argument");
     if (cfg->max_slots < 1 || cfg->max_slots > 256) fail(QS_ERR_INVALID, "max_slots must be 1..256");
+    if (cfg->small_slots < 0 || cfg->small_slots > 256) fail(QS_ERR_INVALID, "small_slots must be 0..256");
     if (cfg->hbm_budget_bytes == 0) fail(QS_ERR_INVALID, "zero HBM budget");
     *out = nullptr;
     qs_server *p = new qs_server();
@@ -284,7 +304,7 @@ int qs_server_create(const qs_server_config *cfg, qs_server **out) {
         QS_CUDA(cudaDeviceGetDefaultMemPool(&S.pool, S.device));
         uint64_t thr = UINT64_MAX;  // keep freed state memory in the pool for reuse
         QS_CUDA(cudaMemPoolSetAttribute(S.pool, cudaMemPoolAttrReleaseThreshold, &thr));
-        for (int i = 0; i < cfg->max_slots; i++) {
+        for (int i = 0; i < cfg->max_slots + cfg->small_slots; i++) {
             Slot *s = new Slot();
             S.slots.push_back(s);
             QS_CUDA(cudaStreamCreateWithFlags(&s->d.stream, cudaStreamNonBlocking));

@@ -66,7 +66,8 @@ class qs_batch_stats(ctypes.Structure):
 
 class qs_server_config(ctypes.Structure):
     _fields_ = [("hbm_budget_bytes", ctypes.c_uint64), ("max_slots", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 5)]
+                ("small_slots", ctypes.c_int32), ("small_max_qubits", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 3)]
 
 
 class qs_request(ctypes.Structure):
@@ -330,10 +331,12 @@ def qs_renormalize(h) -> float:
 
 # ---- serving ----------------------------------------------------------------------
 
-def qs_server_create(hbm_budget_bytes: int, max_slots: int = 8):
+def qs_server_create(hbm_budget_bytes: int, max_slots: int = 8, small_slots: int = 0, small_max_qubits: int = 0):
     cfg = qs_server_config()
     cfg.hbm_budget_bytes = int(hbm_budget_bytes)
     cfg.max_slots = max_slots
+    cfg.small_slots = small_slots
+    cfg.small_max_qubits = small_max_qubits
     h = _VP()
     _check(load().qs_server_create(ctypes.byref(cfg), ctypes.byref(h)))
     return h

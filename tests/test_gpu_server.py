@@ -149,3 +149,34 @@ def test_borrowed_initial_amplitudes(qs):
         assert np.array_equal(a["top_idx"], b["top_idx"]) and np.array_equal(a["top_amp"], b["top_amp"])
         want = oracle.run(psi.copy(), n, g)
         assert np.max(np.abs(a["expz"] - oracle.expz(want, n))) <= 1e-12
+
+
+def test_small_requests_overtake_large_ones(qs):
+    """One regular slot, held by large requests, and a small lane of two slots: small
+    requests submitted after two large ones start at once and finish before the second
+    large one, whose latency includes waiting for the first (large ones keep their order).
+    Results are those of the oracle."""
+    n_big, k = 26, 8
+    big = inputs.brickwork(n_big, 30, seed=1)
+    sv = qs.qs_server_create(8 << 30, max_slots=1, small_slots=2, small_max_qubits=12)
+    try:
+        t_big = [qs.qs_submit(sv, n_big, 2, big, top_k=k) for _ in range(2)]
+        smalls = [(10 + (i % 3), inputs.brickwork(10 + (i % 3), 20, seed=100 + i)) for i in range(6)]
+        t_small = [qs.qs_submit(sv, n, 1, g, top_k=k) for n, g in smalls]
+        r_small = [wait(qs, sv, t, n, k) for t, (n, g) in zip(t_small, smalls)]
+        r_big = [wait(qs, sv, t, n_big, k) for t in t_big]
+    finally:
+        qs.qs_server_drain(sv)
+        qs.qs_server_destroy(sv)
+    assert r_big[0]["latency_s"] < r_big[1]["latency_s"]
+    assert max(r["latency_s"] for r in r_small) < r_big[1]["latency_s"]
+    assert np.array_equal(r_big[0]["expz"], r_big[1]["expz"])
+    for (n, g), r in zip(smalls, r_small):
+        want = oracle.run(oracle.zero_state(n), n, g)
+        assert np.max(np.abs(r["expz"] - oracle.expz(want, n))) <= 1e-5
+
+
+def test_server_rejects_bad_small_lane(qs):
+    with pytest.raises(qs.QsError) as e:
+        qs.qs_server_create(1 << 30, max_slots=2, small_slots=-1)
+    assert e.value.code == qs.QS_ERR_INVALID
