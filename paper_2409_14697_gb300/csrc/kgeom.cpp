@@ -512,6 +512,12 @@ std::vector<KOp> build_register_phases(const std::vector<Op> &ops, const int *po
             const int npay = e.type == RP_X ? 0 : e.type == RP_PH ? 2
                              : (e.type == RP_M1 && e.form != RP_GENERAL) ? 4 : 8;
             p.pay.assign(e.pay, e.pay + npay);
+            // a general matrix with a real first entry on a slot that no lane conjugates
+            // (positions 4 and up carry no bit of sigma): 7 multiply-adds instead of 8
+            if (e.type == RP_M1 && e.form == RP_GENERAL && e.pay[1] == 0.0 && e.tgt >= 4) {
+                p.eb = RP_R0;
+                p.pay = {e.pay[0], e.pay[2], e.pay[3], e.pay[4], e.pay[5], e.pay[6], e.pay[7]};
+            }
             pend.push_back(std::move(p));
         }
         k.mat = (int32_t)mats.size();

@@ -71,7 +71,9 @@ enum RpType : int {
                 // number of patterns with x_a != x_b (equal-angle RZZ / RZ layers), np <= 15
 };
 constexpr int kRpMaxParity = 15;
-enum RpForm : int { RP_GENERAL = 0, RP_REAL = 1, RP_RX = 2 };
+// RP_R0: 7 reals (m00 real; m01, m10, m11 as re, im), only on slots whose position is 4 or
+// more (their bit of sigma is 0 in every lane, so the matrix is never conjugated)
+enum RpForm : int { RP_GENERAL = 0, RP_REAL = 1, RP_RX = 2, RP_R0 = 3 };
 
 // Host+device description of one op in a given index space (HBM amplitude/element
 // indices for K1, tile-local indices for K2).

@@ -304,10 +304,16 @@ int qs_server_create(const qs_server_config *cfg, qs_server **out) {
         QS_CUDA(cudaDeviceGetDefaultMemPool(&S.pool, S.device));
         uint64_t thr = UINT64_MAX;  // keep freed state memory in the pool for reuse
         QS_CUDA(cudaMemPoolSetAttribute(S.pool, cudaMemPoolAttrReleaseThreshold, &thr));
+        // small-lane slots get the device's highest stream priority: when the persistent
+        // kernels of a large request end, the CTA scheduler starts a small request's pending
+        // kernels first instead of the large request's next pass
+        int prio_low = 0, prio_high = 0;
+        QS_CUDA(cudaDeviceGetStreamPriorityRange(&prio_low, &prio_high));
         for (int i = 0; i < cfg->max_slots + cfg->small_slots; i++) {
             Slot *s = new Slot();
             S.slots.push_back(s);
-            QS_CUDA(cudaStreamCreateWithFlags(&s->d.stream, cudaStreamNonBlocking));
+            QS_CUDA(cudaStreamCreateWithPriority(&s->d.stream, cudaStreamNonBlocking,
+                                                 i < cfg->max_slots ? prio_low : prio_high));
             s->srv = &S;
             QS_CUDA(cudaMalloc(&s->d.dev_err, sizeof(int)));
             QS_CUDA(cudaMemset(s->d.dev_err, 0, sizeof(int)));

@@ -184,6 +184,9 @@ __device__ __forceinline__ uint32_t rp_mask(int enc, uint32_t sigma, uint32_t ti
     return 0u - ((tid >> enc) & 1u);
 }
 
+// True for an operand that names a register slot (its bit differs between registers).
+__device__ __forceinline__ bool rp_is_slot(int enc) { return (enc & 16) && enc < kRpNever; }
+
 // A mask that is the same for every register (an operand spelled by the thread index).
 __device__ __forceinline__ bool rp_uniform(uint32_t K) { return K == 0u || K == 0xFFFFFFFFu; }
 
@@ -236,6 +239,32 @@ __device__ __forceinline__ void rp_mr(float2 (&v)[kRpRegs], float a, float b, fl
         x.y = fmaf(a, x.y, pxi);
         y.x = fmaf(d, y.x, pyr);
         y.y = fmaf(d, y.y, pyi);
+    }
+}
+
+// (a, m01; m10, m11) with real a (U3 and one-qubit matrices like it): 7 multiply-adds per
+// amplitude; P = a, m01 (re, im), m10 (re, im), m11 (re, im)
+template <int J>
+__device__ __forceinline__ void rp_mr0(float2 (&v)[kRpRegs], const float *P) {
+    const float a = P[0], br = P[1], bi = P[2], cr = P[3], ci = P[4], dr = P[5], di = P[6];
+#pragma unroll
+    for (int r = 0; r < kRpRegs; r++) {
+        if (r & (1 << J)) continue;
+        float2 &x = v[r], &y = v[r | (1 << J)];
+        float p0r = br * y.x;
+        p0r = fmaf(-bi, y.y, p0r);
+        float p0i = br * y.y;
+        p0i = fmaf(bi, y.x, p0i);
+        float p1r = cr * x.x;
+        p1r = fmaf(-ci, x.y, p1r);
+        p1r = fmaf(-di, y.y, p1r);
+        float p1i = cr * x.y;
+        p1i = fmaf(ci, x.x, p1i);
+        p1i = fmaf(di, y.x, p1i);
+        x.x = fmaf(a, x.x, p0r);
+        x.y = fmaf(a, x.y, p0i);
+        y.x = fmaf(dr, y.x, p1r);
+        y.y = fmaf(dr, y.y, p1i);
     }
 }
 
@@ -430,6 +459,16 @@ __device__ __forceinline__ void rphase_run(float2 *tile, const KOp &ph, const fl
         mm += 1 + len;
         switch (type) {
         case RP_M1:
+            if (eb == RP_R0) {
+                switch (J) {
+                case 0: rp_mr0<0>(v, P); break;
+                case 1: rp_mr0<1>(v, P); break;
+                case 2: rp_mr0<2>(v, P); break;
+                case 3: rp_mr0<3>(v, P); break;
+                default: rp_mr0<4>(v, P); break;
+                }
+                break;
+            }
             if (eb != RP_GENERAL) {
                 // the 4-real forms: X M X reverses the payload order
                 const int f = (int)((sigma >> J) & 1u);
@@ -524,9 +563,14 @@ __device__ __forceinline__ void rphase_run(float2 *tile, const KOp &ph, const fl
             // kept in 4 bit planes (a ripple counter over the 32 registers at once)
             const int np = (len - 2) / 3;
             uint32_t c0 = 0, c1 = 0, c2 = 0, c3 = 0;
+            int ku = 0;  // odd patterns on bits that are the same for every register
             for (int q = 0; q < np; q++) {
                 const int e = (int)rp_int(P[q]);
                 const uint32_t M = rp_mask(e & 31, sigma, tid) ^ rp_mask(e >> 5, sigma, tid);
+                if (!rp_is_slot(e & 31) && !rp_is_slot(e >> 5)) {
+                    ku += (int)(M & 1u);
+                    continue;
+                }
                 uint32_t cy = c0 & M;
                 c0 ^= M;
                 uint32_t cz = c1 & cy;
@@ -535,7 +579,7 @@ __device__ __forceinline__ void rphase_run(float2 *tile, const KOp &ph, const fl
                 c2 ^= cz;
                 c3 ^= cy;
             }
-            rp_table(v, P + np, c0, c1, c2, c3);
+            rp_table(v, P + np + 2 * ku, c0, c1, c2, c3);
             break;
         }
         default: rp_ph(v, P[0], P[1], rp_mask(ea, sigma, tid) & rp_mask(eb, sigma, tid)); break;
