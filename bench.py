@@ -895,7 +895,7 @@ class ServedInputs:
 def served_run(qs, prepared, rate, prec):
     """Submits the prepared requests at their Poisson arrival times (scaled to `rate`) and
     polls until all are done; returns (latencies, wall seconds, server stats)."""
-    sv = qs.qs_server_create(150 * 10 ** 9, max_slots=8, small_slots=8, small_max_qubits=20)
+    sv = qs.qs_server_create(150 * 10 ** 9, max_slots=8, small_slots=8, small_max_qubits=18)
     lat = []
     pending = {}
     i = 0
@@ -991,7 +991,7 @@ def wl_served(args, count=None, loads=None):
     return {"workload": f"served: {count} Poisson requests, n 10-30 log-uniform, c64/c128 "
                         f"({args.precision} for c128), <Z_i> + top-1024, 150 GB budget, 8 slots; "
                         f"sweep requests from borrowed page-locked Gaussian states",
-            "lanes": "8 slots + 8 small-request slots (n <= 20 may overtake larger requests)",
+            "lanes": "8 slots + 8 small-request slots (n <= 18 may overtake larger requests)",
             "metric": "requests/s", "value": main["requests_per_s"], "offered_req_per_s": loads[0],
             "p50_latency_s": main["p50_latency_s"], "p99_latency_s": main["p99_latency_s"],
             "sequential_requests_per_s": round(count / seq_wall, 2), "sequential_wall_s": round(seq_wall, 2),

@@ -282,7 +282,10 @@ int qs_expectation_z_noalloc(const void *dev_psi, int n_qubits, qs_dtype dt, voi
 typedef struct {
     uint64_t hbm_budget_bytes;  /* admission budget for the states in flight */
     int32_t max_slots;          /* requests in flight at once (1..256) */
-    int32_t small_slots;        /* extra slots that only small requests use (0..256; 0: none) */
+    int32_t small_slots;        /* extra slots that only small requests use (0..256; 0: none);
+                                   their buffers are sized at creation for small_max_qubits,
+                                   so serving a small request frees no memory (cudaFree waits
+                                   for the whole device) */
     int32_t small_max_qubits;   /* a request of at most this many qubits is small */
     int32_t reserved[3];
 } qs_server_config;

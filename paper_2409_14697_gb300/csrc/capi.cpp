@@ -82,6 +82,20 @@ void arena_end(DeviceState &st) {
     QS_CUDA(cudaEventRecord(st.arena_ev[st.arena_cur], st.stream));
 }
 
+void arena_reserve(DeviceState &st, size_t bytes) {
+    for (int c = 0; c < kArenas; c++) {
+        if (st.arena_cap[c] >= bytes) continue;
+        if (st.arena_ev[c]) QS_CUDA(cudaEventSynchronize(st.arena_ev[c]));
+        if (st.arena_dev[c]) QS_CUDA(cudaFree(st.arena_dev[c]));
+        if (st.arena_host[c]) QS_CUDA(cudaFreeHost(st.arena_host[c]));
+        st.arena_dev[c] = st.arena_host[c] = nullptr;
+        st.arena_cap[c] = 0;
+        QS_CUDA(cudaMalloc(&st.arena_dev[c], bytes));
+        QS_CUDA(cudaMallocHost(&st.arena_host[c], bytes));
+        st.arena_cap[c] = bytes;
+    }
+}
+
 void *upload_params(DeviceState &st, const void *host, size_t bytes) {
     const int c = st.arena_cur;
     const size_t need = ((st.arena_used + 255) & ~size_t(255)) + bytes;

@@ -199,6 +199,10 @@ void free_device_state(DeviceState &d);
 void tpb_free(DeviceState &d);
 void arena_begin(DeviceState &st);
 void arena_end(DeviceState &st);
+// Gives every parameter arena of st at least `bytes` of capacity now, so that later calls
+// with programs that fit never grow one (growing frees memory later, and cudaFree waits for
+// the whole device).
+void arena_reserve(DeviceState &st, size_t bytes);
 
 // Launchers (kernels live in the .cu files).  All are asynchronous on st.stream.
 void launch_stream_op(DeviceState &st, const Op &op);           // K1, one op, one pass

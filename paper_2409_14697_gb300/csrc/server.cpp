@@ -121,6 +121,28 @@ size_t amp_bytes_of(int dtype) { return dtype == QS_C128 ? 16 : 8; }
 
 void notify_server(Server *srv) { srv->cv.notify_all(); }
 
+namespace {
+
+// Sizes a slot's device and pinned buffers for requests of up to n qubits and top_k
+// amplitudes, so that serving them never frees memory (cudaFree and cudaFreeHost wait for
+// the whole device, which would hold a small request behind every large one in flight).
+void presize_slot(Slot &s, int n, uint32_t k) {
+    DeviceState &d = s.d;
+    d.n = n;
+    ensure_scratch(d, std::max(scratch_expz_bytes(n), scratch_topk_bytes(n, std::max<uint32_t>(k, 1))));
+    s.cap_n = n;
+    s.cap_k = std::max<uint32_t>(k, 1);
+    QS_CUDA(cudaMalloc(&s.d_out, sizeof(double) * (s.cap_n + 1)));
+    QS_CUDA(cudaMalloc(&s.d_idx, sizeof(uint64_t) * s.cap_k));
+    QS_CUDA(cudaMalloc(&s.d_amp, sizeof(double) * 2 * s.cap_k));
+    QS_CUDA(cudaMallocHost(&s.h_out, sizeof(double) * (s.cap_n + 1)));
+    QS_CUDA(cudaMallocHost(&s.h_idx, sizeof(uint64_t) * s.cap_k));
+    QS_CUDA(cudaMallocHost(&s.h_amp, sizeof(double) * 2 * s.cap_k));
+    arena_reserve(d, (size_t)1 << 20);
+}
+
+}  // namespace
+
 void Server::start_request(Slot &s, Request &r) {
     DeviceState &d = s.d;
     d.n = r.n;
@@ -319,6 +341,10 @@ int qs_server_create(const qs_server_config *cfg, qs_server **out) {
             QS_CUDA(cudaMemset(s->d.dev_err, 0, sizeof(int)));
             QS_CUDA(cudaMallocHost(&s->h_err, sizeof(int)));
             *s->h_err = 0;
+            if (i >= cfg->max_slots && cfg->small_max_qubits > 0) {
+                const int ns = std::min(cfg->small_max_qubits, QS_MAX_QUBITS);
+                presize_slot(*s, ns, (uint32_t)std::min<uint64_t>(1ull << std::min(ns, 12), 4096));
+            }
         }
         S.worker = std::thread([&S]() { S.run(); });
     } catch (...) {
