@@ -489,9 +489,11 @@ std::vector<KOp> build_register_phases(const std::vector<Op> &ops, const int *po
             cd e, f;
         };
         std::vector<Pending> pend;
+        uint32_t x_slots = 0;  // slots an exchange may have relabelled (bits of sigma it toggles)
         for (int i : best) {
             const RpMember &e = mb[i];
             done[i] = 1;
+            if (e.type == RP_X) x_slots |= 1u << slot_of[e.tgt];
             const int ea = enc(e.a), eb = enc(e.b), pair = ea | eb << 5;
             Pending *last = pend.empty() ? nullptr : &pend.back();
             if (e.type == RP_NEG) {
@@ -513,8 +515,10 @@ std::vector<KOp> build_register_phases(const std::vector<Op> &ops, const int *po
                              : (e.type == RP_M1 && e.form != RP_GENERAL) ? 4 : 8;
             p.pay.assign(e.pay, e.pay + npay);
             // a general matrix with a real first entry on a slot that no lane conjugates
-            // (positions 4 and up carry no bit of sigma): 7 multiply-adds instead of 8
-            if (e.type == RP_M1 && e.form == RP_GENERAL && e.pay[1] == 0.0 && e.tgt >= 4) {
+            // (positions 4 and up carry no bit of sigma at the phase's start, and no
+            // exchange on the slot has toggled it since): 7 multiply-adds instead of 8
+            if (e.type == RP_M1 && e.form == RP_GENERAL && e.pay[1] == 0.0 && e.tgt >= 4 &&
+                !((x_slots >> slot_of[e.tgt]) & 1u)) {
                 p.eb = RP_R0;
                 p.pay = {e.pay[0], e.pay[2], e.pay[3], e.pay[4], e.pay[5], e.pay[6], e.pay[7]};
             }

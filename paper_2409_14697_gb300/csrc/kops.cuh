@@ -71,8 +71,9 @@ enum RpType : int {
                 // number of patterns with x_a != x_b (equal-angle RZZ / RZ layers), np <= 15
 };
 constexpr int kRpMaxParity = 15;
-// RP_R0: 7 reals (m00 real; m01, m10, m11 as re, im), only on slots whose position is 4 or
-// more (their bit of sigma is 0 in every lane, so the matrix is never conjugated)
+// RP_R0: 7 reals (m00 real; m01, m10, m11 as re, im), only on slots whose bit of sigma is 0
+// in every lane: positions 4 and up, with no exchange on the slot earlier in the phase (an
+// exchange toggles the slot's bit of sigma), so the matrix is never conjugated
 enum RpForm : int { RP_GENERAL = 0, RP_REAL = 1, RP_RX = 2, RP_R0 = 3 };
 
 // Host+device description of one op in a given index space (HBM amplitude/element
