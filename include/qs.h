@@ -58,7 +58,7 @@ enum {
     QS_ERR_CUDA = -3,        /* a CUDA runtime/driver call failed */
     QS_ERR_TIMEOUT = -4,     /* a bounded device-side wait gave up */
     QS_ERR_BUSY = -5,        /* object still has work in flight */
-    QS_ERR_UNSUPPORTED = -6  /* valid request this build does not implement */
+    QS_ERR_UNSUPPORTED = -6  /* valid request the library does not implement */
 };
 
 /* Gate types.  Matrices (first operand most significant in the group index):

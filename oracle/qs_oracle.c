@@ -56,7 +56,7 @@ int or_set_threads(int t)
 
 int or_get_threads(void) { return g_threads; }
 
-/* 1 if this build was compiled with OpenMP. */
+/* 1 if this library was compiled with OpenMP. */
 int or_has_openmp(void)
 {
 #ifdef _OPENMP

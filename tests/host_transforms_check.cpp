@@ -322,6 +322,166 @@ void check_h_runs(const std::vector<Op> &ops, int trial) {
 // qubit is 1 in the tile; F_HCDIAGK the unscaled butterfly across its control first.
 int g_joins = 0;
 
+// A register phase (F_RPHASE) as the chunk kernel runs it, thread by thread: every thread
+// holds the 2^kRpBits amplitudes spanned by the phase's register positions, register r
+// holding the one whose register bits are r ^ sigma (sigma from the lane bits for
+// positions below 4, as the kernel lays them out), and applies the members in program
+// order with the same operand encoding, conjugation by sigma, exchange relabelling and
+// parity counting; then stores in the final register order.  Double precision.
+int g_rp_members = 0;
+
+void apply_rphase(State &tile, int m, const KOp &ph, const std::vector<double> &mats) {
+    const int nt = ph.nt;
+    const uint32_t threads = 1u << nt;
+    if (m != nt + kRpBits) fail(QS_ERR_INVALID, "register phase: m != thread bits + 5");
+    const double *prog = mats.data() + ph.mat;
+    const uint32_t pattern[5] = {0xAAAAAAAAu, 0xCCCCCCCCu, 0xF0F0F0F0u, 0xFF00FF00u, 0xFFFF0000u};
+    for (uint32_t tid = 0; tid < threads; tid++) {
+        const uint32_t lane = tid & 31u;
+        // geometry: register positions, sigma, base
+        uint32_t pb[kRpBits], sigma = 0, base = 0;
+        int nlow = 0;
+        for (int j = 0; j < kRpBits; j++) {
+            pb[j] = 1u << ph.pos[j];
+            nlow += ph.pos[j] < 4 ? 1 : 0;
+        }
+        int li = 4 - nlow;
+        for (int j = 0; j < kRpBits; j++)
+            if (ph.pos[j] < 4) {
+                sigma |= ((lane >> li) & 1u) << j;
+                li++;
+            }
+        for (int i = 0; i < nt; i++) base |= ((tid >> i) & 1u) << (uint32_t)((ph.off[0] >> (4 * i)) & 15u);
+        const uint32_t sigma0 = sigma;
+        auto index = [&](uint32_t r, uint32_t sg) {
+            uint32_t o = base;
+            for (int j = 0; j < kRpBits; j++)
+                if (((r ^ sg) >> j) & 1u) o ^= pb[j];
+            return o;
+        };
+        cd v[32];
+        for (uint32_t r = 0; r < 32; r++) v[r] = tile[index(r, sigma0)];
+        auto mask = [&](int enc) -> uint32_t {
+            if (enc == kRpAlways) return 0xFFFFFFFFu;
+            if (enc == kRpNever) return 0u;
+            if (enc & 16) {
+                const int j = enc & 15;
+                return ((sigma >> j) & 1u) ? ~pattern[j] : pattern[j];
+            }
+            return ((tid >> enc) & 1u) ? 0xFFFFFFFFu : 0u;
+        };
+        auto is_slot = [](int enc) { return (enc & 16) && enc < kRpNever; };
+        auto pairs = [&](int J, auto fn) {
+            for (uint32_t r = 0; r < 32; r++)
+                if (!((r >> J) & 1u)) fn(r, r | (1u << J));
+        };
+        const int nmem = (int)prog[0];
+        const double *mm = prog + 1;
+        for (int i = 0; i < nmem; i++) {
+            g_rp_members++;
+            const int code = (int)mm[0];
+            const int type = code & 7, J = (code >> 3) & 7, ea = (code >> 6) & 31, eb = (code >> 11) & 31;
+            const int len = (code >> 16) & 255;
+            const double *P = mm + 1;
+            mm += 1 + len;
+            const int f = (int)((sigma >> J) & 1u);
+            auto general = [&](cd (&M)[4]) {  // X M X where bit J of sigma is set
+                const cd g[4] = {cd(P[0], P[1]), cd(P[2], P[3]), cd(P[4], P[5]), cd(P[6], P[7])};
+                if (f) { M[0] = g[3]; M[1] = g[2]; M[2] = g[1]; M[3] = g[0]; }
+                else { M[0] = g[0]; M[1] = g[1]; M[2] = g[2]; M[3] = g[3]; }
+            };
+            switch (type) {
+            case RP_M1: {
+                cd M[4];
+                if (eb == RP_R0) {
+                    if (f) fail(QS_ERR_INVALID, "register phase: 7-real form on a conjugated slot");
+                    M[0] = P[0]; M[1] = cd(P[1], P[2]); M[2] = cd(P[3], P[4]); M[3] = cd(P[5], P[6]);
+                } else if (eb == RP_REAL || eb == RP_RX) {
+                    const double q0 = P[3 * f], q1 = P[1 + f], q2 = P[2 - f], q3 = P[3 - 3 * f];
+                    if (eb == RP_REAL) { M[0] = q0; M[1] = q1; M[2] = q2; M[3] = q3; }
+                    else { M[0] = q0; M[1] = cd(0, q1); M[2] = cd(0, q2); M[3] = q3; }
+                } else {
+                    general(M);
+                }
+                pairs(J, [&](uint32_t a, uint32_t b) {
+                    const cd x = v[a], y = v[b];
+                    v[a] = M[0] * x + M[1] * y;
+                    v[b] = M[2] * x + M[3] * y;
+                });
+                break;
+            }
+            case RP_C1: {
+                cd M[4];
+                general(M);
+                const uint32_t K = mask(ea);
+                pairs(J, [&](uint32_t a, uint32_t b) {
+                    if (!((K >> a) & 1u)) return;
+                    const cd x = v[a], y = v[b];
+                    v[a] = M[0] * x + M[1] * y;
+                    v[b] = M[2] * x + M[3] * y;
+                });
+                break;
+            }
+            case RP_X: {
+                const uint32_t K = mask(ea);
+                if (K == 0u || K == 0xFFFFFFFFu) {
+                    sigma ^= (K & 1u) << J;
+                    break;
+                }
+                pairs(J, [&](uint32_t a, uint32_t b) {
+                    if ((K >> a) & 1u) std::swap(v[a], v[b]);
+                });
+                break;
+            }
+            case RP_DIAG: {
+                const uint32_t Ka = mask(ea), Kb = mask(eb);
+                for (uint32_t r = 0; r < 32; r++) {
+                    const int s = (int)(2 * ((Ka >> r) & 1u) + ((Kb >> r) & 1u));
+                    v[r] *= cd(P[2 * s], P[2 * s + 1]);
+                }
+                break;
+            }
+            case RP_NEG: {
+                uint32_t K = 0;
+                for (int q = 0; q <= J; q++) {
+                    const int e = (int)P[q];
+                    K ^= mask(e & 31) & mask(e >> 5);
+                }
+                for (uint32_t r = 0; r < 32; r++)
+                    if ((K >> r) & 1u) v[r] = -v[r];
+                break;
+            }
+            case RP_PARITY: {
+                const uint32_t K = mask(ea) ^ mask(eb);
+                for (uint32_t r = 0; r < 32; r++) v[r] *= ((K >> r) & 1u) ? cd(P[2], P[3]) : cd(P[0], P[1]);
+                break;
+            }
+            case RP_PARITYN: {
+                const int np = (len - 2) / 3;
+                int cnt[32] = {0};
+                int slot_patterns = 0;
+                for (int q = 0; q < np; q++) {
+                    const int e = (int)P[q];
+                    const uint32_t M = mask(e & 31) ^ mask(e >> 5);
+                    slot_patterns += is_slot(e & 31) || is_slot(e >> 5);
+                    for (uint32_t r = 0; r < 32; r++) cnt[r] += (int)((M >> r) & 1u);
+                }
+                if (slot_patterns > 15) fail(QS_ERR_INVALID, "register phase: more than 15 counted patterns");
+                for (uint32_t r = 0; r < 32; r++) v[r] *= cd(P[np + 2 * cnt[r]], P[np + 2 * cnt[r] + 1]);
+                break;
+            }
+            default: {  // RP_PH
+                const uint32_t K = mask(ea) & mask(eb);
+                for (uint32_t r = 0; r < 32; r++)
+                    if ((K >> r) & 1u) v[r] *= cd(P[0], P[1]);
+                break;
+            }
+            }
+        }
+        for (uint32_t r = 0; r < 32; r++) tile[index(r, sigma)] = v[r];
+    }
+}
+
 void apply_kop(State &tile, int m, const KOp &k, const std::vector<double> &mats, uint64_t base) {
     auto C = [&](int i) { return cd(mats[(size_t)k.mat + 2 * i], mats[(size_t)k.mat + 2 * i + 1]); };
     const uint32_t N = 1u << m;
@@ -392,6 +552,7 @@ void apply_kop(State &tile, int m, const KOp &k, const std::vector<double> &mats
     case F_PHASE: case F_NEG: nt = 1; break;
     case F_H: case F_SWAP: case F_DIAG1: case F_DENSE1: nt = 2; break;
     case F_DIAG2: case F_DENSE2: nt = 4; break;
+    case F_RPHASE: apply_rphase(tile, m, k, mats); return;
     default: fail(QS_ERR_INVALID, "tile op kind outside this check");
     }
     uint32_t fm = 0;
@@ -509,12 +670,12 @@ void apply_phasefn(State &psi, const Op &op) {
 int g_planned_passes = 0, g_planned_terms = 0, g_phasefns = 0;
 
 void check_planned(const State &psi0, const State &ref, int n, const std::vector<Op> &ops, int chunk_m, int prec,
-                   int mode, double tol, int trial, int dtype = QS_C128) {
+                   int mode, double tol, int trial, int dtype = QS_C128, bool reg_phases = false) {
     DeviceState st;
     st.n = n;
     st.dtype = dtype;
     st.prec = prec;
-    st.reg_phases = false;  // complex64: the shared-memory ops, not register phases
+    st.reg_phases = reg_phases;  // complex64: register phases, or one shared-memory sweep per op
     qs_options o{};
     o.mode = mode;
     o.chunk_m = chunk_m;
@@ -549,9 +710,14 @@ void check_planned(const State &psi0, const State &ref, int n, const std::vector
             if ((p.lmask >> b) & 1ull) pos[b] = r++;
         std::vector<double> mats;
         std::vector<KOp> kops;
-        for (const Op &op : prog) {
-            kops.push_back(make_tile_kop(op, pos, mats));
-            g_planned_terms += (int)op.hi.size();
+        if (dtype == QS_C64 && reg_phases && rphase_applicable(r, kTileThreadBits)) {
+            // the register-phase programs launch_pass_ops builds for complex64 tiles
+            kops = build_register_phases(prog, pos, r, kTileThreadBits, mats);
+        } else {
+            for (const Op &op : prog) {
+                kops.push_back(make_tile_kop(op, pos, mats));
+                g_planned_terms += (int)op.hi.size();
+            }
         }
         if (dtype == QS_C128 && prec == QS_PREC_FP64) kops = join_h_cdiag(kops, mats);
         psi = run_tiles(psi, n, p.lmask, kops, mats);
@@ -761,6 +927,9 @@ int main(int argc, char **argv) {
                 const State ref2 = run(q0, ops2);
                 for (int prec : {QS_PREC_FP64, QS_PREC_DF32})
                     check_planned(q0, ref2, n2, ops2, 6, prec, QS_MODE_AUTO, tol, trial);
+                // complex64 register phases: tiles of 2^13 amplitudes (256 threads x 32
+                // registers), the phase programs interpreted thread by thread
+                check_planned(q0, ref2, n2, ops2, 13, QS_PREC_FP64, QS_MODE_AUTO, tol, trial, QS_C64, true);
             }
             check_tpb(g, n, mix, tol, trial);
         } catch (const Error &e) {
@@ -769,11 +938,13 @@ int main(int argc, char **argv) {
         }
     }
     if (trials >= 2) check(g_tpb_taken > 0, "booster never took an op", -1);
+    if (trials >= 4) check(g_rp_members > 0, "no register phase interpreted", -1);
     // QFT-like circuits must have exercised the join
     if (trials >= 2) check(g_joins > 0, "no Hadamard joined with its controlled block", -1);
         if (trials >= 4) check(g_planned_terms > 0 && g_phasefns > 0, "planned path not exercised", -1);
     std::printf("%s (%d trials, %d joined Hadamards, %d planned passes, %d non-local terms, %d phase functions, "
-                "%d booster ops)\n",
-                g_bad ? "FAIL" : "OK", trials, g_joins, g_planned_passes, g_planned_terms, g_phasefns, g_tpb_taken);
+                "%d booster ops, %d register-phase members)\n",
+                g_bad ? "FAIL" : "OK", trials, g_joins, g_planned_passes, g_planned_terms, g_phasefns, g_tpb_taken,
+                g_rp_members);
     return g_bad ? 1 : 0;
 }

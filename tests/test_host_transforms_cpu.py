@@ -1,7 +1,8 @@
 """CPU test of the host rewrites the executor applies before its kernels run (global-phase
 fold, deferred Hadamard scale, gate fusion, U3 split, diagonal merge with non-local
-controlled phases, their chunk-pass order, and the Tensor Product Booster's prefix and
-groups): builds ``host_transforms_check.cpp``
+controlled phases, their chunk-pass order, the Tensor Product Booster's prefix and groups,
+and the complex64 register-phase programs, interpreted thread by thread as the chunk
+kernel runs them): builds ``host_transforms_check.cpp``
 against the package's host sources with g++ and runs it on seeded random circuits.  Each
 rewrite must leave a 10-qubit state unchanged to 1e-12 and keep the limits the kernels
 rely on; the resulting tile programs (kernel ops on tile positions, with non-local terms
