@@ -488,6 +488,10 @@ std::vector<KOp> build_register_phases(const std::vector<Op> &ops, const int *po
             std::vector<int> pairs;
             cd e, f;
         };
+        // consecutive one-position phases and sign pairs (diagonal, so in any order) collect in
+        // a run that becomes one RP_PH member in its run form (slot field 1) when it holds
+        // at least kRpMinRunPhases phases; pay: (position, re, im) per phase
+        constexpr int kPhaseRun = -1;
         std::vector<Pending> pend;
         uint32_t x_slots = 0;  // slots an exchange may have relabelled (bits of sigma it toggles)
         for (int i : best) {
@@ -496,9 +500,19 @@ std::vector<KOp> build_register_phases(const std::vector<Op> &ops, const int *po
             if (e.type == RP_X) x_slots |= 1u << slot_of[e.tgt];
             const int ea = enc(e.a), eb = enc(e.b), pair = ea | eb << 5;
             Pending *last = pend.empty() ? nullptr : &pend.back();
-            if (e.type == RP_NEG) {
-                if (last && last->type == RP_NEG && last->pairs.size() < 8) last->pairs.push_back(pair);
-                else pend.push_back({RP_NEG, 0, 0, 0, {}, {pair}, 0.0, 0.0});
+            const bool one_pos_phase = e.type == RP_PH && e.a == e.b;
+            if (one_pos_phase || e.type == RP_NEG) {
+                if (!last || last->type != kPhaseRun || (int)last->pay.size() / 3 >= kRpMaxRunPhases ||
+                    (int)last->pairs.size() >= kRpMaxRunPairs)
+                    pend.push_back({kPhaseRun, 0, 0, 0, {}, {}, 0.0, 0.0});
+                Pending &run = pend.back();
+                if (one_pos_phase) {
+                    run.pay.push_back((double)ea);
+                    run.pay.push_back(e.pay[0]);
+                    run.pay.push_back(e.pay[1]);
+                } else {
+                    run.pairs.push_back(pair);
+                }
                 continue;
             }
             if (e.type == RP_PARITY) {
@@ -525,15 +539,31 @@ std::vector<KOp> build_register_phases(const std::vector<Op> &ops, const int *po
             pend.push_back(std::move(p));
         }
         k.mat = (int32_t)mats.size();
-        mats.push_back((double)pend.size());
+        mats.push_back(0.0);  // member count, set below (a short run of phases emits several)
+        int n_emitted = 0;
         auto emit = [&](int type, int slot, int ea, int eb, const std::vector<double> &pay) {
+            n_emitted++;
             // the device reads codes below 2^23 without a conversion instruction
             if (pay.size() >= 128) fail(QS_ERR_INVALID, "internal: register-phase member payload too long");
             mats.push_back((double)(type | slot << 3 | ea << 6 | eb << 11 | (int)pay.size() << 16));
             mats.insert(mats.end(), pay.begin(), pay.end());
         };
         for (const Pending &p : pend) {
-            if (p.type == RP_NEG) {
+            if (p.type == kPhaseRun) {
+                const int nf = (int)p.pay.size() / 3, ns = (int)p.pairs.size();
+                if (nf >= kRpMinRunPhases) {
+                    std::vector<double> pay = p.pay;
+                    pay.insert(pay.end(), p.pairs.begin(), p.pairs.end());
+                    emit(RP_PH, 1, nf, ns, pay);
+                } else {
+                    for (int q = 0; q < nf; q++)
+                        emit(RP_PH, 0, (int)p.pay[3 * q], (int)p.pay[3 * q], {p.pay[3 * q + 1], p.pay[3 * q + 2]});
+                    for (int q = 0; q < ns; q += 8) {
+                        const int c = std::min(8, ns - q);
+                        emit(RP_NEG, c - 1, 0, 0, std::vector<double>(p.pairs.begin() + q, p.pairs.begin() + q + c));
+                    }
+                }
+            } else if (p.type == RP_NEG) {
                 emit(RP_NEG, (int)p.pairs.size() - 1, 0, 0, std::vector<double>(p.pairs.begin(), p.pairs.end()));
             } else if (p.type == RP_PARITY && p.pairs.size() == 1) {
                 emit(RP_PARITY, 0, p.pairs[0] & 31, p.pairs[0] >> 5,
@@ -553,6 +583,7 @@ std::vector<KOp> build_register_phases(const std::vector<Op> &ops, const int *po
                 emit(p.type, p.slot, p.ea, p.eb, p.pay);
             }
         }
+        mats[(size_t)k.mat] = (double)n_emitted;
         k.nmat = (int32_t)mats.size() - k.mat;
         out.push_back(k);
         phases++;

@@ -65,12 +65,20 @@ enum RpType : int {
     RP_DIAG,    // multiply by d[2 x_a + x_b] (one position: a = b, d1 = d2 unused)
     RP_NEG,     // negate where an odd number of slot + 1 patterns x_a x_b hold; the pairs
                 // (a | b << 5) are payload reals 0..slot
-    RP_PH,      // multiply by payload[0] + i payload[1] where x_a = x_b = 1
+    RP_PH,      // multiply by payload[0] + i payload[1] where x_a = x_b = 1; with slot field 1
+                // (run form) a = nf one-position phases (position, re, im) and b = ns sign
+                // pairs (a | b << 5): multiply by every phase whose position bit is 1, negate
+                // where an odd number of pairs have both bits 1
     RP_PARITY,  // multiply by payload (0, 1) where x_a = x_b, by payload (2, 3) elsewhere
     RP_PARITYN, // np parity patterns (a | b << 5), then np + 1 factors (re, im) indexed by the
                 // number of patterns with x_a != x_b (equal-angle RZZ / RZ layers), np <= 15
 };
 constexpr int kRpMaxParity = 15;
+// Run form of RP_PH: at most 31 phases and 31 sign pairs (5-bit counts); below
+// kRpMinRunPhases phases the separate members cost less.
+constexpr int kRpMaxRunPhases = 31;
+constexpr int kRpMaxRunPairs = 31;
+constexpr int kRpMinRunPhases = 3;
 // RP_R0: 7 reals (m00 real; m01, m10, m11 as re, im), only on slots whose bit of sigma is 0
 // in every lane: positions 4 and up, with no exchange on the slot earlier in the phase (an
 // exchange toggles the slot's bit of sigma), so the matrix is never conjugated

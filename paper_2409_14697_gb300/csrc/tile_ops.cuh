@@ -388,6 +388,79 @@ __device__ __forceinline__ void rp_ph(float2 (&v)[kRpRegs], float pr, float pi, 
     }
 }
 
+// Run form of RP_PH: multiply register r by T * prod_j (x_j(r) ? g_j : 1) * (-1)^(odd sign
+// pairs), where T is the product of the phases on thread-index positions and g_j that of the
+// phases on register slot j.  The slot factors are built as two tables over the register
+// bits (slots 0-2: 8 entries, slots 3-4: 4) indexed by x = r ^ sigma, then permuted into
+// register order by sigma's bits; each register then costs two complex multiplies.
+__device__ __forceinline__ void rp_swap_if(bool c, float2 &a, float2 &b) {
+    const float2 x = a, y = b;
+    a = c ? y : x;
+    b = c ? x : y;
+}
+
+__device__ __forceinline__ float2 rp_mul2(float2 a, float2 b) { return rp_cmul(a, b.x, b.y); }
+
+__device__ __forceinline__ void rp_phase_run(float2 (&v)[kRpRegs], const float *P, int nf, int ns, uint32_t sigma,
+                                             uint32_t tid) {
+    float2 T = make_float2(1.f, 0.f), g0 = T, g1 = T, g2 = T, g3 = T, g4 = T;
+    for (int q = 0; q < nf; q++) {
+        const int enc = (int)rp_int(P[3 * q]);
+        const float2 f = make_float2(P[3 * q + 1], P[3 * q + 2]);
+        if (rp_is_slot(enc)) {
+            switch (enc & 15) {
+            case 0: g0 = rp_mul2(g0, f); break;
+            case 1: g1 = rp_mul2(g1, f); break;
+            case 2: g2 = rp_mul2(g2, f); break;
+            case 3: g3 = rp_mul2(g3, f); break;
+            default: g4 = rp_mul2(g4, f); break;
+            }
+        } else {
+            const float2 t = rp_mul2(T, f);
+            T = (rp_mask(enc, sigma, tid) & 1u) ? t : T;
+        }
+    }
+    uint32_t K = 0;
+    for (int q = 0; q < ns; q++) {
+        const int e = (int)rp_int(P[3 * nf + q]);
+        K ^= rp_mask(e & 31, sigma, tid) & rp_mask(e >> 5, sigma, tid);
+    }
+    float2 A[8], B[4];
+    A[0] = T;
+    A[1] = rp_mul2(T, g0);
+    A[2] = rp_mul2(T, g1);
+    A[3] = rp_mul2(A[1], g1);
+#pragma unroll
+    for (int i = 0; i < 4; i++) A[4 + i] = rp_mul2(A[i], g2);
+    B[0] = make_float2(1.f, 0.f);
+    B[1] = g3;
+    B[2] = g4;
+    B[3] = rp_mul2(g3, g4);
+    // register r holds x = r ^ sigma: entry x of a table moves to register x ^ sigma
+#pragma unroll
+    for (int b = 0; b < 3; b++) {
+        const bool c = (sigma >> b) & 1u;
+#pragma unroll
+        for (int i = 0; i < 8; i++)
+            if (!(i & (1 << b))) rp_swap_if(c, A[i], A[i | (1 << b)]);
+    }
+#pragma unroll
+    for (int b = 0; b < 2; b++) {
+        const bool c = (sigma >> (3 + b)) & 1u;
+#pragma unroll
+        for (int i = 0; i < 4; i++)
+            if (!(i & (1 << b))) rp_swap_if(c, B[i], B[i | (1 << b)]);
+    }
+#pragma unroll
+    for (int r = 0; r < kRpRegs; r++) {
+        float2 d = rp_mul2(A[r & 7], B[r >> 3]);
+        const uint32_t sgn = (K << (31 - r)) & 0x80000000u;
+        d.x = __uint_as_float(__float_as_uint(d.x) ^ sgn);
+        d.y = __uint_as_float(__float_as_uint(d.y) ^ sgn);
+        v[r] = rp_mul2(v[r], d);
+    }
+}
+
 // Tile index of register 0 of this thread (register r: base ^ XOR of pb[j] over the bits
 // j of r), sigma and the per-slot position bits of phase ph.
 __device__ __forceinline__ void rp_geometry(const KOp &ph, uint32_t tid, uint32_t (&pb)[kRpBits], uint32_t &base,
@@ -582,7 +655,10 @@ __device__ __forceinline__ void rphase_run(float2 *tile, const KOp &ph, const fl
             rp_table(v, P + np + 2 * ku, c0, c1, c2, c3);
             break;
         }
-        default: rp_ph(v, P[0], P[1], rp_mask(ea, sigma, tid) & rp_mask(eb, sigma, tid)); break;
+        default:  // RP_PH: one phase, or a run of one-position phases and sign pairs
+            if (J == 1) rp_phase_run(v, P, ea, eb, sigma, tid);
+            else rp_ph(v, P[0], P[1], rp_mask(ea, sigma, tid) & rp_mask(eb, sigma, tid));
+            break;
         }
     }
     // the addresses are rebuilt from shared memory rather than kept live through the

@@ -329,6 +329,7 @@ int g_joins = 0;
 // order with the same operand encoding, conjugation by sigma, exchange relabelling and
 // parity counting; then stores in the final register order.  Double precision.
 int g_rp_members = 0;
+int g_rp_runs = 0;
 
 void apply_rphase(State &tile, int m, const KOp &ph, const std::vector<double> &mats) {
     const int nt = ph.nt;
@@ -470,7 +471,23 @@ void apply_rphase(State &tile, int m, const KOp &ph, const std::vector<double> &
                 for (uint32_t r = 0; r < 32; r++) v[r] *= cd(P[np + 2 * cnt[r]], P[np + 2 * cnt[r] + 1]);
                 break;
             }
-            default: {  // RP_PH
+            default: {  // RP_PH: one phase, or (slot field 1) a run of phases and sign pairs
+                if (J == 1) {
+                    g_rp_runs++;
+                    for (int q = 0; q < ea; q++) {
+                        const uint32_t K = mask((int)P[3 * q]);
+                        for (uint32_t r = 0; r < 32; r++)
+                            if ((K >> r) & 1u) v[r] *= cd(P[3 * q + 1], P[3 * q + 2]);
+                    }
+                    uint32_t K = 0;
+                    for (int q = 0; q < eb; q++) {
+                        const int e = (int)P[3 * ea + q];
+                        K ^= mask(e & 31) & mask(e >> 5);
+                    }
+                    for (uint32_t r = 0; r < 32; r++)
+                        if ((K >> r) & 1u) v[r] = -v[r];
+                    break;
+                }
                 const uint32_t K = mask(ea) & mask(eb);
                 for (uint32_t r = 0; r < 32; r++)
                     if ((K >> r) & 1u) v[r] *= cd(P[0], P[1]);
@@ -723,7 +740,7 @@ void check_planned(const State &psi0, const State &ref, int n, const std::vector
         psi = run_tiles(psi, n, p.lmask, kops, mats);
     }
     for (int c : seen) check(c == 1, "op not run exactly once", trial);
-    check(rel_err(ref, psi) < tol, "planned path", trial);
+    check(rel_err(ref, psi) < tol, reg_phases ? "planned path (register phases)" : "planned path", trial);
 }
 
 }  // namespace
@@ -939,12 +956,13 @@ int main(int argc, char **argv) {
     }
     if (trials >= 2) check(g_tpb_taken > 0, "booster never took an op", -1);
     if (trials >= 4) check(g_rp_members > 0, "no register phase interpreted", -1);
+    if (trials >= 4) check(g_rp_runs > 0, "no run of phases interpreted", -1);
     // QFT-like circuits must have exercised the join
     if (trials >= 2) check(g_joins > 0, "no Hadamard joined with its controlled block", -1);
         if (trials >= 4) check(g_planned_terms > 0 && g_phasefns > 0, "planned path not exercised", -1);
     std::printf("%s (%d trials, %d joined Hadamards, %d planned passes, %d non-local terms, %d phase functions, "
-                "%d booster ops, %d register-phase members)\n",
+                "%d booster ops, %d register-phase members, %d phase runs)\n",
                 g_bad ? "FAIL" : "OK", trials, g_joins, g_planned_passes, g_planned_terms, g_phasefns, g_tpb_taken,
-                g_rp_members);
+                g_rp_members, g_rp_runs);
     return g_bad ? 1 : 0;
 }
