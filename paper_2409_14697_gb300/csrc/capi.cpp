@@ -47,16 +47,19 @@ int device_sm_count() {
     return sms;
 }
 
+// Device buffers a state grows while it runs (scratch, parameter arenas, the booster's
+// sub-states) are stream-ordered allocations on the state's stream: growing one never waits
+// for the whole device (cudaFree does), which would stall a serving worker behind every
+// request in flight.
 void ensure_scratch(DeviceState &st, size_t bytes) {
     if (st.scratch_bytes >= bytes) return;
     if (st.scratch) {
-        QS_CUDA(cudaStreamSynchronize(st.stream));
-        QS_CUDA(cudaFree(st.scratch));
+        QS_CUDA(cudaFreeAsync(st.scratch, st.stream));
         st.scratch = nullptr;
         st.scratch_bytes = 0;
     }
     const size_t cap = std::max<size_t>(bytes, 1 << 20);
-    QS_CUDA(cudaMalloc(&st.scratch, cap));
+    QS_CUDA(cudaMallocAsync(&st.scratch, cap, st.stream));
     st.scratch_bytes = cap;
 }
 
@@ -68,10 +71,11 @@ void arena_begin(DeviceState &st) {
     st.arena_used = 0;
     const int c = st.arena_cur;
     if (st.arena_ev[c]) QS_CUDA(cudaEventSynchronize(st.arena_ev[c]));
-    // buffers this arena outgrew during its last use are idle now
+    // buffers this arena outgrew during its last use are idle now; the page-locked ones are
+    // kept until the state is freed (cudaFreeHost waits for the whole device)
     for (auto &r : st.arena_retired[c]) {
-        if (r.first) cudaFree(r.first);
-        if (r.second) cudaFreeHost(r.second);
+        if (r.first) QS_CUDA(cudaFreeAsync(r.first, st.stream));
+        if (r.second) st.pinned_retired.push_back(r.second);
     }
     st.arena_retired[c].clear();
 }
@@ -86,11 +90,11 @@ void arena_reserve(DeviceState &st, size_t bytes) {
     for (int c = 0; c < kArenas; c++) {
         if (st.arena_cap[c] >= bytes) continue;
         if (st.arena_ev[c]) QS_CUDA(cudaEventSynchronize(st.arena_ev[c]));
-        if (st.arena_dev[c]) QS_CUDA(cudaFree(st.arena_dev[c]));
-        if (st.arena_host[c]) QS_CUDA(cudaFreeHost(st.arena_host[c]));
+        if (st.arena_dev[c]) QS_CUDA(cudaFreeAsync(st.arena_dev[c], st.stream));
+        if (st.arena_host[c]) st.pinned_retired.push_back(st.arena_host[c]);
         st.arena_dev[c] = st.arena_host[c] = nullptr;
         st.arena_cap[c] = 0;
-        QS_CUDA(cudaMalloc(&st.arena_dev[c], bytes));
+        QS_CUDA(cudaMallocAsync(&st.arena_dev[c], bytes, st.stream));
         QS_CUDA(cudaMallocHost(&st.arena_host[c], bytes));
         st.arena_cap[c] = bytes;
     }
@@ -106,7 +110,7 @@ void *upload_params(DeviceState &st, const void *host, size_t bytes) {
         st.arena_retired[c].push_back({st.arena_dev[c], st.arena_host[c]});
         st.arena_dev[c] = st.arena_host[c] = nullptr;
         const size_t cap = std::max<size_t>(need * 2, 1 << 16);
-        QS_CUDA(cudaMalloc(&st.arena_dev[c], cap));
+        QS_CUDA(cudaMallocAsync(&st.arena_dev[c], cap, st.stream));
         QS_CUDA(cudaMallocHost(&st.arena_host[c], cap));
         st.arena_cap[c] = cap;
         st.arena_used = 0;
@@ -200,10 +204,10 @@ void free_device_state(DeviceState &d) {
     if (d.stream) cudaStreamSynchronize(d.stream);
     tpb_free(d);
     for (int c = 0; c < kArenas; c++) {
-        if (d.arena_dev[c]) cudaFree(d.arena_dev[c]);
+        if (d.arena_dev[c]) cudaFreeAsync(d.arena_dev[c], d.stream);
         if (d.arena_host[c]) cudaFreeHost(d.arena_host[c]);
         for (auto &r : d.arena_retired[c]) {
-            if (r.first) cudaFree(r.first);
+            if (r.first) cudaFreeAsync(r.first, d.stream);
             if (r.second) cudaFreeHost(r.second);
         }
         d.arena_retired[c].clear();
@@ -212,7 +216,9 @@ void free_device_state(DeviceState &d) {
         d.arena_ev[c] = nullptr;
         d.arena_cap[c] = 0;
     }
-    if (d.scratch) cudaFree(d.scratch);
+    for (void *p : d.pinned_retired) cudaFreeHost(p);
+    d.pinned_retired.clear();
+    if (d.scratch) cudaFreeAsync(d.scratch, d.stream);
     if (d.dev_err) cudaFree(d.dev_err);
     if (d.dev_norms) cudaFree(d.dev_norms);
     d.dev_norms = nullptr;

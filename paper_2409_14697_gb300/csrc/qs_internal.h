@@ -166,7 +166,7 @@ struct DeviceState {
     int prec = QS_PREC_FP64;  // complex128 arithmetic: QS_PREC_FP64 or QS_PREC_DF32
     bool reg_phases = true;   // complex64 chunk passes: register phases (2^13-amplitude tiles)
     cudaStream_t stream = nullptr;
-    // scratch for reductions (owned by the state)
+    // scratch for reductions (owned by the state; stream-ordered allocation on `stream`)
     void *scratch = nullptr;
     size_t scratch_bytes = 0;
     int num_sms = 0;
@@ -178,6 +178,7 @@ struct DeviceState {
     int arena_cur = 0;
     cudaEvent_t arena_ev[kArenas] = {};
     std::vector<std::pair<void *, void *>> arena_retired[kArenas];  // outgrown (device, pinned) buffers
+    std::vector<void *> pinned_retired;  // outgrown page-locked buffers, freed with the state
     // device error word written by bounded waits (QS_ERR_TIMEOUT), checked on sync
     int *dev_err = nullptr;
     // two FP64 squared norms (before / after) for the norm-preserving correction

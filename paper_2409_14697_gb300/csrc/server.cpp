@@ -123,21 +123,28 @@ void notify_server(Server *srv) { srv->cv.notify_all(); }
 
 namespace {
 
-// Sizes a slot's device and pinned buffers for requests of up to n qubits and top_k
-// amplitudes, so that serving them never frees memory (cudaFree and cudaFreeHost wait for
-// the whole device, which would hold a small request behind every large one in flight).
-void presize_slot(Slot &s, int n, uint32_t k) {
-    DeviceState &d = s.d;
-    d.n = n;
-    ensure_scratch(d, std::max(scratch_expz_bytes(n), scratch_topk_bytes(n, std::max<uint32_t>(k, 1))));
-    s.cap_n = n;
-    s.cap_k = std::max<uint32_t>(k, 1);
+// Result buffers of a slot for any request (QS_MAX_QUBITS + 1 values, 4096 amplitudes), so
+// they never grow: growing frees memory, and cudaFree / cudaFreeHost wait for the whole
+// device, which would stall the worker behind every request in flight.
+void presize_results(Slot &s) {
+    s.cap_n = QS_MAX_QUBITS;
+    s.cap_k = 4096;
     QS_CUDA(cudaMalloc(&s.d_out, sizeof(double) * (s.cap_n + 1)));
     QS_CUDA(cudaMalloc(&s.d_idx, sizeof(uint64_t) * s.cap_k));
     QS_CUDA(cudaMalloc(&s.d_amp, sizeof(double) * 2 * s.cap_k));
     QS_CUDA(cudaMallocHost(&s.h_out, sizeof(double) * (s.cap_n + 1)));
     QS_CUDA(cudaMallocHost(&s.h_idx, sizeof(uint64_t) * s.cap_k));
     QS_CUDA(cudaMallocHost(&s.h_amp, sizeof(double) * 2 * s.cap_k));
+}
+
+// A small-lane slot: also scratch for requests of up to n qubits and top-k amplitudes, and
+// parameter arenas of 1 MiB each, so small requests never grow (or free) anything.
+void presize_slot(Slot &s, int n, uint32_t k) {
+    DeviceState &d = s.d;
+    d.n = n;
+    const uint32_t kk = (uint32_t)std::min<uint64_t>(std::max<uint32_t>(k, 1), 1ull << n);
+    ensure_scratch(d, std::max(scratch_expz_bytes(n), scratch_topk_bytes(n, kk)));
+    presize_results(s);
     arena_reserve(d, (size_t)1 << 20);
 }
 
@@ -341,10 +348,12 @@ int qs_server_create(const qs_server_config *cfg, qs_server **out) {
             QS_CUDA(cudaMemset(s->d.dev_err, 0, sizeof(int)));
             QS_CUDA(cudaMallocHost(&s->h_err, sizeof(int)));
             *s->h_err = 0;
-            if (i >= cfg->max_slots && cfg->small_max_qubits > 0) {
-                const int ns = std::min(cfg->small_max_qubits, QS_MAX_QUBITS);
-                presize_slot(*s, ns, (uint32_t)std::min<uint64_t>(1ull << std::min(ns, 12), 4096));
-            }
+            // small slots: scratch and arenas for their largest request; every slot: result
+            // buffers for any request (at most QS_MAX_QUBITS values and 4096 amplitudes)
+            if (i >= cfg->max_slots && cfg->small_max_qubits > 0)
+                presize_slot(*s, std::min(cfg->small_max_qubits, QS_MAX_QUBITS), 4096);
+            else
+                presize_results(*s);
         }
         S.worker = std::thread([&S]() { S.run(); });
     } catch (...) {

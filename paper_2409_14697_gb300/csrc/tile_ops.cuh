@@ -636,14 +636,9 @@ __device__ __forceinline__ void rphase_run(float2 *tile, const KOp &ph, const fl
             // kept in 4 bit planes (a ripple counter over the 32 registers at once)
             const int np = (len - 2) / 3;
             uint32_t c0 = 0, c1 = 0, c2 = 0, c3 = 0;
-            int ku = 0;  // odd patterns on bits that are the same for every register
             for (int q = 0; q < np; q++) {
                 const int e = (int)rp_int(P[q]);
                 const uint32_t M = rp_mask(e & 31, sigma, tid) ^ rp_mask(e >> 5, sigma, tid);
-                if (!rp_is_slot(e & 31) && !rp_is_slot(e >> 5)) {
-                    ku += (int)(M & 1u);
-                    continue;
-                }
                 uint32_t cy = c0 & M;
                 c0 ^= M;
                 uint32_t cz = c1 & cy;
@@ -652,7 +647,7 @@ __device__ __forceinline__ void rphase_run(float2 *tile, const KOp &ph, const fl
                 c2 ^= cz;
                 c3 ^= cy;
             }
-            rp_table(v, P + np + 2 * ku, c0, c1, c2, c3);
+            rp_table(v, P + np, c0, c1, c2, c3);
             break;
         }
         default:  // RP_PH: one phase, or a run of one-position phases and sign pairs

@@ -133,14 +133,13 @@ void tpb_execute(DeviceState &st, const std::vector<Op> &ops, const TpbPlan &tp,
     const int G = (int)tp.group_mask.size();
     size_t need = 0;
     for (uint64_t g : tp.group_mask) need += ((B << __builtin_popcountll(g)) + 255) & ~size_t(255);
-    if (st.tpb_buf_bytes < need) {
+    if (st.tpb_buf_bytes < need) {  // stream-ordered: no wait for other streams' work
         if (st.tpb_buf) {
-            QS_CUDA(cudaStreamSynchronize(st.stream));
-            QS_CUDA(cudaFree(st.tpb_buf));
+            QS_CUDA(cudaFreeAsync(st.tpb_buf, st.stream));
             st.tpb_buf = nullptr;
             st.tpb_buf_bytes = 0;
         }
-        QS_CUDA(cudaMalloc(&st.tpb_buf, need));
+        QS_CUDA(cudaMallocAsync(&st.tpb_buf, need, st.stream));
         st.tpb_buf_bytes = need;
     }
     const void *tables[kTpbMaxGroups];
@@ -180,7 +179,7 @@ void tpb_free(DeviceState &d) {
         delete d.tpb_sub[g];
         d.tpb_sub[g] = nullptr;
     }
-    if (d.tpb_buf) cudaFree(d.tpb_buf);
+    if (d.tpb_buf) cudaFreeAsync(d.tpb_buf, d.stream);
     d.tpb_buf = nullptr;
     d.tpb_buf_bytes = 0;
 }
