@@ -330,9 +330,18 @@ int qs_server_create(const qs_server_config *cfg, qs_server **out) {
     S.cfg = *cfg;
     try {
         QS_CUDA(cudaGetDevice(&S.device));
-        QS_CUDA(cudaDeviceGetDefaultMemPool(&S.pool, S.device));
-        uint64_t thr = UINT64_MAX;  // keep freed state memory in the pool for reuse
+        // a pool of the server's own for the request states: freed state memory stays in it for
+        // reuse, but an allocation never reuses memory whose free is still pending on another
+        // slot's stream (that would make the new request wait for the old one's work)
+        cudaMemPoolProps props{};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = S.device;
+        QS_CUDA(cudaMemPoolCreate(&S.pool, &props));
+        uint64_t thr = UINT64_MAX;
         QS_CUDA(cudaMemPoolSetAttribute(S.pool, cudaMemPoolAttrReleaseThreshold, &thr));
+        int no_wait = 0;
+        QS_CUDA(cudaMemPoolSetAttribute(S.pool, cudaMemPoolReuseAllowInternalDependencies, &no_wait));
         // small-lane slots get the device's highest stream priority: when the persistent
         // kernels of a large request end, the CTA scheduler starts a small request's pending
         // kernels first instead of the large request's next pass
@@ -362,6 +371,7 @@ int qs_server_create(const qs_server_config *cfg, qs_server **out) {
             if (s->d.stream) cudaStreamDestroy(s->d.stream);
             delete s;
         }
+        if (S.pool) cudaMemPoolDestroy(S.pool);
         delete p;
         throw;
     }
@@ -497,6 +507,10 @@ int qs_server_destroy(qs_server *p) {
         if (s->h_err) cudaFreeHost(s->h_err);
         if (s->d.stream) cudaStreamDestroy(s->d.stream);
         delete s;
+    }
+    if (S.pool) {
+        cudaDeviceSynchronize();  // the pool's last frees are stream-ordered
+        cudaMemPoolDestroy(S.pool);
     }
     delete p;
     QS_API_END

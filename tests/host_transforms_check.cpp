@@ -947,6 +947,37 @@ int main(int argc, char **argv) {
                 // complex64 register phases: tiles of 2^13 amplitudes (256 threads x 32
                 // registers), the phase programs interpreted thread by thread
                 check_planned(q0, ref2, n2, ops2, 13, QS_PREC_FP64, QS_MODE_AUTO, tol, trial, QS_C64, true);
+                // layers of one-qubit phases (P, S, T) with CZ and U3: runs of phases
+                std::vector<Op> ph;
+                std::uniform_real_distribution<double> ang(0.0, 2.0 * M_PI);
+                for (int layer = 0; layer < 6; layer++) {
+                    for (int q = 0; q < n2; q++) {
+                        qs_gate r{};
+                        r.type = (q % 3 == 0) ? QS_S : (q % 3 == 1) ? QS_T : QS_P;
+                        r.nq = 1;
+                        r.q[0] = q;
+                        r.p[0] = ang(g);
+                        ph.push_back(lower_gate(r));
+                    }
+                    for (int a = layer % 2; a + 1 < n2; a += 2) {
+                        qs_gate r{};
+                        r.type = QS_CZ;
+                        r.nq = 2;
+                        r.q[0] = a;
+                        r.q[1] = a + 1;
+                        ph.push_back(lower_gate(r));
+                    }
+                    for (int q = 0; q < n2; q++) {
+                        qs_gate r{};
+                        r.type = QS_U3;
+                        r.nq = 1;
+                        r.q[0] = q;
+                        for (double &p : r.p) p = ang(g);
+                        ph.push_back(lower_gate(r));
+                    }
+                }
+                const State ref3 = run(q0, ph);
+                check_planned(q0, ref3, n2, ph, 13, QS_PREC_FP64, QS_MODE_AUTO, tol, trial, QS_C64, true);
             }
             check_tpb(g, n, mix, tol, trial);
         } catch (const Error &e) {

@@ -301,3 +301,25 @@ def test_qft_hadamard_joined_with_controlled_block(qs, n, m, prec):
         assert st["tile_sweeps"] < st["ops_after_fuse"]
     else:
         assert st["tile_sweeps"] == st["ops_after_fuse"]
+
+
+@pytest.mark.parametrize("n", [13, 20])
+def test_register_phases_phase_layers(qs, n):
+    """complex64 register phases with layers of one-qubit phases (S, T, P on every qubit),
+    CZ brickwork and U3: runs of phases and sign pairs applied as one member, against the
+    oracle."""
+    r = np.random.default_rng(n)
+    gates = []
+    for layer in range(6):
+        for q in range(n):
+            name = ("s", "t", "p")[q % 3]
+            gates.append((name, (q,), (float(r.uniform(0, 6.28)),) if name == "p" else ()))
+        for a in range(layer % 2, n - 1, 2):
+            gates.append(("cz", (a, a + 1), ()))
+        for q in range(n):
+            gates.append(("u3", (q,), tuple(float(x) for x in r.uniform(0, 6.28, 3))))
+    psi0 = inputs.gaussian_state(n, seed=n).astype(np.complex64)
+    want = oracle.run(psi0.astype(np.complex128), n, gates)
+    got, st = _run_c64(qs, n, psi0, gates)
+    assert np.max(np.abs(got - want)) <= TOL_C64
+    assert fidelity_gap(got, want) <= 1e-6
