@@ -8,8 +8,8 @@
 // A request's work is queued on its slot's stream: stream-ordered state allocation
 // (cudaMallocAsync), the initial state (|0...0> or the caller's amplitudes), the planned
 // circuit, the <Z_q> reduction, top-K, and copies of the results into pinned host memory,
-// then a host callback that timestamps completion.  The worker then retires the slot
-// (stream-ordered free) and publishes the result.  All kernels are deterministic (no
+// then an event that the worker polls to timestamp completion.  The worker then retires
+// the slot (stream-ordered free) and publishes the result.  All kernels are deterministic (no
 // floating-point atomics, fixed reduction order, the plan depends only on the circuit),
 // so a result is bitwise the same alone and in any mix.
 #include <atomic>
@@ -78,7 +78,7 @@ struct Slot {
     void *h_init = nullptr;  // pinned staging of the initial amplitudes
     size_t h_init_cap = 0;
     int *h_err = nullptr;    // pinned copy of the slot's device error word
-    std::atomic<int> done{0};
+    cudaEvent_t ev_done = nullptr;  // recorded after the request's last operation
     Clock::time_point t_done;
 };
 
@@ -104,22 +104,11 @@ struct Server {
     void finish_slot(Slot &s);
 };
 
-void notify_server(Server *srv);
-
 namespace {
-
-void CUDART_CB on_done(void *p) {
-    Slot *s = (Slot *)p;
-    s->t_done = Clock::now();
-    s->done.store(1, std::memory_order_release);
-    notify_server(s->srv);
-}
 
 size_t amp_bytes_of(int dtype) { return dtype == QS_C128 ? 16 : 8; }
 
 }  // namespace
-
-void notify_server(Server *srv) { srv->cv.notify_all(); }
 
 namespace {
 
@@ -200,8 +189,10 @@ void Server::start_request(Slot &s, Request &r) {
     QS_CUDA(cudaMemcpyAsync(s.h_err, d.dev_err, sizeof(int), cudaMemcpyDeviceToHost, d.stream));
     QS_CUDA(cudaFreeAsync(d.psi, d.stream));
     d.psi = nullptr;
-    s.done.store(0);
-    QS_CUDA(cudaLaunchHostFunc(d.stream, on_done, &s));
+    // completion is polled with the event (host functions of independent streams may run
+    // one after the other in launch order, which would finish a small request only after
+    // every large one launched before it)
+    QS_CUDA(cudaEventRecord(s.ev_done, d.stream));
 }
 
 void Server::finish_slot(Slot &s) {
@@ -232,8 +223,17 @@ void Server::run() {
     cudaSetDevice(device);
     for (;;) {
         // 1. retire finished slots
-        for (Slot *s : slots)
-            if (s->busy && s->done.load(std::memory_order_acquire)) finish_slot(*s);
+        for (Slot *s : slots) {
+            if (!s->busy) continue;
+            const cudaError_t q = cudaEventQuery(s->ev_done);
+            if (q == cudaErrorNotReady) {
+                cudaGetLastError();  // not an error: clear it so later launch checks do not see it
+                continue;
+            }
+            s->t_done = Clock::now();
+            if (q != cudaSuccess && *s->h_err == 0) *s->h_err = QS_ERR_CUDA;
+            finish_slot(*s);
+        }
         // 2. admit: large requests in submission order (the first that cannot start holds
         // back the later large ones); small requests whenever a slot and the budget allow,
         // small-lane slots first
@@ -301,9 +301,8 @@ void Server::run() {
         bool any_busy = false;
         for (Slot *s : slots) any_busy |= s->busy;
         if (!admitted) {
-            // wait for a submission, or poll slot completion at a fine grain
-            // completion callbacks and submissions notify; the timeout is a safety net
-            cv.wait_for(lk, std::chrono::milliseconds(any_busy ? 1 : 20));
+            // wait for a submission (it notifies), or poll the busy slots' events again
+            cv.wait_for(lk, any_busy ? std::chrono::microseconds(200) : std::chrono::microseconds(20000));
         }
     }
 }
@@ -357,6 +356,7 @@ int qs_server_create(const qs_server_config *cfg, qs_server **out) {
             QS_CUDA(cudaMemset(s->d.dev_err, 0, sizeof(int)));
             QS_CUDA(cudaMallocHost(&s->h_err, sizeof(int)));
             *s->h_err = 0;
+            QS_CUDA(cudaEventCreateWithFlags(&s->ev_done, cudaEventDisableTiming));
             // small slots: scratch and arenas for their largest request; every slot: result
             // buffers for any request (at most QS_MAX_QUBITS values and 4096 amplitudes)
             if (i >= cfg->max_slots && cfg->small_max_qubits > 0)
@@ -505,6 +505,7 @@ int qs_server_destroy(qs_server *p) {
         cudaFreeHost(s->h_out); cudaFreeHost(s->h_idx); cudaFreeHost(s->h_amp);
         if (s->h_init) cudaFreeHost(s->h_init);
         if (s->h_err) cudaFreeHost(s->h_err);
+        if (s->ev_done) cudaEventDestroy(s->ev_done);
         if (s->d.stream) cudaStreamDestroy(s->d.stream);
         delete s;
     }

@@ -153,11 +153,12 @@ def test_borrowed_initial_amplitudes(qs):
 
 def test_small_requests_overtake_large_ones(qs):
     """One regular slot, held by large requests, and a small lane of two slots: small
-    requests submitted after two large ones start at once and finish before the second
-    large one, whose latency includes waiting for the first (large ones keep their order).
-    Results are those of the oracle."""
+    requests submitted after two large ones start at once and finish before the first large
+    one (whose kernels run meanwhile; the small lane's streams have the higher priority), and
+    the second large one waits for the first (large ones keep their order).  Results are
+    those of the oracle."""
     n_big, k = 26, 8
-    big = inputs.brickwork(n_big, 30, seed=1)
+    big = inputs.brickwork(n_big, 60, seed=1)
     sv = qs.qs_server_create(8 << 30, max_slots=1, small_slots=2, small_max_qubits=12)
     try:
         t_big = [qs.qs_submit(sv, n_big, 2, big, top_k=k) for _ in range(2)]
@@ -169,7 +170,8 @@ def test_small_requests_overtake_large_ones(qs):
         qs.qs_server_drain(sv)
         qs.qs_server_destroy(sv)
     assert r_big[0]["latency_s"] < r_big[1]["latency_s"]
-    assert max(r["latency_s"] for r in r_small) < r_big[1]["latency_s"]
+    assert max(r["latency_s"] for r in r_small) < r_big[0]["latency_s"], \
+        ([r["latency_s"] for r in r_small], r_big[0]["latency_s"])
     assert np.array_equal(r_big[0]["expz"], r_big[1]["expz"])
     for (n, g), r in zip(smalls, r_small):
         want = oracle.run(oracle.zero_state(n), n, g)
