@@ -27,6 +27,11 @@ import time
 
 import numpy as np
 
+# Hardware work queues for concurrent streams (read when the CUDA context is created): with
+# the default 8, the served workload's 16 slot streams share queues and a small request's
+# kernels wait behind a large one's.
+os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 

@@ -277,7 +277,10 @@ int qs_expectation_z_noalloc(const void *dev_psi, int n_qubits, qs_dtype dt, voi
  * norm and its top_k amplitudes.  Results are bitwise identical whatever else runs.
  * Large requests are admitted in submission order.  Small requests (small_max_qubits) may
  * overtake them: they take a free small slot, else a free regular one, as soon as the
- * budget allows, so a burst of large states does not hold them back. */
+ * budget allows, so a burst of large states does not hold them back.  Their streams have
+ * the device's highest priority.  Slots only overlap on the device if their streams get
+ * hardware queues of their own: set CUDA_DEVICE_MAX_CONNECTIONS (default 8, at most 32)
+ * to at least the number of slots before the process first uses CUDA. */
 
 typedef struct {
     uint64_t hbm_budget_bytes;  /* admission budget for the states in flight */
