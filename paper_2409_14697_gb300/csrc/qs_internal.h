@@ -198,6 +198,9 @@ void run_circuit(DeviceState &d, const std::vector<Op> &ops, const qs_options &o
 void free_device_state(DeviceState &d);
 // Frees the booster's sub-states and memory (part of free_device_state).
 void tpb_free(DeviceState &d);
+// Creates the booster's sub-states of d now, each with parameter arenas of `arena_bytes`
+// (so that a later call needs no page-locked allocation).
+void tpb_reserve(DeviceState &d, size_t arena_bytes);
 void arena_begin(DeviceState &st);
 void arena_end(DeviceState &st);
 // Gives every parameter arena of st at least `bytes` of capacity now, so that later calls

@@ -358,11 +358,17 @@ int qs_server_create(const qs_server_config *cfg, qs_server **out) {
             *s->h_err = 0;
             QS_CUDA(cudaEventCreateWithFlags(&s->ev_done, cudaEventDisableTiming));
             // small slots: scratch and arenas for their largest request; every slot: result
-            // buffers for any request (at most QS_MAX_QUBITS values and 4096 amplitudes)
-            if (i >= cfg->max_slots && cfg->small_max_qubits > 0)
+            // buffers for any request (at most QS_MAX_QUBITS values and 4096 amplitudes),
+            // parameter arenas and the booster's sub-states.  Page-locked and plain device
+            // allocations make the device finish other streams' work first, so a request
+            // must not need one while others run.
+            if (i >= cfg->max_slots && cfg->small_max_qubits > 0) {
                 presize_slot(*s, std::min(cfg->small_max_qubits, QS_MAX_QUBITS), 4096);
-            else
+            } else {
                 presize_results(*s);
+                arena_reserve(s->d, (size_t)4 << 20);
+                tpb_reserve(s->d, (size_t)256 << 10);
+            }
         }
         S.worker = std::thread([&S]() { S.run(); });
     } catch (...) {

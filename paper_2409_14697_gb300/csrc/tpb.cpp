@@ -170,6 +170,16 @@ void tpb_execute(DeviceState &st, const std::vector<Op> &ops, const TpbPlan &tp,
     stats.tpb_gates += (int64_t)tp.taken.size();
 }
 
+void tpb_reserve(DeviceState &d, size_t arena_bytes) {
+    for (int g = 0; g < kTpbMaxGroups; g++) {
+        if (!d.tpb_sub[g]) d.tpb_sub[g] = new DeviceState();
+        DeviceState &sub = *d.tpb_sub[g];
+        sub.stream = d.stream;
+        sub.dtype = d.dtype;
+        arena_reserve(sub, arena_bytes);
+    }
+}
+
 void tpb_free(DeviceState &d) {
     for (int g = 0; g < kTpbMaxGroups; g++) {
         if (!d.tpb_sub[g]) continue;

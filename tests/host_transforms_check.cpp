@@ -60,6 +60,7 @@ void run_circuit(DeviceState &, const std::vector<Op> &, const qs_options &, qs_
     fail(QS_ERR_INVALID, "no GPU in this check");
 }
 void free_device_state(DeviceState &) {}
+void arena_reserve(DeviceState &, size_t) { fail(QS_ERR_INVALID, "no GPU in this check"); }
 }  // namespace qs
 
 using namespace qs;
