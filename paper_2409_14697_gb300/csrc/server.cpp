@@ -79,6 +79,8 @@ struct Slot {
     size_t h_init_cap = 0;
     int *h_err = nullptr;    // pinned copy of the slot's device error word
     cudaEvent_t ev_done = nullptr;  // recorded after the request's last operation
+    void *own_psi = nullptr;        // small-lane slots: a state buffer of their own
+    size_t own_psi_bytes = 0;
     Clock::time_point t_done;
 };
 
@@ -144,7 +146,9 @@ void Server::start_request(Slot &s, Request &r) {
     d.n = r.n;
     d.dtype = r.dtype;
     const size_t state_bytes = r.bytes;
-    QS_CUDA(cudaMallocFromPoolAsync(&d.psi, state_bytes, pool, d.stream));
+    const bool own = s.own_psi && state_bytes <= s.own_psi_bytes;
+    if (own) d.psi = s.own_psi;
+    else QS_CUDA(cudaMallocFromPoolAsync(&d.psi, state_bytes, pool, d.stream));
     d.known_zero = false;
     if (r.init_borrowed) {
         QS_CUDA(cudaMemcpyAsync(d.psi, r.init_borrowed, state_bytes, cudaMemcpyHostToDevice, d.stream));
@@ -187,7 +191,7 @@ void Server::start_request(Slot &s, Request &r) {
         QS_CUDA(cudaMemcpyAsync(s.h_amp, s.d_amp, sizeof(double) * 2 * r.top_k, cudaMemcpyDeviceToHost, d.stream));
     }
     QS_CUDA(cudaMemcpyAsync(s.h_err, d.dev_err, sizeof(int), cudaMemcpyDeviceToHost, d.stream));
-    QS_CUDA(cudaFreeAsync(d.psi, d.stream));
+    if (!own) QS_CUDA(cudaFreeAsync(d.psi, d.stream));
     d.psi = nullptr;
     // completion is polled with the event (host functions of independent streams may run
     // one after the other in launch order, which would finish a small request only after
@@ -363,17 +367,34 @@ int qs_server_create(const qs_server_config *cfg, qs_server **out) {
             // allocations make the device finish other streams' work first, so a request
             // must not need one while others run.
             if (i >= cfg->max_slots && cfg->small_max_qubits > 0) {
-                presize_slot(*s, std::min(cfg->small_max_qubits, QS_MAX_QUBITS), 4096);
+                const int ns = std::min(cfg->small_max_qubits, 30);
+                presize_slot(*s, ns, 4096);
+                s->own_psi_bytes = (size_t)16 << ns;  // the largest small state, either dtype
+                QS_CUDA(cudaMalloc(&s->own_psi, s->own_psi_bytes));
             } else {
                 presize_results(*s);
                 arena_reserve(s->d, (size_t)4 << 20);
                 tpb_reserve(s->d, (size_t)256 << 10);
             }
         }
+        // grow the pool to the budget now (at most 90 % of the free memory): a pool that grows
+        // while requests run allocates device memory, and that makes the device finish the
+        // other slots' work first
+        {
+            size_t free_b = 0, total_b = 0;
+            QS_CUDA(cudaMemGetInfo(&free_b, &total_b));
+            const size_t reserve = std::min<size_t>(cfg->hbm_budget_bytes, free_b / 10 * 9);
+            void *p = nullptr;
+            cudaStream_t s0 = S.slots[0]->d.stream;
+            QS_CUDA(cudaMallocFromPoolAsync(&p, reserve, S.pool, s0));
+            QS_CUDA(cudaFreeAsync(p, s0));
+            QS_CUDA(cudaStreamSynchronize(s0));
+        }
         S.worker = std::thread([&S]() { S.run(); });
     } catch (...) {
         for (Slot *s : S.slots) {
             free_device_state(s->d);
+            if (s->own_psi) cudaFree(s->own_psi);
             if (s->d.stream) cudaStreamDestroy(s->d.stream);
             delete s;
         }
@@ -512,6 +533,7 @@ int qs_server_destroy(qs_server *p) {
         if (s->h_init) cudaFreeHost(s->h_init);
         if (s->h_err) cudaFreeHost(s->h_err);
         if (s->ev_done) cudaEventDestroy(s->ev_done);
+        if (s->own_psi) cudaFree(s->own_psi);
         if (s->d.stream) cudaStreamDestroy(s->d.stream);
         delete s;
     }
