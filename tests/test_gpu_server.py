@@ -161,6 +161,11 @@ def test_small_requests_overtake_large_ones(qs):
     big = inputs.brickwork(n_big, 60, seed=1)
     sv = qs.qs_server_create(8 << 30, max_slots=1, small_slots=2, small_max_qubits=12)
     try:
+        # first use of the server's slots and streams, alone (the first requests of a fresh
+        # server were measured not to overlap)
+        for n, dt, g in ((n_big, 2, big), (10, 1, inputs.brickwork(10, 2, seed=99)),
+                         (10, 1, inputs.brickwork(10, 2, seed=98))):
+            wait(qs, sv, qs.qs_submit(sv, n, dt, g, top_k=k), n, k)
         t_big = [qs.qs_submit(sv, n_big, 2, big, top_k=k) for _ in range(2)]
         smalls = [(10 + (i % 3), inputs.brickwork(10 + (i % 3), 20, seed=100 + i)) for i in range(6)]
         t_small = [qs.qs_submit(sv, n, 1, g, top_k=k) for n, g in smalls]
