@@ -897,10 +897,13 @@ class ServedInputs:
         return self.buf[(r["n"], r["dtype"])].data_ptr() if r["init_seed"] else 0
 
 
+SERVED_SMALL_MAX = 18   # requests of at most this many qubits may run in the small-request slots
+
+
 def served_run(qs, prepared, rate, prec):
     """Submits the prepared requests at their Poisson arrival times (scaled to `rate`) and
     polls until all are done; returns (latencies, wall seconds, server stats)."""
-    sv = qs.qs_server_create(150 * 10 ** 9, max_slots=8, small_slots=8, small_max_qubits=18)
+    sv = qs.qs_server_create(150 * 10 ** 9, max_slots=8, small_slots=8, small_max_qubits=SERVED_SMALL_MAX)
     lat = []
     pending = {}
     i = 0
@@ -979,16 +982,16 @@ def wl_served(args, count=None, loads=None):
     for rate in loads:
         nl, wall, st = served_run(qs, prepared, rate, prec)
         lat = nl[:, 1]
-        small = nl[nl[:, 0] <= 20, 1]
-        large = nl[nl[:, 0] > 20, 1]
+        small = nl[nl[:, 0] <= SERVED_SMALL_MAX, 1]
+        large = nl[nl[:, 0] > SERVED_SMALL_MAX, 1]
         rows[f"{rate:g}"] = {"requests_per_s": round(count / wall, 2),
                              "p50_latency_s": round(float(np.percentile(lat, 50)), 4),
                              "p99_latency_s": round(float(np.percentile(lat, 99)), 4),
                              "mean_latency_s": round(float(lat.mean()), 4), "wall_s": round(wall, 2),
-                             "small_n_le_20": {"count": int(small.size),
+                             f"small_n_le_{SERVED_SMALL_MAX}": {"count": int(small.size),
                                                "p50_latency_s": round(float(np.percentile(small, 50)), 4) if small.size else None,
                                                "p99_latency_s": round(float(np.percentile(small, 99)), 4) if small.size else None},
-                             "large_n_gt_20": {"count": int(large.size),
+                             f"large_n_gt_{SERVED_SMALL_MAX}": {"count": int(large.size),
                                                "p50_latency_s": round(float(np.percentile(large, 50)), 4) if large.size else None,
                                                "p99_latency_s": round(float(np.percentile(large, 99)), 4) if large.size else None},
                              "peak_bytes": st["peak_bytes"], "failed": st["failed"]}
@@ -996,7 +999,7 @@ def wl_served(args, count=None, loads=None):
     return {"workload": f"served: {count} Poisson requests, n 10-30 log-uniform, c64/c128 "
                         f"({args.precision} for c128), <Z_i> + top-1024, 150 GB budget, 8 slots; "
                         f"sweep requests from borrowed page-locked Gaussian states",
-            "lanes": "8 slots + 8 small-request slots (n <= 18 may overtake larger requests)",
+            "lanes": f"8 slots + 8 small-request slots (n <= {SERVED_SMALL_MAX} may overtake larger requests)",
             "metric": "requests/s", "value": main["requests_per_s"], "offered_req_per_s": loads[0],
             "p50_latency_s": main["p50_latency_s"], "p99_latency_s": main["p99_latency_s"],
             "sequential_requests_per_s": round(count / seq_wall, 2), "sequential_wall_s": round(seq_wall, 2),
