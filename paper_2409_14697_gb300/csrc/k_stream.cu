@@ -514,6 +514,11 @@ void launch_typed(DeviceState &st, const Op &op) {
 
 }  // namespace
 
+static thread_local int t_yield_iters = 0;
+
+LaunchYield::LaunchYield(int iters) : prev(t_yield_iters) { t_yield_iters = iters; }
+LaunchYield::~LaunchYield() { t_yield_iters = prev; }
+
 // Persistent grid size: SMs x resident blocks of this kernel (cached per kernel).
 int persistent_grid(const void *fn, int threads, size_t smem, uint64_t work_blocks) {
     static std::mutex mu;
@@ -530,7 +535,10 @@ int persistent_grid(const void *fn, int threads, size_t smem, uint64_t work_bloc
         }
         per_sm = it->second;
     }
-    const uint64_t full = (uint64_t)device_sm_count() * per_sm;
+    uint64_t full = (uint64_t)device_sm_count() * per_sm;
+    if (t_yield_iters > 0)
+        full = std::max<uint64_t>(full, std::min<uint64_t>((work_blocks + t_yield_iters - 1) / t_yield_iters,
+                                                           (uint64_t)INT32_MAX));
     return (int)std::max<uint64_t>(1, std::min<uint64_t>(full, work_blocks));
 }
 

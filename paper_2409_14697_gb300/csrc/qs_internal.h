@@ -247,8 +247,17 @@ constexpr int kCopyEngines = -1;
 double stream_bytes(const Op &op, int n, int dtype);
 
 // Persistent grid: SMs x resident blocks of kernel fn at this block size / smem, capped
-// by the number of work blocks.
+// by the number of work blocks.  Inside a LaunchYield scope of the calling thread, grids
+// grow so that no block loops over more than `iters` work blocks: the grid-stride kernels
+// compute the same results with any grid, and their blocks then end every few hundred
+// microseconds, which lets the CTA scheduler start pending blocks of higher-priority
+// streams (the serving loop's small requests) instead of waiting for a whole launch.
 int persistent_grid(const void *fn, int threads, size_t smem, uint64_t work_blocks);
+struct LaunchYield {
+    explicit LaunchYield(int iters);
+    ~LaunchYield();
+    int prev;
+};
 
 // Copies `bytes` of host data into the state's device parameter arena (asynchronously,
 // ordered on st.stream before any later launch) and returns the device address.

@@ -141,6 +141,8 @@ void presize_slot(Slot &s, int n, uint32_t k) {
 
 }  // namespace
 
+constexpr int kYieldIters = 16;
+
 void Server::start_request(Slot &s, Request &r) {
     DeviceState &d = s.d;
     d.n = r.n;
@@ -167,7 +169,15 @@ void Server::start_request(Slot &s, Request &r) {
         QS_CUDA(cudaMemcpyAsync(d.psi, s.h_init, state_bytes, cudaMemcpyHostToDevice, d.stream));
     }
     qs_stats st{};
-    run_circuit(d, r.ops, r.opt, st);
+    {
+        // with a small-request lane, a larger request's gate kernels run as grids whose blocks
+        // loop over at most kYieldIters work blocks (tiles, or groups of amplitudes for 256
+        // threads), about 0.1-1 ms each, so that a small request's kernels on their
+        // high-priority streams start within a block's time instead of a launch's
+        const bool yield = cfg.small_slots > 0 && r.n > cfg.small_max_qubits;
+        LaunchYield ly(yield ? kYieldIters : 0);
+        run_circuit(d, r.ops, r.opt, st);
+    }
     // results
     if (s.cap_n < r.n || s.cap_k < r.top_k) {
         QS_CUDA(cudaStreamSynchronize(d.stream));

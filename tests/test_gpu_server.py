@@ -156,7 +156,7 @@ def test_small_requests_overtake_large_ones(qs):
     requests submitted after two large ones start at once and finish before the first large
     one (whose kernels run meanwhile; the small lane's streams have the higher priority), and
     the second large one waits for the first (large ones keep their order).  Results are
-    those of the oracle."""
+    those of the oracle, and the large ones' those of the plain entry points bit for bit."""
     n_big, k = 26, 8
     big = inputs.brickwork(n_big, 60, seed=1)
     sv = qs.qs_server_create(8 << 30, max_slots=1, small_slots=2, small_max_qubits=12)
@@ -178,6 +178,15 @@ def test_small_requests_overtake_large_ones(qs):
     assert max(r["latency_s"] for r in r_small) < r_big[0]["latency_s"], \
         ([r["latency_s"] for r in r_small], r_big[0]["latency_s"])
     assert np.array_equal(r_big[0]["expz"], r_big[1]["expz"])
+    # the large requests ran as grids of short-lived blocks (a small lane is configured):
+    # bitwise the results of the same circuit through the plain entry points
+    h = qs.qs_create(n_big, 2)
+    try:
+        qs.qs_apply_circuit(h, big)
+        ez, nrm = qs.qs_expectation_z(h)
+    finally:
+        qs.qs_destroy(h)
+    assert np.array_equal(r_big[0]["expz"], ez) and r_big[0]["norm"] == nrm
     for (n, g), r in zip(smalls, r_small):
         want = oracle.run(oracle.zero_state(n), n, g)
         assert np.max(np.abs(r["expz"] - oracle.expz(want, n))) <= 1e-5
