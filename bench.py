@@ -307,6 +307,12 @@ def run_ours(args, rank, world, local):
         "dtype": "f64" if B == 16 else "f32", "data": "synthetic (seeded Gaussian state, seeded angles)",
         "config": {"workload": f"{n}-qubit gate benchmark, {args.dtype}, 8 gate types x 30 targets, gate-by-gate",
                    "qubits": n, "state_bytes": B << n, "gates_per_step": n_gates,
+                   "gate_forms": "one launch per gate; every RZ of a call but its last multiplies only "
+                                 "the half of the state where its qubit is 1 (the global phase joins "
+                                 "the call's last RZ); Hadamards run as unscaled butterflies whose "
+                                 "2^(-k/2) scale joins a later H (the call's last, or every 64th, to "
+                                 "keep the range); the call's final state is exact; per_gate bytes "
+                                 "count what each launch moves",
                    "l2": "inputs larger than L2 (no flush)", "parallelism": f"replicas x{world}"},
         "hbm_GBps_all_gates": round(agg_gbps, 1),
         "per_gate": per_gate,
