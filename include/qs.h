@@ -254,9 +254,10 @@ int qs_renormalize(qs_state *s, double *old_norm);
  *   stream    cudaStream_t to run on (NULL: legacy default stream); the call waits for it;
  *   out_expz  host array of n_qubits doubles (or NULL), out_norm host double (or NULL).
  * Scratch: a file-scope device array of about 2.5 MB that every GPU loading this library
- * holds until process exit; nothing is allocated per call.  The first call on a device
- * looks up that array's device address (cudaGetSymbolAddress), so make it before any
- * stream capture.  The address is kept for the life of the process: after a
+ * holds until process exit; nothing is allocated per call.  The call ends by waiting for
+ * its stream, so it cannot be captured into a CUDA graph.  The first call on a device
+ * looks up that array's device address (cudaGetSymbolAddress); the address is kept for
+ * the life of the process: after a
  * cudaDeviceReset of that device it is stale, so do not call this entry point again in a
  * process that has reset the device.  All calls share the one array and it keeps the last
  * call's contents;
