@@ -108,6 +108,19 @@ def load_peaks():
         return 6800.0, "fallback"
 
 
+def tf32_peak_tflops():
+    """Dense TF32 tensor peak: the measured bf16 peak (sustained, for kernels inside a long
+    circuit) times the nominal TF32 / bf16 ratio 1.1 / 2.25; else the fallback 1.7 PF/s
+    sustained bf16 times the same ratio."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        bf16, kind = float(p.get("bf16_tflops_sustained") or p["bf16_tflops"]), "measured"
+    except Exception:
+        bf16, kind = 1700.0, "fallback"
+    return bf16 * 1.1 / 2.25, kind
+
+
 class ClockSampler:
     """nvidia-smi clock/throttle samples taken while the timed region runs."""
 
@@ -694,6 +707,13 @@ def wl_circuits33(args):
                           "gates_per_s": round(len(gates) * 1e3 / ms, 1),
                           "pass_GBps": round(st["bytes"] / (ms * 1e-3) / 1e9, 1),
                           "norm_minus_1": nrm - 1.0}
+            if st["tc_blocks"]:
+                # tensor-core work over the whole circuit's time (passes, SIMT ops included)
+                tpk, tkind = tf32_peak_tflops()
+                tf = st["tc_flops"] / (ms * 1e-3) / 1e12
+                rows[name]["tc_tflops"] = round(tf, 1)
+                rows[name]["tc_frac_of_tf32_peak"] = round(tf / tpk, 4)
+                rows[name]["tf32_peak"] = f"{tpk:.0f} TFLOP/s ({tkind} bf16 x 1.1/2.25)"
             if with_inverse:
                 qs.qs_apply_circuit(h, inv, opts)
                 a0 = qs.qs_amplitudes(h, 0, 1)[0]
@@ -1051,6 +1071,7 @@ def workload_summaries(args):
             res[key] = {"path": v["path"]}
             for fam, row in v["circuits"].items():
                 res[key][fam] = {x: row[x] for x in ("ms", "passes", "pass_GBps", "gates", "tc_blocks",
+                                                      "tc_tflops", "tc_frac_of_tf32_peak",
                                                       "norm_minus_1", "inverse_infidelity_normalised")
                                  if x in row}
         return res

@@ -41,7 +41,7 @@
 extern "C" {
 #endif
 
-#define QS_ABI_VERSION 3
+#define QS_ABI_VERSION 4
 #define QS_MAX_QUBITS 36      /* index arithmetic limit; memory is the real limit */
 #define QS_MAX_GATE_QUBITS 8  /* operands per gate record */
 
@@ -155,6 +155,9 @@ typedef struct {
     int64_t tc_blocks;     /* dense blocks applied on the tensor cores (tcgen05), summed over
                               passes */
     int64_t tpb_gates;     /* gates built by the Tensor Product Booster (QS_OPT_NO_TPB) */
+    double tc_flops;       /* floating-point operations of the tensor-core blocks: a k-qubit
+                              block on n qubits is 2^(n+k+2) real multiply-adds per TF32
+                              product, three products (hi x hi, hi x lo, lo x hi) */
 } qs_stats;
 
 /* ---- library ------------------------------------------------------------------ */

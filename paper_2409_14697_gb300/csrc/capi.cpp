@@ -176,7 +176,7 @@ void run_circuit(DeviceState &d, const std::vector<Op> &ops, const qs_options &o
                     // block's qubits plus the lowest others up to 2^13 amplitudes
                     uint64_t L = op.qmask();
                     for (int b = 0; b < d.n && __builtin_popcountll(L) < m_tc; b++) L |= 1ull << b;
-                    st.tile_sweeps += launch_pass_ops(d, L, {op}, true, &st.tc_blocks);
+                    st.tile_sweeps += launch_pass_ops(d, L, {op}, true, &st);
                     st.bytes += 2.0 * 8.0 * (double)(1ull << d.n);
                 } else {
                     launch_stream_op(d, op);

@@ -16,6 +16,7 @@
 // memory.  A pass holding a single op runs on the streaming kernel instead, which
 // touches only the amplitudes that op changes.
 #include <algorithm>
+#include <cmath>
 
 #include "chunk.h"
 #include "kgeom.h"
@@ -44,9 +45,10 @@ bool chunkable(const Op &op, const PlanParams &pp) {
 }  // namespace
 
 // Launches one chunk pass over lmask applying `fused` (tensor cores where allowed);
-// returns the number of tile sweeps and adds the tensor-core blocks to *tc_blocks.
+// returns the number of tile sweeps and adds the tensor-core blocks and their operations
+// to *tc_stats.
 int launch_pass_ops(DeviceState &st, uint64_t lmask, const std::vector<Op> &fused, bool use_tc,
-                    int64_t *tc_blocks) {
+                    qs_stats *tc_stats) {
     const int n = st.n;
     int pos[64] = {0};
     int r = 0;
@@ -79,7 +81,11 @@ int launch_pass_ops(DeviceState &st, uint64_t lmask, const std::vector<Op> &fuse
             b_floats = std::max<uint32_t>(b_floats, (uint32_t)(cnt / 2));
             kops.push_back(k);
             any_tc = true;
-            if (tc_blocks) (*tc_blocks)++;
+            if (tc_stats) {
+                // 2^(n-k) groups x 2^(k+1) x 2^(k+1) real multiply-adds, three TF32 products
+                tc_stats->tc_blocks++;
+                tc_stats->tc_flops += 6.0 * std::ldexp(1.0, st.n + op.k + 2);
+            }
         } else {
             kops.push_back(make_tile_kop(op, pos, mats));
         }
@@ -353,7 +359,7 @@ void run_planned(DeviceState &st, const std::vector<Op> &ops, const qs_options &
             continue;
         }
         const std::vector<Op> fused = pass_program(st, pp, p, ops_r);
-        stats.tile_sweeps += launch_pass_ops(st, p.lmask, fused, pp.tc, &stats.tc_blocks);
+        stats.tile_sweeps += launch_pass_ops(st, p.lmask, fused, pp.tc, &stats);
         stats.passes++;
         stats.bytes += 2.0 * B * (double)(1ull << n);
         n_ops += (int64_t)fused.size();

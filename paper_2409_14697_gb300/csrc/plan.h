@@ -42,9 +42,10 @@ std::vector<Pass> choose_plan(const std::vector<Op> &ops, int n, const PlanParam
 //     (complex64 register phases hold one- and two-qubit diagonals without a sweep).
 // ops: the list the pass's indices refer to (choose_plan's merged list where it made one).
 std::vector<Op> pass_program(const DeviceState &st, const PlanParams &pp, const Pass &p, const std::vector<Op> &ops);
-// One chunk pass over lmask applying ops already fused (tensor cores if use_tc).
+// One chunk pass over lmask applying ops already fused (tensor cores if use_tc); the
+// tensor-core blocks and their operations are added to tc_stats.
 int launch_pass_ops(DeviceState &st, uint64_t lmask, const std::vector<Op> &fused, bool use_tc,
-                    int64_t *tc_blocks = nullptr);
+                    qs_stats *tc_stats = nullptr);
 // Plans `ops` into passes and launches them on st.stream, filling stats.
 void run_planned(DeviceState &st, const std::vector<Op> &ops, const qs_options &o, qs_stats &stats);
 

@@ -51,7 +51,8 @@ class qs_options(ctypes.Structure):
 class qs_stats(ctypes.Structure):
     _fields_ = [("gates_in", ctypes.c_int64), ("ops_after_fuse", ctypes.c_int64),
                 ("passes", ctypes.c_int64), ("launches", ctypes.c_int64), ("bytes", ctypes.c_double),
-                ("tile_sweeps", ctypes.c_int64), ("tc_blocks", ctypes.c_int64), ("tpb_gates", ctypes.c_int64)]
+                ("tile_sweeps", ctypes.c_int64), ("tc_blocks", ctypes.c_int64), ("tpb_gates", ctypes.c_int64),
+                ("tc_flops", ctypes.c_double)]
 
 
 class qs_circuit(ctypes.Structure):

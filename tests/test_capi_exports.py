@@ -39,7 +39,7 @@ def test_version_without_gpu():
     from paper_2409_14697_gb300 import build as b, qs
     b.build()
     abi, ndev = qs.qs_version()
-    assert abi == 3 and ndev >= 0
+    assert abi == 4 and ndev >= 0
 
 
 def test_gate_record_layout():

@@ -40,6 +40,8 @@ def test_single_dense_block_fused_mode(qs, k):
     got, st = run(qs, n, psi0, gates, mode=qs.QS_MODE_FUSED, fuse_k=k)
     assert st["passes"] == 1
     assert st["tc_blocks"] == 1          # the block ran on the tensor cores
+    # 2^(n-k) groups x 2^(k+1) x 2^(k+1) multiply-adds, three TF32 products, 2 flops each
+    assert st["tc_flops"] == 6.0 * 2.0 ** (n + k + 2)
     assert np.max(np.abs(got - want)) <= TOL_C64
     assert fidelity_gap(got, want) <= 1e-6
 
