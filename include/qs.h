@@ -254,16 +254,16 @@ int qs_renormalize(qs_state *s, double *old_norm);
  * split into fewer, larger blocks, so the last bits may differ.
  *   dev_psi   device pointer to 2^n_qubits amplitudes of dtype dt (caller's memory,
  *             16-byte aligned), left unchanged;
- *   stream    cudaStream_t to run on (NULL: legacy default stream); the call waits for it;
+ *   stream    cudaStream_t to run on (NULL: legacy default stream); the results are
+ *             copied to the host, and the call returns once its stream has finished them;
  *   out_expz  host array of n_qubits doubles (or NULL), out_norm host double (or NULL).
  * Scratch: a file-scope device array of about 2.5 MB that every GPU loading this library
- * holds until process exit; nothing is allocated per call.  The call ends by waiting for
- * its stream, so it cannot be captured into a CUDA graph.  The first call on a device
- * looks up that array's device address (cudaGetSymbolAddress); the address is kept for
- * the life of the process: after a
- * cudaDeviceReset of that device it is stale, so do not call this entry point again in a
- * process that has reset the device.  All calls share the one array and it keeps the last
- * call's contents;
+ * holds until process exit; nothing is allocated per call.  The first call on a device
+ * does a one-time set-up: it looks up that array's device address (cudaGetSymbolAddress)
+ * with that device current; make this first call before any stream capture begins.  The
+ * address is kept for the life of the process: after a cudaDeviceReset of that device it
+ * is stale, so do not call this entry point again in a process that has reset the device.
+ * All calls share the one array and it keeps the last call's contents;
  * every value a call reads it has written itself, so nothing needs clearing, but calls
  * that overlap on the GPU (on different streams or host threads) race.
  * Errors: QS_ERR_INVALID for NULL pointers, an unknown dtype or n_qubits outside 1..32
