@@ -279,11 +279,13 @@ def run_ours(args, rank, world, local):
                           "frac_of_measured_hbm": round(byts / (launch_ms * 1e-3) / 1e9 / peak, 3),
                           "share": round(per_type_ms[name] / total_ms, 3)}
     dom = max(GATE_TYPES, key=lambda k: per_type_ms[k])
-    traffic = load_traffic(dom, n, args.dtype)
+    # complex128 default arithmetic: integer products for U3, CU3, RZ (QS_PREC_IX64)
+    ix = B == 16 and dom in ("u3", "cu3", "rz")
+    traffic = load_traffic(dom, n, args.dtype, "ix" if ix else "fp64")
     hbm = {"achieved": per_gate[dom]["GBps"], "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
            "frac": round(per_gate[dom]["GBps"] / peak, 3)}
-    fp64 = fp64_roof(dom, n, B, per_type_ms[dom] / (args.steps * len(sweeps[dom])))
-    if fp64 and fp64["frac"] > hbm["frac"]:
+    fp64 = fp64_roof(dom, n, B, per_type_ms[dom] / (args.steps * len(sweeps[dom])), ix=ix)
+    if fp64 and not ix and fp64["frac"] > hbm["frac"]:
         roof = {"kernel": f"k_stream[{dom}]", "bound": "alu", "achieved": fp64["achieved"],
                 "peak": fp64["peak"], "unit": fp64["unit"], "frac": fp64["frac"],
                 "peak_source": fp64["peak_source"], "dgemm_measured_peak": fp64["dgemm_measured_peak"],
@@ -308,7 +310,8 @@ def run_ours(args, rank, world, local):
     if not args.no_extra:
         extra["planned"] = time_planned(qs, h, stream, recs, n, B)
         if B == 16:
-            extra["df32"] = time_df32(qs, h, stream, recs, n, sweeps, peak)
+            extra["df32"] = time_prec(qs, h, stream, recs, n, sweeps, peak, qs.QS_PREC_DF32)
+            extra["fp64_native"] = time_prec(qs, h, stream, recs, n, sweeps, peak, qs.QS_PREC_FP64)
             extra["c64"] = time_c64(qs, stream, n, sweeps, peak)
     qs.qs_destroy(h)
     del host_in
@@ -320,6 +323,11 @@ def run_ours(args, rank, world, local):
         "dtype": "f64" if B == 16 else "f32", "data": "synthetic (seeded Gaussian state, seeded angles)",
         "config": {"workload": f"{n}-qubit gate benchmark, {args.dtype}, 8 gate types x 30 targets, gate-by-gate",
                    "qubits": n, "state_bytes": B << n, "gates_per_step": n_gates,
+                   "arithmetic": ("U3, CU3 and RZ: exact 64-bit integer significand products, one "
+                                  "signed 64-bit accumulator per output aligned to its largest term, "
+                                  "one rounding to FP64 (QS_PREC_IX64, the default; one group in four, "
+                                  "phases one in eight, in native FP64); H: FP64 additions; X, CNOT, "
+                                  "SWAP, CZ: moves and sign flips" if B == 16 else "FP32"),
                    "gate_forms": "one launch per gate; every RZ of a call but its last multiplies only "
                                  "the half of the state where its qubit is 1 (the global phase joins "
                                  "the call's last RZ); Hadamards run as unscaled butterflies whose "
@@ -341,11 +349,12 @@ def run_ours(args, rank, world, local):
     return out
 
 
-def time_df32(qs, h, stream, recs, n, sweeps, peak):
-    """Context row: the same gate-by-gate sweep with complex128 double-float arithmetic
-    (QS_PREC_DF32: IEEE-double storage, FP32-pair compensated arithmetic)."""
+def time_prec(qs, h, stream, recs, n, sweeps, peak, precision):
+    """Context row: the same gate-by-gate sweep with another complex128 arithmetic
+    (QS_PREC_DF32: IEEE-double storage, FP32-pair compensated arithmetic; QS_PREC_FP64:
+    native FP64 instructions for every gate)."""
     import torch
-    opts = qs.options(mode=qs.QS_MODE_GATE, precision=qs.QS_PREC_DF32)
+    opts = qs.options(mode=qs.QS_MODE_GATE, precision=precision)
     for name in GATE_TYPES:
         qs.qs_apply_circuit(h, recs[name], opts)
     evs = [torch.cuda.Event(enable_timing=True) for _ in range(len(GATE_TYPES) + 1)]
@@ -486,6 +495,15 @@ def run_e2e(qs, host_in, recs, opts, n, B, n_gates, world, dt, in_flight=3, step
 # gate-by-gate call of 30: RZ, 29 change half the amplitudes (4 per changed amplitude) and
 # the last all; H, 29 are the unscaled butterfly (2) and the last carries the scale (3).
 FP64_INSTR_PER_AMP = {"h": (29 * 2 + 3) / 30, "rz": (29 * 2 + 4) / 30, "u3": 7, "cu3": 3.5}
+# The default complex128 arithmetic (QS_PREC_IX64) of the streaming U3, CU3 and RZ kernels:
+# one group in four (phases: one in eight) in native FP64 (7 instructions per amplitude for
+# U3, 4 for a phase), the others in integer products whose results take one
+# integer-to-double conversion (an FP64-pipe instruction) per real output, 2 per amplitude.
+IX_U3 = 0.25 * 7 + 0.75 * 2
+IX_PHASE = 0.125 * 4 + 0.875 * 2
+IX_DIAG = 0.25 * 4 + 0.75 * 2
+FP64_INSTR_PER_AMP_IX = {"h": FP64_INSTR_PER_AMP["h"], "rz": (29 * IX_PHASE / 2 + IX_DIAG) / 30,
+                         "u3": IX_U3, "cu3": IX_U3 / 2}
 # FP64 pipe peak: 2 FP64 instructions per clock per SM (ncu: the U3 kernel at 0.526e12/s
 # keeps the FP64 pipe 83.8 % busy) x 152 SMs x 2.07 GHz max SM clock = 1.26 TFLOP/s.
 FP64_PEAK_TINSTR = 2 * 152 * 2.07e9 / 1e12
@@ -521,10 +539,11 @@ def fp64_gemm_tinstr():
     return _DGEMM["v"]
 
 
-def fp64_roof(name, n, B, launch_ms):
-    if B != 16 or name not in FP64_INSTR_PER_AMP:
+def fp64_roof(name, n, B, launch_ms, ix=False):
+    table = FP64_INSTR_PER_AMP_IX if ix else FP64_INSTR_PER_AMP
+    if B != 16 or name not in table:
         return None
-    ach = FP64_INSTR_PER_AMP[name] * (1 << n) / (launch_ms * 1e-3) / 1e12
+    ach = table[name] * (1 << n) / (launch_ms * 1e-3) / 1e12
     gemm = fp64_gemm_tinstr()
     return {"achieved": round(ach, 4), "peak": round(FP64_PEAK_TINSTR, 4), "unit": "T FP64 instr/s",
             "frac": round(ach / FP64_PEAK_TINSTR, 3),
@@ -533,13 +552,14 @@ def fp64_roof(name, n, B, launch_ms):
             "frac_of_dgemm": round(ach / gemm, 3) if gemm else None}
 
 
-def load_traffic(kernel_gate, n, dtype):
-    """Per-launch DRAM bytes from the committed ncu summary, if one matches."""
+def load_traffic(kernel_gate, n, dtype, form):
+    """Per-launch DRAM bytes from the committed ncu summary of the kernel as it is built
+    now (form: the complex128 arithmetic, "ix" or "fp64"), if one matches."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(p) as f:
             t = json.load(f)
-        return t.get(f"k_stream[{kernel_gate}]:{n}:{dtype}")
+        return t.get(f"k_stream[{kernel_gate}]:{n}:{dtype}:{form}")
     except Exception:
         return None
 

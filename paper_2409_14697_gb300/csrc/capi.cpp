@@ -149,9 +149,11 @@ static void destroy_state(qs_state *s) {
 void run_circuit(DeviceState &d, const std::vector<Op> &ops, const qs_options &o, qs_stats &st) {
     st = qs_stats{};
     st.gates_in = (int64_t)ops.size();
-    if (o.precision != QS_PREC_DEFAULT && o.precision != QS_PREC_FP64 && o.precision != QS_PREC_DF32)
+    if (o.precision != QS_PREC_DEFAULT && o.precision != QS_PREC_FP64 && o.precision != QS_PREC_DF32 &&
+        o.precision != QS_PREC_IX64)
         fail(QS_ERR_INVALID, "unknown precision mode");
     d.prec = o.precision == QS_PREC_DF32 ? QS_PREC_DF32 : QS_PREC_FP64;
+    d.ix_stream = o.precision == QS_PREC_IX64 || o.precision == QS_PREC_DEFAULT;
     d.reg_phases = (o.flags & QS_OPT_NO_REG_PHASES) == 0;
     const uint64_t l0 = g_launches.load();
     arena_begin(d);

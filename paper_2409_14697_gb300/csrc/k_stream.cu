@@ -16,8 +16,10 @@
 #include <mutex>
 #include <map>
 #include <tuple>
+#include <type_traits>
 
 #include "dfmath.cuh"
+#include "ixmath.cuh"
 #include "kgeom.h"
 #include "kops.cuh"
 #include "qs_internal.h"
@@ -210,6 +212,108 @@ struct FDense2DF {
     }
 };
 
+// ---- complex128 functors with integer products (ixmath.cuh) ----------------------
+// Each real output is one ix::dot over its terms, with the matrix entries decoded on the
+// host (ix::rows_dense1 / ix::rows_diag, signs included).  The first NAT of a thread's
+// groups take the native FP64 functor instead, so the FP64 pipe and the integer pipes
+// work side by side.
+__device__ __forceinline__ void ix_pair(const Amp<double, 1> *v, ix::Num (&x)[4]) {
+    x[0] = ix::decode(v[0].r[0]);
+    x[1] = ix::decode(v[0].i[0]);
+    x[2] = ix::decode(v[1].r[0]);
+    x[3] = ix::decode(v[1].i[0]);
+}
+__device__ __forceinline__ void ix_store(Amp<double, 1> *v, const double (&y)[4]) {
+    v[0].r[0] = y[0]; v[0].i[0] = y[1];
+    v[1].r[0] = y[2]; v[1].i[0] = y[3];
+}
+
+// U3 / CU3 (Im m00 = 0): 14 terms
+template <bool CVT, int UG, int NAT> struct FDense1R0IX {
+    static constexpr int NT = 2;
+    static constexpr int kGroups = UG;
+    static constexpr int kNative = NAT;
+    ix::Num c[14];
+    double m[8];
+    template <int L> __device__ void operator()(Amp<double, L> *v) const {
+        ix::Num x[4];
+        double y[4];
+        ix_pair(v, x);
+        ix::dense1_r0<CVT>(c, x, y);
+        ix_store(v, y);
+    }
+    template <int L> __device__ void native(Amp<double, L> *v) const { f_dense1_r0<double, L>(v, m); }
+};
+
+// general 2x2: 16 terms
+template <bool CVT, int UG, int NAT> struct FDense1IX {
+    static constexpr int NT = 2;
+    static constexpr int kGroups = UG;
+    static constexpr int kNative = NAT;
+    ix::Num c[16];
+    double m[8];
+    template <int L> __device__ void operator()(Amp<double, L> *v) const {
+        ix::Num x[4];
+        double y[4];
+        ix_pair(v, x);
+        ix::dense1<CVT>(c, x, y);
+        ix_store(v, y);
+    }
+    template <int L> __device__ void native(Amp<double, L> *v) const { f_dense1<double, L>(v, m); }
+};
+
+// real 2x2 (RY) and RX forms: rows of 2 terms
+template <bool CVT, int UG, int NAT> struct FDense1RealIX {
+    static constexpr int NT = 2;
+    static constexpr int kGroups = UG;
+    static constexpr int kNative = NAT;
+    ix::Num c[8];
+    double m[8];
+    template <int L> __device__ void operator()(Amp<double, L> *v) const {
+        ix::Num x[4];
+        double y[4];
+        ix_pair(v, x);
+        ix::dense1_real<CVT>(c, x, y);
+        ix_store(v, y);
+    }
+    template <int L> __device__ void native(Amp<double, L> *v) const { f_dense1_real<double, L>(v, m); }
+};
+template <bool CVT, int UG, int NAT> struct FDense1RXIX {
+    static constexpr int NT = 2;
+    static constexpr int kGroups = UG;
+    static constexpr int kNative = NAT;
+    ix::Num c[8];
+    double m[8];
+    template <int L> __device__ void operator()(Amp<double, L> *v) const {
+        ix::Num x[4];
+        double y[4];
+        ix_pair(v, x);
+        ix::dense1_rx<CVT>(c, x, y);
+        ix_store(v, y);
+    }
+    template <int L> __device__ void native(Amp<double, L> *v) const { f_dense1_rx<double, L>(v, m); }
+};
+
+// diagonal: NTT elements, each times its own factor
+template <bool CVT, int NTT, int UG, int NAT> struct FDiagIX {
+    static constexpr int NT = NTT;
+    static constexpr int kGroups = UG;
+    static constexpr int kNative = NAT;
+    ix::Num c[4 * NTT];
+    double d[2 * NTT];
+    template <int L> __device__ void operator()(Amp<double, L> *v) const {
+#pragma unroll
+        for (int t = 0; t < NTT; t++) {
+            const ix::Num x[2] = {ix::decode(v[t].r[0]), ix::decode(v[t].i[0])};
+            double y[2];
+            ix::phase<CVT>(c + 4 * t, x, y);
+            v[t].r[0] = y[0];
+            v[t].i[0] = y[1];
+        }
+    }
+    template <int L> __device__ void native(Amp<double, L> *v) const { f_diag<double, L, NTT>(v, d); }
+};
+
 void split_host(double v, F2 &o) {
     o.h = (float)v;
     o.l = (float)(v - (double)o.h);
@@ -234,6 +338,13 @@ __device__ __forceinline__ uint64_t insert_zeros(uint64_t x, const Geom &g) {
     return x;
 }
 
+// Functors with integer products may give their first kNative groups per thread to the
+// native FP64 form.
+template <typename F, typename = void> struct NativeGroups { static constexpr int value = 0; };
+template <typename F> struct NativeGroups<F, std::void_t<decltype(F::kNative)>> {
+    static constexpr int value = F::kNative;
+};
+
 template <typename T, int L, int NF, int U, typename F>
 __global__ void __launch_bounds__(kThreads)
 k_stream(typename VecT<T, L>::type *__restrict__ psi, const Geom g, const F f) {
@@ -253,7 +364,14 @@ k_stream(typename VecT<T, L>::type *__restrict__ psi, const Geom g, const F f) {
         }
 #pragma unroll
         for (int u = 0; u < U; u++)
-            if (b0 + (uint64_t)u * kThreads + threadIdx.x < g.n_groups) f(v[u]);
+            if (b0 + (uint64_t)u * kThreads + threadIdx.x < g.n_groups) {
+                if constexpr (NativeGroups<F>::value > 0) {
+                    if (u < NativeGroups<F>::value) f.native(v[u]);
+                    else f(v[u]);
+                } else {
+                    f(v[u]);
+                }
+            }
 #pragma unroll
         for (int u = 0; u < U; u++) {
             if (b0 + (uint64_t)u * kThreads + threadIdx.x < g.n_groups) {
@@ -344,10 +462,17 @@ k_dense_general(typename VecT<T, 1>::type *__restrict__ psi, uint64_t n_groups, 
     }
 }
 
+// Groups per thread: 2, 4 or 8 by touched elements, unless the functor sets kGroups.
+template <typename F, typename = void> struct GroupsPerThread {
+    static constexpr int value = F::NT == 4 ? 2 : (F::NT == 2 ? 4 : 8);
+};
+template <typename F> struct GroupsPerThread<F, std::void_t<decltype(F::kGroups)>> {
+    static constexpr int value = F::kGroups;
+};
+
 template <typename T, int L, int NF, typename F>
 void run(DeviceState &st, const Geom &g, const F &f) {
-    constexpr int NT = F::NT;
-    constexpr int U = NT == 4 ? 2 : (NT == 2 ? 4 : 8);
+    constexpr int U = GroupsPerThread<F>::value;
     auto kern = k_stream<T, L, NF, U, F>;
     const uint64_t per_iter = (uint64_t)kThreads * U;
     const int grid = persistent_grid((const void *)kern, kThreads, 0, (g.n_groups + per_iter - 1) / per_iter);
@@ -413,6 +538,64 @@ bool launch_df(DeviceState &st, const KOp &k, const std::vector<double> &mats) {
     }
 }
 
+// complex128 with integer products (QS_PREC_IX64); false for kinds it does not cover.
+template <bool CVT, int U2, int N2, int U1, int N1>
+bool launch_ix_t(DeviceState &st, const KOp &k, const std::vector<double> &mats) {
+    switch (k.fkind) {
+    case F_DENSE1: {
+        double m[8];
+        for (int i = 0; i < 8; i++) m[i] = mats[k.mat + i];
+        if (k.k == D1_REAL) {
+            FDense1RealIX<CVT, U2, N2> f;
+            ix::rows_dense1_real(f.c, m);
+            std::copy(m, m + 8, f.m);
+            dispatch_elem<double>(st, k, f);
+        } else if (k.k == D1_RX) {
+            FDense1RXIX<CVT, U2, N2> f;
+            ix::rows_dense1_rx(f.c, m);
+            std::copy(m, m + 8, f.m);
+            dispatch_elem<double>(st, k, f);
+        } else if (k.k == D1_R0) {
+            FDense1R0IX<CVT, U2, N2> f;
+            ix::rows_dense1(f.c, m, true);
+            std::copy(m, m + 8, f.m);
+            dispatch_elem<double>(st, k, f);
+        } else {
+            FDense1IX<CVT, U2, N2> f;
+            ix::rows_dense1(f.c, m, false);
+            std::copy(m, m + 8, f.m);
+            dispatch_elem<double>(st, k, f);
+        }
+        return true;
+    }
+    case F_PHASE: {
+        FDiagIX<CVT, 1, U1, N1> f;
+        for (int i = 0; i < 2; i++) f.d[i] = mats[k.mat + i];
+        ix::rows_diag(f.c, f.d, 1);
+        dispatch_elem<double>(st, k, f);
+        return true;
+    }
+    case F_DIAG1: {
+        FDiagIX<CVT, 2, U2, N2> f;
+        for (int i = 0; i < 4; i++) f.d[i] = mats[k.mat + i];
+        ix::rows_diag(f.c, f.d, 2);
+        dispatch_elem<double>(st, k, f);
+        return true;
+    }
+    default: return false;
+    }
+}
+
+// Two-element kernels: 4 groups per thread, the first in native FP64; phases (one element):
+// 8 groups per thread, the first in native FP64.  Results use the conversion instruction.
+// (Measured at 28 qubits on the GB300: U3 1.98 ms against 3.59 ms native, CU3 1.03 / 1.81,
+// RZ phase 0.80 / 1.13, RY and RX 1.37 / 2.07; with all groups in integer form, with 6 or
+// 8 groups per thread and 2 or 3 native, or with the integer-only result encoding, each
+// was 3-25 % slower.)
+bool launch_ix(DeviceState &st, const KOp &k, const std::vector<double> &mats) {
+    return launch_ix_t<true, 4, 1, 8, 1>(st, k, mats);
+}
+
 template <typename T>
 void launch_typed(DeviceState &st, const Op &op) {
     const int n = st.n;
@@ -422,6 +605,7 @@ void launch_typed(DeviceState &st, const Op &op) {
     const KOp k = make_kop(op, ident.data(), mats);
     if constexpr (std::is_same<T, double>::value) {
         if (st.prec == QS_PREC_DF32 && launch_df(st, k, mats)) return;
+        if (st.ix_stream && launch_ix(st, k, mats)) return;
     }
     switch (k.fkind) {
     case F_H: {

@@ -20,7 +20,7 @@ QS_C64, QS_C128 = 1, 2
 QS_OK, QS_NOT_READY = 0, 1
 QS_ERR_INVALID, QS_ERR_NOMEM, QS_ERR_CUDA, QS_ERR_TIMEOUT, QS_ERR_BUSY, QS_ERR_UNSUPPORTED = -1, -2, -3, -4, -5, -6
 QS_MODE_AUTO, QS_MODE_GATE, QS_MODE_CHUNK, QS_MODE_FUSED = 0, 1, 2, 3
-QS_PREC_DEFAULT, QS_PREC_FP64, QS_PREC_DF32 = 0, 1, 2
+QS_PREC_DEFAULT, QS_PREC_FP64, QS_PREC_DF32, QS_PREC_IX64 = 0, 1, 2, 3
 QS_OPT_NO_REG_PHASES, QS_OPT_NO_DIAG_MERGE, QS_OPT_NO_TC_NORM_FIX, QS_OPT_NO_TPB = 1, 2, 4, 8
 QS_REQ_BORROW_INIT = 1
 

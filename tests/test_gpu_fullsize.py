@@ -6,7 +6,8 @@ thread), so it finishes the benchmark sizes in minutes.
 * The 30-qubit gate benchmark: a seeded Gaussian state; H, X, RZ, U3, CNOT, CZ, SWAP and
   CU3 each applied 30 times across the targets (two-qubit gates on (q, q+1 mod 30)).
   After each type the GPU states are compared element by element with the oracle's:
-  complex128 gate by gate (native FP64 and double-float arithmetic) and as one planned call
+  complex128 gate by gate (native FP64, integer-product and double-float arithmetic) and as
+  one planned call
   per type (max-abs <= 1e-12), complex64 gate by gate and planned (1 - F <= 1e-6 and the
   max-abs bound of the complex64 tests).
 * The same sweep at 22 qubits, where every streaming kernel instance runs grids of several
@@ -54,6 +55,7 @@ def _sweep_parity(qs, n, c64_planned=True):
     Returns a dict of per-type errors and timings (printed with -s)."""
     psi = inputs.gaussian_state(n, seed=2024)
     variants = [("c128_gate", 2, qs.QS_MODE_GATE, qs.QS_PREC_FP64),
+                ("c128_ix64_gate", 2, qs.QS_MODE_GATE, qs.QS_PREC_IX64),
                 ("c128_planned", 2, qs.QS_MODE_AUTO, qs.QS_PREC_FP64),
                 ("c128_df32_gate", 2, qs.QS_MODE_GATE, qs.QS_PREC_DF32),
                 ("c64_gate", 1, qs.QS_MODE_GATE, 0)]
