@@ -326,7 +326,7 @@ def run_ours(args, rank, world, local):
                    "arithmetic": ("U3, CU3 and RZ: exact 64-bit integer significand products, one "
                                   "signed 64-bit accumulator per output aligned to its largest term, "
                                   "one rounding to FP64 (QS_PREC_IX64, the default; one group in four, "
-                                  "phases one in eight, in native FP64); H: FP64 additions; X, CNOT, "
+                                  "phases one in six, in native FP64); H: FP64 additions; X, CNOT, "
                                   "SWAP, CZ: moves and sign flips" if B == 16 else "FP32"),
                    "gate_forms": "one launch per gate; every RZ of a call but its last multiplies only "
                                  "the half of the state where its qubit is 1 (the global phase joins "
@@ -496,11 +496,11 @@ def run_e2e(qs, host_in, recs, opts, n, B, n_gates, world, dt, in_flight=3, step
 # the last all; H, 29 are the unscaled butterfly (2) and the last carries the scale (3).
 FP64_INSTR_PER_AMP = {"h": (29 * 2 + 3) / 30, "rz": (29 * 2 + 4) / 30, "u3": 7, "cu3": 3.5}
 # The default complex128 arithmetic (QS_PREC_IX64) of the streaming U3, CU3 and RZ kernels:
-# one group in four (phases: one in eight) in native FP64 (7 instructions per amplitude for
+# one group in four (phases: one in six) in native FP64 (7 instructions per amplitude for
 # U3, 4 for a phase), the others in integer products whose results take one
 # integer-to-double conversion (an FP64-pipe instruction) per real output, 2 per amplitude.
 IX_U3 = 0.25 * 7 + 0.75 * 2
-IX_PHASE = 0.125 * 4 + 0.875 * 2
+IX_PHASE = 4 / 6 + 2 * 5 / 6
 IX_DIAG = 0.25 * 4 + 0.75 * 2
 FP64_INSTR_PER_AMP_IX = {"h": FP64_INSTR_PER_AMP["h"], "rz": (29 * IX_PHASE / 2 + IX_DIAG) / 30,
                          "u3": IX_U3, "cu3": IX_U3 / 2}

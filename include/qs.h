@@ -112,7 +112,7 @@ enum {
                              to a double: within 0.5 ulp + 2^-56.4 x the largest |matrix
                              entry x amplitude| of the exact value (a chain of FP64
                              multiply-adds: about one ulp of each partial sum per term).
-                             One group in four (phases: in eight) of every thread runs the
+                             One group in four (phases: in six) of every thread runs the
                              native FP64 form, so both pipes work.  Inputs below 2^-1022 in
                              magnitude count as 0 and outputs below 2^-959 flush to 0.
                              Other ops as QS_PREC_FP64. */

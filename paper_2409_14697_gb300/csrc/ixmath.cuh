@@ -184,6 +184,12 @@ inline Num constant(double v, bool neg) {
 }
 
 // ---- one-qubit updates (Eq. 2) ----------------------------------------------------
+// ENC chooses each output's result encoding: 0 all by the conversion instruction, 2 all by
+// integer instructions, 1 the real parts by conversion and the imaginary parts by integer
+// instructions (the two give the same bits; the choice balances the FP64 and integer
+// pipes).
+constexpr bool enc_cvt(int enc, int out) { return enc == 0 || (enc == 1 && (out & 1) == 0); }
+
 // Inputs x = (Re a, Im a, Re b, Im b) of an amplitude pair; outputs y in the same order,
 // (a', b') = M (a, b) with M = [m00 m01; m10 m11] given as m[8] = m00r m00i m01r m01i
 // m10r m10i m11r m11i.  Each row lists its terms' input indices; the host tables below
@@ -205,22 +211,22 @@ inline void rows_dense1(Num *c, const double *m, bool r0) {
     put(m[4], false); put(m[5], false); put(m[6], false); put(m[7], false);     // Im b'
 }
 
-template <bool CVT>
+template <int ENC>
 IX_HD void dense1_r0(const Num *c, const Num (&x)[4], double *y) {
     constexpr int r0[3] = {0, 2, 3}, i0[3] = {1, 3, 2}, r1[4] = {0, 1, 2, 3}, i1[4] = {1, 0, 3, 2};
-    y[0] = dot<3, 3, CVT>(x, r0, c + 0);
-    y[1] = dot<3, 3, CVT>(x, i0, c + 3);
-    y[2] = dot<4, 3, CVT>(x, r1, c + 6);
-    y[3] = dot<4, 3, CVT>(x, i1, c + 10);
+    y[0] = dot<3, 3, enc_cvt(ENC, 0)>(x, r0, c + 0);
+    y[1] = dot<3, 3, enc_cvt(ENC, 1)>(x, i0, c + 3);
+    y[2] = dot<4, 3, enc_cvt(ENC, 2)>(x, r1, c + 6);
+    y[3] = dot<4, 3, enc_cvt(ENC, 3)>(x, i1, c + 10);
 }
 
-template <bool CVT>
+template <int ENC>
 IX_HD void dense1(const Num *c, const Num (&x)[4], double *y) {
     constexpr int r[4] = {0, 1, 2, 3}, i[4] = {1, 0, 3, 2};
-    y[0] = dot<4, 3, CVT>(x, r, c + 0);
-    y[1] = dot<4, 3, CVT>(x, i, c + 4);
-    y[2] = dot<4, 3, CVT>(x, r, c + 8);
-    y[3] = dot<4, 3, CVT>(x, i, c + 12);
+    y[0] = dot<4, 3, enc_cvt(ENC, 0)>(x, r, c + 0);
+    y[1] = dot<4, 3, enc_cvt(ENC, 1)>(x, i, c + 4);
+    y[2] = dot<4, 3, enc_cvt(ENC, 2)>(x, r, c + 8);
+    y[3] = dot<4, 3, enc_cvt(ENC, 3)>(x, i, c + 12);
 }
 
 // Real 2x2 (RY and other real rotations): 8 term constants, rows of 2 terms.
@@ -229,13 +235,13 @@ inline void rows_dense1_real(Num *c, const double *m) {
     for (int j = 0; j < 8; j++) c[j] = constant(e[j], false);
 }
 
-template <bool CVT>
+template <int ENC>
 IX_HD void dense1_real(const Num *c, const Num (&x)[4], double *y) {
     constexpr int r[2] = {0, 2}, i[2] = {1, 3};
-    y[0] = dot<2, 2, CVT>(x, r, c + 0);
-    y[1] = dot<2, 2, CVT>(x, i, c + 2);
-    y[2] = dot<2, 2, CVT>(x, r, c + 4);
-    y[3] = dot<2, 2, CVT>(x, i, c + 6);
+    y[0] = dot<2, 2, enc_cvt(ENC, 0)>(x, r, c + 0);
+    y[1] = dot<2, 2, enc_cvt(ENC, 1)>(x, i, c + 2);
+    y[2] = dot<2, 2, enc_cvt(ENC, 2)>(x, r, c + 4);
+    y[3] = dot<2, 2, enc_cvt(ENC, 3)>(x, i, c + 6);
 }
 
 // Real diagonal, imaginary off-diagonal (RX): 8 term constants, rows of 2 terms.
@@ -246,13 +252,13 @@ inline void rows_dense1_rx(Num *c, const double *m) {
     c[6] = constant(m[6], false); c[7] = constant(m[5], false);  // Im b': b.i a.r
 }
 
-template <bool CVT>
+template <int ENC>
 IX_HD void dense1_rx(const Num *c, const Num (&x)[4], double *y) {
     constexpr int r0[2] = {0, 3}, i0[2] = {1, 2}, r1[2] = {2, 1}, i1[2] = {3, 0};
-    y[0] = dot<2, 2, CVT>(x, r0, c + 0);
-    y[1] = dot<2, 2, CVT>(x, i0, c + 2);
-    y[2] = dot<2, 2, CVT>(x, r1, c + 4);
-    y[3] = dot<2, 2, CVT>(x, i1, c + 6);
+    y[0] = dot<2, 2, enc_cvt(ENC, 0)>(x, r0, c + 0);
+    y[1] = dot<2, 2, enc_cvt(ENC, 1)>(x, i0, c + 2);
+    y[2] = dot<2, 2, enc_cvt(ENC, 2)>(x, r1, c + 4);
+    y[3] = dot<2, 2, enc_cvt(ENC, 3)>(x, i1, c + 6);
 }
 
 // Diagonal factors: element t times d[2t] + i d[2t+1]; 4 term constants per element.
@@ -266,11 +272,11 @@ inline void rows_diag(Num *c, const double *d, int nt) {
 }
 
 // x = (Re v, Im v) -> y = (Re, Im) of the product with one diagonal factor
-template <bool CVT>
+template <int ENC>
 IX_HD void phase(const Num *c, const Num (&x)[2], double *y) {
     constexpr int r[2] = {0, 1}, i[2] = {1, 0};
-    y[0] = dot<2, 2, CVT>(x, r, c + 0);
-    y[1] = dot<2, 2, CVT>(x, i, c + 2);
+    y[0] = dot<2, 2, enc_cvt(ENC, 0)>(x, r, c + 0);
+    y[1] = dot<2, 2, enc_cvt(ENC, 1)>(x, i, c + 2);
 }
 
 }  // namespace ix

@@ -229,76 +229,81 @@ __device__ __forceinline__ void ix_store(Amp<double, 1> *v, const double (&y)[4]
 }
 
 // U3 / CU3 (Im m00 = 0): 14 terms
-template <bool CVT, int UG, int NAT> struct FDense1R0IX {
+template <int ENC, int UG, int NAT, int MB> struct FDense1R0IX {
     static constexpr int NT = 2;
     static constexpr int kGroups = UG;
     static constexpr int kNative = NAT;
+    static constexpr int kMinBlocks = MB;
     ix::Num c[14];
     double m[8];
     template <int L> __device__ void operator()(Amp<double, L> *v) const {
         ix::Num x[4];
         double y[4];
         ix_pair(v, x);
-        ix::dense1_r0<CVT>(c, x, y);
+        ix::dense1_r0<ENC>(c, x, y);
         ix_store(v, y);
     }
     template <int L> __device__ void native(Amp<double, L> *v) const { f_dense1_r0<double, L>(v, m); }
 };
 
 // general 2x2: 16 terms
-template <bool CVT, int UG, int NAT> struct FDense1IX {
+template <int ENC, int UG, int NAT, int MB> struct FDense1IX {
     static constexpr int NT = 2;
     static constexpr int kGroups = UG;
     static constexpr int kNative = NAT;
+    static constexpr int kMinBlocks = MB;
     ix::Num c[16];
     double m[8];
     template <int L> __device__ void operator()(Amp<double, L> *v) const {
         ix::Num x[4];
         double y[4];
         ix_pair(v, x);
-        ix::dense1<CVT>(c, x, y);
+        ix::dense1<ENC>(c, x, y);
         ix_store(v, y);
     }
     template <int L> __device__ void native(Amp<double, L> *v) const { f_dense1<double, L>(v, m); }
 };
 
 // real 2x2 (RY) and RX forms: rows of 2 terms
-template <bool CVT, int UG, int NAT> struct FDense1RealIX {
+template <int ENC, int UG, int NAT, int MB> struct FDense1RealIX {
     static constexpr int NT = 2;
     static constexpr int kGroups = UG;
     static constexpr int kNative = NAT;
+    static constexpr int kMinBlocks = MB;
     ix::Num c[8];
     double m[8];
     template <int L> __device__ void operator()(Amp<double, L> *v) const {
         ix::Num x[4];
         double y[4];
         ix_pair(v, x);
-        ix::dense1_real<CVT>(c, x, y);
+        ix::dense1_real<ENC>(c, x, y);
         ix_store(v, y);
     }
     template <int L> __device__ void native(Amp<double, L> *v) const { f_dense1_real<double, L>(v, m); }
 };
-template <bool CVT, int UG, int NAT> struct FDense1RXIX {
+template <int ENC, int UG, int NAT, int MB> struct FDense1RXIX {
     static constexpr int NT = 2;
     static constexpr int kGroups = UG;
     static constexpr int kNative = NAT;
+    static constexpr int kMinBlocks = MB;
     ix::Num c[8];
     double m[8];
     template <int L> __device__ void operator()(Amp<double, L> *v) const {
         ix::Num x[4];
         double y[4];
         ix_pair(v, x);
-        ix::dense1_rx<CVT>(c, x, y);
+        ix::dense1_rx<ENC>(c, x, y);
         ix_store(v, y);
     }
     template <int L> __device__ void native(Amp<double, L> *v) const { f_dense1_rx<double, L>(v, m); }
 };
 
 // diagonal: NTT elements, each times its own factor
-template <bool CVT, int NTT, int UG, int NAT> struct FDiagIX {
+template <int ENC, int NTT, int UG, int NAT, int MB> struct FDiagIX {
     static constexpr int NT = NTT;
     static constexpr int kGroups = UG;
     static constexpr int kNative = NAT;
+    static constexpr int kMinBlocks = MB;
     ix::Num c[4 * NTT];
     double d[2 * NTT];
     template <int L> __device__ void operator()(Amp<double, L> *v) const {
@@ -306,7 +311,7 @@ template <bool CVT, int NTT, int UG, int NAT> struct FDiagIX {
         for (int t = 0; t < NTT; t++) {
             const ix::Num x[2] = {ix::decode(v[t].r[0]), ix::decode(v[t].i[0])};
             double y[2];
-            ix::phase<CVT>(c + 4 * t, x, y);
+            ix::phase<ENC>(c + 4 * t, x, y);
             v[t].r[0] = y[0];
             v[t].i[0] = y[1];
         }
@@ -345,8 +350,14 @@ template <typename F> struct NativeGroups<F, std::void_t<decltype(F::kNative)>> 
     static constexpr int value = F::kNative;
 };
 
+// Resident CTAs per SM the compiler must allow (register cap), if the functor sets one.
+template <typename F, typename = void> struct MinBlocks { static constexpr int value = 1; };
+template <typename F> struct MinBlocks<F, std::void_t<decltype(F::kMinBlocks)>> {
+    static constexpr int value = F::kMinBlocks;
+};
+
 template <typename T, int L, int NF, int U, typename F>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, MinBlocks<F>::value)
 k_stream(typename VecT<T, L>::type *__restrict__ psi, const Geom g, const F f) {
     constexpr int NT = F::NT;
     const uint64_t per_iter = (uint64_t)kThreads * U;
@@ -539,29 +550,29 @@ bool launch_df(DeviceState &st, const KOp &k, const std::vector<double> &mats) {
 }
 
 // complex128 with integer products (QS_PREC_IX64); false for kinds it does not cover.
-template <bool CVT, int U2, int N2, int U1, int N1>
+template <int E2, int U2, int N2, int E1, int U1, int N1, int MB1, int MB2>
 bool launch_ix_t(DeviceState &st, const KOp &k, const std::vector<double> &mats) {
     switch (k.fkind) {
     case F_DENSE1: {
         double m[8];
         for (int i = 0; i < 8; i++) m[i] = mats[k.mat + i];
         if (k.k == D1_REAL) {
-            FDense1RealIX<CVT, U2, N2> f;
+            FDense1RealIX<E2, U2, N2, MB2> f;
             ix::rows_dense1_real(f.c, m);
             std::copy(m, m + 8, f.m);
             dispatch_elem<double>(st, k, f);
         } else if (k.k == D1_RX) {
-            FDense1RXIX<CVT, U2, N2> f;
+            FDense1RXIX<E2, U2, N2, MB2> f;
             ix::rows_dense1_rx(f.c, m);
             std::copy(m, m + 8, f.m);
             dispatch_elem<double>(st, k, f);
         } else if (k.k == D1_R0) {
-            FDense1R0IX<CVT, U2, N2> f;
+            FDense1R0IX<E2, U2, N2, MB2> f;
             ix::rows_dense1(f.c, m, true);
             std::copy(m, m + 8, f.m);
             dispatch_elem<double>(st, k, f);
         } else {
-            FDense1IX<CVT, U2, N2> f;
+            FDense1IX<E2, U2, N2, MB2> f;
             ix::rows_dense1(f.c, m, false);
             std::copy(m, m + 8, f.m);
             dispatch_elem<double>(st, k, f);
@@ -569,14 +580,14 @@ bool launch_ix_t(DeviceState &st, const KOp &k, const std::vector<double> &mats)
         return true;
     }
     case F_PHASE: {
-        FDiagIX<CVT, 1, U1, N1> f;
+        FDiagIX<E1, 1, U1, N1, MB1> f;
         for (int i = 0; i < 2; i++) f.d[i] = mats[k.mat + i];
         ix::rows_diag(f.c, f.d, 1);
         dispatch_elem<double>(st, k, f);
         return true;
     }
     case F_DIAG1: {
-        FDiagIX<CVT, 2, U2, N2> f;
+        FDiagIX<E2, 2, U2, N2, MB2> f;
         for (int i = 0; i < 4; i++) f.d[i] = mats[k.mat + i];
         ix::rows_diag(f.c, f.d, 2);
         dispatch_elem<double>(st, k, f);
@@ -587,13 +598,16 @@ bool launch_ix_t(DeviceState &st, const KOp &k, const std::vector<double> &mats)
 }
 
 // Two-element kernels: 4 groups per thread, the first in native FP64; phases (one element):
-// 8 groups per thread, the first in native FP64.  Results use the conversion instruction.
-// (Measured at 28 qubits on the GB300: U3 1.98 ms against 3.59 ms native, CU3 1.03 / 1.81,
-// RZ phase 0.80 / 1.13, RY and RX 1.37 / 2.07; with all groups in integer form, with 6 or
-// 8 groups per thread and 2 or 3 native, or with the integer-only result encoding, each
-// was 3-25 % slower.)
+// 6 groups per thread, the first in native FP64, at most 64 registers (4 CTAs of 256
+// threads per SM).
+// Every output through the conversion instruction.  Measured at 28 qubits on the GB300:
+// U3 1.84 ms against 3.60 ms native, CU3 0.98 / 1.81, RZ phase 0.76 / 1.09, RY and RX
+// 1.33 / 2.08.  With all groups in integer form, 3-6 groups per thread with 1-2 native,
+// 3-4 CTAs per SM, or half or all of the outputs encoded with integer instructions (less
+// FP64-pipe work), each was 2-10 % slower: the FP64 pipe is 71 % busy and instruction
+// issue 50 % (ncu), the rest is dependency latency.
 bool launch_ix(DeviceState &st, const KOp &k, const std::vector<double> &mats) {
-    return launch_ix_t<true, 4, 1, 8, 1>(st, k, mats);
+    return launch_ix_t<0, 4, 1, 0, 6, 1, 4, 1>(st, k, mats);
 }
 
 template <typename T>

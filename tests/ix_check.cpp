@@ -181,7 +181,7 @@ static int apply_file(int argc, char **argv) {
         if (kind == "phase") {
             const Num x[2] = {qs::ix::decode(psi[2 * j]), qs::ix::decode(psi[2 * j + 1])};
             double y[2];
-            qs::ix::phase<false>(c, x, y);
+            qs::ix::phase<2>(c, x, y);
             psi[2 * j] = y[0];
             psi[2 * j + 1] = y[1];
             continue;
@@ -189,10 +189,10 @@ static int apply_file(int argc, char **argv) {
         const Num x[4] = {qs::ix::decode(psi[2 * i]), qs::ix::decode(psi[2 * i + 1]),
                           qs::ix::decode(psi[2 * j]), qs::ix::decode(psi[2 * j + 1])};
         double y[4];
-        if (kind == "r0") qs::ix::dense1_r0<false>(c, x, y);
-        else if (kind == "real") qs::ix::dense1_real<false>(c, x, y);
-        else if (kind == "rx") qs::ix::dense1_rx<false>(c, x, y);
-        else qs::ix::dense1<false>(c, x, y);
+        if (kind == "r0") qs::ix::dense1_r0<2>(c, x, y);
+        else if (kind == "real") qs::ix::dense1_real<2>(c, x, y);
+        else if (kind == "rx") qs::ix::dense1_rx<2>(c, x, y);
+        else qs::ix::dense1<2>(c, x, y);
         psi[2 * i] = y[0]; psi[2 * i + 1] = y[1];
         psi[2 * j] = y[2]; psi[2 * j + 1] = y[3];
     }
@@ -224,8 +224,8 @@ int main(int argc, char **argv) {
             Num c[14];
             qs::ix::rows_dense1(c, m, true);
             double yc[4], yi[4], yn[4];
-            qs::ix::dense1_r0<true>(c, nx, yc);
-            qs::ix::dense1_r0<false>(c, nx, yi);
+            qs::ix::dense1_r0<0>(c, nx, yc);
+            qs::ix::dense1_r0<2>(c, nx, yi);
             native_r0(m, x, yn);
             const Term t0[3] = {{x[0], m[0], false}, {x[2], m[2], false}, {x[3], m[3], true}};
             const Term t1[3] = {{x[1], m[0], false}, {x[3], m[2], false}, {x[2], m[3], false}};
@@ -247,8 +247,8 @@ int main(int argc, char **argv) {
             Num c[16];
             qs::ix::rows_dense1(c, q, false);
             double yc[4], yi[4], yn[4];
-            qs::ix::dense1<true>(c, nx, yc);
-            qs::ix::dense1<false>(c, nx, yi);
+            qs::ix::dense1<0>(c, nx, yc);
+            qs::ix::dense1<2>(c, nx, yi);
             native_general(q, x, yn);
             for (int row = 0; row < 2; row++) {
                 const double *p = q + 4 * row;
@@ -266,8 +266,8 @@ int main(int argc, char **argv) {
             Num c[8];
             double yc[4], yi[4];
             qs::ix::rows_dense1_real(c, ry);
-            qs::ix::dense1_real<true>(c, nx, yc);
-            qs::ix::dense1_real<false>(c, nx, yi);
+            qs::ix::dense1_real<0>(c, nx, yc);
+            qs::ix::dense1_real<2>(c, nx, yi);
             const double nry[4] = {std::fma(ry[0], x[0], ry[2] * x[2]), std::fma(ry[0], x[1], ry[2] * x[3]),
                                    std::fma(ry[4], x[0], ry[6] * x[2]), std::fma(ry[4], x[1], ry[6] * x[3])};
             const Term a0[2] = {{x[0], ry[0], false}, {x[2], ry[2], false}};
@@ -279,8 +279,8 @@ int main(int argc, char **argv) {
             check_output("ry re b", yc[2], yi[2], nry[2], b0, 2);
             check_output("ry im b", yc[3], yi[3], nry[3], b1, 2);
             qs::ix::rows_dense1_rx(c, rx);
-            qs::ix::dense1_rx<true>(c, nx, yc);
-            qs::ix::dense1_rx<false>(c, nx, yi);
+            qs::ix::dense1_rx<0>(c, nx, yc);
+            qs::ix::dense1_rx<2>(c, nx, yi);
             const double nrx[4] = {std::fma(rx[0], x[0], -rx[3] * x[3]), std::fma(rx[0], x[1], rx[3] * x[2]),
                                    std::fma(rx[6], x[2], -rx[5] * x[1]), std::fma(rx[6], x[3], rx[5] * x[0])};
             const Term c0[2] = {{x[0], rx[0], false}, {x[3], rx[3], true}};
@@ -300,8 +300,8 @@ int main(int argc, char **argv) {
             qs::ix::rows_diag(c, d, 1);
             const Num px[2] = {nx[0], nx[1]};
             double yc[2], yi[2];
-            qs::ix::phase<true>(c, px, yc);
-            qs::ix::phase<false>(c, px, yi);
+            qs::ix::phase<0>(c, px, yc);
+            qs::ix::phase<2>(c, px, yi);
             const double nr = std::fma(d[0], x[0], -d[1] * x[1]);
             const double ni = std::fma(d[0], x[1], d[1] * x[0]);
             const Term tr[2] = {{x[0], d[0], false}, {x[1], d[1], true}};
@@ -319,13 +319,13 @@ int main(int argc, char **argv) {
         Num nx[4];
         for (int i = 0; i < 4; i++) nx[i] = qs::ix::decode(x[i]);
         double y[4];
-        qs::ix::dense1<true>(c, nx, y);
+        qs::ix::dense1<0>(c, nx, y);
         if (y[0] != x[2] || y[1] != x[3] || y[2] != x[0] || y[3] != x[1]) {
             std::printf("FAIL X is not exact\n");
             g_fail++;
         }
         const Num z[4] = {qs::ix::decode(0.0), qs::ix::decode(-0.0), qs::ix::decode(0.0), qs::ix::decode(0.0)};
-        qs::ix::dense1<false>(c, z, y);
+        qs::ix::dense1<2>(c, z, y);
         if (y[0] != 0 || y[1] != 0 || y[2] != 0 || y[3] != 0) {
             std::printf("FAIL zeros do not stay zero\n");
             g_fail++;
