@@ -98,24 +98,25 @@ enum {
 /* Arithmetic used for complex128 gate updates (complex64 always uses FP32).  The state
  * is stored as IEEE doubles in every mode. */
 enum {
-    QS_PREC_DEFAULT = 0,  /* QS_PREC_IX64 for streaming one-qubit dense and diagonal gates,
-                             native FP64 for everything else */
+    QS_PREC_DEFAULT = 0,  /* QS_PREC_IX64 */
     QS_PREC_FP64 = 1,     /* native FP64 instructions */
     QS_PREC_DF32 = 2,     /* double-float: FP32 pairs with compensated products and sums
                              (TwoProd/TwoSum); each update is within ~2^-46 of the sum of
                              |matrix entry x amplitude| of the exact value.  Applies to
                              the streaming and the in-cache (chunk) passes. */
-    QS_PREC_IX64 = 3      /* streaming one-qubit dense and diagonal gates (gate-by-gate
-                             calls, and such ops of fused calls): each real output as a dot
-                             product of 64-bit integer significand products, aligned to its
-                             largest term in one signed 64-bit accumulator and rounded once
-                             to a double: within 0.5 ulp + 2^-56.4 x the largest |matrix
-                             entry x amplitude| of the exact value (a chain of FP64
-                             multiply-adds: about one ulp of each partial sum per term).
-                             One group in four (phases: in six) of every thread runs the
-                             native FP64 form, so both pipes work.  Inputs below 2^-1022 in
-                             magnitude count as 0 and outputs below 2^-959 flush to 0.
-                             Other ops as QS_PREC_FP64. */
+    QS_PREC_IX64 = 3      /* one-qubit dense gates and diagonal ops with constant factors
+                             (streaming launches and chunk passes), and the factor multiply
+                             of merged diagonal runs: each real output as a dot product of
+                             64-bit integer significand products, aligned to its largest
+                             term in one signed 64-bit accumulator and rounded once to a
+                             double: within 0.5 ulp + 2^-56.4 x the largest |matrix entry x
+                             amplitude| of the exact value (a chain of FP64 multiply-adds:
+                             about one ulp of each partial sum per term).  About one value
+                             in four of every thread runs the native FP64 form, so both
+                             pipes work.  Inputs below 2^-1022 in magnitude count as 0 and
+                             outputs below 2^-959 flush to 0.  Other ops (Hadamards,
+                             table-driven diagonal blocks, dense blocks of 2+ qubits) as
+                             QS_PREC_FP64. */
 };
 
 /* Bits of qs_options.flags (all off by default). */

@@ -153,7 +153,7 @@ void run_circuit(DeviceState &d, const std::vector<Op> &ops, const qs_options &o
         o.precision != QS_PREC_IX64)
         fail(QS_ERR_INVALID, "unknown precision mode");
     d.prec = o.precision == QS_PREC_DF32 ? QS_PREC_DF32 : QS_PREC_FP64;
-    d.ix_stream = o.precision == QS_PREC_IX64 || o.precision == QS_PREC_DEFAULT;
+    d.ix = o.precision == QS_PREC_IX64 || o.precision == QS_PREC_DEFAULT;
     d.reg_phases = (o.flags & QS_OPT_NO_REG_PHASES) == 0;
     const uint64_t l0 = g_launches.load();
     arena_begin(d);

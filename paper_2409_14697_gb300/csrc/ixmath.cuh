@@ -176,8 +176,8 @@ IX_HD double dot(const Num *x, const int (&idx)[K], const Num *c) {
     return CVT ? encode_cvt(acc, k2) : encode_int(acc, k2);
 }
 
-// Host: a matrix entry with the sign its term takes (neg flips it).
-inline Num constant(double v, bool neg) {
+// A matrix entry with the sign its term takes (neg flips it).
+IX_HD Num constant(double v, bool neg) {
     Num r = decode(v);
     if (neg) r.s = ~r.s;
     return r;
@@ -197,18 +197,21 @@ constexpr bool enc_cvt(int enc, int out) { return enc == 0 || (enc == 1 && (out 
 
 // Term constants of the general 2x2 update (16) or, with r0 (Im m00 = 0: U3, CU3, RX,
 // RY), of the 14-term form whose first two rows have 3 terms.
-inline void rows_dense1(Num *c, const double *m, bool r0) {
+IX_HD void rows_dense1(Num *c, const double *m, bool r0) {
     int j = 0;
-    auto put = [&](double v, bool neg) { c[j++] = constant(v, neg); };
     if (r0) {
-        put(m[0], false); put(m[2], false); put(m[3], true);    // Re a': a.r b.r b.i
-        put(m[0], false); put(m[2], false); put(m[3], false);   // Im a': a.i b.i b.r
+        c[j++] = constant(m[0], false); c[j++] = constant(m[2], false); c[j++] = constant(m[3], true);   // Re a': a.r b.r b.i
+        c[j++] = constant(m[0], false); c[j++] = constant(m[2], false); c[j++] = constant(m[3], false);  // Im a': a.i b.i b.r
     } else {
-        put(m[0], false); put(m[1], true); put(m[2], false); put(m[3], true);    // a.r a.i b.r b.i
-        put(m[0], false); put(m[1], false); put(m[2], false); put(m[3], false);  // a.i a.r b.i b.r
+        c[j++] = constant(m[0], false); c[j++] = constant(m[1], true);                  // Re a': a.r a.i
+        c[j++] = constant(m[2], false); c[j++] = constant(m[3], true);                  //        b.r b.i
+        c[j++] = constant(m[0], false); c[j++] = constant(m[1], false);                 // Im a': a.i a.r
+        c[j++] = constant(m[2], false); c[j++] = constant(m[3], false);                 //        b.i b.r
     }
-    put(m[4], false); put(m[5], true); put(m[6], false); put(m[7], true);       // Re b'
-    put(m[4], false); put(m[5], false); put(m[6], false); put(m[7], false);     // Im b'
+    c[j++] = constant(m[4], false); c[j++] = constant(m[5], true);                      // Re b': a.r a.i
+    c[j++] = constant(m[6], false); c[j++] = constant(m[7], true);                      //        b.r b.i
+    c[j++] = constant(m[4], false); c[j++] = constant(m[5], false);                     // Im b': a.i a.r
+    c[j++] = constant(m[6], false); c[j++] = constant(m[7], false);                     //        b.i b.r
 }
 
 template <int ENC>
@@ -230,7 +233,7 @@ IX_HD void dense1(const Num *c, const Num (&x)[4], double *y) {
 }
 
 // Real 2x2 (RY and other real rotations): 8 term constants, rows of 2 terms.
-inline void rows_dense1_real(Num *c, const double *m) {
+IX_HD void rows_dense1_real(Num *c, const double *m) {
     const double e[8] = {m[0], m[2], m[0], m[2], m[4], m[6], m[4], m[6]};
     for (int j = 0; j < 8; j++) c[j] = constant(e[j], false);
 }
@@ -245,7 +248,7 @@ IX_HD void dense1_real(const Num *c, const Num (&x)[4], double *y) {
 }
 
 // Real diagonal, imaginary off-diagonal (RX): 8 term constants, rows of 2 terms.
-inline void rows_dense1_rx(Num *c, const double *m) {
+IX_HD void rows_dense1_rx(Num *c, const double *m) {
     c[0] = constant(m[0], false); c[1] = constant(m[3], true);   // Re a': a.r b.i
     c[2] = constant(m[0], false); c[3] = constant(m[3], false);  // Im a': a.i b.r
     c[4] = constant(m[6], false); c[5] = constant(m[5], true);   // Re b': b.r a.i
@@ -262,13 +265,25 @@ IX_HD void dense1_rx(const Num *c, const Num (&x)[4], double *y) {
 }
 
 // Diagonal factors: element t times d[2t] + i d[2t+1]; 4 term constants per element.
-inline void rows_diag(Num *c, const double *d, int nt) {
+IX_HD void rows_diag(Num *c, const double *d, int nt) {
     for (int t = 0; t < nt; t++) {
         c[4 * t + 0] = constant(d[2 * t], false);  // Re: x.r x.i
         c[4 * t + 1] = constant(d[2 * t + 1], true);
         c[4 * t + 2] = constant(d[2 * t], false);  // Im: x.i x.r
         c[4 * t + 3] = constant(d[2 * t + 1], false);
     }
+}
+
+// y = (dr + i di) x for a factor read per amplitude (diagonal tables): the factor is decoded
+// on the spot.
+template <int ENC>
+IX_HD void cmul(double dr, double di, const Num (&x)[2], double *y) {
+    const Num a = decode(dr), b = decode(di);
+    Num c[4] = {a, b, a, b};
+    c[1].s = ~c[1].s;
+    constexpr int r[2] = {0, 1}, i[2] = {1, 0};
+    y[0] = dot<2, 2, enc_cvt(ENC, 0)>(x, r, c + 0);
+    y[1] = dot<2, 2, enc_cvt(ENC, 1)>(x, i, c + 2);
 }
 
 // x = (Re v, Im v) -> y = (Re, Im) of the product with one diagonal factor

@@ -110,7 +110,9 @@ __device__ void fold_hi_terms(const KOp &op, const T *src, T *dst, uint64_t base
 }
 
 // DF: complex128 with double-float arithmetic; mats then holds (hi, lo) float pairs.
-template <typename T, bool DF>
+// IX: complex128 one-qubit dense ops and constant diagonal ops in integer products
+// (QS_PREC_IX64).
+template <typename T, bool DF, bool IX>
 __global__ void __launch_bounds__(kChunkThreads, 2)
 k_chunk(typename C2T<T>::type *__restrict__ psi, const ChunkArgs a, const KOp *__restrict__ ops,
         const T *__restrict__ mats, int *__restrict__ err) {
@@ -190,7 +192,7 @@ k_chunk(typename C2T<T>::type *__restrict__ psi, const ChunkArgs a, const KOp *_
                 }
             }
             if constexpr (DF) apply_op_dftile((double2 *)tile, *op, (const df::F2 *)om, s_fb, a.m);
-            else apply_op_smem<T>(tile, *op, om, a.m);
+            else apply_op_smem<T, true, IX>(tile, *op, om, a.m);
             __syncthreads();
         }
         if constexpr (DF) {
@@ -215,7 +217,7 @@ k_chunk(typename C2T<T>::type *__restrict__ psi, const ChunkArgs a, const KOp *_
     ptx::bulk_wait_all();
 }
 
-template <typename T, bool DF>
+template <typename T, bool DF, bool IX>
 void launch_t(DeviceState &st, const ChunkArgs &a, const std::vector<KOp> &kops, const std::vector<double> &mats) {
     const KOp *d_ops = (const KOp *)upload_params(st, kops.data(), kops.size() * sizeof(KOp));
     const T *d_m;
@@ -244,7 +246,7 @@ void launch_t(DeviceState &st, const ChunkArgs &a, const std::vector<KOp> &kops,
     ca.n_reals = (uint32_t)mats.size();
     ca.staged = tile_bytes + ops_bytes + reals_bytes <= kStagedSmemLimit ? 1 : 0;
     if (ca.staged) smem = (tile_bytes + ops_bytes + reals_bytes + 15) / 16 * 16;
-    auto kern = k_chunk<T, DF>;
+    auto kern = k_chunk<T, DF, IX>;
     static bool attr_set = false;
     if (!attr_set) {
         QS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
@@ -277,10 +279,11 @@ void launch_chunk_pass(DeviceState &st, uint64_t lmask, const std::vector<KOp> &
     if ((B << a.c0) % 16 != 0) fail(QS_ERR_INVALID, "chunk runs must be multiples of 16 bytes");
     if ((B << a.m) > 200 * 1024) fail(QS_ERR_INVALID, "chunk tile exceeds shared memory");
     if (st.dtype == QS_C128) {
-        if (st.prec == QS_PREC_DF32) launch_t<double, true>(st, a, kops, mats);
-        else launch_t<double, false>(st, a, kops, mats);
+        if (st.prec == QS_PREC_DF32) launch_t<double, true, false>(st, a, kops, mats);
+        else if (st.ix) launch_t<double, false, true>(st, a, kops, mats);
+        else launch_t<double, false, false>(st, a, kops, mats);
     } else {
-        launch_t<float, false>(st, a, kops, mats);
+        launch_t<float, false, false>(st, a, kops, mats);
     }
 }
 

@@ -10,6 +10,7 @@
 // counter over the 16 registers at once) for pairs that touch register bits.
 #include <algorithm>
 
+#include "ixmath.cuh"
 #include "kops.cuh"
 #include "phasefn.h"
 
@@ -59,7 +60,16 @@ __device__ __forceinline__ typename C2T<T>::type pf_cmul(typename C2T<T>::type a
     return y;
 }
 
-template <typename T>
+// complex128 with integer products (QS_PREC_IX64): the factor is decoded per amplitude;
+// registers 0, 4, 8 and 12 take the native FP64 product, so both pipes work.
+__device__ __forceinline__ double2 pf_cmul_ix(double2 a, double2 f) {
+    const ix::Num x[2] = {ix::decode(a.x), ix::decode(a.y)};
+    double y[2];
+    ix::cmul<0>(f.x, f.y, x, y);
+    return make_double2(y[0], y[1]);
+}
+
+template <typename T, bool IX>
 __global__ void __launch_bounds__(kPfThreads)
 k_phasefn(typename C2T<T>::type *__restrict__ psi, const PfArgs a, const uint32_t *__restrict__ pairs,
           const typename C2T<T>::type *__restrict__ table) {
@@ -117,11 +127,18 @@ k_phasefn(typename C2T<T>::type *__restrict__ psi, const PfArgs a, const uint32_
             }
         }
 #pragma unroll
-        for (int r = 0; r < kPfRegs; r++) psi[xu + ((uint64_t)r << 5)] = pf_cmul<T>(v[r], s_tab[idx[r]]);
+        for (int r = 0; r < kPfRegs; r++) {
+            if constexpr (IX) {
+                psi[xu + ((uint64_t)r << 5)] =
+                    (r % 4 == 0) ? pf_cmul<T>(v[r], s_tab[idx[r]]) : pf_cmul_ix(v[r], s_tab[idx[r]]);
+            } else {
+                psi[xu + ((uint64_t)r << 5)] = pf_cmul<T>(v[r], s_tab[idx[r]]);
+            }
+        }
     }
 }
 
-template <typename T>
+template <typename T, bool IX>
 void launch_t(DeviceState &st, const PhaseFn &pf) {
     using V = typename C2T<T>::type;
     PfArgs a{};
@@ -150,7 +167,7 @@ void launch_t(DeviceState &st, const PhaseFn &pf) {
     const V *d_tab = (const V *)upload_params(st, tab.data(), tab.size() * sizeof(V));
     const uint32_t *d_pairs = (const uint32_t *)upload_params(st, pl.data(), pl.size() * sizeof(uint32_t));
     const size_t smem = tab.size() * sizeof(V) + (size_t)a.total_pairs * sizeof(uint32_t);
-    auto kern = k_phasefn<T>;
+    auto kern = k_phasefn<T, IX>;
     static bool attr = false;
     if (!attr) {
         QS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024));
@@ -170,8 +187,9 @@ bool phasefn_supported(int n) { return n >= kPfUnitBits; }
 void launch_phasefn(DeviceState &st, const Op &op) {
     if (op.kind != K_PHASEFN || !op.pf) fail(QS_ERR_INVALID, "not a phase function");
     if (!phasefn_supported(st.n)) fail(QS_ERR_UNSUPPORTED, "phase functions need at least 9 qubits");
-    if (st.dtype == QS_C128) launch_t<double>(st, *op.pf);
-    else launch_t<float>(st, *op.pf);
+    if (st.dtype == QS_C128 && st.ix) launch_t<double, true>(st, *op.pf);
+    else if (st.dtype == QS_C128) launch_t<double, false>(st, *op.pf);
+    else launch_t<float, false>(st, *op.pf);
 }
 
 }  // namespace qs

@@ -619,7 +619,7 @@ void launch_typed(DeviceState &st, const Op &op) {
     const KOp k = make_kop(op, ident.data(), mats);
     if constexpr (std::is_same<T, double>::value) {
         if (st.prec == QS_PREC_DF32 && launch_df(st, k, mats)) return;
-        if (st.ix_stream && launch_ix(st, k, mats)) return;
+        if (st.ix && launch_ix(st, k, mats)) return;
     }
     switch (k.fkind) {
     case F_H: {

@@ -164,7 +164,8 @@ struct DeviceState {
     int n = 0;            // qubits
     int dtype = QS_C128;
     int prec = QS_PREC_FP64;  // complex128 arithmetic: QS_PREC_FP64 or QS_PREC_DF32
-    bool ix_stream = false;   // complex128 streaming dense / phase gates: integer products
+    bool ix = false;          // complex128 one-qubit dense and diagonal ops (streaming and
+                              // chunk passes): integer products (QS_PREC_IX64)
     bool reg_phases = true;   // complex64 chunk passes: register phases (2^13-amplitude tiles)
     cudaStream_t stream = nullptr;
     // scratch for reductions (owned by the state; stream-ordered allocation on `stream`)

@@ -5,6 +5,7 @@
 #include <type_traits>
 
 #include "dfmath.cuh"
+#include "ixmath.cuh"
 #include "kops.cuh"
 
 namespace qs {
@@ -80,6 +81,83 @@ template <typename T, int NT> struct SDiag {
     const T *d;
     __device__ void operator()(Amp<T, 1> *v) const { f_diag<T, 1, NT>(v, d); }
 };
+
+// ---- complex128 integer-product forms (ixmath.cuh) of one-qubit dense and diagonal ops ----
+// Each thread decodes the op's constants from the matrix reals in shared memory once; every
+// fourth of its groups (iterations 0, 4, 8, ...) runs the native FP64 form, so the FP64 pipe
+// and the integer pipes share the work, as in the streaming kernel.
+constexpr uint32_t kIxNativeEvery = 4;
+
+__device__ __forceinline__ void ix_load(const double2 &a, ix::Num (&x)[2]) {
+    x[0] = ix::decode(a.x);
+    x[1] = ix::decode(a.y);
+}
+
+template <int FORM>  // a D1_* class
+__device__ __forceinline__ void ix_dense1_tile(double2 *tile, const KOp &op, int m, const double *sm) {
+    ix::Num c[16];
+    if (FORM == D1_R0) ix::rows_dense1(c, sm, true);
+    else if (FORM == D1_REAL) ix::rows_dense1_real(c, sm);
+    else if (FORM == D1_RX) ix::rows_dense1_rx(c, sm);
+    else ix::rows_dense1(c, sm, false);
+    const uint32_t ng = 1u << (m - op.nf);
+    const uint32_t set = (uint32_t)op.set_mask;
+    uint32_t it = 0;
+    for (uint32_t g = threadIdx.x; g < ng; g += blockDim.x, it++) {
+        const uint32_t base = (uint32_t)insert_zero_bits(g, op.nf, op.fb) | set;
+        double2 *pa = tile + (base + (uint32_t)op.off[0]);
+        double2 *pb = tile + (base + (uint32_t)op.off[1]);
+        const double2 a = *pa, b = *pb;
+        double y[4];
+        if (it % kIxNativeEvery == 0) {
+            Amp<double, 1> v[2];
+            v[0].r[0] = a.x; v[0].i[0] = a.y; v[1].r[0] = b.x; v[1].i[0] = b.y;
+            if (FORM == D1_R0) f_dense1_r0<double, 1>(v, sm);
+            else if (FORM == D1_REAL) f_dense1_real<double, 1>(v, sm);
+            else if (FORM == D1_RX) f_dense1_rx<double, 1>(v, sm);
+            else f_dense1<double, 1>(v, sm);
+            y[0] = v[0].r[0]; y[1] = v[0].i[0]; y[2] = v[1].r[0]; y[3] = v[1].i[0];
+        } else {
+            const ix::Num x[4] = {ix::decode(a.x), ix::decode(a.y), ix::decode(b.x), ix::decode(b.y)};
+            if (FORM == D1_R0) ix::dense1_r0<0>(c, x, y);
+            else if (FORM == D1_REAL) ix::dense1_real<0>(c, x, y);
+            else if (FORM == D1_RX) ix::dense1_rx<0>(c, x, y);
+            else ix::dense1<0>(c, x, y);
+        }
+        *pa = make_double2(y[0], y[1]);
+        *pb = make_double2(y[2], y[3]);
+    }
+}
+
+// NT elements per group, element t times the factor (sm[2t], sm[2t+1])
+template <int NT>
+__device__ __forceinline__ void ix_diag_tile(double2 *tile, const KOp &op, int m, const double *sm) {
+    ix::Num c[4 * NT];
+    ix::rows_diag(c, sm, NT);
+    const uint32_t ng = 1u << (m - op.nf);
+    const uint32_t set = (uint32_t)op.set_mask;
+    uint32_t it = 0;
+    for (uint32_t g = threadIdx.x; g < ng; g += blockDim.x, it++) {
+        const uint32_t base = (uint32_t)insert_zero_bits(g, op.nf, op.fb) | set;
+#pragma unroll
+        for (int t = 0; t < NT; t++) {
+            double2 *p = tile + (base + (uint32_t)op.off[t]);
+            const double2 a = *p;
+            double y[2];
+            if (it % kIxNativeEvery == 0) {
+                Amp<double, 1> v;
+                v.r[0] = a.x; v.i[0] = a.y;
+                f_diag<double, 1, 1>(&v, sm + 2 * t);
+                y[0] = v.r[0]; y[1] = v.i[0];
+            } else {
+                ix::Num x[2];
+                ix_load(a, x);
+                ix::phase<0>(c + 4 * t, x, y);
+            }
+            *p = make_double2(y[0], y[1]);
+        }
+    }
+}
 
 template <typename T, int K>
 __device__ __forceinline__ void dense_k_smem(typename C2T<T>::type *tile, const KOp &op, const T *m, int mbits) {
@@ -671,8 +749,27 @@ __device__ __forceinline__ void rphase_run(float2 *tile, const KOp &ph, const fl
 // Applies one op to the tile; op and its matrix entries are in shared memory.  RP = false
 // leaves the register-phase code out (kernels that never receive F_RPHASE ops keep their
 // registers for themselves).
-template <typename T, bool RP = true>
+template <typename T, bool RP = true, bool IX = false>
 __device__ __forceinline__ void apply_op_smem(typename C2T<T>::type *tile, const KOp &op, const T *sm, int m) {
+    if constexpr (IX && std::is_same<T, double>::value) {
+        // complex128 integer products (QS_PREC_IX64) for one-qubit dense ops and diagonal ops
+        // with constant factors.  Diagonal blocks read from tables (F_DIAGK, F_CDIAGK,
+        // F_HCDIAGK) stay native: decoding a factor per amplitude measured slower there.
+        double2 *t2 = (double2 *)tile;
+        switch (op.fkind) {
+        case F_DENSE1:
+            if (op.k == D1_REAL) ix_dense1_tile<D1_REAL>(t2, op, m, sm);
+            else if (op.k == D1_RX) ix_dense1_tile<D1_RX>(t2, op, m, sm);
+            else if (op.k == D1_R0) ix_dense1_tile<D1_R0>(t2, op, m, sm);
+            else ix_dense1_tile<D1_GENERAL>(t2, op, m, sm);
+            return;
+        case F_DIAG1: ix_diag_tile<2>(t2, op, m, sm); return;
+        case F_PHASE: ix_diag_tile<1>(t2, op, m, sm); return;
+        case F_DIAG2: ix_diag_tile<4>(t2, op, m, sm); return;
+        default:
+            break;  // everything else in native FP64
+        }
+    }
     switch (op.fkind) {
     case F_H:  // scale in the reals when a pass defers it (1: the unscaled butterfly)
         if (op.nmat >= 1 && sm[0] == (T)1) groups_apply<T, 2>(tile, op, m, SHSum<T>{});

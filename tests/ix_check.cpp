@@ -302,6 +302,11 @@ int main(int argc, char **argv) {
             double yc[2], yi[2];
             qs::ix::phase<0>(c, px, yc);
             qs::ix::phase<2>(c, px, yi);
+            double yt[2];  // the same factor decoded per amplitude (diagonal tables)
+            qs::ix::cmul<0>(d[0], d[1], px, yt);
+            if (qs::ix::bits_of(yt[0]) != qs::ix::bits_of(yc[0]) || qs::ix::bits_of(yt[1]) != qs::ix::bits_of(yc[1])) {
+                if (g_fail++ < 10) std::printf("FAIL table factor form differs\n");
+            }
             const double nr = std::fma(d[0], x[0], -d[1] * x[1]);
             const double ni = std::fma(d[0], x[1], d[1] * x[0]);
             const Term tr[2] = {{x[0], d[0], false}, {x[1], d[1], true}};

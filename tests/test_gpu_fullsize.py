@@ -57,6 +57,7 @@ def _sweep_parity(qs, n, c64_planned=True):
     variants = [("c128_gate", 2, qs.QS_MODE_GATE, qs.QS_PREC_FP64),
                 ("c128_ix64_gate", 2, qs.QS_MODE_GATE, qs.QS_PREC_IX64),
                 ("c128_planned", 2, qs.QS_MODE_AUTO, qs.QS_PREC_FP64),
+                ("c128_planned_ix64", 2, qs.QS_MODE_AUTO, qs.QS_PREC_IX64),
                 ("c128_df32_gate", 2, qs.QS_MODE_GATE, qs.QS_PREC_DF32),
                 ("c64_gate", 1, qs.QS_MODE_GATE, 0)]
     if c64_planned:

@@ -6,6 +6,9 @@ significand products, one rounding per output), through the C ABI.
   (max-abs <= 1e-12) and against the native FP64 kernels (the two differ by rounding
   only).
 * The U3, CU3 and RZ sweeps of the gate benchmark at 20 qubits against the oracle.
+* Planned calls (chunk passes with one-qubit dense and diagonal tile ops, phase functions)
+  of QFT, fully connected QAOA, TFIM, brickwork and U3 sweeps at 16 qubits, against the
+  oracle and the native FP64 plan.
 * Bit for bit against the host build of the same arithmetic (tests/ix_check.cpp): caller
   matrices (U3-class, general unitary, real rotation, RX-class, diagonal) on a 16-qubit
   Gaussian state.  Groups a
@@ -81,6 +84,37 @@ def test_benchmark_sweeps_20q(qs, name):
     want = oracle.run(psi.copy(), n, seg)
     got = _run(qs, n, psi, seg, qs.QS_PREC_IX64)
     assert np.max(np.abs(got - want)) <= TOL_C128
+
+
+FAMILIES = {
+    "qft": lambda n: inputs.qft(n),
+    "qaoa_complete_p5": lambda n: inputs.qaoa_complete(n, p=5, seed=5),
+    "tfim20": lambda n: inputs.tfim(n, steps=20, dt=0.05),
+    "brickwork10": lambda n: inputs.brickwork(n, 10, seed=12),
+    "u3_sweep": lambda n: inputs.gate_sweep(n, "u3", seed=2, count=2 * n),
+}
+
+
+@pytest.mark.parametrize("family", list(FAMILIES))
+@pytest.mark.parametrize("chunk_m", [0, 9])
+def test_planned_circuits_vs_oracle(qs, family, chunk_m):
+    """Planned calls (chunk passes, phase functions, streaming ops) with integer products:
+    against the oracle and against the same plan in native FP64."""
+    n = 16
+    psi = inputs.gaussian_state(n, seed=61)
+    gates = FAMILIES[family](n)
+    want = oracle.run(psi.copy(), n, gates)
+    h = qs.qs_create(n, qs.QS_C128)
+    try:
+        out = {}
+        for prec in (qs.QS_PREC_IX64, qs.QS_PREC_FP64):
+            qs.qs_set_amplitudes(h, psi)
+            qs.qs_apply_circuit(h, gates, qs.options(chunk_m=chunk_m, precision=prec))
+            out[prec] = qs.qs_amplitudes(h)
+    finally:
+        qs.qs_destroy(h)
+    assert np.max(np.abs(out[qs.QS_PREC_IX64] - want)) <= TOL_C128
+    assert np.max(np.abs(out[qs.QS_PREC_IX64] - out[qs.QS_PREC_FP64])) <= 1e-14 * np.max(np.abs(want))
 
 
 @pytest.fixture(scope="module")
