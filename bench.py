@@ -36,6 +36,8 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 N_QUBITS = 30
+# complex128 arithmetic by --precision (the values of QS_PREC_DEFAULT / _FP64 / _DF32)
+PRECISIONS = {"ix64": 0, "fp64": 1, "df32": 2}
 GATE_TYPES = ("h", "x", "rz", "u3", "cnot", "cz", "swap", "cu3")
 METRIC = "gates/sec (30-qubit gate benchmark, complex128, gate-by-gate)"
 
@@ -62,8 +64,9 @@ def parse():
     ap.add_argument("--rate", type=float, default=2000.0)
     ap.add_argument("--no-rphases", action="store_true",
                     help="complex64 passes: one shared-memory sweep per op (no register phases)")
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "df32"],
-                    help="complex128 arithmetic of the served workload")
+    ap.add_argument("--precision", default="ix64", choices=["ix64", "fp64", "df32"],
+                    help="complex128 arithmetic of the served and paper workloads (ix64: the "
+                         "library default, integer products for one-qubit dense and diagonal ops)")
     ap.add_argument("--loads", default="",
                     help="served: comma-separated offered loads in req/s for a load sweep")
     ap.add_argument("--no-workloads", action="store_true",
@@ -888,7 +891,7 @@ def wl_paper(args):
     import torch
     from paper_2409_14697_gb300 import inputs, qs
     sizes = [args.qubits] if args.qubits != N_QUBITS else list(range(23, 31))
-    prec = qs.QS_PREC_DF32 if args.precision == "df32" else qs.QS_PREC_FP64
+    prec = PRECISIONS[args.precision]
     out = {"workload": f"paper tables II-IV, complex128 ({args.precision})", "sizes": {}}
     stream = torch.cuda.Stream()
     for n in sizes:
@@ -1030,7 +1033,7 @@ def wl_served(args, count=None, loads=None):
     for r in reqs:
         prepared.append({"t": r["t"], "n": r["n"], "dt": qs.QS_C128 if r["dtype"] == "c128" else qs.QS_C64,
                          "recs": qs.gate_records(r["gates"]), "k": min(1024, 1 << r["n"]), "init": si.ptr(r)})
-    prec = qs.QS_PREC_DF32 if args.precision == "df32" else qs.QS_PREC_FP64
+    prec = PRECISIONS[args.precision]
     seq_wall = served_sequential(qs, prepared, prec)
     rows = {}
     for rate in loads:

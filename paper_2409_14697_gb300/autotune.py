@@ -63,12 +63,12 @@ def signature(kind: str, n, dtype: int, gates_or_circuits) -> str:
 def candidates(dtype: int, n: int, kind: str = "circuit"):
     """Candidate option sets: chunk width, fusion width (complex64: k = 1 applies gates
     unfused, in register phases on 2^13-amplitude tiles; tensor cores when k >= 4), and for
-    complex128 the arithmetic (native FP64 or double-float)."""
+    complex128 the arithmetic (integer products, native FP64 or double-float)."""
     from . import qs
     out = []
     ms = [m for m in ((10, 11, 12) if dtype == qs.QS_C128 else (11, 12, 13)) if m <= max(n, 1)] or [0]
     if dtype == qs.QS_C128:
-        precs = (qs.QS_PREC_FP64,) if kind == "batch" else (qs.QS_PREC_FP64, qs.QS_PREC_DF32)
+        precs = (qs.QS_PREC_FP64,) if kind == "batch" else (qs.QS_PREC_IX64, qs.QS_PREC_FP64, qs.QS_PREC_DF32)
         for m in ms:
             for prec in precs:
                 for k in (1, 2):

@@ -42,7 +42,7 @@ def test_signature_ignores_angles_but_not_gate_mix():
 def test_candidates_cover_both_dtypes():
     c128 = autotune.candidates(qs.QS_C128, 30)
     c64 = autotune.candidates(qs.QS_C64, 30)
-    assert {c["precision"] for c in c128} == {qs.QS_PREC_FP64, qs.QS_PREC_DF32}
+    assert {c["precision"] for c in c128} == {qs.QS_PREC_IX64, qs.QS_PREC_FP64, qs.QS_PREC_DF32}
     assert max(c["fuse_k"] for c in c64) == 6
     assert min(c["fuse_k"] for c in c64) == 1
     assert all(c["fuse_k"] <= 4 for c in autotune.candidates(qs.QS_C64, 20, "batch"))
