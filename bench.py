@@ -323,7 +323,9 @@ def run_ours(args, rank, world, local):
         "metric": METRIC, "value": round(value, 2), "unit": "gates/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_per_step, 3),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f64" if B == 16 else "f32", "data": "synthetic (seeded Gaussian state, seeded angles)",
+        # complex128: FP64 storage and additions, 64-bit integer significand products for
+        # U3, CU3 and RZ (config.arithmetic)
+        "dtype": "f64+i64" if B == 16 else "f32", "data": "synthetic (seeded Gaussian state, seeded angles)",
         "config": {"workload": f"{n}-qubit gate benchmark, {args.dtype}, 8 gate types x 30 targets, gate-by-gate",
                    "qubits": n, "state_bytes": B << n, "gates_per_step": n_gates,
                    "arithmetic": ("U3, CU3 and RZ: exact 64-bit integer significand products, one "
